@@ -1,0 +1,314 @@
+"""CPU oracle for the encoder-analysis path (test infrastructure only).
+
+This package is the plain, slow statement of what the GPU library computes:
+per-band min-max quantisation to 10-bit planes with three-band packing
+(paper Sec. 2.1), integer full-search + quarter-pel motion estimation, the
+HEVC-style integer core transform, quantise / dequantise / inverse /
+reconstruct, and the PSNR and bits-per-pixel-per-band reductions (paper
+Sec. 2.3).  The arithmetic lives in ``xvo.c`` (plain C loops, compiled with
+gcc); this module only marshals numpy arrays.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libxvo.so")
+_SRC = os.path.join(_HERE, "xvo.c")
+_lock = threading.Lock()
+_lib = None
+
+F32, U16 = 0, 1
+BIT_DEPTH = 10
+
+
+def build(force: bool = False) -> str:
+    """Compile xvo.c into a shared library (OpenMP when the compiler has it)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "xvo.h"))
+    ):
+        return _LIB_PATH
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, i, i64, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint
+            L.xvo_group_count.argtypes = [i]
+            L.xvo_group_band.argtypes = [i, i, i]
+            L.xvo_minmax.argtypes = [vp, i, i, i, i, i, vp, vp]
+            L.xvo_quantize_pack.argtypes = [vp, i, i, i, i, i, i, vp, vp]
+            L.xvo_transform_matrix.argtypes = [i, vp]
+            L.xvo_fwd_transform.argtypes = [i, vp, vp]
+            L.xvo_inv_transform.argtypes = [i, vp, vp]
+            L.xvo_quant.argtypes = [ctypes.c_int32, i, i]
+            L.xvo_quant.restype = ctypes.c_int32
+            L.xvo_dequant.argtypes = [ctypes.c_int32, i, i]
+            L.xvo_dequant.restype = ctypes.c_int32
+            L.xvo_lambdas.argtypes = [i, vp, vp]
+            L.xvo_ue_len_se.argtypes = [i]
+            L.xvo_mv_bits.argtypes = [i, i]
+            L.xvo_mv_cost.argtypes = [i, i, i64]
+            L.xvo_mv_cost.restype = ctypes.c_uint32
+            L.xvo_interp_block.argtypes = [vp, i, i, i, i, i, i, i, i, vp]
+            L.xvo_hadamard8.argtypes = [vp, vp]
+            L.xvo_satd.argtypes = [vp, i, i]
+            L.xvo_satd.restype = ctypes.c_uint32
+            L.xvo_me_int.argtypes = [vp, vp, i, i, i, i, i64, vp, vp]
+            L.xvo_me_qpel.argtypes = [vp, vp, i, i, i, i64, vp, vp, vp]
+            L.xvo_tqr_frame.argtypes = [vp, vp, vp, i, i, i, u, i, i64, vp, vp, vp, vp]
+            L.xvo_tqr_frame.restype = ctypes.c_uint64
+            L.xvo_encode_planes.argtypes = [vp, i, i, i, i, i, i, u, i, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.xvo_psnr.argtypes = [vp, i, i, i, i, i, vp, vp, i, i, vp, vp, vp, vp, vp]
+            L.xvo_max_threads.restype = i
+            L.xvo_set_threads.argtypes = [i]
+            _lib = L
+        return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().xvo_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().xvo_max_threads())
+
+
+# ----------------------------------------------------------------- C2 / C3
+def group_count(bands: int) -> int:
+    return int(lib().xvo_group_count(bands))
+
+
+def group_bands(bands: int) -> list[list[int]]:
+    """Band index held by each (group, channel) slot."""
+    L = lib()
+    return [[int(L.xvo_group_band(bands, g, c)) for c in range(3)] for g in range(group_count(bands))]
+
+
+def plane_geometry(H: int, W: int, ctu: int) -> tuple[int, int]:
+    return -(-H // ctu) * ctu, -(-W // ctu) * ctu
+
+
+# ----------------------------------------------------------------- C1
+def _src(src: np.ndarray):
+    src = np.ascontiguousarray(src)
+    if src.dtype == np.float32:
+        return src, F32
+    if src.dtype == np.uint16:
+        return src, U16
+    raise TypeError("source must be float32 or uint16")
+
+
+def minmax(src: np.ndarray):
+    """(mm[bands,2] float64, nan_count[bands]) for a [bands,T,H,W] cube."""
+    src, dt = _src(src)
+    bands, T, H, W = src.shape
+    mm = np.zeros((bands, 2), np.float64)
+    nn = np.zeros(bands, np.int64)
+    lib().xvo_minmax(_p(src), dt, bands, T, H, W, _p(mm), _p(nn))
+    return mm, nn
+
+
+def quantize_pack(src: np.ndarray, ctu: int, mm: np.ndarray) -> np.ndarray:
+    """u16 planes [G,T,3,Hp,Wp]."""
+    src, dt = _src(src)
+    bands, T, H, W = src.shape
+    Hp, Wp = plane_geometry(H, W, ctu)
+    G = group_count(bands)
+    out = np.zeros((G, T, 3, Hp, Wp), np.uint16)
+    mm = np.ascontiguousarray(mm, np.float64)
+    lib().xvo_quantize_pack(_p(src), dt, bands, T, H, W, ctu, _p(mm), _p(out))
+    return out
+
+
+# ----------------------------------------------------------------- C10 / C11
+def transform_matrix(N: int) -> np.ndarray:
+    T = np.zeros((N, N), np.int32)
+    lib().xvo_transform_matrix(N, _p(T))
+    return T
+
+
+def fwd_transform(X: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(X, np.int32)
+    C = np.zeros_like(X)
+    lib().xvo_fwd_transform(X.shape[0], _p(X), _p(C))
+    return C
+
+
+def inv_transform(C: np.ndarray) -> np.ndarray:
+    C = np.ascontiguousarray(C, np.int32)
+    R = np.zeros_like(C)
+    lib().xvo_inv_transform(C.shape[0], _p(C), _p(R))
+    return R
+
+
+def quant(c, qp: int, log2N: int):
+    f = lib().xvo_quant
+    return np.vectorize(lambda v: int(f(int(v), qp, log2N)), otypes=[np.int32])(np.asarray(c))
+
+
+def dequant(level, qp: int, log2N: int):
+    f = lib().xvo_dequant
+    return np.vectorize(lambda v: int(f(int(v), qp, log2N)), otypes=[np.int32])(np.asarray(level))
+
+
+# ----------------------------------------------------------------- C7
+def lambdas(qp: int) -> tuple[int, int]:
+    a = np.zeros(1, np.int64)
+    b = np.zeros(1, np.int64)
+    lib().xvo_lambdas(qp, _p(a), _p(b))
+    return int(a[0]), int(b[0])
+
+
+def ue_len_se(v: int) -> int:
+    return int(lib().xvo_ue_len_se(int(v)))
+
+
+def mv_bits(mvx_q: int, mvy_q: int) -> int:
+    return int(lib().xvo_mv_bits(int(mvx_q), int(mvy_q)))
+
+
+def mv_cost(mvx_q: int, mvy_q: int, lambda_mv_fp16: int) -> int:
+    return int(lib().xvo_mv_cost(int(mvx_q), int(mvy_q), int(lambda_mv_fp16)))
+
+
+# ----------------------------------------------------------------- C8 / C9
+def interp_block(ref: np.ndarray, x0: int, y0: int, w: int, h: int, mvx_q: int, mvy_q: int):
+    ref = np.ascontiguousarray(ref, np.uint16)
+    out = np.zeros((h, w), np.uint16)
+    lib().xvo_interp_block(_p(ref), ref.shape[0], ref.shape[1], x0, y0, w, h, mvx_q, mvy_q, _p(out))
+    return out
+
+
+def hadamard8(d: np.ndarray) -> np.ndarray:
+    d = np.ascontiguousarray(d, np.int32)
+    out = np.zeros((8, 8), np.int32)
+    lib().xvo_hadamard8(_p(d), _p(out))
+    return out
+
+
+def satd(d: np.ndarray) -> int:
+    d = np.ascontiguousarray(d, np.int32)
+    return int(lib().xvo_satd(_p(d), d.shape[1], d.shape[0]))
+
+
+# ----------------------------------------------------------------- C7 / C8 per frame
+def me_int(cur: np.ndarray, ref: np.ndarray, ctu: int, R: int, lambda_mv_fp16: int):
+    """Integer full search on single planes [Hp,Wp] -> (mv_int [nPU,2] px, J [nPU])."""
+    cur = np.ascontiguousarray(cur, np.uint16)
+    ref = np.ascontiguousarray(ref, np.uint16)
+    Hp, Wp = cur.shape
+    n = (Hp // ctu) * (Wp // ctu)
+    mv = np.zeros((n, 2), np.int16)
+    J = np.zeros(n, np.uint32)
+    lib().xvo_me_int(_p(cur), _p(ref), Hp, Wp, ctu, R, lambda_mv_fp16, _p(mv), _p(J))
+    return mv, J
+
+
+def me_qpel(cur: np.ndarray, ref: np.ndarray, ctu: int, lambda_mv_fp16: int, mv_int: np.ndarray):
+    """Quarter-pel refinement on single planes -> (mv [nPU,2] qpel, J [nPU])."""
+    cur = np.ascontiguousarray(cur, np.uint16)
+    ref = np.ascontiguousarray(ref, np.uint16)
+    mv_int = np.ascontiguousarray(mv_int, np.int16)
+    Hp, Wp = cur.shape
+    n = (Hp // ctu) * (Wp // ctu)
+    mv = np.zeros((n, 2), np.int16)
+    J = np.zeros(n, np.uint32)
+    lib().xvo_me_qpel(_p(cur), _p(ref), Hp, Wp, ctu, lambda_mv_fp16, _p(mv_int), _p(mv), _p(J))
+    return mv, J
+
+
+def tqr_frame(cur: np.ndarray, ref, mv, ctu: int, tu_mask: int, qp: int):
+    """One frame [3,Hp,Wp] -> dict(recon, levels, tu_log2, cu_bits, bits)."""
+    cur = np.ascontiguousarray(cur, np.uint16)
+    _, Hp, Wp = cur.shape
+    n = (Hp // ctu) * (Wp // ctu)
+    lf8, _ = lambdas(qp)
+    recon = np.zeros_like(cur)
+    levels = np.zeros(cur.shape, np.int16)
+    tu = np.zeros(n, np.uint8)
+    cub = np.zeros(n, np.uint64)
+    ref = None if ref is None else np.ascontiguousarray(ref, np.uint16)
+    mv = np.zeros((n, 2), np.int16) if mv is None else np.ascontiguousarray(mv, np.int16)
+    total = lib().xvo_tqr_frame(_p(cur), _p(ref), _p(mv), Hp, Wp, ctu, tu_mask, qp, lf8,
+                                _p(recon), _p(levels), _p(tu), _p(cub))
+    return dict(recon=recon, levels=levels, tu_log2=tu, cu_bits=cub, bits=int(total))
+
+
+# ----------------------------------------------------------------- C4 chain
+def encode_planes(planes: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, want_levels=True):
+    planes = np.ascontiguousarray(planes, np.uint16)
+    G, T, _, Hp, Wp = planes.shape
+    n = (Hp // ctu) * (Wp // ctu)
+    out = dict(
+        recon=np.zeros_like(planes),
+        mv=np.zeros((G, T, n, 2), np.int16),
+        cost=np.zeros((G, T, n), np.uint32),
+        mv_int=np.zeros((G, T, n, 2), np.int16),
+        cost_int=np.zeros((G, T, n), np.uint32),
+        levels=np.zeros(planes.shape, np.int16) if want_levels else None,
+        tu_log2=np.zeros((G, T, n), np.uint8),
+        bits=np.zeros((G, T), np.uint64),
+    )
+    lib().xvo_encode_planes(_p(planes), G, T, Hp, Wp, ctu, R, tu_mask, qp, _p(out["recon"]),
+                            _p(out["mv"]), _p(out["cost"]), _p(out["mv_int"]), _p(out["cost_int"]),
+                            _p(out["levels"]), _p(out["tu_log2"]), _p(out["bits"]))
+    return out
+
+
+# ----------------------------------------------------------------- C14 / C13
+def psnr(src: np.ndarray, planes: np.ndarray, recon: np.ndarray, mm: np.ndarray):
+    src, dt = _src(src)
+    bands, T, H, W = src.shape
+    Hp, Wp = planes.shape[-2:]
+    planes = np.ascontiguousarray(planes, np.uint16)
+    recon = np.ascontiguousarray(recon, np.uint16)
+    mm = np.ascontiguousarray(mm, np.float64)
+    ps = np.zeros(bands)
+    mse = np.zeros(bands)
+    sse10 = np.zeros(bands, np.uint64)
+    ps10 = np.zeros(bands)
+    lib().xvo_psnr(_p(src), dt, bands, T, H, W, _p(planes), _p(recon), Hp, Wp, _p(mm), _p(ps),
+                   _p(mse), _p(sse10), _p(ps10))
+    return dict(psnr_band=ps, mse_band=mse, sse10_band=sse10, psnr10_band=ps10,
+                psnr_mean=float(np.mean(ps)))
+
+
+def encode_cube(src: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, mm=None, want_levels=True):
+    """The whole path on one cube [bands,T,H,W]: A1..A11."""
+    if mm is None:
+        mm, _ = minmax(src)
+    planes = quantize_pack(src, ctu, mm)
+    enc = encode_planes(planes, ctu, R, tu_mask, qp, want_levels=want_levels)
+    met = psnr(src, planes, enc["recon"], mm)
+    bands, T, H, W = src.shape
+    total_bits = int(enc["bits"].sum())
+    enc.update(met)
+    enc.update(mm=mm, planes=planes, total_bits=total_bits,
+               bpppb=total_bits / float(H * W * T * bands))
+    return enc

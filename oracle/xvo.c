@@ -1,0 +1,587 @@
+/*
+ * xvo.c -- CPU oracle (test infrastructure only; see xvo.h).
+ *
+ * Written as the plain definitions, one loop nest per step, in the order the
+ * method runs them:
+ *   Sec. 2.1 of the paper: bands are packed three to a video, the last group
+ *     padded by repeating its last band; the data are converted to an N-bit
+ *     integer video (here 10 bit, per-band min-max).
+ *   HEVC-style encoder analysis (the paper drives libx265, Sec. 2.1 and
+ *     Table A.1; the analysis stages are stated here from the public H.265
+ *     definitions): integer full-search motion estimation with SAD, quarter-pel
+ *     refinement with the 8-tap luma filters and Hadamard SATD, the integer
+ *     core transform, flat-matrix quantisation and its inverse, reconstruction.
+ *   Sec. 2.3: bpppb = bits / (pixels x bands); PSNR against the per-channel
+ *     maximum of the original sequence.
+ * No blocking, fusion or reordering beyond those definitions.  Compile with
+ * -ffp-contract=off: every double operation is rounded on its own.
+ */
+#include "xvo.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define BITDEPTH 10
+#define PIXMAX 1023
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+static int64_t clamp64(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
+/* rs(x, s) = (x + 2^(s-1)) >> s, arithmetic shift (C10). */
+static int64_t rshift_round(int64_t x, int s) { return (x + ((int64_t)1 << (s - 1))) >> s; }
+static int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+int xvo_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+void xvo_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ======================= C2/C3: grouping and geometry ======================== */
+
+/* Sec. 2.1: bands go three to a video; the remainder is repeated up to three. */
+int xvo_group_count(int bands) { return (bands + 2) / 3; }
+
+int xvo_group_band(int bands, int g, int c) {
+    int b = 3 * g + c;
+    return b < bands ? b : bands - 1;
+}
+
+void xvo_plane_geometry(int H, int W, int ctu, int* Hp, int* Wp) {
+    *Hp = (H + ctu - 1) / ctu * ctu;
+    *Wp = (W + ctu - 1) / ctu * ctu;
+}
+
+static double src_value(const void* src, int dtype, int64_t idx) {
+    if (dtype == XVO_F32) return (double)((const float*)src)[idx];
+    return (double)((const uint16_t*)src)[idx];
+}
+
+/* ========================= C1: min-max quantisation ========================== */
+
+/* Per band: min and max over the finite samples of all T*H*W values.  A band
+ * with no finite sample gets min = max = 0. */
+void xvo_minmax(const void* src, int dtype, int bands, int T, int H, int W, double* mm,
+                int64_t* nan_count) {
+    int64_t plane = (int64_t)T * H * W;
+    for (int b = 0; b < bands; ++b) {
+        double lo = INFINITY, hi = -INFINITY;
+        int64_t nn = 0;
+        for (int64_t i = 0; i < plane; ++i) {
+            double v = src_value(src, dtype, (int64_t)b * plane + i);
+            if (!isfinite(v)) { ++nn; continue; }
+            if (v < lo) lo = v;
+            if (v > hi) hi = v;
+        }
+        if (nn == plane) { lo = 0.0; hi = 0.0; }
+        mm[2 * b] = lo;
+        mm[2 * b + 1] = hi;
+        if (nan_count) nan_count[b] = nn;
+    }
+}
+
+/* q = clamp(floor((x - min) * s + 0.5), 0, 1023) with s = 1023 / (max - min),
+ * each operation rounded separately; s = 0 for a constant band; non-finite
+ * samples map to 0. */
+static int quantize_one(double x, double lo, double s) {
+    if (!isfinite(x)) return 0;
+    double d = x - lo;
+    double p = d * s;
+    double r = p + 0.5;
+    double f = floor(r);
+    if (f < 0.0) return 0;
+    if (f > (double)PIXMAX) return PIXMAX;
+    return (int)f;
+}
+
+void xvo_quantize_pack(const void* src, int dtype, int bands, int T, int H, int W, int ctu,
+                       const double* mm, uint16_t* planes) {
+    int G = xvo_group_count(bands), Hp, Wp;
+    xvo_plane_geometry(H, W, ctu, &Hp, &Wp);
+    for (int g = 0; g < G; ++g)
+        for (int c = 0; c < 3; ++c) {
+            int b = xvo_group_band(bands, g, c);
+            double lo = mm[2 * b], hi = mm[2 * b + 1];
+            double s = (hi > lo) ? (double)PIXMAX / (hi - lo) : 0.0;
+            for (int t = 0; t < T; ++t)
+                for (int y = 0; y < Hp; ++y)
+                    for (int x = 0; x < Wp; ++x) {
+                        int sy = y < H ? y : H - 1, sx = x < W ? x : W - 1;
+                        int64_t si = (((int64_t)b * T + t) * H + sy) * W + sx;
+                        int64_t di = ((((int64_t)g * T + t) * 3 + c) * Hp + y) * Wp + x;
+                        planes[di] = (uint16_t)quantize_one(src_value(src, dtype, si), lo, s);
+                    }
+        }
+}
+
+/* ============================ C10: core transform ============================ */
+
+/* The HEVC integer DCT matrix: DC row 64, other rows the scaled cosine table
+ * indexed by k(2n+1)(32/N) mod 128 with the cosine's symmetry folded in. */
+static const int cos_tab[33] = {64, 90, 90, 90, 89, 88, 87, 85, 83, 82, 80, 78, 75, 73, 70, 67, 64,
+                                61, 57, 54, 50, 46, 43, 38, 36, 31, 25, 22, 18, 13, 9,  4,  0};
+
+void xvo_transform_matrix(int N, int32_t* Tm) {
+    for (int k = 0; k < N; ++k)
+        for (int n = 0; n < N; ++n) {
+            int v;
+            if (k == 0) {
+                v = 64;
+            } else {
+                int m = (k * (2 * n + 1) * (32 / N)) % 128;
+                if (m > 64) m = 128 - m;
+                v = (m <= 32) ? cos_tab[m] : -cos_tab[64 - m];
+            }
+            Tm[k * N + n] = v;
+        }
+}
+
+/* Forward: rows first, Y = rs(X T^T, log2N + B - 9); then columns,
+ * C = rs(T Y, log2N + 6). */
+void xvo_fwd_transform(int N, const int32_t* X, int32_t* C) {
+    int32_t Tm[32 * 32];
+    int64_t Y[32 * 32];
+    int L = ilog2(N);
+    xvo_transform_matrix(N, Tm);
+    for (int y = 0; y < N; ++y)
+        for (int k = 0; k < N; ++k) {
+            int64_t acc = 0;
+            for (int x = 0; x < N; ++x) acc += (int64_t)X[y * N + x] * Tm[k * N + x];
+            Y[y * N + k] = rshift_round(acc, L + BITDEPTH - 9);
+        }
+    for (int k = 0; k < N; ++k)
+        for (int u = 0; u < N; ++u) {
+            int64_t acc = 0;
+            for (int y = 0; y < N; ++y) acc += (int64_t)Tm[k * N + y] * Y[y * N + u];
+            C[k * N + u] = (int32_t)rshift_round(acc, L + 6);
+        }
+}
+
+/* Inverse: columns first, E = clip16(rs(T^T C, 7)); then rows,
+ * R = rs(E T, 20 - B). */
+void xvo_inv_transform(int N, const int32_t* C, int32_t* R) {
+    int32_t Tm[32 * 32];
+    int64_t E[32 * 32];
+    xvo_transform_matrix(N, Tm);
+    for (int y = 0; y < N; ++y)
+        for (int u = 0; u < N; ++u) {
+            int64_t acc = 0;
+            for (int v = 0; v < N; ++v) acc += (int64_t)Tm[v * N + y] * C[v * N + u];
+            E[y * N + u] = clamp64(rshift_round(acc, 7), -32768, 32767);
+        }
+    for (int y = 0; y < N; ++y)
+        for (int x = 0; x < N; ++x) {
+            int64_t acc = 0;
+            for (int u = 0; u < N; ++u) acc += E[y * N + u] * Tm[u * N + x];
+            R[y * N + x] = (int32_t)rshift_round(acc, 20 - BITDEPTH);
+        }
+}
+
+/* =============================== C11: quantiser ============================== */
+
+static const int64_t quant_scale[6] = {26214, 23302, 20560, 18396, 16384, 14564};
+static const int64_t dequant_scale[6] = {40, 45, 51, 57, 64, 72};
+
+/* qP = QP + 6(B-8); qbits = 14 + qP/6 + 15 - B - log2N; offset 85/512 of the
+ * step; level = sign(c) ((|c| Q + f) >> qbits), clipped to int16. */
+int32_t xvo_quant(int32_t c, int qp, int log2N) {
+    int qP = qp + 6 * (BITDEPTH - 8);
+    int qbits = 14 + qP / 6 + 15 - BITDEPTH - log2N;
+    int64_t f = (int64_t)85 << (qbits - 9);
+    int64_t a = c < 0 ? -(int64_t)c : (int64_t)c;
+    int64_t lv = (a * quant_scale[qP % 6] + f) >> qbits;
+    if (c < 0) lv = -lv;
+    return (int32_t)clamp64(lv, -32768, 32767);
+}
+
+/* Flat scaling list m = 16; bd = B + log2N - 5;
+ * d = clip16((level 16 IQ 2^(qP/6) + 2^(bd-1)) >> bd). */
+int32_t xvo_dequant(int32_t level, int qp, int log2N) {
+    int qP = qp + 6 * (BITDEPTH - 8);
+    int bd = BITDEPTH + log2N - 5;
+    int64_t v = (int64_t)level * 16 * dequant_scale[qP % 6] * ((int64_t)1 << (qP / 6));
+    v = (v + ((int64_t)1 << (bd - 1))) >> bd;
+    return (int32_t)clamp64(v, -32768, 32767);
+}
+
+/* ============================ C7: motion-vector cost ========================= */
+
+void xvo_lambdas(int qp, int64_t* lambda_fp8, int64_t* lambda_mv_fp16) {
+    double lambda = 0.57 * pow(2.0, (qp - 12) / 3.0);
+    *lambda_fp8 = llround(256.0 * lambda);
+    *lambda_mv_fp16 = llround(65536.0 * sqrt(lambda));
+}
+
+/* Length of the 0th-order Exp-Golomb code of the signed value v (se -> ue). */
+int xvo_ue_len_se(int v) {
+    int64_t k = v > 0 ? 2 * (int64_t)v - 1 : -2 * (int64_t)v;
+    int l = 0;
+    while (((int64_t)1 << (l + 1)) <= k + 1) ++l; /* l = floor(log2(k+1)) */
+    return 2 * l + 1;
+}
+
+int xvo_mv_bits(int mvx_q, int mvy_q) { return xvo_ue_len_se(mvx_q) + xvo_ue_len_se(mvy_q); }
+
+uint32_t xvo_mv_cost(int mvx_q, int mvy_q, int64_t lambda_mv_fp16) {
+    return (uint32_t)((lambda_mv_fp16 * xvo_mv_bits(mvx_q, mvy_q) + 32768) >> 16);
+}
+
+/* ====================== C8: quarter-sample interpolation ===================== */
+
+static const int luma_filter[4][8] = {
+    {0, 0, 0, 64, 0, 0, 0, 0},
+    {-1, 4, -10, 58, 17, -5, 1, 0},
+    {-1, 4, -11, 40, 40, -11, 4, -1},
+    {0, 1, -5, 17, 58, -10, 4, -1},
+};
+
+static int refpx(const uint16_t* ref, int Hp, int Wp, int y, int x) {
+    return ref[clampi(y, 0, Hp - 1) * Wp + clampi(x, 0, Wp - 1)];
+}
+
+/* The predicted sample at (x0 + x, y0 + y) for a quarter-sample motion vector:
+ * shift1 = B - 8, shift2 = 6, full samples scaled by 2^(14-B), then the
+ * default weighted-prediction rounding back to B bits. */
+static int interp_sample(const uint16_t* ref, int Hp, int Wp, int xs, int ys, int mvx_q, int mvy_q) {
+    int xi = xs + (mvx_q >> 2), yi = ys + (mvy_q >> 2);
+    int fx = mvx_q & 3, fy = mvy_q & 3;
+    int shift1 = BITDEPTH - 8, shift2 = 6, shift3 = 14 - BITDEPTH;
+    int v;
+    if (fx == 0 && fy == 0) {
+        v = refpx(ref, Hp, Wp, yi, xi) << shift3;
+    } else if (fy == 0) {
+        int acc = 0;
+        for (int i = 0; i < 8; ++i) acc += luma_filter[fx][i] * refpx(ref, Hp, Wp, yi, xi + i - 3);
+        v = acc >> shift1;
+    } else if (fx == 0) {
+        int acc = 0;
+        for (int j = 0; j < 8; ++j) acc += luma_filter[fy][j] * refpx(ref, Hp, Wp, yi + j - 3, xi);
+        v = acc >> shift1;
+    } else {
+        int tmp[8];
+        for (int j = 0; j < 8; ++j) {
+            int acc = 0;
+            for (int i = 0; i < 8; ++i)
+                acc += luma_filter[fx][i] * refpx(ref, Hp, Wp, yi + j - 3, xi + i - 3);
+            tmp[j] = acc >> shift1;
+        }
+        int acc = 0;
+        for (int j = 0; j < 8; ++j) acc += luma_filter[fy][j] * tmp[j];
+        v = acc >> shift2;
+    }
+    int shiftw = 14 - BITDEPTH;
+    return clampi((v + (1 << (shiftw - 1))) >> shiftw, 0, PIXMAX);
+}
+
+void xvo_interp_block(const uint16_t* ref, int Hp, int Wp, int x0, int y0, int w, int h,
+                      int mvx_q, int mvy_q, uint16_t* out) {
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x)
+            out[y * w + x] = (uint16_t)interp_sample(ref, Hp, Wp, x0 + x, y0 + y, mvx_q, mvy_q);
+}
+
+/* ================================ C9: SATD =================================== */
+
+static int hadamard_entry(int i, int j) { return (__builtin_popcount(i & j) & 1) ? -1 : 1; }
+
+void xvo_hadamard8(const int32_t* d, int32_t* out) {
+    int32_t tmp[64];
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            int32_t acc = 0;
+            for (int k = 0; k < 8; ++k) acc += hadamard_entry(i, k) * d[k * 8 + j];
+            tmp[i * 8 + j] = acc;
+        }
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            int32_t acc = 0;
+            for (int k = 0; k < 8; ++k) acc += tmp[i * 8 + k] * hadamard_entry(j, k);
+            out[i * 8 + j] = acc;
+        }
+}
+
+static uint32_t satd_sub(const int32_t* d, int stride, int n) {
+    int32_t tmp[64];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int32_t acc = 0;
+            for (int k = 0; k < n; ++k) acc += hadamard_entry(i, k) * d[k * stride + j];
+            tmp[i * n + j] = acc;
+        }
+    uint32_t s = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int32_t acc = 0;
+            for (int k = 0; k < n; ++k) acc += tmp[i * n + k] * hadamard_entry(j, k);
+            s += (uint32_t)(acc < 0 ? -acc : acc);
+        }
+    return n == 8 ? (s + 2) >> 2 : (s + 1) >> 1;
+}
+
+/* Sum over 8x8 sub-blocks (4x4 when a side is not a multiple of 8) of the
+ * normalised absolute Hadamard coefficients of the difference d. */
+uint32_t xvo_satd(const int32_t* d, int w, int h) {
+    int n = (w % 8 == 0 && h % 8 == 0) ? 8 : 4;
+    uint32_t s = 0;
+    for (int by = 0; by < h; by += n)
+        for (int bx = 0; bx < w; bx += n) s += satd_sub(d + by * w + bx, w, n);
+    return s;
+}
+
+/* ======================== C7: integer full search ============================ */
+
+void xvo_me_int(const uint16_t* cur, const uint16_t* ref, int Hp, int Wp, int ctu, int R,
+                int64_t lambda_mv_fp16, int16_t* mv_int, uint32_t* cost_int) {
+    int nx = Wp / ctu, ny = Hp / ctu;
+#pragma omp parallel for schedule(dynamic)
+    for (int pu = 0; pu < nx * ny; ++pu) {
+        int x0 = (pu % nx) * ctu, y0 = (pu / nx) * ctu;
+        uint64_t best = UINT64_MAX;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                uint32_t sad = 0;
+                for (int y = 0; y < ctu; ++y)
+                    for (int x = 0; x < ctu; ++x) {
+                        int a = cur[(y0 + y) * Wp + x0 + x];
+                        int b = refpx(ref, Hp, Wp, y0 + y + dy, x0 + x + dx);
+                        sad += (uint32_t)(a > b ? a - b : b - a);
+                    }
+                uint64_t J = (uint64_t)sad + xvo_mv_cost(4 * dx, 4 * dy, lambda_mv_fp16);
+                uint64_t idx = (uint64_t)(dy + R) * (2 * R + 1) + (dx + R);
+                uint64_t key = (J << 32) | idx;
+                if (key < best) best = key;
+            }
+        int idx = (int)(best & 0xffffffffu);
+        mv_int[2 * pu] = (int16_t)(idx % (2 * R + 1) - R);
+        mv_int[2 * pu + 1] = (int16_t)(idx / (2 * R + 1) - R);
+        cost_int[pu] = (uint32_t)(best >> 32);
+    }
+}
+
+/* ======================== C8: quarter-pel refinement ========================= */
+
+static uint32_t satd_cost(const uint16_t* cur, const uint16_t* ref, int Hp, int Wp, int x0, int y0,
+                          int n, int mvx_q, int mvy_q, int64_t lambda_mv_fp16) {
+    int32_t d[64 * 64];
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x)
+            d[y * n + x] = (int32_t)cur[(y0 + y) * Wp + x0 + x] -
+                           interp_sample(ref, Hp, Wp, x0 + x, y0 + y, mvx_q, mvy_q);
+    return xvo_satd(d, n, n) + xvo_mv_cost(mvx_q, mvy_q, lambda_mv_fp16);
+}
+
+static const int ring_x[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+static const int ring_y[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+
+void xvo_me_qpel(const uint16_t* cur, const uint16_t* ref, int Hp, int Wp, int ctu,
+                 int64_t lambda_mv_fp16, const int16_t* mv_int, int16_t* mv, uint32_t* cost) {
+    int nx = Wp / ctu, ny = Hp / ctu;
+#pragma omp parallel for schedule(dynamic)
+    for (int pu = 0; pu < nx * ny; ++pu) {
+        int x0 = (pu % nx) * ctu, y0 = (pu / nx) * ctu;
+        int bx = 4 * mv_int[2 * pu], by = 4 * mv_int[2 * pu + 1];
+        uint32_t bJ = satd_cost(cur, ref, Hp, Wp, x0, y0, ctu, bx, by, lambda_mv_fp16);
+        for (int step = 2; step >= 1; step /= 2) {
+            int cx = bx, cy = by;
+            for (int k = 0; k < 8; ++k) {
+                int mx = cx + step * ring_x[k], my = cy + step * ring_y[k];
+                uint32_t J = satd_cost(cur, ref, Hp, Wp, x0, y0, ctu, mx, my, lambda_mv_fp16);
+                if (J < bJ) { bJ = J; bx = mx; by = my; }
+            }
+        }
+        mv[2 * pu] = (int16_t)bx;
+        mv[2 * pu + 1] = (int16_t)by;
+        cost[pu] = bJ;
+    }
+}
+
+/* ============ C4/C11/C12/C13: transform, quantise, reconstruct ============== */
+
+uint64_t xvo_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, int Hp, int Wp,
+                       int ctu, unsigned tu_mask, int qp, int64_t lambda_fp8, uint16_t* recon,
+                       int16_t* levels, uint8_t* tu_log2, uint64_t* cu_bits) {
+    int nx = Wp / ctu, ny = Hp / ctu, ncu = nx * ny;
+    int64_t plane = (int64_t)Hp * Wp;
+    uint64_t* bits_per_cu = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)ncu);
+#pragma omp parallel for schedule(dynamic)
+    for (int cu = 0; cu < ncu; ++cu) {
+        int x0 = (cu % nx) * ctu, y0 = (cu / nx) * ctu;
+        int n2 = ctu * ctu;
+        int32_t* pred = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+        int32_t* rec_try = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+        int32_t* lev_try = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+        int32_t* rec_best = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+        int32_t* lev_best = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+        int mvx = ref ? mv[2 * cu] : 0, mvy = ref ? mv[2 * cu + 1] : 0;
+        /* C4: frame 0 is predicted by the flat value 2^(B-1); later frames by
+         * motion compensation from the previous reconstruction, all channels
+         * sharing channel 0's vector (C5). */
+        for (int c = 0; c < 3; ++c)
+            for (int y = 0; y < ctu; ++y)
+                for (int x = 0; x < ctu; ++x)
+                    pred[c * n2 + y * ctu + x] =
+                        ref ? interp_sample(ref + c * plane, Hp, Wp, x0 + x, y0 + y, mvx, mvy)
+                            : (1 << (BITDEPTH - 1));
+        int64_t bestJ = INT64_MAX;
+        int bestL = -1;
+        uint64_t bestBits = 0;
+        for (int L = 2; L <= 5; ++L) {
+            int N = 1 << L;
+            if (!(tu_mask & (1u << L)) || N > ctu) continue;
+            uint64_t sse = 0, bits = 0;
+            int32_t X[32 * 32], C[32 * 32], D[32 * 32], Rr[32 * 32];
+            for (int c = 0; c < 3; ++c)
+                for (int ty = 0; ty < ctu; ty += N)
+                    for (int tx = 0; tx < ctu; tx += N) {
+                        for (int y = 0; y < N; ++y)
+                            for (int x = 0; x < N; ++x) {
+                                int yy = ty + y, xx = tx + x;
+                                X[y * N + x] = (int32_t)cur[c * plane + (y0 + yy) * Wp + x0 + xx] -
+                                               pred[c * n2 + yy * ctu + xx];
+                            }
+                        xvo_fwd_transform(N, X, C);
+                        uint64_t tb = 1; /* coded-block flag */
+                        for (int i = 0; i < N * N; ++i) {
+                            int32_t lv = xvo_quant(C[i], qp, L);
+                            lev_try[c * n2 + (ty + i / N) * ctu + tx + i % N] = lv;
+                            if (lv != 0) tb += (uint64_t)(2 * L + xvo_ue_len_se(lv));
+                            D[i] = xvo_dequant(lv, qp, L);
+                        }
+                        bits += tb;
+                        xvo_inv_transform(N, D, Rr);
+                        for (int y = 0; y < N; ++y)
+                            for (int x = 0; x < N; ++x) {
+                                int yy = ty + y, xx = tx + x;
+                                int r = clampi(pred[c * n2 + yy * ctu + xx] + Rr[y * N + x], 0, PIXMAX);
+                                rec_try[c * n2 + yy * ctu + xx] = r;
+                                int e = (int)cur[c * plane + (y0 + yy) * Wp + x0 + xx] - r;
+                                sse += (uint64_t)((int64_t)e * e);
+                            }
+                    }
+            /* C12: J = (SSE << 8) + lambda_fp8 * bits; ascending N, ties to
+             * the larger N. */
+            int64_t J = (int64_t)(sse << 8) + lambda_fp8 * (int64_t)bits;
+            if (J <= bestJ) {
+                bestJ = J;
+                bestL = L;
+                bestBits = bits;
+                memcpy(rec_best, rec_try, sizeof(int32_t) * 3 * (size_t)n2);
+                memcpy(lev_best, lev_try, sizeof(int32_t) * 3 * (size_t)n2);
+            }
+        }
+        for (int c = 0; c < 3; ++c)
+            for (int y = 0; y < ctu; ++y)
+                for (int x = 0; x < ctu; ++x) {
+                    int64_t o = c * plane + (int64_t)(y0 + y) * Wp + x0 + x;
+                    recon[o] = (uint16_t)rec_best[c * n2 + y * ctu + x];
+                    if (levels) levels[o] = (int16_t)lev_best[c * n2 + y * ctu + x];
+                }
+        if (tu_log2) tu_log2[cu] = (uint8_t)bestL;
+        /* C13: 2 bits for the TU size, the motion vector (none in frame 0),
+         * then the coded TUs. */
+        bits_per_cu[cu] = 2 + (ref ? (uint64_t)xvo_mv_bits(mvx, mvy) : 0) + bestBits;
+        free(pred); free(rec_try); free(lev_try); free(rec_best); free(lev_best);
+    }
+    uint64_t total = 0;
+    for (int cu = 0; cu < ncu; ++cu) {
+        total += bits_per_cu[cu];
+        if (cu_bits) cu_bits[cu] = bits_per_cu[cu];
+    }
+    free(bits_per_cu);
+    return total;
+}
+
+/* ===================== C4: the closed-loop chain per group ==================== */
+
+int xvo_encode_planes(const uint16_t* planes, int G, int T, int Hp, int Wp, int ctu, int R,
+                      unsigned tu_mask, int qp, uint16_t* recon, int16_t* mv, uint32_t* cost,
+                      int16_t* mv_int, uint32_t* cost_int, int16_t* levels, uint8_t* tu_log2,
+                      uint64_t* bits) {
+    int64_t lf8, lmv;
+    xvo_lambdas(qp, &lf8, &lmv);
+    int npu = (Hp / ctu) * (Wp / ctu);
+    int64_t fsz = 3 * (int64_t)Hp * Wp;
+    int16_t* mvi = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)npu);
+    uint32_t* ci = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)npu);
+    int16_t* mvq = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)npu);
+    uint32_t* cq = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)npu);
+    for (int g = 0; g < G; ++g)
+        for (int t = 0; t < T; ++t) {
+            int64_t f = (int64_t)g * T + t;
+            const uint16_t* cur = planes + f * fsz;
+            const uint16_t* ref = t > 0 ? recon + (f - 1) * fsz : NULL;
+            if (ref) {
+                xvo_me_int(cur, ref, Hp, Wp, ctu, R, lmv, mvi, ci);
+                xvo_me_qpel(cur, ref, Hp, Wp, ctu, lmv, mvi, mvq, cq);
+            } else {
+                memset(mvi, 0, sizeof(int16_t) * 2 * (size_t)npu);
+                memset(ci, 0, sizeof(uint32_t) * (size_t)npu);
+                memset(mvq, 0, sizeof(int16_t) * 2 * (size_t)npu);
+                memset(cq, 0, sizeof(uint32_t) * (size_t)npu);
+            }
+            if (mv) memcpy(mv + f * 2 * npu, mvq, sizeof(int16_t) * 2 * (size_t)npu);
+            if (cost) memcpy(cost + f * npu, cq, sizeof(uint32_t) * (size_t)npu);
+            if (mv_int) memcpy(mv_int + f * 2 * npu, mvi, sizeof(int16_t) * 2 * (size_t)npu);
+            if (cost_int) memcpy(cost_int + f * npu, ci, sizeof(uint32_t) * (size_t)npu);
+            bits[f] = xvo_tqr_frame(cur, ref, mvq, Hp, Wp, ctu, tu_mask, qp, lf8, recon + f * fsz,
+                                    levels ? levels + f * fsz : NULL,
+                                    tu_log2 ? tu_log2 + f * npu : NULL, NULL);
+        }
+    free(mvi); free(ci); free(mvq); free(cq);
+    return 0;
+}
+
+/* ============================== C14: PSNR ==================================== */
+
+/* Per real band b (slot: group b/3, channel b%3): x^ = min + q^ (max-min)/1023,
+ * MSE over the valid finite samples (Kahan-summed), PSNR = 10 log10(peak^2 /
+ * MSE) with peak = max (max - min when max <= 0), +inf when MSE = 0.  Also the
+ * exact 10-bit SSE against the quantised original and its PSNR at peak 1023. */
+void xvo_psnr(const void* src, int dtype, int bands, int T, int H, int W, const uint16_t* planes,
+              const uint16_t* recon, int Hp, int Wp, const double* mm, double* psnr_band,
+              double* mse_band, uint64_t* sse10_band, double* psnr10_band) {
+    for (int b = 0; b < bands; ++b) {
+        int g = b / 3, c = b % 3;
+        double lo = mm[2 * b], hi = mm[2 * b + 1];
+        double delta = (hi - lo) / (double)PIXMAX;
+        double sum = 0.0, comp = 0.0;
+        int64_t count = 0;
+        uint64_t sse10 = 0;
+        for (int t = 0; t < T; ++t)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    int64_t pi = ((((int64_t)g * T + t) * 3 + c) * Hp + y) * Wp + x;
+                    int rq = recon[pi];
+                    int e10 = (int)planes[pi] - rq;
+                    sse10 += (uint64_t)((int64_t)e10 * e10);
+                    double xv = src_value(src, dtype, (((int64_t)b * T + t) * H + y) * W + x);
+                    if (!isfinite(xv)) continue;
+                    double xh = lo + (double)rq * delta;
+                    double e = xv - xh;
+                    double term = e * e;
+                    double yk = term - comp; /* Kahan summation */
+                    double tk = sum + yk;
+                    comp = (tk - sum) - yk;
+                    sum = tk;
+                    ++count;
+                }
+        double mse = count > 0 ? sum / (double)count : 0.0;
+        double peak = hi > 0.0 ? hi : hi - lo;
+        mse_band[b] = mse;
+        psnr_band[b] = mse > 0.0 ? 10.0 * log10(peak * peak / mse) : INFINITY;
+        sse10_band[b] = sse10;
+        double n = (double)T * H * W;
+        psnr10_band[b] = sse10 > 0 ? 10.0 * log10((double)PIXMAX * PIXMAX * n / (double)sse10) : INFINITY;
+    }
+}

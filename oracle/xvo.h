@@ -1,0 +1,95 @@
+/*
+ * xvo.h -- CPU oracle for the encoder-analysis path of "Video Compression for
+ * Spatiotemporal Earth System Data" (arXiv 2506.19656).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, loop-by-loop statement of
+ * what the GPU library computes, used to check it.  Only the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or helper with the CUDA library and includes nothing
+ * from it.
+ *
+ * The paper fixes only the band grouping (Sec. 2.1), the bpppb metric and the
+ * PSNR peak (Sec. 2.3).  Everything else -- the HEVC-style integer transform,
+ * quantiser, interpolation filter, SATD, motion-cost model and the rate proxy
+ * -- is a reading written down in the repository's design notes (conventions
+ * C1..C15); each function below names the convention it follows.
+ *
+ * All signed right shifts are arithmetic (floor).  Bit depth B = 10.
+ */
+#ifndef XVO_H
+#define XVO_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XVO_F32 0
+#define XVO_U16 1
+
+/* ---- C1/C2/C3: min-max quantisation and band packing ---------------------- */
+int  xvo_group_count(int bands);
+int  xvo_group_band(int bands, int g, int c);
+void xvo_plane_geometry(int H, int W, int ctu, int* Hp, int* Wp);
+void xvo_minmax(const void* src, int dtype, int bands, int T, int H, int W,
+                double* mm /*[bands][2]*/, int64_t* nan_count /*[bands] or NULL*/);
+void xvo_quantize_pack(const void* src, int dtype, int bands, int T, int H, int W,
+                       int ctu, const double* mm, uint16_t* planes /*[G][T][3][Hp][Wp]*/);
+
+/* ---- C10: core transform ----------------------------------------------------- */
+void xvo_transform_matrix(int N, int32_t* Tm /*[N][N]*/);
+void xvo_fwd_transform(int N, const int32_t* X, int32_t* C);
+void xvo_inv_transform(int N, const int32_t* C, int32_t* R);
+
+/* ---- C11: quantiser ---------------------------------------------------------- */
+int32_t xvo_quant(int32_t c, int qp, int log2N);
+int32_t xvo_dequant(int32_t level, int qp, int log2N);
+
+/* ---- C7: motion cost ---------------------------------------------------------- */
+void     xvo_lambdas(int qp, int64_t* lambda_fp8, int64_t* lambda_mv_fp16);
+int      xvo_ue_len_se(int v);
+int      xvo_mv_bits(int mvx_q, int mvy_q);
+uint32_t xvo_mv_cost(int mvx_q, int mvy_q, int64_t lambda_mv_fp16);
+
+/* ---- C8/C9: interpolation and SATD ------------------------------------------- */
+void     xvo_interp_block(const uint16_t* ref, int Hp, int Wp, int x0, int y0, int w, int h,
+                          int mvx_q, int mvy_q, uint16_t* out /*[h][w]*/);
+void     xvo_hadamard8(const int32_t* d /*[8][8]*/, int32_t* out /*[8][8]*/);
+uint32_t xvo_satd(const int32_t* d, int w, int h);
+
+/* ---- C7/C8: motion estimation for one frame of one group --------------------- */
+void xvo_me_int(const uint16_t* cur, const uint16_t* ref, int Hp, int Wp, int ctu, int R,
+                int64_t lambda_mv_fp16, int16_t* mv_int /*[nPU][2]*/, uint32_t* cost_int);
+void xvo_me_qpel(const uint16_t* cur, const uint16_t* ref, int Hp, int Wp, int ctu,
+                 int64_t lambda_mv_fp16, const int16_t* mv_int, int16_t* mv /*[nPU][2]*/,
+                 uint32_t* cost);
+
+/* ---- C4/C11/C12/C13: transform, quantise, reconstruct one frame -------------- */
+uint64_t xvo_tqr_frame(const uint16_t* cur /*[3][Hp][Wp]*/, const uint16_t* ref /*NULL: frame 0*/,
+                       const int16_t* mv /*[nCU][2] qpel, ignored for frame 0*/,
+                       int Hp, int Wp, int ctu, unsigned tu_mask, int qp,
+                       int64_t lambda_fp8, uint16_t* recon /*[3][Hp][Wp]*/,
+                       int16_t* levels /*[3][Hp][Wp] or NULL*/, uint8_t* tu_log2 /*[nCU] or NULL*/,
+                       uint64_t* cu_bits /*[nCU] or NULL*/);
+
+/* ---- whole-cube chain (C4): frames in order, all groups ---------------------- */
+int xvo_encode_planes(const uint16_t* planes /*[G][T][3][Hp][Wp]*/, int G, int T, int Hp, int Wp,
+                      int ctu, int R, unsigned tu_mask, int qp,
+                      uint16_t* recon /*[G][T][3][Hp][Wp]*/, int16_t* mv /*[G][T][nPU][2] or NULL*/,
+                      uint32_t* cost /*[G][T][nPU] or NULL*/, int16_t* mv_int /*or NULL*/,
+                      uint32_t* cost_int /*or NULL*/, int16_t* levels /*or NULL*/,
+                      uint8_t* tu_log2 /*[G][T][nCU] or NULL*/, uint64_t* bits /*[G][T]*/);
+
+/* ---- C14/C13: PSNR and bits per pixel per band ------------------------------- */
+void xvo_psnr(const void* src, int dtype, int bands, int T, int H, int W,
+              const uint16_t* planes, const uint16_t* recon, int Hp, int Wp, const double* mm,
+              double* psnr_band /*[bands]*/, double* mse_band /*[bands]*/,
+              uint64_t* sse10_band /*[bands]*/, double* psnr10_band /*[bands]*/);
+
+int xvo_max_threads(void);
+void xvo_set_threads(int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
