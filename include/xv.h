@@ -1,0 +1,231 @@
+/*
+ * xv.h -- C ABI of the GPU encoder-analysis library (libxv.so, sm_103a).
+ *
+ * The library compresses multichannel spatiotemporal cubes the way the paper
+ * "Video Compression for Spatiotemporal Earth System Data" (arXiv 2506.19656)
+ * does -- bands packed three to a video and coded as 10-bit video -- but
+ * stops at the encoder analysis: it computes, bit-exactly and on the GPU,
+ * the quantised planes, motion vectors, transform levels, reconstruction,
+ * and the PSNR / bits-per-pixel-per-band reductions.  There is no entropy
+ * coder; "bits" is the rate proxy defined at xv_transform_quant_recon.
+ *
+ * Conventions for every call:
+ *  - All data pointers are caller-owned.  Unless stated otherwise they are
+ *    DEVICE pointers on the context's device.  The library never frees them.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it unless marked "synchronous".
+ *  - Every call returns an xv_status; nothing aborts or traps.  On error the
+ *    message is available from xv_last_error() (thread-local).
+ *  - Plane layout: uint16 [G][T][3][Hp][Wp] holding 10-bit samples, G =
+ *    ceil(bands / 3) groups, Hp/Wp = H/W rounded up to the CTU size.
+ *  - Signed right shifts are arithmetic.  Bit depth B = 10.
+ */
+#ifndef XV_H
+#define XV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XV_OK = 0,
+    XV_EINVAL = -1,     /* a shape, pointer or parameter is out of range */
+    XV_ENOMEM = -2,     /* a device allocation failed */
+    XV_EBUDGET = -3,    /* the request does not fit the context's memory budget */
+    XV_ETIMEOUT = -4,   /* a device-side dependency wait ran out of time */
+    XV_EBUSY = -5,      /* the serving queue is full */
+    XV_ECUDA = -6,      /* a CUDA runtime call or kernel launch failed */
+    XV_ECANCELLED = -7, /* the serving request was cancelled */
+    XV_ENOTFOUND = -8   /* unknown serving ticket */
+} xv_status;
+
+typedef enum { XV_F32 = 0, XV_U16 = 1 } xv_dtype;
+
+#define XV_MAX_BANDS 16
+
+/* Encoder parameters of one cube; restates the paper's per-video mapping
+ * rules (Sec. 2.1: codec parameters and output bit depth per video). */
+typedef struct {
+    int bit_depth;          /* 10 (the only depth in scope) */
+    int ctu;                /* PU = CU = CTU size: 8, 16, 32 or 64 */
+    int search_range;       /* R: integer search over [-R, R]^2, 1..64 */
+    unsigned tu_mask;       /* bit k set: TU size 2^k allowed (k = 2..5); >= 1 size <= ctu */
+    int qp;                 /* QP_Y in [-12, 51]; qP = qp + 6 (B - 8) */
+    int64_t lambda_fp8;     /* round(256 * lambda), lambda = 0.57 * 2^((qp - 12) / 3) */
+    int64_t lambda_mv_fp16; /* round(65536 * sqrt(lambda)) */
+} xv_params;
+
+typedef struct xv_ctx xv_ctx;
+
+/* ------------------------------------------------------------------ context */
+
+/* Creates a context on `device`.  `mem_budget_bytes` caps the device memory
+ * the context itself allocates (scratch, serving buffers); 0 = no cap.
+ * Synchronous. */
+xv_status xv_create(xv_ctx** ctx, int device, size_t mem_budget_bytes);
+/* Frees everything the context allocated.  Synchronous.  NULL is a no-op. */
+void xv_destroy(xv_ctx* ctx);
+/* Message of the last failing call on this thread ("" if none). */
+const char* xv_last_error(void);
+const char* xv_status_string(xv_status s);
+/* Device bytes the context currently holds. */
+size_t xv_ctx_bytes(const xv_ctx* ctx);
+
+/* Fills `p` for (ctu, R, tu_mask, qp) and derives the fixed-point lambdas on
+ * the host (the device only sees integers).  XV_EINVAL when ctu is not 8..64
+ * power of two, R is outside 1..64, no TU size <= ctu is allowed, a TU bit
+ * outside 2..5 is set, or qp is outside [-12, 51]. */
+xv_status xv_params_init(xv_params* p, int ctu, int search_range, unsigned tu_mask, int qp);
+
+/* G = ceil(bands / 3), Hp = ceil(H / ctu) * ctu, Wp likewise.  Host only. */
+xv_status xv_plane_geometry(int bands, int H, int W, int ctu, int* G, int* Hp, int* Wp);
+
+/* ------------------------------------------------- A1/A2: quantise and pack */
+
+/* Per-band minimum and maximum over the finite samples of a cube (paper
+ * Sec. 2.1 converts every band to an N-bit integer video; the per-band range
+ * is the metadata needed to undo it).  src: [bands][T][H][W] float32 or
+ * uint16.  minmax: device double [bands][2] (min, max), written.  A band
+ * without finite samples gets (0, 0).  Uses context scratch. */
+xv_status xv_minmax(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                    double* minmax, void* stream);
+
+/* Min-max quantisation to 10 bit and packing three bands to a group (paper
+ * Sec. 2.1: the remaining bands of the last group are repeated, e.g.
+ * R,G,B | NIR,NIR,NIR).  q = clamp(floor((x - min) s + 0.5), 0, 1023) with
+ * s = 1023 / (max - min) in IEEE double (s = 0 for a constant band), each
+ * operation rounded separately; non-finite samples give 0.  Planes are
+ * padded to the CTU grid by repeating the last row and column.
+ * minmax: device double [bands][2]; computed first (as xv_minmax) unless
+ * `minmax_fixed` is non-zero, in which case it is read.  planes: device
+ * uint16 [G][T][3][Hp][Wp], written. */
+xv_status xv_quantize_pack(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                           int ctu, double* minmax, int minmax_fixed, uint16_t* planes, void* stream);
+
+/* ---------------------------------------------- A3/A4: motion estimation */
+
+/* Block motion estimation of one frame for G groups (the paper codes every
+ * group with libx265, Sec. 2.1; this is the HEVC-style analysis it runs).
+ * Per CTU-sized PU, on channel 0 of each group:
+ *  integer full search over (dx, dy) in [-R, R]^2 against `ref` with the
+ *  sample coordinates clamped to the plane, J = SAD + mvcost(4dx, 4dy), the
+ *  smallest (J, (dy+R)(2R+1) + dx+R) wins; then quarter-sample refinement:
+ *  the 8 half-sample neighbours, then the 8 quarter-sample neighbours of the
+ *  best, each J = SATD(8x8 Hadamard) + mvcost, replacing the best only when
+ *  strictly lower.  mvcost(mx, my) = (lambda_mv_fp16 (|se(mx)| + |se(my)|)
+ *  + 2^15) >> 16 with |se| the signed Exp-Golomb code length.
+ * cur/ref: device uint16, group g's frame at cur + g * plane_gstride, layout
+ *   [3][Hp][Wp] (only channel 0 is read).
+ * mv: int16 [G][nPU][2] quarter-sample (x, y); cost: uint32 [G][nPU] (final
+ *   J); mv_int/cost_int: the integer-search result (may be NULL).  Group g's
+ *   rows start at g * pu_gstride PUs.  nPU = (Hp/ctu)(Wp/ctu), raster order. */
+xv_status xv_motion_search(xv_ctx* ctx, const uint16_t* cur, const uint16_t* ref, int G,
+                           int64_t plane_gstride, int Hp, int Wp, const xv_params* p, int16_t* mv,
+                           uint32_t* cost, int16_t* mv_int, uint32_t* cost_int, int64_t pu_gstride,
+                           void* stream);
+
+/* -------------------------- A5..A9: transform, quantise, reconstruct */
+
+/* Transform, quantisation and reconstruction of one frame for G groups.
+ * Prediction: ref == NULL (first frame) predicts every sample by 512; else
+ * each CU is motion-compensated from `ref` (all 3 channels, the CU's
+ * quarter-sample vector, HEVC 8-tap luma filter, default weighted rounding).
+ * For every allowed TU size N <= ctu (ascending), the CU is tiled by N x N
+ * TUs, each channel's residual goes through the HEVC integer core transform
+ * (rows: shift log2N + 1; columns: shift log2N + 6), the flat quantiser
+ * (qbits = 14 + qP/6 + 15 - B - log2N, offset 85 << (qbits - 9)), the
+ * dequantiser (m = 16, levelScale), the inverse (columns: shift 7 + int16
+ * clip; rows: shift 20 - B) and recon = clip(pred + r, 0, 1023).  The size
+ * with the least J = (SSE << 8) + lambda_fp8 * bits wins, ties to the larger.
+ * Rate proxy per CU: 2 (TU size) + |se(mvx)| + |se(mvy)| (not in frame 0) +
+ * per TU and channel 1 + sum over nonzero levels of (2 log2N + |se(level)|).
+ * cur/ref/recon: device uint16, group g at + g * plane_gstride, [3][Hp][Wp].
+ * mv: int16 [G][nPU][2] at + g * pu_gstride * 2 (ignored when ref == NULL).
+ * recon: written (it is the next frame's reference).  levels: int16 in the
+ *   plane layout (may be NULL).  tu_log2: uint8 [G][nCU] at + g * pu_gstride
+ *   (may be NULL).  bits: uint64, group g's frame total is ADDED to
+ *   bits[g * bits_gstride] (zero it first). */
+xv_status xv_transform_quant_recon(xv_ctx* ctx, const uint16_t* cur, const uint16_t* ref,
+                                   const int16_t* mv, int G, int64_t plane_gstride, int Hp, int Wp,
+                                   const xv_params* p, int64_t pu_gstride, uint16_t* recon,
+                                   int16_t* levels, uint8_t* tu_log2, uint64_t* bits,
+                                   int64_t bits_gstride, void* stream);
+
+/* ----------------------------------------------- A10/A11: PSNR and rate */
+
+/* PSNR per real band (paper Sec. 2.3: peak = the maximum of the original
+ * sequence for that band; max - min when max <= 0).  Band b is read from
+ * group b/3, channel b%3 of `recon`, de-quantised as min + q (max-min)/1023,
+ * and compared with the finite samples of `src` over the valid H x W region.
+ * Also the exact 10-bit SSE against `planes`.  psnr_band, mse_band,
+ * sse10_band: HOST arrays [bands] (any may be NULL); psnr_mean: HOST, the
+ * mean of the per-band PSNR (+inf when any band is exact).  Synchronous. */
+xv_status xv_psnr(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                  const uint16_t* planes, const uint16_t* recon, int Hp, int Wp, const double* minmax,
+                  double* psnr_band, double* mse_band, uint64_t* sse10_band, double* psnr_mean,
+                  void* stream);
+
+/* ------------------------------------------------------ whole cubes */
+
+/* One cube.  Device buffers, caller-owned: */
+typedef struct {
+    const void* src;     /* [bands][T][H][W] float32 or uint16 */
+    xv_dtype dtype;
+    int bands, T, H, W;  /* bands <= XV_MAX_BANDS */
+    xv_params p;
+    double* minmax;      /* [bands][2]; computed unless minmax_fixed */
+    int minmax_fixed;
+    uint16_t* planes;    /* [G][T][3][Hp][Wp] quantised input (written) */
+    uint16_t* recon;     /* [G][T][3][Hp][Wp] reconstruction (written) */
+    int16_t* mv;         /* [G][T][nPU][2] final vectors, or NULL */
+    uint32_t* cost;      /* [G][T][nPU] final J, or NULL */
+    int16_t* levels;     /* plane layout, or NULL */
+    uint8_t* tu_log2;    /* [G][T][nCU], or NULL */
+    uint64_t* bits;      /* [G][T] per-frame rate proxy, or NULL */
+} xv_job;
+
+typedef struct {
+    xv_status status;
+    int bands;
+    double psnr_mean;    /* mean over bands of psnr_band */
+    double bpppb;        /* total bits / (H W T bands) -- rate proxy, see above */
+    uint64_t total_bits;
+    double psnr_band[XV_MAX_BANDS];
+    double mse_band[XV_MAX_BANDS];
+    uint64_t sse10_band[XV_MAX_BANDS];
+    double latency_s;    /* serving: arrival to completion */
+} xv_result;
+
+/* Bytes of device scratch a job needs beyond its own buffers. */
+size_t xv_job_scratch_bytes(const xv_job* job);
+
+/* Plain path: quantise/pack, then frame by frame one motion-search and one
+ * transform launch for all groups, then PSNR.  `result` is a HOST struct.
+ * Synchronous (waits for the PSNR read-back). */
+xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void* stream);
+
+/* Batched path: all jobs' frames run in ONE persistent launch over a device
+ * work queue of (job, group, frame, PU) items ordered frame-major; an item
+ * waits (with a bounded spin) until the previous frame's reconstruction rows
+ * it reads are complete.  Output is bit-identical to xv_encode_cube for each
+ * job.  results: HOST [njobs].  Synchronous.  XV_ETIMEOUT if a wait ran out
+ * of time (results then invalid). */
+xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
+
+/* ------------------------------------------------------ test hooks */
+
+/* Spin budget (SM clock cycles, default 4e9, about 2 s) of each dependency
+ * wait in xv_encode_batch.  Host only. */
+xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
+/* Make the dependency of work item `item` (ticket index within its CTU
+ * class) impossible to satisfy, so that its wait runs out and the batch
+ * returns XV_ETIMEOUT without any fault; -1 disables.  Host only. */
+xv_status xv_debug_stall_item(xv_ctx* ctx, long long item);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XV_H */

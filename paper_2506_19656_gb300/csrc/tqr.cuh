@@ -1,0 +1,236 @@
+// tqr.cuh -- transform, quantise, reconstruct one CU by one thread block.
+//
+// Definitions: xv_transform_quant_recon in include/xv.h.  For each allowed
+// TU size (ascending) the whole CU goes through
+//   rows:    Y = rs(X T^T, log2N + 1)             one thread per TU row
+//   columns: C = rs(T Y, log2N + 6), quantise, dequantise,
+//            E = clip16(rs(T^T D, 7))             one thread per TU column
+//   rows:    r = rs(E T, 10), recon = clip(pred + r)
+// and the size with the least (SSE << 8) + lambda * bits is kept (ties to the
+// larger).  The kept size's reconstruction and levels are copied out as soon
+// as a size improves on the best so far, so no second buffer set is needed.
+//
+// Shared memory (all [3][N][N] unless noted):
+//   cur u16, pred u16, work int16 (Y, then E), lev int16, rec u16,
+//   stage int16 [(N+7)*(N+7)] (the motion-compensation window of one
+//   channel; reused as the horizontal-pass buffer), reductions.
+#pragma once
+#include <cstdint>
+#include "xv_dev.cuh"
+
+namespace xvd {
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+// Byte offsets of the shared-memory regions (every region 16-byte aligned).
+__host__ __device__ constexpr size_t tqr_off_stage(int N) { return align16((size_t)5 * 3 * N * N * 2); }
+__host__ __device__ constexpr size_t tqr_off_hbuf(int N) { return tqr_off_stage(N) + align16((size_t)(N + 7) * (N + 7) * 2); }
+__host__ __device__ constexpr size_t tqr_off_red(int N) { return tqr_off_hbuf(N) + align16((size_t)(N + 7) * (N + 7) * 2); }
+__host__ __device__ constexpr size_t tqr_smem_bytes(int N) { return tqr_off_red(N) + 64 * 8; }
+
+template <int NT>
+__device__ __forceinline__ void block_sum2(uint64_t& a, uint32_t& b, uint64_t* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { red[warp] = a; red[32 + warp] = b; }
+    __syncthreads();
+    a = 0; b = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) { a += red[w]; b += (uint32_t)red[32 + w]; }
+    __syncthreads();
+}
+
+// Motion-compensated prediction of the CU for all 3 channels.
+template <int N, int NT, bool kCoherent>
+__device__ void mc_predict(const uint16_t* __restrict__ ref, int64_t plane, int Hp, int Wp, int x0, int y0,
+                           int mvx, int mvy, uint16_t* __restrict__ pred, int16_t* __restrict__ stage,
+                           int16_t* __restrict__ hbuf) {
+    const int tid = threadIdx.x;
+    constexpr int SW = N + 7;
+    const int ix = mvx >> 2, iy = mvy >> 2, fx = mvx & 3, fy = mvy & 3;
+    for (int c = 0; c < 3; ++c) {
+        const uint16_t* rp = ref + c * plane;
+        // window rows y0+iy-3 .. +N+3, columns x0+ix-3 .. +N+3, clamped
+        for (int idx = tid; idx < SW * SW; idx += NT) {
+            int r = idx / SW, q = idx - r * SW;
+            int yy = min(max(y0 + iy - 3 + r, 0), Hp - 1), xx = min(max(x0 + ix - 3 + q, 0), Wp - 1);
+            stage[idx] = (int16_t)ld_ref<kCoherent>(rp + (size_t)yy * Wp + xx);
+        }
+        __syncthreads();
+        if (fx != 0) {  // horizontal pass over all SW rows
+            for (int idx = tid; idx < SW * N; idx += NT) {
+                int r = idx / N, x = idx - r * N;
+                int acc = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc += luma_tap(fx, i) * stage[r * SW + x + i];
+                hbuf[idx] = (int16_t)(acc >> kShift1);
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < N * N; idx += NT) {
+            int y = idx / N, x = idx - y * N;
+            int v;
+            if (fx == 0 && fy == 0) {
+                v = stage[(y + 3) * SW + x + 3] << kShift3;
+            } else if (fy == 0) {
+                v = hbuf[(y + 3) * N + x];
+            } else if (fx == 0) {
+                int acc = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc += luma_tap(fy, t) * stage[(y + t) * SW + x + 3];
+                v = acc >> kShift1;
+            } else {
+                int acc = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc += luma_tap(fy, t) * hbuf[(y + t) * N + x];
+                v = acc >> kShift2;
+            }
+            pred[c * N * N + idx] = (uint16_t)wp_round(v);
+        }
+        __syncthreads();
+    }
+}
+
+// One TU size over the whole CU; returns (SSE, bits) through the reduction.
+template <int N, int TS, int NT>
+__device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
+                        int16_t* __restrict__ work, int16_t* __restrict__ lev, uint16_t* __restrict__ rec,
+                        int qp, uint64_t& sse_out, uint32_t& bits_out, uint64_t* red) {
+    constexpr int L = TS == 4 ? 2 : TS == 8 ? 3 : TS == 16 ? 4 : 5;
+    constexpr int NTU = N / TS;            // TUs per CU side
+    constexpr int TASKS = 3 * N * NTU;     // rows (or columns) of all TUs of all channels
+    const int tid = threadIdx.x;
+    const QuantParams q = quant_params(qp, L);
+    // forward rows
+    for (int t = tid; t < TASKS; t += NT) {
+        int c = t / (N * NTU), rem = t - c * N * NTU;
+        int y = rem / NTU, tx = rem - y * NTU;
+        const int base = c * N * N + y * N + tx * TS;
+        int x[TS], yv[TS];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) x[i] = (int)cur[base + i] - (int)pred[base + i];
+        fwd1d<TS>(x, yv);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) work[base + i] = (int16_t)rshift_round(yv[i], L + kBitDepth - 9);
+    }
+    __syncthreads();
+    // columns: forward, quantise, dequantise, inverse
+    uint32_t bits = 0;
+    for (int t = tid; t < TASKS; t += NT) {
+        int c = t / (N * NTU), rem = t - c * N * NTU;
+        int ty = rem / N, x = rem - ty * N;
+        const int base = c * N * N + ty * TS * N + x;
+        int col[TS], cf[TS];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) col[i] = work[base + i * N];
+        fwd1d<TS>(col, cf);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) {
+            int lv = quantize(rshift_round(cf[i], L + 6), q);
+            lev[base + i * N] = (int16_t)lv;
+            if (lv != 0) bits += (uint32_t)(2 * L + se_len(lv));
+            col[i] = dequantize(lv, q);
+        }
+        inv1d<TS>(col, cf);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) work[base + i * N] = (int16_t)clip16(rshift_round(cf[i], 7));
+    }
+    __syncthreads();
+    // inverse rows and reconstruction
+    uint64_t sse = 0;
+    for (int t = tid; t < TASKS; t += NT) {
+        int c = t / (N * NTU), rem = t - c * N * NTU;
+        int y = rem / NTU, tx = rem - y * NTU;
+        const int base = c * N * N + y * N + tx * TS;
+        int e[TS], r[TS];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) e[i] = work[base + i];
+        inv1d<TS>(e, r);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) {
+            int v = clip_pix((int)pred[base + i] + rshift_round(r[i], 20 - kBitDepth));
+            rec[base + i] = (uint16_t)v;
+            int d = (int)cur[base + i] - v;
+            sse += (uint64_t)(d * d);
+        }
+    }
+    block_sum2<NT>(sse, bits, red);
+    sse_out = sse;
+    bits_out = bits + 3u * NTU * NTU;  // one coded-block flag per TU and channel
+}
+
+template <int N, int NT>
+__device__ __forceinline__ void copy_out(const uint16_t* __restrict__ rec, const int16_t* __restrict__ lev,
+                                         uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
+                                         int64_t plane, int Wp, int x0, int y0) {
+    for (int idx = threadIdx.x; idx < 3 * N * N; idx += NT) {
+        int c = idx / (N * N), rem = idx - c * N * N;
+        int y = rem / N, x = rem - y * N;
+        size_t o = (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + x;
+        recon[o] = rec[idx];
+        if (levels) levels[o] = lev[idx];
+    }
+}
+
+// Transform/quantise/reconstruct the CU at (x0, y0).  cur/ref/recon/levels:
+// the group's frame [3][Hp][Wp] (ref == nullptr: first frame).  Returns the
+// CU's rate-proxy bits; writes recon (and levels) and *tu_log2.
+template <int N, int NT, bool kCoherent = false>
+__device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
+                           int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
+                           int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
+                           uint8_t* tu_log2, unsigned char* smem) {
+    const int tid = threadIdx.x;
+    uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* s_pred = s_cur + 3 * N * N;
+    int16_t* s_work = reinterpret_cast<int16_t*>(s_pred + 3 * N * N);
+    int16_t* s_lev = s_work + 3 * N * N;
+    uint16_t* s_rec = reinterpret_cast<uint16_t*>(s_lev + 3 * N * N);
+    int16_t* s_stage = reinterpret_cast<int16_t*>(smem + tqr_off_stage(N));
+    int16_t* s_hbuf = reinterpret_cast<int16_t*>(smem + tqr_off_hbuf(N));
+    uint64_t* red = reinterpret_cast<uint64_t*>(smem + tqr_off_red(N));
+
+    for (int idx = tid; idx < 3 * N * N; idx += NT) {
+        int c = idx / (N * N), rem = idx - c * N * N;
+        int y = rem / N, x = rem - y * N;
+        s_cur[idx] = __ldg(cur + (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + x);
+        if (!ref) s_pred[idx] = (uint16_t)kFlat;
+    }
+    if (ref) {
+        __syncthreads();
+        mc_predict<N, NT, kCoherent>(ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_pred, s_stage, s_hbuf);
+    } else {
+        __syncthreads();
+    }
+
+    int64_t bestJ = INT64_MAX;
+    int bestL = 0;
+    uint32_t bestBits = 0;
+    auto consider = [&](int L, uint64_t sse, uint32_t bits) {
+        int64_t J = (int64_t)(sse << 8) + lf8 * (int64_t)bits;
+        if (J <= bestJ) {  // ascending sizes: ties go to the larger
+            bestJ = J;
+            bestL = L;
+            bestBits = bits;
+            copy_out<N, NT>(s_rec, s_lev, recon, levels, plane, Wp, x0, y0);
+        }
+        __syncthreads();
+    };
+    uint64_t sse;
+    uint32_t bits;
+    if (tu_mask & (1u << 2)) { tu_pass<N, 4, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(2, sse, bits); }
+    if constexpr (N >= 8)
+        if (tu_mask & (1u << 3)) { tu_pass<N, 8, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(3, sse, bits); }
+    if constexpr (N >= 16)
+        if (tu_mask & (1u << 4)) { tu_pass<N, 16, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(4, sse, bits); }
+    if constexpr (N >= 32)
+        if (tu_mask & (1u << 5)) { tu_pass<N, 32, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(5, sse, bits); }
+    if (tid == 0 && tu_log2) *tu_log2 = (uint8_t)bestL;
+    uint32_t mvbits = ref ? (uint32_t)(se_len(mvx) + se_len(mvy)) : 0u;
+    return 2u + mvbits + bestBits;
+}
+
+}  // namespace xvd

@@ -1,0 +1,566 @@
+// xv_api.cu -- the C ABI of include/xv.h: context, argument checks, the plain
+// (per-frame) and batched (persistent) cube paths, and PSNR finalisation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "me.cuh"
+#include "tqr.cuh"
+#include "xv_internal.h"
+
+using xvh::BandQ;
+using xvh::DevBuf;
+
+struct xv_ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t held = 0;
+    // scratch of the single-cube calls
+    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax;
+    // scratch of the batched path
+    DevBuf b_jobs, b_items, b_rowdone, b_ctl, b_bits, b_bandq, b_minmax;
+    long long wait_budget = 4000000000LL;  // cycles per dependency wait (about 2 s)
+    long long stall_item = -1;             // test hook (xv_debug_stall_item)
+};
+
+namespace xvh {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+xv_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return XV_ECUDA;
+}
+
+}  // namespace xvh
+
+using xvh::cuda_fail;
+using xvh::set_error;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+xv_status ensure(xv_ctx* c, DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (b.bytes >= bytes) return XV_OK;
+    size_t nb = (bytes + 255) / 256 * 256;
+    if (c->budget && c->held - b.bytes + nb > c->budget) {
+        set_error("device scratch of %zu bytes exceeds the context budget (%zu of %zu held)", nb, c->held,
+                  c->budget);
+        return XV_EBUDGET;
+    }
+    if (b.ptr) {
+        cudaDeviceSynchronize();
+        cudaFree(b.ptr);
+        c->held -= b.bytes;
+        b = DevBuf{};
+    }
+    cudaError_t e = cudaMalloc(&b.ptr, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu): %s", nb, cudaGetErrorString(e));
+        return XV_ENOMEM;
+    }
+    b.bytes = nb;
+    c->held += nb;
+    return XV_OK;
+}
+
+void release(xv_ctx* c, DevBuf& b) {
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        c->held -= b.bytes;
+    }
+    b = DevBuf{};
+}
+
+bool valid_params(const xv_params* p) {
+    if (!p) { set_error("params is NULL"); return false; }
+    if (p->bit_depth != 10) { set_error("bit_depth %d: only 10 is supported", p->bit_depth); return false; }
+    if (p->ctu != 8 && p->ctu != 16 && p->ctu != 32 && p->ctu != 64) {
+        set_error("ctu %d: must be 8, 16, 32 or 64", p->ctu);
+        return false;
+    }
+    if (p->search_range < 1 || p->search_range > 64) {
+        set_error("search_range %d: must be in 1..64", p->search_range);
+        return false;
+    }
+    if (p->tu_mask & ~0x3cu) { set_error("tu_mask 0x%x: only bits 2..5 (TU 4..32) may be set", p->tu_mask); return false; }
+    bool any = false;
+    for (int k = 2; k <= 5; ++k)
+        if ((p->tu_mask & (1u << k)) && (1 << k) <= p->ctu) any = true;
+    if (!any) { set_error("tu_mask 0x%x allows no TU size <= ctu %d", p->tu_mask, p->ctu); return false; }
+    if (p->qp < -12 || p->qp > 51) { set_error("qp %d: must be in [-12, 51]", p->qp); return false; }
+    if (xvd::me_smem_bytes(p->ctu, p->search_range) > 227 * 1024) {
+        set_error("ctu %d with search range %d needs more shared memory than a block has", p->ctu, p->search_range);
+        return false;
+    }
+    return true;
+}
+
+bool valid_frame(int G, int Hp, int Wp, int ctu) {
+    if (G < 1 || G > 255) { set_error("G %d: must be in 1..255", G); return false; }
+    if (Hp < ctu || Wp < ctu || Hp % ctu || Wp % ctu) {
+        set_error("plane %dx%d is not a positive multiple of the CTU size %d", Hp, Wp, ctu);
+        return false;
+    }
+    return true;
+}
+
+bool valid_cube(const void* src, xv_dtype dt, int bands, int T, int H, int W) {
+    if (!src) { set_error("src is NULL"); return false; }
+    if (dt != XV_F32 && dt != XV_U16) { set_error("dtype %d: must be XV_F32 or XV_U16", (int)dt); return false; }
+    if (bands < 1 || bands > XV_MAX_BANDS) { set_error("bands %d: must be in 1..%d", bands, XV_MAX_BANDS); return false; }
+    if (T < 1 || H < 1 || W < 1) { set_error("cube %dx%dx%d has an empty dimension", T, H, W); return false; }
+    if (T > 65535) { set_error("T %d: at most 65535 frames", T); return false; }
+    return true;
+}
+
+int plane_dim(int n, int ctu) { return (n + ctu - 1) / ctu * ctu; }
+
+xv_status check_launch(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return XV_OK;
+}
+
+// min/max (unless fixed) and the per-band quantiser constants into `bq`.
+xv_status prepare_bands(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, double* minmax,
+                        int fixed, BandQ* bq, cudaStream_t st) {
+    if (fixed) return check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants");
+    xv_status s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * bands);
+    if (s) return s;
+    return check_launch(xvh::launch_minmax(src, dt, bands, (int64_t)T * H * W, (unsigned*)c->mm_enc.ptr, minmax, bq, st),
+                        "min/max");
+}
+
+// PSNR of one cube into `r` (host), from device band constants `bq`.
+xv_status psnr_into(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W,
+                    const uint16_t* planes, const uint16_t* recon, int Hp, int Wp, const BandQ* bq, double* psnr,
+                    double* mse, uint64_t* sse10, double* mean, cudaStream_t st) {
+    const int nblk = xvh::psnr_blocks_per_band((int64_t)T * H * W);
+    xv_status s = ensure(c, c->psnr_part, sizeof(xvh::PsnrPart) * (size_t)nblk * bands);
+    if (s) return s;
+    if ((s = ensure(c, c->psnr_out, sizeof(xvh::PsnrPart) * bands))) return s;
+    s = check_launch(xvh::launch_psnr(src, dt, bands, T, H, W, planes, recon, Hp, Wp, bq,
+                                      (xvh::PsnrPart*)c->psnr_part.ptr, nblk, (xvh::PsnrPart*)c->psnr_out.ptr, st),
+                     "psnr");
+    if (s) return s;
+    std::vector<xvh::PsnrPart> out(bands);
+    std::vector<BandQ> hq(bands);
+    cudaError_t e = cudaMemcpyAsync(out.data(), c->psnr_out.ptr, sizeof(xvh::PsnrPart) * bands,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), bq, sizeof(BandQ) * bands, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "psnr read-back");
+    double acc = 0.0;
+    bool inf = false;
+    for (int b = 0; b < bands; ++b) {
+        const double cnt = (double)out[b].count;
+        const double m = cnt > 0 ? out[b].sse / cnt : 0.0;
+        const double peak = hq[b].hi > 0.0 ? hq[b].hi : hq[b].hi - hq[b].lo;
+        const double p = m > 0.0 ? 10.0 * std::log10(peak * peak / m) : INFINITY;
+        if (psnr) psnr[b] = p;
+        if (mse) mse[b] = m;
+        if (sse10) sse10[b] = out[b].sse10;
+        if (std::isinf(p)) inf = true; else acc += p;
+    }
+    if (mean) *mean = inf ? INFINITY : acc / bands;
+    return XV_OK;
+}
+
+xv_status fill_result(const xv_job* j, const uint64_t* bits_dev, int G, xv_result* r, cudaStream_t st) {
+    std::vector<uint64_t> hb((size_t)G * j->T);
+    cudaError_t e = cudaMemcpyAsync(hb.data(), bits_dev, sizeof(uint64_t) * hb.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "bits read-back");
+    uint64_t tot = 0;
+    for (uint64_t v : hb) tot += v;
+    r->total_bits = tot;
+    r->bands = j->bands;
+    r->bpppb = (double)tot / ((double)j->H * j->W * j->T * j->bands);
+    return XV_OK;
+}
+
+bool valid_job(const xv_job* j) {
+    if (!j) { set_error("job is NULL"); return false; }
+    if (!valid_cube(j->src, j->dtype, j->bands, j->T, j->H, j->W)) return false;
+    if (!valid_params(&j->p)) return false;
+    if (!j->planes || !j->recon) { set_error("job planes and recon buffers are required"); return false; }
+    if (j->minmax_fixed && !j->minmax) { set_error("minmax_fixed needs a minmax array"); return false; }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xv_last_error(void) { return xvh::g_err.c_str(); }
+
+const char* xv_status_string(xv_status s) {
+    switch (s) {
+        case XV_OK: return "ok";
+        case XV_EINVAL: return "invalid argument";
+        case XV_ENOMEM: return "out of device memory";
+        case XV_EBUDGET: return "over the memory budget";
+        case XV_ETIMEOUT: return "device wait timed out";
+        case XV_EBUSY: return "queue full";
+        case XV_ECUDA: return "CUDA error";
+        case XV_ECANCELLED: return "cancelled";
+        case XV_ENOTFOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+xv_status xv_create(xv_ctx** out, int device, size_t budget) {
+    if (!out) { set_error("ctx out-pointer is NULL"); return XV_EINVAL; }
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) { set_error("device %d: %d device(s) present", device, n); return XV_EINVAL; }
+    xv_ctx* c = new xv_ctx;
+    c->device = device;
+    c->budget = budget;
+    *out = c;
+    return XV_OK;
+}
+
+void xv_destroy(xv_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax,
+                      &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_ctl, &c->b_bits, &c->b_bandq, &c->b_minmax};
+    for (DevBuf* b : bufs) release(c, *b);
+    delete c;
+}
+
+size_t xv_ctx_bytes(const xv_ctx* c) { return c ? c->held : 0; }
+
+xv_status xv_params_init(xv_params* p, int ctu, int R, unsigned tu_mask, int qp) {
+    if (!p) { set_error("params is NULL"); return XV_EINVAL; }
+    xv_params q;
+    q.bit_depth = 10;
+    q.ctu = ctu;
+    q.search_range = R;
+    q.tu_mask = tu_mask;
+    q.qp = qp;
+    const double lambda = 0.57 * std::pow(2.0, (qp - 12) / 3.0);
+    q.lambda_fp8 = std::llround(256.0 * lambda);
+    q.lambda_mv_fp16 = std::llround(65536.0 * std::sqrt(lambda));
+    if (!valid_params(&q)) return XV_EINVAL;
+    *p = q;
+    return XV_OK;
+}
+
+xv_status xv_plane_geometry(int bands, int H, int W, int ctu, int* G, int* Hp, int* Wp) {
+    if (bands < 1 || H < 1 || W < 1 || (ctu != 8 && ctu != 16 && ctu != 32 && ctu != 64)) {
+        set_error("bad geometry bands=%d H=%d W=%d ctu=%d", bands, H, W, ctu);
+        return XV_EINVAL;
+    }
+    if (G) *G = (bands + 2) / 3;
+    if (Hp) *Hp = plane_dim(H, ctu);
+    if (Wp) *Wp = plane_dim(W, ctu);
+    return XV_OK;
+}
+
+xv_status xv_minmax(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, double* minmax,
+                    void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (!minmax) { set_error("minmax is NULL"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    xv_status s = ensure(c, c->bandq, sizeof(BandQ) * bands);
+    if (s) return s;
+    return prepare_bands(c, src, dt, bands, T, H, W, minmax, 0, (BandQ*)c->bandq.ptr, (cudaStream_t)stream);
+}
+
+xv_status xv_quantize_pack(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, int ctu,
+                           double* minmax, int fixed, uint16_t* planes, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (ctu != 8 && ctu != 16 && ctu != 32 && ctu != 64) { set_error("ctu %d", ctu); return XV_EINVAL; }
+    if (!minmax || !planes) { set_error("minmax and planes are required"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    xv_status s = ensure(c, c->bandq, sizeof(BandQ) * bands);
+    if (s) return s;
+    BandQ* bq = (BandQ*)c->bandq.ptr;
+    if ((s = prepare_bands(c, src, dt, bands, T, H, W, minmax, fixed, bq, st))) return s;
+    return check_launch(xvh::launch_quantize_pack(src, dt, bands, T, H, W, plane_dim(H, ctu), plane_dim(W, ctu), bq,
+                                                  planes, st),
+                        "quantize_pack");
+}
+
+xv_status xv_motion_search(xv_ctx* c, const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp,
+                           int Wp, const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
+                           uint32_t* cost_int, int64_t pu_gstride, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    if (!cur || !ref || !mv) { set_error("cur, ref and mv are required"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    return check_launch(xvh::launch_me_frame(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride,
+                                             (cudaStream_t)stream),
+                        "motion_search");
+}
+
+xv_status xv_transform_quant_recon(xv_ctx* c, const uint16_t* cur, const uint16_t* ref, const int16_t* mv, int G,
+                                   int64_t gstride, int Hp, int Wp, const xv_params* p, int64_t pu_gstride,
+                                   uint16_t* recon, int16_t* levels, uint8_t* tu_log2, uint64_t* bits,
+                                   int64_t bits_gstride, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    if (!cur || !recon || !bits || (ref && !mv)) { set_error("cur, recon, bits (and mv with ref) are required"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    return check_launch(xvh::launch_tqr_frame(cur, ref, mv, G, gstride, Hp, Wp, p, pu_gstride, recon, levels, tu_log2,
+                                              bits, bits_gstride, (cudaStream_t)stream),
+                        "transform_quant_recon");
+}
+
+xv_status xv_psnr(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* planes,
+                  const uint16_t* recon, int Hp, int Wp, const double* minmax, double* psnr, double* mse,
+                  uint64_t* sse10, double* mean, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (!planes || !recon || !minmax) { set_error("planes, recon and minmax are required"); return XV_EINVAL; }
+    if (Hp < H || Wp < W) { set_error("plane %dx%d smaller than the cube %dx%d", Hp, Wp, H, W); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    xv_status s = ensure(c, c->bandq, sizeof(BandQ) * bands);
+    if (s) return s;
+    BandQ* bq = (BandQ*)c->bandq.ptr;
+    if ((s = check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants"))) return s;
+    return psnr_into(c, src, dt, bands, T, H, W, planes, recon, Hp, Wp, bq, psnr, mse, sse10, mean, st);
+}
+
+size_t xv_job_scratch_bytes(const xv_job* j) {
+    if (!j) return 0;
+    const int G = (j->bands + 2) / 3, ctu = j->p.ctu > 0 ? j->p.ctu : 8;
+    const int64_t npu = (int64_t)(plane_dim(j->H, ctu) / ctu) * (plane_dim(j->W, ctu) / ctu);
+    return (size_t)G * j->T * (npu * 4 + npu * 4 + 8) + 4096;
+}
+
+xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_job(j)) return XV_EINVAL;
+    if (!r) { set_error("result is NULL"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const xv_params& p = j->p;
+    const int G = (j->bands + 2) / 3, Hp = plane_dim(j->H, p.ctu), Wp = plane_dim(j->W, p.ctu), T = j->T;
+    const int64_t npu = (int64_t)(Hp / p.ctu) * (Wp / p.ctu);
+    const int64_t fsz = 3LL * Hp * Wp;
+    std::memset(r, 0, sizeof *r);
+    xv_status s;
+    double* minmax = j->minmax;
+    if (!minmax) {
+        if ((s = ensure(c, c->tmp_minmax, sizeof(double) * 2 * j->bands))) return s;
+        minmax = (double*)c->tmp_minmax.ptr;
+    }
+    if ((s = ensure(c, c->bandq, sizeof(BandQ) * j->bands))) return s;
+    BandQ* bq = (BandQ*)c->bandq.ptr;
+    if ((s = prepare_bands(c, j->src, j->dtype, j->bands, T, j->H, j->W, minmax, j->minmax_fixed, bq, st))) return s;
+    if ((s = check_launch(xvh::launch_quantize_pack(j->src, j->dtype, j->bands, T, j->H, j->W, Hp, Wp, bq, j->planes, st),
+                          "quantize_pack")))
+        return s;
+    int16_t* mv = j->mv;
+    if (!mv) {
+        if ((s = ensure(c, c->tmp_mv, sizeof(int16_t) * 2 * npu * G * T))) return s;
+        mv = (int16_t*)c->tmp_mv.ptr;
+    }
+    uint64_t* bits = j->bits;
+    if (!bits) {
+        if ((s = ensure(c, c->tmp_bits, sizeof(uint64_t) * G * T))) return s;
+        bits = (uint64_t*)c->tmp_bits.ptr;
+    }
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(uint64_t) * G * T, st);
+    for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {  // frame 0 has no motion
+        e = cudaMemsetAsync(mv + (int64_t)gi * T * npu * 2, 0, sizeof(int16_t) * 2 * npu, st);
+        if (e == cudaSuccess && j->cost) e = cudaMemsetAsync(j->cost + (int64_t)gi * T * npu, 0, sizeof(uint32_t) * npu, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    for (int t = 0; t < T; ++t) {
+        const uint16_t* cur = j->planes + t * fsz;
+        const uint16_t* ref = t > 0 ? j->recon + (t - 1) * fsz : nullptr;
+        if (ref) {
+            if ((s = check_launch(xvh::launch_me_frame(cur, ref, G, T * fsz, Hp, Wp, &p, mv + t * npu * 2,
+                                                       j->cost ? j->cost + t * npu : nullptr, nullptr, nullptr, T * npu, st),
+                                  "motion_search")))
+                return s;
+        }
+        if ((s = check_launch(xvh::launch_tqr_frame(cur, ref, mv + t * npu * 2, G, T * fsz, Hp, Wp, &p, T * npu,
+                                                    j->recon + t * fsz, j->levels ? j->levels + t * fsz : nullptr,
+                                                    j->tu_log2 ? j->tu_log2 + t * npu : nullptr, bits + t, T, st),
+                              "transform_quant_recon")))
+            return s;
+    }
+    r->status = XV_OK;
+    if ((s = psnr_into(c, j->src, j->dtype, j->bands, T, j->H, j->W, j->planes, j->recon, Hp, Wp, bq, r->psnr_band,
+                       r->mse_band, r->sse10_band, &r->psnr_mean, st)))
+        return s;
+    return fill_result(j, bits, G, r, st);
+}
+
+xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* results, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (njobs < 1 || njobs > 255 || !jobs || !results) { set_error("njobs %d: must be 1..255 with jobs and results", njobs); return XV_EINVAL; }
+    for (int i = 0; i < njobs; ++i)
+        if (!valid_job(&jobs[i])) return XV_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    xv_status s;
+    // per-job device descriptors and internal buffers
+    std::vector<xvh::JobDev> jd(njobs);
+    std::vector<int64_t> bits_off(njobs), row_off(njobs);
+    int64_t nbits = 0, nrows = 0;
+    for (int i = 0; i < njobs; ++i) {
+        const xv_job& j = jobs[i];
+        const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
+        bits_off[i] = nbits;
+        nbits += (int64_t)G * j.T;
+        row_off[i] = nrows;
+        nrows += (int64_t)G * j.T * (Hp / j.p.ctu);
+    }
+    if ((s = ensure(c, c->b_jobs, sizeof(xvh::JobDev) * njobs))) return s;
+    if ((s = ensure(c, c->b_bits, sizeof(uint64_t) * nbits))) return s;
+    if ((s = ensure(c, c->b_rowdone, sizeof(unsigned) * nrows))) return s;
+    if ((s = ensure(c, c->b_bandq, sizeof(BandQ) * XV_MAX_BANDS * njobs))) return s;
+    if ((s = ensure(c, c->b_minmax, sizeof(double) * 2 * XV_MAX_BANDS * njobs))) return s;
+    // one control block per CTU class (8, 16, 32, 64)
+    if ((s = ensure(c, c->b_ctl, sizeof(xvh::BatchCtl) * 4))) return s;
+    uint64_t* bits_all = (uint64_t*)c->b_bits.ptr;
+    unsigned* rows_all = (unsigned*)c->b_rowdone.ptr;
+    BandQ* bq_all = (BandQ*)c->b_bandq.ptr;
+    double* mm_all = (double*)c->b_minmax.ptr;
+    cudaError_t e = cudaMemsetAsync(rows_all, 0, sizeof(unsigned) * nrows, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bits_all, 0, sizeof(uint64_t) * nbits, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    for (int i = 0; i < njobs; ++i) {
+        const xv_job& j = jobs[i];
+        const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
+        double* mm = j.minmax ? j.minmax : mm_all + 2 * XV_MAX_BANDS * i;
+        BandQ* bq = bq_all + XV_MAX_BANDS * i;
+        if ((s = prepare_bands(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, mm, j.minmax_fixed, bq, st))) return s;
+        if ((s = check_launch(xvh::launch_quantize_pack(j.src, j.dtype, j.bands, j.T, j.H, j.W, Hp, Wp, bq, j.planes, st),
+                              "quantize_pack")))
+            return s;
+        xvh::JobDev& d = jd[i];
+        d.planes = j.planes;
+        d.recon = j.recon;
+        d.mv = j.mv;
+        d.cost = j.cost;
+        d.levels = j.levels;
+        d.tu = j.tu_log2;
+        d.bits = j.bits ? j.bits : bits_all + bits_off[i];
+        d.rowdone = rows_all + row_off[i];
+        d.lf8 = j.p.lambda_fp8;
+        d.lmv = j.p.lambda_mv_fp16;
+        d.G = G; d.T = j.T; d.Hp = Hp; d.Wp = Wp; d.ctu = j.p.ctu; d.R = j.p.search_range; d.qp = j.p.qp;
+        d.tu_mask = j.p.tu_mask;
+        d.nx = Wp / j.p.ctu;
+        d.ny = Hp / j.p.ctu;
+        if (j.bits && (e = cudaMemsetAsync(j.bits, 0, sizeof(uint64_t) * G * j.T, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+    }
+    e = cudaMemcpyAsync(c->b_jobs.ptr, jd.data(), sizeof(xvh::JobDev) * njobs, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "job descriptors");
+    // frame-major work lists, one per CTU class
+    const int ctus[4] = {8, 16, 32, 64};
+    std::vector<uint64_t> items[4];
+    size_t smem[4] = {0, 0, 0, 0};
+    int maxT = 0;
+    for (int i = 0; i < njobs; ++i) maxT = jobs[i].T > maxT ? jobs[i].T : maxT;
+    for (int t = 0; t < maxT; ++t)
+        for (int i = 0; i < njobs; ++i) {
+            if (t >= jobs[i].T) continue;
+            const xvh::JobDev& d = jd[i];
+            const int k = d.ctu == 8 ? 0 : d.ctu == 16 ? 1 : d.ctu == 32 ? 2 : 3;
+            for (int gi = 0; gi < d.G; ++gi)
+                for (int pu = 0; pu < d.nx * d.ny; ++pu) items[k].push_back(xvh::make_item(i, gi, t, pu));
+            size_t need = xvh::persist_smem_bytes(d.ctu, d.R, jobs[i].T > 1);
+            smem[k] = need > smem[k] ? need : smem[k];
+        }
+    size_t total_items = 0;
+    for (auto& v : items) total_items += v.size();
+    if ((s = ensure(c, c->b_items, sizeof(uint64_t) * total_items))) return s;
+    uint64_t* items_dev = (uint64_t*)c->b_items.ptr;
+    xvh::BatchCtl* ctl = (xvh::BatchCtl*)c->b_ctl.ptr;
+    size_t off = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (items[k].empty()) continue;
+        e = cudaMemcpyAsync(items_dev + off, items[k].data(), sizeof(uint64_t) * items[k].size(), cudaMemcpyHostToDevice, st);
+        xvh::BatchCtl h{0u, 0, c->stall_item >= 0 ? (unsigned)c->stall_item : 0xffffffffu, 0u, c->wait_budget};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctl + k, &h, sizeof h, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "work list");
+        const int grid = xvh::persist_grid(ctus[k], smem[k]);
+        if ((s = check_launch(xvh::launch_persist(ctus[k], (const xvh::JobDev*)c->b_jobs.ptr, items_dev + off,
+                                                  (unsigned)items[k].size(), ctl + k, smem[k], grid, st),
+                              "persistent encode")))
+            return s;
+        off += items[k].size();
+    }
+    // timeouts are reported before any result is read
+    xvh::BatchCtl hc[4];
+    e = cudaMemcpyAsync(hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent encode");
+    for (int k = 0; k < 4; ++k)
+        if (!items[k].empty() && hc[k].err) {
+            set_error("a dependency wait of the persistent encode (CTU %d) ran out of time", ctus[k]);
+            for (int i = 0; i < njobs; ++i) results[i].status = XV_ETIMEOUT;
+            return (xv_status)hc[k].err;
+        }
+    for (int i = 0; i < njobs; ++i) {
+        const xv_job& j = jobs[i];
+        xv_result* r = &results[i];
+        std::memset(r, 0, sizeof *r);
+        const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
+        if ((s = psnr_into(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, j.planes, j.recon, Hp, Wp,
+                           bq_all + XV_MAX_BANDS * i, r->psnr_band, r->mse_band, r->sse10_band, &r->psnr_mean, st)))
+            return s;
+        if ((s = fill_result(&j, jd[i].bits, G, r, st))) return s;
+        r->status = XV_OK;
+    }
+    return XV_OK;
+}
+
+// Test hooks for the bounded device waits of the persistent path.
+xv_status xv_debug_set_wait_budget(xv_ctx* c, long long cycles) {
+    if (!c || cycles < 1) { set_error("bad wait budget"); return XV_EINVAL; }
+    c->wait_budget = cycles;
+    return XV_OK;
+}
+
+xv_status xv_debug_stall_item(xv_ctx* c, long long item) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    c->stall_item = item;
+    return XV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// xv_dev.cuh -- device-side building blocks of the encoder analysis.
+//
+// Everything here is integer arithmetic that must match the definitions in
+// include/xv.h bit for bit:
+//   * the HEVC core-transform matrix (H.265 subclause 8.6.4.2: a 32x32 table
+//     of scaled cosines; an N-point transform uses rows k * 32/N), applied by
+//     partial butterflies -- an exact re-association of the matrix product;
+//   * the HEVC 8-tap luma interpolation filter (H.265 8.5.3.3.3.1);
+//   * signed Exp-Golomb code lengths for the motion and level rate proxy.
+#pragma once
+#include <cstdint>
+
+namespace xvd {
+
+constexpr int kBitDepth = 10;
+constexpr int kPixMax = (1 << kBitDepth) - 1;
+constexpr int kFlat = 1 << (kBitDepth - 1);  // first-frame prediction value
+
+// ---------------------------------------------------------------- transform
+// Scaled cosine 64*sqrt(2)*cos(m*pi/64) as HEVC rounds it, for m = 0..32
+// (m = 0 only ever appears in the DC row, whose value is 64).
+__host__ __device__ constexpr int hevc_cos(int m) {
+    constexpr int c[33] = {64, 90, 90, 90, 89, 88, 87, 85, 83, 82, 80, 78, 75, 73, 70, 67, 64,
+                           61, 57, 54, 50, 46, 43, 38, 36, 31, 25, 22, 18, 13, 9,  4,  0};
+    return c[m];
+}
+
+// Entry (k, n) of the 32-point matrix: DC row 64; otherwise the cosine of
+// angle k(2n+1) pi/64, folded into [0, pi/2] with its sign.
+__host__ __device__ constexpr int t32(int k, int n) {
+    if (k == 0) return 64;
+    int a = (k * (2 * n + 1)) & 127;  // angle in units of pi/64, modulo 2 pi
+    if (a > 64) a = 128 - a;          // cos(2pi - t) = cos(t)
+    return a <= 32 ? hevc_cos(a) : -hevc_cos(64 - a);  // cos(pi - t) = -cos(t)
+}
+
+// Entry (k, n) of the N-point matrix: row k * 32/N of the 32-point matrix.
+template <int N>
+__host__ __device__ constexpr int tN(int k, int n) { return t32(k * (32 / N), n); }
+
+// y[k] = sum_n T_N[k][n] x[n]  (no rounding), partial butterfly.
+template <int N>
+__device__ __forceinline__ void fwd1d(const int (&x)[N], int (&y)[N]) {
+    if constexpr (N == 2) {
+        y[0] = 64 * (x[0] + x[1]);
+        y[1] = 64 * (x[0] - x[1]);
+    } else {
+        int e[N / 2], o[N / 2], ye[N / 2];
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            e[k] = x[k] + x[N - 1 - k];
+            o[k] = x[k] - x[N - 1 - k];
+        }
+        fwd1d<N / 2>(e, ye);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) y[2 * i] = ye[i];
+#pragma unroll
+        for (int k = 1; k < N; k += 2) {
+            int acc = 0;
+#pragma unroll
+            for (int n = 0; n < N / 2; ++n) acc += tN<N>(k, n) * o[n];
+            y[k] = acc;
+        }
+    }
+}
+
+// x[n] = sum_k T_N[k][n] c[k]  (no rounding), partial butterfly.
+template <int N>
+__device__ __forceinline__ void inv1d(const int (&c)[N], int (&x)[N]) {
+    if constexpr (N == 2) {
+        x[0] = 64 * (c[0] + c[1]);
+        x[1] = 64 * (c[0] - c[1]);
+    } else {
+        int ce[N / 2], ee[N / 2];
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) ce[i] = c[2 * i];
+        inv1d<N / 2>(ce, ee);
+#pragma unroll
+        for (int n = 0; n < N / 2; ++n) {
+            int o = 0;
+#pragma unroll
+            for (int i = 0; i < N / 2; ++i) o += tN<N>(2 * i + 1, n) * c[2 * i + 1];
+            x[n] = ee[n] + o;
+            x[N - 1 - n] = ee[n] - o;
+        }
+    }
+}
+
+__device__ __forceinline__ int rshift_round(int v, int s) { return (v + (1 << (s - 1))) >> s; }
+__device__ __forceinline__ int clip16(int v) { return v < -32768 ? -32768 : (v > 32767 ? 32767 : v); }
+__device__ __forceinline__ int clip_pix(int v) { return v < 0 ? 0 : (v > kPixMax ? kPixMax : v); }
+
+// ---------------------------------------------------------------- quantiser
+__device__ __forceinline__ int quant_scale(int r) {
+    return r == 0 ? 26214 : r == 1 ? 23302 : r == 2 ? 20560 : r == 3 ? 18396 : r == 4 ? 16384 : 14564;
+}
+__device__ __forceinline__ int level_scale(int r) {
+    return r == 0 ? 40 : r == 1 ? 45 : r == 2 ? 51 : r == 3 ? 57 : r == 4 ? 64 : 72;
+}
+
+struct QuantParams {
+    int qbits;        // 14 + qP/6 + 15 - B - log2N
+    int64_t offset;   // 85 << (qbits - 9)
+    int64_t qscale;   // forward scale for qP % 6
+    int64_t dqscale;  // 16 * levelScale[qP % 6] << (qP / 6)
+    int bd;           // B + log2N - 5
+};
+
+__device__ __forceinline__ QuantParams quant_params(int qp, int log2n) {
+    QuantParams q;
+    int qP = qp + 6 * (kBitDepth - 8);
+    q.qbits = 14 + qP / 6 + 15 - kBitDepth - log2n;
+    q.offset = (int64_t)85 << (q.qbits - 9);
+    q.qscale = quant_scale(qP % 6);
+    q.dqscale = ((int64_t)16 * level_scale(qP % 6)) << (qP / 6);
+    q.bd = kBitDepth + log2n - 5;
+    return q;
+}
+
+__device__ __forceinline__ int quantize(int c, const QuantParams& q) {
+    int64_t a = c < 0 ? -(int64_t)c : (int64_t)c;
+    int64_t m = (a * q.qscale + q.offset) >> q.qbits;
+    if (m > 32767) m = c < 0 ? 32768 : 32767;  // int16 clip of +/- magnitude
+    return c < 0 ? -(int)m : (int)m;
+}
+
+__device__ __forceinline__ int dequantize(int level, const QuantParams& q) {
+    int64_t v = ((int64_t)level * q.dqscale + ((int64_t)1 << (q.bd - 1))) >> q.bd;
+    return v < -32768 ? -32768 : (v > 32767 ? 32767 : (int)v);
+}
+
+// ------------------------------------------------------------------ rate
+// Length of the Exp-Golomb code of the signed value v (se(v) -> ue(k)).
+__device__ __forceinline__ int se_len(int v) {
+    unsigned k = v > 0 ? 2u * (unsigned)v - 1u : 2u * (unsigned)(-v);
+    return 2 * (31 - __clz((int)(k + 1u))) + 1;
+}
+__device__ __forceinline__ uint32_t mv_cost(int mvx, int mvy, int64_t lambda_mv_fp16) {
+    return (uint32_t)((lambda_mv_fp16 * (se_len(mvx) + se_len(mvy)) + 32768) >> 16);
+}
+
+// ----------------------------------------------------------- interpolation
+// HEVC luma filter tap i (0..7, at offset i - 3) for fractional phase f.
+__device__ __forceinline__ int luma_tap(int f, int i) {
+    // phase 1: -1 4 -10 58 17 -5 1 0; phase 2: -1 4 -11 40 40 -11 4 -1;
+    // phase 3 is phase 1 mirrored.
+    if (f == 3) { f = 1; i = 7 - i; }
+    if (f == 1) {
+        return i == 0 ? -1 : i == 1 ? 4 : i == 2 ? -10 : i == 3 ? 58 : i == 4 ? 17 : i == 5 ? -5 : i == 6 ? 1 : 0;
+    }
+    return (i == 0 || i == 7) ? -1 : (i == 1 || i == 6) ? 4 : (i == 2 || i == 5) ? -11 : 40;
+}
+
+// Intermediate shifts for B = 10: shift1 = B - 8, shift2 = 6, full-sample
+// scale 2^(14 - B); weighted-prediction rounding back to B bits.
+constexpr int kShift1 = kBitDepth - 8;
+constexpr int kShift2 = 6;
+constexpr int kShift3 = 14 - kBitDepth;
+__device__ __forceinline__ int wp_round(int v) {
+    return clip_pix((v + (1 << (kShift3 - 1))) >> kShift3);
+}
+
+// Loads of the reference frame.  Within one launch of the per-frame kernels
+// the reference is read-only (read-only cache path); in the persistent kernel
+// other blocks write it during the launch, so it is read through L2 only.
+template <bool kCoherent>
+__device__ __forceinline__ int ld_ref(const uint16_t* p) {
+    if constexpr (kCoherent) return (int)__ldcg(p);
+    else return (int)__ldg(p);
+}
+
+}  // namespace xvd

@@ -1,0 +1,95 @@
+// xv_internal.h -- host-side internals of libxv shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/xv.h"
+
+namespace xvh {
+
+// Per-band quantiser constants computed on the device from min/max.
+struct BandQ {
+    double lo, hi, s, delta;  // s = 1023/(hi-lo) (0 if hi <= lo); delta = (hi-lo)/1023
+    float lo_f, s_f;          // float copies for the exact fast path
+    int fast_ok;              // lo is a float value and s is in float range
+    int pad;
+};
+
+// Device scratch regions owned by a context (grown on demand).
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+void set_error(const char* fmt, ...);
+xv_status cuda_fail(cudaError_t e, const char* what);
+
+// ---- launchers (stream = cudaStream_t)
+cudaError_t launch_minmax(const void* src, xv_dtype dt, int bands, int64_t n_per_band, unsigned* enc,
+                          double* minmax, BandQ* bq, cudaStream_t st);
+cudaError_t launch_bandq(const double* minmax, int bands, BandQ* bq, cudaStream_t st);
+cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T, int H, int W, int Hp, int Wp,
+                                 const BandQ* bq, uint16_t* planes, cudaStream_t st);
+
+cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
+                            const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
+                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st);
+cudaError_t launch_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, int G, int64_t gstride,
+                             int Hp, int Wp, const xv_params* p, int64_t pu_gstride, uint16_t* recon,
+                             int16_t* levels, uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride,
+                             cudaStream_t st);
+
+// PSNR partial sums: per band, `nblk` partials of (sse double, sse10, count).
+struct PsnrPart {
+    double sse;
+    unsigned long long sse10;
+    unsigned long long count;
+    double pad;
+};
+int psnr_blocks_per_band(int64_t rows_per_band);
+cudaError_t launch_psnr(const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* planes,
+                        const uint16_t* recon, int Hp, int Wp, const BandQ* bq, PsnrPart* part, int nblk,
+                        PsnrPart* out, cudaStream_t st);
+
+}  // namespace xvh
+
+namespace xvh {
+
+// One cube of a batch, as the persistent kernel sees it.
+struct JobDev {
+    const uint16_t* planes;  // [G][T][3][Hp][Wp]
+    uint16_t* recon;
+    int16_t* mv;             // [G][T][nPU][2] or null
+    uint32_t* cost;          // [G][T][nPU] or null
+    int16_t* levels;         // plane layout or null
+    uint8_t* tu;             // [G][T][nPU] or null
+    uint64_t* bits;          // [G][T]
+    unsigned* rowdone;       // [G][T][ny]: finished PUs per CTU row
+    int64_t lf8, lmv;
+    int G, T, Hp, Wp, ctu, R, qp;
+    unsigned tu_mask;
+    int nx, ny;
+};
+
+// Work-queue control block (device).
+struct BatchCtl {
+    unsigned next;         // next ticket
+    int err;               // 0, or an xv_status (XV_ETIMEOUT) set by a block
+    unsigned stall_item;   // test hook: this item's dependency can never be met
+    unsigned pad;
+    long long budget;      // spin budget per wait, in SM clock cycles
+};
+
+// Item key: job (8 bits) | group (8) | frame (16) | PU (32), frame-major order.
+inline uint64_t make_item(int job, int g, int t, int pu) {
+    return ((uint64_t)job << 56) | ((uint64_t)g << 48) | ((uint64_t)t << 32) | (uint32_t)pu;
+}
+
+size_t persist_smem_bytes(int ctu, int R, bool has_me);
+cudaError_t launch_persist(int ctu, const JobDev* jobs, const uint64_t* items, unsigned nitems, BatchCtl* ctl,
+                           size_t smem, int grid, cudaStream_t st);
+int persist_grid(int ctu, size_t smem);
+
+}  // namespace xvh

@@ -1,0 +1,247 @@
+"""Thin Python binding of libxv (include/xv.h): same names, argument
+marshalling only.  Every step of the path runs in the CUDA library; this
+module converts torch tensors to device pointers and checks status codes.
+
+Raises ``XvError`` on any non-OK status and ``RuntimeError`` when the library
+has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB
+
+XV_OK, XV_EINVAL, XV_ENOMEM, XV_EBUDGET, XV_ETIMEOUT, XV_EBUSY, XV_ECUDA, XV_ECANCELLED, XV_ENOTFOUND = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+XV_F32, XV_U16 = 0, 1
+XV_MAX_BANDS = 16
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+
+
+class xv_params(ctypes.Structure):
+    _fields_ = [("bit_depth", _i), ("ctu", _i), ("search_range", _i), ("tu_mask", ctypes.c_uint),
+                ("qp", _i), ("lambda_fp8", _i64), ("lambda_mv_fp16", _i64)]
+
+
+class xv_job(ctypes.Structure):
+    _fields_ = [("src", _vp), ("dtype", _i), ("bands", _i), ("T", _i), ("H", _i), ("W", _i),
+                ("p", xv_params), ("minmax", _vp), ("minmax_fixed", _i), ("planes", _vp), ("recon", _vp),
+                ("mv", _vp), ("cost", _vp), ("levels", _vp), ("tu_log2", _vp), ("bits", _vp)]
+
+
+class xv_result(ctypes.Structure):
+    _fields_ = [("status", _i), ("bands", _i), ("psnr_mean", ctypes.c_double), ("bpppb", ctypes.c_double),
+                ("total_bits", ctypes.c_uint64), ("psnr_band", ctypes.c_double * XV_MAX_BANDS),
+                ("mse_band", ctypes.c_double * XV_MAX_BANDS), ("sse10_band", ctypes.c_uint64 * XV_MAX_BANDS),
+                ("latency_s", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.bands
+        return dict(status=self.status, psnr_mean=self.psnr_mean, bpppb=self.bpppb, total_bits=self.total_bits,
+                    psnr_band=list(self.psnr_band[:n]), mse_band=list(self.mse_band[:n]),
+                    sse10_band=list(self.sse10_band[:n]), latency_s=self.latency_s)
+
+
+class XvError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_SIGS = {
+    "xv_create": [ctypes.POINTER(_vp), _i, ctypes.c_size_t],
+    "xv_destroy": [_vp],
+    "xv_ctx_bytes": [_vp],
+    "xv_params_init": [ctypes.POINTER(xv_params), _i, _i, ctypes.c_uint, _i],
+    "xv_plane_geometry": [_i, _i, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)],
+    "xv_minmax": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp],
+    "xv_quantize_pack": [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _i, _vp, _vp],
+    "xv_motion_search": [_vp, _vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _vp, _vp, _vp, _vp, _i64, _vp],
+    "xv_transform_quant_recon": [_vp, _vp, _vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp,
+                                 _vp, _vp, _i64, _vp],
+    "xv_psnr": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
+    "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
+    "xv_encode_batch": [_vp, ctypes.POINTER(xv_job), _i, ctypes.POINTER(xv_result), _vp],
+    "xv_debug_set_wait_budget": [_vp, ctypes.c_longlong],
+    "xv_debug_stall_item": [_vp, ctypes.c_longlong],
+}
+
+
+def lib():
+    """Load libxv.so (it must have been built: ``paper_2506_19656_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libxv.so not built ({LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _i
+        L.xv_destroy.restype = None
+        L.xv_ctx_bytes.restype = ctypes.c_size_t
+        L.xv_job_scratch_bytes.restype = ctypes.c_size_t
+        L.xv_last_error.restype = ctypes.c_char_p
+        L.xv_status_string.restype = ctypes.c_char_p
+        L.xv_status_string.argtypes = [_i]
+        _lib = L
+    return _lib
+
+
+def check(status, where):
+    if status != XV_OK:
+        raise XvError(status, where, lib().xv_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return XV_F32
+    if t.dtype == torch.uint16:
+        return XV_U16
+    raise TypeError("cube must be float32 or uint16")
+
+
+class Context:
+    """An xv_ctx: device scratch, budgets and the batched path's state."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        h = _vp()
+        check(lib().xv_create(ctypes.byref(h), device, mem_budget_bytes), "xv_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().xv_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def bytes(self) -> int:
+        return int(lib().xv_ctx_bytes(self.handle))
+
+
+def xv_params_init(ctu: int, search_range: int, tu_mask: int, qp: int) -> xv_params:
+    p = xv_params()
+    check(lib().xv_params_init(ctypes.byref(p), ctu, search_range, tu_mask, qp), "xv_params_init")
+    return p
+
+
+def xv_plane_geometry(bands: int, H: int, W: int, ctu: int):
+    G, Hp, Wp = _i(), _i(), _i()
+    check(lib().xv_plane_geometry(bands, H, W, ctu, ctypes.byref(G), ctypes.byref(Hp), ctypes.byref(Wp)),
+          "xv_plane_geometry")
+    return G.value, Hp.value, Wp.value
+
+
+def xv_minmax(ctx: Context, src, minmax, stream=None):
+    bands, T, H, W = src.shape
+    check(lib().xv_minmax(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, _ptr(minmax), _stream(stream)),
+          "xv_minmax")
+
+
+def xv_quantize_pack(ctx: Context, src, ctu: int, minmax, planes, minmax_fixed: bool = False, stream=None):
+    bands, T, H, W = src.shape
+    check(lib().xv_quantize_pack(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, ctu, _ptr(minmax),
+                                 int(minmax_fixed), _ptr(planes), _stream(stream)), "xv_quantize_pack")
+
+
+def xv_motion_search(ctx: Context, cur, ref, G: int, plane_gstride: int, Hp: int, Wp: int, p: xv_params, mv,
+                     cost=None, mv_int=None, cost_int=None, pu_gstride: int = 0, stream=None):
+    check(lib().xv_motion_search(ctx.handle, _ptr(cur), _ptr(ref), G, plane_gstride, Hp, Wp, ctypes.byref(p),
+                                 _ptr(mv), _ptr(cost), _ptr(mv_int), _ptr(cost_int), pu_gstride, _stream(stream)),
+          "xv_motion_search")
+
+
+def xv_transform_quant_recon(ctx: Context, cur, ref, mv, G: int, plane_gstride: int, Hp: int, Wp: int,
+                             p: xv_params, pu_gstride: int, recon, levels, tu_log2, bits, bits_gstride: int,
+                             stream=None):
+    check(lib().xv_transform_quant_recon(ctx.handle, _ptr(cur), _ptr(ref), _ptr(mv), G, plane_gstride, Hp, Wp,
+                                         ctypes.byref(p), pu_gstride, _ptr(recon), _ptr(levels), _ptr(tu_log2),
+                                         _ptr(bits), bits_gstride, _stream(stream)), "xv_transform_quant_recon")
+
+
+def xv_psnr(ctx: Context, src, planes, recon, minmax, stream=None):
+    """Returns dict(psnr_band, mse_band, sse10_band, psnr_mean) (host values)."""
+    bands, T, H, W = src.shape
+    Hp, Wp = planes.shape[-2:]
+    ps = (ctypes.c_double * bands)()
+    mse = (ctypes.c_double * bands)()
+    s10 = (ctypes.c_uint64 * bands)()
+    mean = ctypes.c_double()
+    check(lib().xv_psnr(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, _ptr(planes), _ptr(recon), Hp, Wp,
+                        _ptr(minmax), ps, mse, s10, ctypes.byref(mean), _stream(stream)), "xv_psnr")
+    return dict(psnr_band=list(ps), mse_band=list(mse), sse10_band=list(s10), psnr_mean=mean.value)
+
+
+def make_job(src, p: xv_params, planes, recon, minmax=None, minmax_fixed=False, mv=None, cost=None, levels=None,
+             tu_log2=None, bits=None) -> xv_job:
+    bands, T, H, W = src.shape
+    return xv_job(src=_ptr(src), dtype=_dtype_code(src), bands=bands, T=T, H=H, W=W, p=p, minmax=_ptr(minmax),
+                  minmax_fixed=int(minmax_fixed), planes=_ptr(planes), recon=_ptr(recon), mv=_ptr(mv),
+                  cost=_ptr(cost), levels=_ptr(levels), tu_log2=_ptr(tu_log2), bits=_ptr(bits))
+
+
+def xv_encode_cube(ctx: Context, job: xv_job, stream=None) -> dict:
+    r = xv_result()
+    check(lib().xv_encode_cube(ctx.handle, ctypes.byref(job), ctypes.byref(r), _stream(stream)), "xv_encode_cube")
+    return r.as_dict()
+
+
+def xv_encode_batch(ctx: Context, jobs, stream=None) -> list:
+    n = len(jobs)
+    arr = (xv_job * n)(*jobs)
+    res = (xv_result * n)()
+    check(lib().xv_encode_batch(ctx.handle, arr, n, res, _stream(stream)), "xv_encode_batch")
+    return [r.as_dict() for r in res]
+
+
+def xv_debug_set_wait_budget(ctx: Context, cycles: int):
+    check(lib().xv_debug_set_wait_budget(ctx.handle, cycles), "xv_debug_set_wait_budget")
+
+
+def xv_debug_stall_item(ctx: Context, item: int):
+    check(lib().xv_debug_stall_item(ctx.handle, item), "xv_debug_stall_item")
+
+
+# ------------------------------------------------------------ tensor helpers
+def alloc_cube_buffers(bands: int, T: int, H: int, W: int, p: xv_params, device="cuda", levels=True):
+    """Device buffers of one cube (planes, recon, mv, cost, levels, tu_log2, bits, minmax)."""
+    import torch
+    G, Hp, Wp = xv_plane_geometry(bands, H, W, p.ctu)
+    npu = (Hp // p.ctu) * (Wp // p.ctu)
+    kw = dict(device=device)
+    return dict(
+        planes=torch.empty((G, T, 3, Hp, Wp), dtype=torch.uint16, **kw),
+        recon=torch.empty((G, T, 3, Hp, Wp), dtype=torch.uint16, **kw),
+        mv=torch.empty((G, T, npu, 2), dtype=torch.int16, **kw),
+        cost=torch.empty((G, T, npu), dtype=torch.int32, **kw),
+        levels=torch.empty((G, T, 3, Hp, Wp), dtype=torch.int16, **kw) if levels else None,
+        tu_log2=torch.empty((G, T, npu), dtype=torch.uint8, **kw),
+        bits=torch.empty((G, T), dtype=torch.int64, **kw),
+        minmax=torch.empty((bands, 2), dtype=torch.float64, **kw),
+    )

@@ -1,0 +1,130 @@
+"""Whole-cube GPU parity: the plain per-frame path (xv_encode_cube) and the
+batched persistent path (xv_encode_batch) against the oracle, on the seeded
+synthetic workloads, their causal prefixes and ragged shapes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import to_dev, to_np
+from paper_2506_19656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xv():
+    from paper_2506_19656_gb300 import build, xv as _xv
+    build.build()
+    oracle.build()
+    return _xv
+
+
+@pytest.fixture(scope="module")
+def ctx(xv):
+    c = xv.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_job(xv, cube, ctu, R, mask, qp, minmax=None):
+    bands, T, H, W = cube.shape
+    p = xv.xv_params_init(ctu, R, mask, qp)
+    buf = xv.alloc_cube_buffers(bands, T, H, W, p)
+    buf["src"] = to_dev(cube)
+    if minmax is not None:
+        buf["minmax"] = to_dev(np.asarray(minmax, np.float64))
+    job = xv.make_job(buf["src"], p, buf["planes"], buf["recon"], minmax=buf["minmax"],
+                      minmax_fixed=minmax is not None, mv=buf["mv"], cost=buf["cost"], levels=buf["levels"],
+                      tu_log2=buf["tu_log2"], bits=buf["bits"])
+    return job, buf
+
+
+def assert_matches(buf, res, want, frames=None):
+    sl = slice(None) if frames is None else slice(0, frames)
+    assert np.array_equal(to_np(buf["planes"])[:, sl], want["planes"][:, sl])
+    assert np.array_equal(to_np(buf["mv"])[:, sl], want["mv"][:, sl])
+    assert np.array_equal(to_np(buf["cost"])[:, sl].astype(np.uint32), want["cost"][:, sl])
+    assert np.array_equal(to_np(buf["recon"])[:, sl], want["recon"][:, sl])
+    assert np.array_equal(to_np(buf["levels"])[:, sl], want["levels"][:, sl])
+    assert np.array_equal(to_np(buf["tu_log2"])[:, sl], want["tu_log2"][:, sl])
+    assert np.array_equal(to_np(buf["bits"])[:, sl].astype(np.uint64), want["bits"][:, sl])
+    if frames is None:
+        assert res["total_bits"] == want["total_bits"]
+        for g, w in zip(res["psnr_band"], want["psnr_band"]):
+            assert (np.isinf(g) and np.isinf(w)) or abs(g - w) <= 1e-9 * abs(w)
+        assert res["sse10_band"] == [int(v) for v in want["sse10_band"]]
+
+
+def test_tiny_config_plain(xv, ctx):
+    c = synth.CONFIGS[0]
+    cube = synth.make_cube(0)
+    want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, c.qps[0])
+    job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, c.qps[0])
+    res = xv.xv_encode_cube(ctx, job)
+    assert_matches(buf, res, want)
+
+
+@pytest.mark.parametrize("qp", [22, 27, 32])
+def test_deepextremecubes_prefix_plain_and_batched(xv, ctx, qp):
+    """The first 6 frames of the 10-band 128x128 cube (CTU 16, R 32, TU 4-16)."""
+    c = synth.CONFIGS[1]
+    cube = synth.make_cube(1, T=6)
+    want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, qp)
+    job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, qp)
+    assert_matches(buf, xv.xv_encode_cube(ctx, job), want)
+    job2, buf2 = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, qp)
+    assert_matches(buf2, xv.xv_encode_batch(ctx, [job2])[0], want)
+
+
+def test_ragged_shapes_and_mixed_batch(xv, ctx):
+    """Uneven cubes of different CTU sizes in one batch = each alone = oracle."""
+    specs = [((4, 5, 40, 56), 8, 6, 0b1100, 30), ((5, 3, 37, 53), 16, 9, 0b11100, 22),
+             ((2, 4, 70, 33), 32, 5, 0b111100, 27), ((3, 2, 64, 64), 64, 4, 0b111100, 35),
+             ((1, 7, 24, 16), 8, 3, 0b1000, 12)]
+    jobs, bufs, wants = [], [], []
+    for i, (shape, ctu, R, mask, qp) in enumerate(specs):
+        rng = np.random.default_rng(i)
+        cube, _ = synth.tiny_cube(100 + i, T=shape[1], H=shape[2], W=shape[3], bands=shape[0])
+        cube = (cube + rng.normal(0, 0.01, cube.shape)).astype(np.float32)
+        wants.append(oracle.encode_cube(cube, ctu, R, mask, qp))
+        j, b = gpu_job(xv, cube, ctu, R, mask, qp)
+        jobs.append(j)
+        bufs.append(b)
+    results = xv.xv_encode_batch(ctx, jobs)
+    for b, r, w in zip(bufs, results, wants):
+        assert_matches(b, r, w)
+    # the first cube alone through the plain path gives the same bytes
+    cube, _ = synth.tiny_cube(100, T=5, H=40, W=56, bands=4)
+    cube = (cube + np.random.default_rng(0).normal(0, 0.01, cube.shape)).astype(np.float32)
+    j, b = gpu_job(xv, cube, 8, 6, 0b1100, 30)
+    assert_matches(b, xv.xv_encode_cube(ctx, j), wants[0])
+
+
+def test_uint16_dynamicearthnet_prefix(xv, ctx):
+    """Two frames of a DynamicEarthNet-shaped uint16 cube (CTU 64, R 64, TU 4-32),
+    with a min/max fixed in advance (as a causal prefix of a longer cube would)."""
+    c = synth.CONFIGS[2]
+    cube = synth.dynamicearthnet_cube(2000, T=2, H=256, W=320)
+    mm = np.array([[0.0, 10000.0]] * 4)
+    want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27, mm=mm)
+    job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27, minmax=mm)
+    assert_matches(buf, xv.xv_encode_cube(ctx, job), want)
+
+
+def test_batch_timeout_is_reported_and_context_survives(xv, ctx):
+    """A dependency that is never met: the bounded wait returns XV_ETIMEOUT
+    (no fault, no hang) and the same context then encodes correctly."""
+    c = synth.CONFIGS[0]
+    cube = synth.make_cube(0, T=3)
+    job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
+    xv.xv_debug_set_wait_budget(ctx, 20_000_000)  # ~10 ms
+    xv.xv_debug_stall_item(ctx, 70)  # an item of frame 1
+    with pytest.raises(xv.XvError) as e:
+        xv.xv_encode_batch(ctx, [job])
+    assert e.value.status == xv.XV_ETIMEOUT
+    xv.xv_debug_stall_item(ctx, -1)
+    xv.xv_debug_set_wait_budget(ctx, 4_000_000_000)
+    want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27)
+    job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
+    assert_matches(buf, xv.xv_encode_batch(ctx, [job])[0], want)
