@@ -207,23 +207,43 @@ size_t xv_job_scratch_bytes(const xv_job* job);
  * Synchronous (waits for the PSNR read-back). */
 xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void* stream);
 
-/* Batched path: all jobs' frames run in ONE persistent launch over a device
- * work queue of (job, group, frame, PU) items ordered frame-major; an item
- * waits (with a bounded spin) until the previous frame's reconstruction rows
- * it reads are complete.  Output is bit-identical to xv_encode_cube for each
- * job.  results: HOST [njobs].  Synchronous.  XV_ETIMEOUT if a wait ran out
- * of time (results then invalid). */
+/* Batched path: all jobs' frames run in ONE persistent launch per CTU size,
+ * scheduled by data flow over a device ready queue of (job, group, frame, PU)
+ * items: an item is queued once the previous frame's reconstruction rows it
+ * reads are complete, and blocks take queued items in order.  The block size
+ * is chosen by an autotuner: the first batch of a given shape on a context
+ * runs once per candidate size and the fastest is kept for later batches of
+ * that shape.  Output is bit-identical to xv_encode_cube for each job, for
+ * every block size.  results: HOST [njobs].  Synchronous.  XV_ETIMEOUT if a
+ * bounded device wait ran out of time (results then invalid; the context
+ * stays usable). */
 xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
+
+/* ------------------------------------------------------ measurement */
+
+/* Device time of the persistent kernel launches of the last xv_encode_batch
+ * on this context (CUDA events recorded on the call's stream around the
+ * launches), in milliseconds.  Host only. */
+xv_status xv_last_batch_kernel_ms(const xv_ctx* ctx, double* ms);
+/* Threads per block of the last xv_encode_batch persistent launch (the
+ * autotuner's choice for that batch shape).  Host only. */
+xv_status xv_last_batch_block_size(const xv_ctx* ctx, int* block_size);
+/* Number of kernels this context has launched so far.  Host only. */
+uint64_t xv_ctx_launches(const xv_ctx* ctx);
 
 /* ------------------------------------------------------ test hooks */
 
 /* Spin budget (SM clock cycles, default 4e9, about 2 s) of each dependency
  * wait in xv_encode_batch.  Host only. */
 xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
-/* Make the dependency of work item `item` (ticket index within its CTU
- * class) impossible to satisfy, so that its wait runs out and the batch
- * returns XV_ETIMEOUT without any fault; -1 disables.  Host only. */
-xv_status xv_debug_stall_item(xv_ctx* ctx, long long item);
+/* Run xv_encode_batch with this block size (128, 192 or 256) instead of the
+ * autotuner's choice; 0 restores the autotuner.  Host only. */
+xv_status xv_debug_force_block_size(xv_ctx* ctx, int block_size);
+/* Make one dependency counter of xv_encode_batch impossible to complete: the
+ * CTU row `row` of the first job, indexed over its [G][T][rows] counters, is
+ * then never queued, a block waiting for it runs out of its budget, and the
+ * batch returns XV_ETIMEOUT without any fault; -1 disables.  Host only. */
+xv_status xv_debug_stall_row(xv_ctx* ctx, long long row);
 
 #ifdef __cplusplus
 }

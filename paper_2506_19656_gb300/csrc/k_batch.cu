@@ -1,17 +1,23 @@
 // k_batch.cu -- the batched path: one persistent launch for every frame of
-// every cube in a batch.
+// every cube in a batch, scheduled by data flow.
 //
-// Items (job, group, frame, PU) are taken from a device work queue in
-// frame-major order by an atomic ticket.  An item of frame t first waits for
-// the CTU rows of frame t-1 that its motion search and compensation read
-// (rows within R + 4 samples of the PU); every dependency has a smaller
-// ticket and was taken by a block that is running, so the waits always end.
-// Each wait is still bounded by a cycle budget: when it runs out the block
-// records XV_ETIMEOUT in the control block, and from then on every block
-// skips its items, so the launch drains quickly and the host reports the
-// error.  The reference is read through L2 (it is written during the
-// launch); a finished item publishes its rows with a fence before its
-// counter increment.
+// A work item is (job, group, frame, PU).  Items enter a device ready queue
+// only when everything they read exists: first-frame items are queued by the
+// host; a frame t+1 item is queued when the CTU rows of frame t that its
+// motion search and compensation read (rows within R + 4 samples of the PU)
+// are complete.  Each CTU row has a completion counter (PUs done); when a row
+// completes, the block that finished it increments the dependency counters of
+// the next frame's rows that read it, and the block that completes such a
+// counter appends that row's items to the queue.  Blocks take queue positions
+// in order with an atomic ticket, so a block only waits when no item is ready
+// at all.  Every queued item depends only on finished items, so the queue
+// always fills; each wait is still bounded by a cycle budget, after which the
+// block records XV_ETIMEOUT and every block drains the queue without working.
+//
+// The reference planes are written during the launch, so they are read through
+// L2 (no read-only cache); a finished item publishes its writes with a fence
+// before its row counter is incremented, and queue slots are read with acquire
+// loads.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,32 +29,74 @@
 namespace xvh {
 namespace {
 
-constexpr int kNT = 256;
+// Resident blocks per SM the register allocation aims for, per CTU size and
+// block size (64 registers per thread at most where shared memory allows
+// several blocks; the CTU-64 window leaves room for one).
+template <int N, int NT>
+constexpr int kMinBlocks = N == 64 ? 1 : (N == 32 ? (NT == 256 ? 2 : 3) : (NT == 256 ? 4 : (NT == 192 ? 5 : 6)));
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
 
-// Thread 0: wait until rows [r0, r1] of the previous frame are complete.
-__device__ bool wait_rows(const unsigned* rowdone, int r0, int r1, unsigned need, BatchCtl* ctl) {
-    const long long start = clock64();
-    for (int r = r0; r <= r1; ++r) {
-        while (ld_acquire(rowdone + r) < need) {
-            if (ld_volatile_int(&ctl->err)) return false;
-            if (clock64() - start > ctl->budget) {
-                atomicCAS(&ctl->err, 0, (int)XV_ETIMEOUT);
-                return false;
-            }
-            __nanosleep(100);
-        }
-    }
-    return true;
+// Rows of the previous frame read by the PUs of CTU row r.
+__device__ __forceinline__ void dep_rows(int r, int N, int R, int ny, int& r0, int& r1) {
+    const int lo = r * N - R - 4, hi = r * N + N - 1 + R + 4;
+    r0 = lo < 0 ? 0 : lo / N;
+    r1 = hi / N;
+    if (r1 > ny - 1) r1 = ny - 1;
 }
 
-template <int N>
+// Thread 0: the item at queue position `pos`, waiting (bounded) until it is
+// filled.  kEmptyItem on error or timeout.
+__device__ uint64_t take_item(uint64_t* queue, unsigned pos, BatchCtl* ctl) {
+    uint64_t key = ld_acquire_u64(queue + pos);
+    if (key != kEmptyItem) return key;
+    const long long start = clock64();
+    for (;;) {
+        __nanosleep(64);
+        key = ld_acquire_u64(queue + pos);
+        if (key != kEmptyItem) return key;
+        if (ld_volatile_int(&ctl->err)) return kEmptyItem;
+        if (clock64() - start > ctl->budget) {
+            atomicCAS(&ctl->err, 0, (int)XV_ETIMEOUT);
+            return kEmptyItem;
+        }
+    }
+}
+
+// Thread 0, after the item's writes are fenced: count the PU in its row; if
+// the row is complete, credit the next frame's rows that read it and queue
+// those that become ready.
+__device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, uint64_t* queue, BatchCtl* ctl) {
+    const int row = pu / J.nx;
+    const int64_t f = (int64_t)g * J.T + t;
+    if (atomicAdd(J.rowdone + f * J.ny + row, 1u) + 1u != (unsigned)J.nx) return;
+    if (t + 1 >= J.T) return;
+    const int reach = (J.R + 4 + J.ctu - 1) / J.ctu + 1;
+    for (int r = row - reach; r <= row + reach; ++r) {
+        if (r < 0 || r >= J.ny) continue;
+        int r0, r1;
+        dep_rows(r, J.ctu, J.R, J.ny, r0, r1);
+        if (row < r0 || row > r1) continue;
+        const int64_t di = (f + 1) * J.ny + r;
+        const unsigned need = (unsigned)(r1 - r0 + 1) + (ctl->stall_row == (long long)di && job == 0 ? 1u : 0u);
+        if (atomicAdd(J.depcnt + di, 1u) + 1u == need) {
+            __threadfence();
+            const unsigned base = atomicAdd(&ctl->tail, (unsigned)J.nx);
+            for (int i = 0; i < J.nx; ++i) {
+                const uint64_t key = ((uint64_t)job << 56) | ((uint64_t)g << 48) | ((uint64_t)(t + 1) << 32) |
+                                     (uint32_t)(r * J.nx + i);
+                asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(queue + base + i), "l"(key) : "memory");
+            }
+        }
+    }
+}
+
+template <int N, int kNT>
 __device__ void item_work(const JobDev& J, int g, int t, int pu, unsigned char* smem) {
     const int64_t plane = (int64_t)J.Hp * J.Wp, fsz = 3 * plane;
     const int64_t f = (int64_t)g * J.T + t;
@@ -69,57 +117,55 @@ __device__ void item_work(const JobDev& J, int g, int t, int pu, unsigned char* 
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kNT)
-k_persist(const JobDev* __restrict__ jobs, const uint64_t* __restrict__ items, unsigned nitems, BatchCtl* ctl) {
+template <int N, int kNT>
+__global__ void __launch_bounds__(kNT, (kMinBlocks<N, kNT>))
+k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_item;
-    __shared__ int s_go;
+    __shared__ unsigned s_pos, s_next;
+    __shared__ uint64_t s_key;
+    const unsigned total = ctl->total;
+    if (threadIdx.x == 0) s_next = atomicAdd(&ctl->head, 1u);
     for (;;) {
         if (threadIdx.x == 0) {
-            unsigned it = atomicAdd(&ctl->next, 1u);
-            int go = 0;
-            if (it < nitems && !ld_volatile_int(&ctl->err)) {
-                const uint64_t key = items[it];
-                const JobDev& J = jobs[key >> 56];
-                const int g = (int)((key >> 48) & 0xff), t = (int)((key >> 32) & 0xffff), pu = (int)(uint32_t)key;
-                go = 1;
-                if (t > 0) {
-                    const int y0 = (pu / J.nx) * N;
-                    int r0 = (y0 - J.R - 4) / N, r1 = (y0 + N - 1 + J.R + 4) / N;
-                    if (y0 - J.R - 4 < 0) r0 = 0;
-                    if (r1 > J.ny - 1) r1 = J.ny - 1;
-                    const unsigned need = (unsigned)J.nx + (it == ctl->stall_item ? 1u : 0u);
-                    go = wait_rows(J.rowdone + ((int64_t)g * J.T + t - 1) * J.ny, r0, r1, need, ctl) ? 1 : 0;
-                }
-            }
-            s_item = it;
-            s_go = go;
+            const unsigned pos = s_next;
+            s_pos = pos;
+            s_key = pos < total ? take_item(queue, pos, ctl) : kEmptyItem;
+            // take the following position now; its atomic overlaps this item
+            if (pos < total) s_next = atomicAdd(&ctl->head, 1u);
         }
         __syncthreads();
-        const unsigned it = s_item;
-        if (it >= nitems) break;
-        if (s_go) {
-            const uint64_t key = items[it];
-            const JobDev& J = jobs[key >> 56];
+        const unsigned pos = s_pos;
+        const uint64_t key = s_key;
+        if (pos >= total) break;
+        if (key != kEmptyItem && !ld_volatile_int(&ctl->err)) {
+            const int job = (int)(key >> 56);
+            const JobDev& J = jobs[job];
             const int g = (int)((key >> 48) & 0xff), t = (int)((key >> 32) & 0xffff), pu = (int)(uint32_t)key;
-            item_work<N>(J, g, t, pu, smem);
+            item_work<N, kNT>(J, g, t, pu, smem);
             __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0)
-                atomicAdd(J.rowdone + ((int64_t)g * J.T + t) * J.ny + pu / J.nx, 1u);
+            if (threadIdx.x == 0) complete_item(J, job, g, t, pu, queue, ctl);
         }
         __syncthreads();
     }
 }
 
-using PersistFn = void (*)(const JobDev*, const uint64_t*, unsigned, BatchCtl*);
-PersistFn persist_fn(int ctu) {
+using PersistFn = void (*)(const JobDev*, uint64_t*, BatchCtl*);
+template <int NT>
+PersistFn persist_fn_nt(int ctu) {
     switch (ctu) {
-        case 8: return k_persist<8>;
-        case 16: return k_persist<16>;
-        case 32: return k_persist<32>;
-        case 64: return k_persist<64>;
+        case 8: return k_persist<8, NT>;
+        case 16: return k_persist<16, NT>;
+        case 32: return k_persist<32, NT>;
+        case 64: return k_persist<64, NT>;
+    }
+    return nullptr;
+}
+PersistFn persist_fn(int ctu, int nt) {
+    switch (nt) {
+        case 128: return persist_fn_nt<128>(ctu);
+        case 192: return persist_fn_nt<192>(ctu);
+        case 256: return persist_fn_nt<256>(ctu);
     }
     return nullptr;
 }
@@ -132,25 +178,25 @@ size_t persist_smem_bytes(int ctu, int R, bool has_me) {
     return a > b ? a : b;
 }
 
-int persist_grid(int ctu, size_t smem) {
-    PersistFn fn = persist_fn(ctu);
+int persist_grid(int ctu, int nt, size_t smem) {
+    PersistFn fn = persist_fn(ctu, nt);
     if (!fn) return 0;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kNT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nt, smem);
     if (per < 1) per = 1;
     return sms * per;
 }
 
-cudaError_t launch_persist(int ctu, const JobDev* jobs, const uint64_t* items, unsigned nitems, BatchCtl* ctl,
-                           size_t smem, int grid, cudaStream_t st) {
-    PersistFn fn = persist_fn(ctu);
+cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,
+                           int grid, cudaStream_t st) {
+    PersistFn fn = persist_fn(ctu, nt);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kNT, smem, st>>>(jobs, items, nitems, ctl);
+    fn<<<grid, nt, smem, st>>>(jobs, queue, ctl);
     return cudaGetLastError();
 }
 

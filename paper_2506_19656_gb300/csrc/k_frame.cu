@@ -13,9 +13,10 @@ namespace xvh {
 namespace {
 
 constexpr int kNT = 256;
+template <int N> constexpr int kMinBlocks = N == 64 ? 1 : (N == 32 ? 2 : 4);
 
 template <int N>
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kNT, kMinBlocks<N>)
 k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t gstride, int Hp, int Wp,
            int R, int64_t lmv, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
            int64_t pu_gstride) {
@@ -34,7 +35,7 @@ k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, i
 }
 
 template <int N>
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kNT, kMinBlocks<N>)
 k_tqr_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, const int16_t* __restrict__ mv,
             int64_t gstride, int Hp, int Wp, int qp, unsigned tu_mask, int64_t lf8, int64_t pu_gstride,
             uint16_t* recon, int16_t* levels, uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride) {

@@ -44,7 +44,35 @@ __host__ __device__ constexpr size_t me_off_blk(int N, int R) { return me_align1
 __host__ __device__ constexpr size_t me_off_hp(int N, int R) { return me_off_blk(N, R) + me_align16((size_t)N * N * 4); }
 __host__ __device__ constexpr size_t me_off_red(int N, int R) { return me_off_hp(N, R) + me_align16((size_t)3 * (N + 8) * N * 2); }
 __host__ __device__ constexpr size_t me_off_satd(int N, int R) { return me_off_red(N, R) + 64 * 8; }
-__host__ __device__ constexpr size_t me_smem_bytes(int N, int R) { return me_off_satd(N, R) + 16 * 4; }
+// motion-cost tables: |se(4d)| for d in [-R, R] (129 at most) and the
+// rounded cost of b bits, b < 64
+__host__ __device__ constexpr size_t me_off_cost(int N, int R) { return me_off_satd(N, R) + 16 * 4; }
+__host__ __device__ constexpr size_t me_off_had(int N, int R) { return me_off_cost(N, R) + me_align16((129 + 64) * 4); }
+// Candidates' horizontally transformed differences (PUs up to 32 only).
+__host__ __device__ constexpr size_t me_had_bytes(int N) { return N <= 32 ? me_align16((size_t)9 * N * N * 2) : 0; }
+__host__ __device__ constexpr size_t me_smem_bytes(int N, int R) { return me_off_had(N, R) + me_had_bytes(N); }
+
+// Samples in the window and block are stored as the float 2^23 + v (v <= 1023).
+// Its bit pattern is 0x4B000000 | v, so the integer path's __sad on the raw
+// bits gives |a - b| exactly, and the float path's |a - b| is exact too (both
+// operands lie in [2^23, 2^24), where the float spacing is 1).
+constexpr int kSampleBias = 0x4B000000;
+__device__ __forceinline__ int enc_sample(int v) { return kSampleBias | v; }
+__device__ __forceinline__ int dec_sample(int bits) { return bits - kSampleBias; }
+
+// Lanes per integer-search unit: the smallest P in {1, 2, 4} whose split of
+// units * P over NT threads wastes least (all P lanes of a unit sit in one
+// warp and interleave the block rows).
+__host__ __device__ inline int me_split(int units, int NT) {
+    // efficiency work / (iters * NT), compared as cross products
+    int bestP = 1;
+    long long bw = units, bd = (long long)((units + NT - 1) / NT) * NT;
+    for (int P = 2; P <= 4; P *= 2) {
+        const long long w = (long long)units * P, d = ((w + NT - 1) / NT) * NT;
+        if (w * bd > bw * d) { bw = w; bd = d; bestP = P; }
+    }
+    return bestP;
+}
 
 template <int NT>
 __device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
@@ -97,6 +125,37 @@ __device__ __forceinline__ void row_sad8(const int* __restrict__ crow, const int
     }
 }
 
+// The same through the FP32 pipe: the words read as floats, |a - b|
+// accumulated in float32, exact because every partial sum is an integer
+// below 2^24.  Running a third of the rows through this path keeps both the
+// integer ALU pipe (one __sad per abs-diff at half the issue rate) and the
+// FP32 pipe busy.
+template <int W>
+__device__ __forceinline__ void row_sad8f(const int* __restrict__ crow_i, const int* __restrict__ rrow_i,
+                                          float (&acc)[8]) {
+    const float* crow = reinterpret_cast<const float*>(crow_i);
+    const float* rrow = reinterpret_cast<const float*>(rrow_i);
+#pragma unroll
+    for (int c0 = 0; c0 < W; c0 += 16) {
+        constexpr int CW = W < 16 ? W : 16;
+        float cv[CW], rv[CW + 8];
+#pragma unroll
+        for (int i = 0; i < CW; i += 4) {
+            float4 t = *reinterpret_cast<const float4*>(crow + c0 + i);
+            cv[i] = t.x; cv[i + 1] = t.y; cv[i + 2] = t.z; cv[i + 3] = t.w;
+        }
+#pragma unroll
+        for (int i = 0; i < CW + 8; i += 4) {
+            float4 t = *reinterpret_cast<const float4*>(rrow + c0 + i);
+            rv[i] = t.x; rv[i + 1] = t.y; rv[i + 2] = t.z; rv[i + 3] = t.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) acc[k] += fabsf(cv[c] - rv[c + k]);
+    }
+}
+
 // In-register 8-point Hadamard (Sylvester order) of v.
 __device__ __forceinline__ void hadamard8_row(int (&v)[8]) {
 #pragma unroll
@@ -130,11 +189,13 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
         const int* wr = win + (rbase + r + R + 4) * S + (x + ix + R + 4);
         int v;
         if (hx == 0) {
-            v = wr[0];
+            v = dec_sample(wr[0]);
         } else {
+            int tap[8];
+            luma_taps(hx, tap);
             int acc = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc += luma_tap(hx, i) * wr[i - 3];
+            for (int i = 0; i < 8; ++i) acc += tap[i] * dec_sample(wr[i - 3]);
             v = acc >> kShift1;
         }
         hp[(j * (N + 8) + r) * N + x] = (int16_t)v;
@@ -155,6 +216,8 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
         const int16_t* col = hp + (size_t)j * (N + 8) * N + bx;
         int r0 = y + iy - 3 - rbase;  // hp row of tap 0
         int d[8];
+        int tap[8];
+        luma_taps(fy == 0 ? 2 : fy, tap);
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
             int v;
@@ -164,10 +227,10 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
             } else {
                 int acc = 0;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc += luma_tap(fy, t) * (int)col[(r0 + t) * N + x];
+                for (int t = 0; t < 8; ++t) acc += tap[t] * (int)col[(r0 + t) * N + x];
                 v = hx == 0 ? acc >> kShift1 : acc >> kShift2;
             }
-            d[x] = blk[y * N + bx + x] - wp_round(v);
+            d[x] = dec_sample(blk[y * N + bx + x]) - wp_round(v);
         }
         hadamard8_row(d);
         // vertical transform across the 8 lanes of the group
@@ -190,6 +253,100 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
     __syncthreads();
 }
 
+// Refinement stage through shared memory (PUs up to 32): horizontally
+// filtered columns, then one task per (candidate, row, 8-column block) that
+// forms the 8 predicted samples, their differences and the row Hadamard,
+// then one task per (candidate, 8x8 block, column) that finishes the column
+// Hadamard; the 8 column tasks of a block are adjacent lanes and add their
+// absolute sums before the block's (S + 2) >> 2.
+template <int N, int NT>
+__device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const int* __restrict__ blk,
+                                int16_t* __restrict__ hp, int16_t* __restrict__ had, int cx, int cy, int s,
+                                const int* cand_x, const int* cand_y, int ncand, uint32_t* satd) {
+    const int tid = threadIdx.x;
+    const int iy_min = (cy - s) >> 2, iy_max = (cy + s) >> 2;
+    const int rbase = iy_min - 3;
+    const int nr = N + 7 + (iy_max - iy_min);
+    for (int idx = tid; idx < 3 * nr * N; idx += NT) {
+        int j = idx / (nr * N), rem = idx - j * nr * N;
+        int r = rem / N, x = rem - r * N;
+        int m = cx + (j - 1) * s;
+        int hx = m & 3, ix = m >> 2;
+        const int* wr = win + (rbase + r + R + 4) * S + (x + ix + R + 4);
+        int v;
+        if (hx == 0) {
+            v = dec_sample(wr[0]);
+        } else {
+            int tap[8];
+            luma_taps(hx, tap);
+            int acc = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc += tap[i] * dec_sample(wr[i - 3]);
+            v = acc >> kShift1;
+        }
+        hp[(j * (N + 8) + r) * N + x] = (int16_t)v;
+    }
+    for (int k = tid; k < ncand; k += NT) satd[k] = 0;
+    __syncthreads();
+    constexpr int NBX = N / 8;
+    for (int task = tid; task < ncand * N * NBX; task += NT) {
+        const int k = task / (N * NBX), rem = task - k * N * NBX;
+        const int y = rem / NBX, bx = (rem - y * NBX) * 8;
+        const int mvx = cand_x[k], mvy = cand_y[k];
+        const int j = (mvx - cx) / s + 1;
+        const int hx = mvx & 3, fy = mvy & 3, iy = mvy >> 2;
+        const int16_t* col = hp + (size_t)j * (N + 8) * N + bx;
+        const int r0 = y + iy - 3 - rbase;
+        int d[8];
+        if (fy == 0) {
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int a = col[(r0 + 3) * N + x];
+                d[x] = dec_sample(blk[y * N + bx + x]) - wp_round(hx == 0 ? a << kShift3 : a);
+            }
+        } else {
+            int tap[8];
+            luma_taps(fy, tap);
+            const int sh = hx == 0 ? kShift1 : kShift2;
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                int acc = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc += tap[t] * (int)col[(r0 + t) * N + x];
+                d[x] = dec_sample(blk[y * N + bx + x]) - wp_round(acc >> sh);
+            }
+        }
+        hadamard8_row(d);
+        uint4 pk;
+        pk.x = (uint32_t)(uint16_t)d[0] | ((uint32_t)(uint16_t)d[1] << 16);
+        pk.y = (uint32_t)(uint16_t)d[2] | ((uint32_t)(uint16_t)d[3] << 16);
+        pk.z = (uint32_t)(uint16_t)d[4] | ((uint32_t)(uint16_t)d[5] << 16);
+        pk.w = (uint32_t)(uint16_t)d[6] | ((uint32_t)(uint16_t)d[7] << 16);
+        *reinterpret_cast<uint4*>(had + ((size_t)k * N + y) * N + bx) = pk;
+    }
+    __syncthreads();
+    constexpr int NB = NBX * NBX;
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    for (int task = tid; task < ncand * NB * 8; task += NT) {
+        const int x = task & 7, kb = task >> 3;
+        const int k = kb / NB, b = kb - k * NB;
+        const int by = (b / NBX) * 8, bx = (b % NBX) * 8;
+        const int16_t* h = had + ((size_t)k * N + by) * N + bx + x;
+        int v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = h[i * N];
+        hadamard8_row(v);
+        int sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sum += v[i] < 0 ? -v[i] : v[i];
+        sum += __shfl_xor_sync(gmask, sum, 1);
+        sum += __shfl_xor_sync(gmask, sum, 2);
+        sum += __shfl_xor_sync(gmask, sum, 4);
+        if (x == 0) atomicAdd(&satd[k], (uint32_t)((sum + 2) >> 2));
+    }
+    __syncthreads();
+}
+
 // Motion estimation of the PU at (x0, y0).  cur0/ref0: channel-0 planes.
 // Must be called by all NT threads of the block; smem holds me_smem_bytes.
 template <int N, int NT, bool kCoherent = false>
@@ -203,39 +360,95 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     int16_t* hp = reinterpret_cast<int16_t*>(smem + me_off_hp(N, R));
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + me_off_red(N, R));
     uint32_t* satd = reinterpret_cast<uint32_t*>(smem + me_off_satd(N, R));
+    int16_t* had = reinterpret_cast<int16_t*>(smem + me_off_had(N, R));
+    int* s_bitsd = reinterpret_cast<int*>(smem + me_off_cost(N, R));  // |se(4d)|, index d + R
+    uint32_t* s_costb = reinterpret_cast<uint32_t*>(s_bitsd + 129);    // cost of b bits
 
-    // window with clamped coordinates, and the current block
+    // window with clamped coordinates, 8 samples (16 bytes) per load where the
+    // aligned chunk lies inside the plane
     const int wx0 = x0 - R - 4, wy0 = y0 - R - 4;
-    for (int idx = tid; idx < WW * WW; idx += NT) {
-        int r = idx / WW, c = idx - r * WW;
-        int yy = min(max(wy0 + r, 0), Hp - 1), xx = min(max(wx0 + c, 0), Wp - 1);
-        win[r * S + c] = ld_ref<kCoherent>(ref0 + (size_t)yy * Wp + xx);
+    const int xa = wx0 - (((wx0 % 8) + 8) % 8);  // 8-aligned start at or left of wx0
+    const int nch = (wx0 + WW - xa + 7) / 8;
+    constexpr int kILP = 2;
+    for (int base = tid; base < WW * nch; base += NT * kILP) {
+        uint16_t v[kILP][8];
+#pragma unroll
+        for (int j = 0; j < kILP; ++j) {
+            const int task = base + j * NT;
+            if (task < WW * nch) {
+                const int r = task / nch, ch = task - r * nch;
+                const int yy = min(max(wy0 + r, 0), Hp - 1), xs = xa + 8 * ch;
+                const uint16_t* rowp = ref0 + (size_t)yy * Wp;
+                if (xs >= 0 && xs + 8 <= Wp) {
+                    uint4 w = ld_ref16<kCoherent>(reinterpret_cast<const uint4*>(rowp + xs));
+                    const uint16_t* e = reinterpret_cast<const uint16_t*>(&w);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[j][i] = e[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[j][i] = (uint16_t)ld_ref<kCoherent>(rowp + min(max(xs + i, 0), Wp - 1));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kILP; ++j) {
+            const int task = base + j * NT;
+            if (task < WW * nch) {
+                const int r = task / nch, ch = task - r * nch;
+                const int c0 = xa + 8 * ch - wx0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int c = c0 + i;
+                    if (c >= 0 && c < WW) win[r * S + c] = enc_sample(v[j][i]);
+                }
+            }
+        }
     }
     for (int idx = tid; idx < N * N; idx += NT) {
         int r = idx / N, c = idx - r * N;
-        blk[idx] = __ldg(cur0 + (size_t)(y0 + r) * Wp + x0 + c);
+        blk[idx] = enc_sample(__ldg(cur0 + (size_t)(y0 + r) * Wp + x0 + c));
+    }
+    for (int i = tid; i < 2 * R + 1 + 64; i += NT) {
+        if (i < 2 * R + 1) s_bitsd[i] = se_len(4 * (i - R));
+        else s_costb[i - (2 * R + 1)] = (uint32_t)((lmv * (int64_t)(i - (2 * R + 1)) + 32768) >> 16);
     }
     __syncthreads();
 
     // ---- integer full search
     const int side = 2 * R + 1;
     const int ngx = (side + 7) / 8;
+    const int units = side * ngx;
+    const int P = me_split(units, NT);      // lanes sharing one unit (rows interleaved)
+    const int q = tid & (P - 1);
+    const unsigned pmask = P == 1 ? 0u : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
     uint64_t best = ~0ull;
-    for (int u = tid; u < side * ngx; u += NT) {
+    for (int u = tid / P; u < units; u += NT / P) {
         int gx = u / side;
         int dy = u - gx * side - R;
         int dx0 = gx * 8 - R;
         uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const int* wrow = win + (dy + R + 4) * S + (dx0 + R + 4);
-#pragma unroll 2
-        for (int r = 0; r < N; ++r) row_sad8<N>(blk + r * N, wrow + r * S, sad);
+        float accf[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int woff = (dy + R + 4) * S + (dx0 + R + 4);
+        // every third row of a lane on the FP32 pipe, the others on the
+        // integer ALU (by iteration, so the lanes of a warp agree)
+#pragma unroll 1
+        for (int i = 0, r = q; r < N; ++i, r += P) {
+            if (i % 3 == 2) row_sad8f<N>(blk + r * N, win + woff + r * S, accf);
+            else row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sad[k] += (uint32_t)accf[k];
+        for (int o = 1; o < P; o <<= 1)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
         const uint32_t rowbase = (uint32_t)((dy + R) * side);
+        const int by = s_bitsd[dy + R];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            int dx = dx0 + k;
-            if (dx <= R) {
-                uint64_t J = (uint64_t)sad[k] + mv_cost(4 * dx, 4 * dy, lmv);
-                uint64_t key = (J << 32) | (rowbase + (uint32_t)(dx + R));
+            const int dx = dx0 + k;
+            if ((k & (P - 1)) == q && dx <= R) {  // the P lanes share the candidates
+                const uint32_t J = sad[k] + s_costb[s_bitsd[dx + R] + by];
+                const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(dx + R));
                 best = key < best ? key : best;
             }
         }
@@ -257,7 +470,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     cand_x[0] = cx; cand_y[0] = cy;
 #pragma unroll
     for (int k = 0; k < 8; ++k) { cand_x[k + 1] = cx + 2 * ring_x[k]; cand_y[k + 1] = cy + 2 * ring_y[k]; }
-    satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 2, cand_x, cand_y, 9, satd);
+    if constexpr (N <= 32) satd_stage_smem<N, NT>(win, S, R, blk, hp, had, cx, cy, 2, cand_x, cand_y, 9, satd);
+    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 2, cand_x, cand_y, 9, satd);
     uint32_t bJ = satd[0] + mv_cost(cx, cy, lmv);
     int bx = cx, by = cy;
 #pragma unroll
@@ -269,7 +483,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     cx = bx; cy = by;
 #pragma unroll
     for (int k = 0; k < 8; ++k) { cand_x[k] = cx + ring_x[k]; cand_y[k] = cy + ring_y[k]; }
-    satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 1, cand_x, cand_y, 8, satd);
+    if constexpr (N <= 32) satd_stage_smem<N, NT>(win, S, R, blk, hp, had, cx, cy, 1, cand_x, cand_y, 8, satd);
+    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 1, cand_x, cand_y, 8, satd);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         uint32_t J = satd[k] + mv_cost(cand_x[k], cand_y[k], lmv);

@@ -25,7 +25,7 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 
 __host__ __device__ constexpr size_t tqr_off_stage(int N) { return align16((size_t)5 * 3 * N * N * 2); }
 __host__ __device__ constexpr size_t tqr_off_hbuf(int N) { return tqr_off_stage(N) + align16((size_t)(N + 7) * (N + 7) * 2); }
 __host__ __device__ constexpr size_t tqr_off_red(int N) { return tqr_off_hbuf(N) + align16((size_t)(N + 7) * (N + 7) * 2); }
-__host__ __device__ constexpr size_t tqr_smem_bytes(int N) { return tqr_off_red(N) + 64 * 8; }
+__host__ __device__ constexpr size_t tqr_seq_smem_bytes(int N) { return tqr_off_red(N) + 64 * 8; }
 
 template <int NT>
 __device__ __forceinline__ void block_sum2(uint64_t& a, uint32_t& b, uint64_t* red) {
@@ -60,12 +60,15 @@ __device__ void mc_predict(const uint16_t* __restrict__ ref, int64_t plane, int 
             stage[idx] = (int16_t)ld_ref<kCoherent>(rp + (size_t)yy * Wp + xx);
         }
         __syncthreads();
+        int htap[8], vtap[8];
+        luma_taps(fx == 0 ? 2 : fx, htap);
+        luma_taps(fy == 0 ? 2 : fy, vtap);
         if (fx != 0) {  // horizontal pass over all SW rows
             for (int idx = tid; idx < SW * N; idx += NT) {
                 int r = idx / N, x = idx - r * N;
                 int acc = 0;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) acc += luma_tap(fx, i) * stage[r * SW + x + i];
+                for (int i = 0; i < 8; ++i) acc += htap[i] * stage[r * SW + x + i];
                 hbuf[idx] = (int16_t)(acc >> kShift1);
             }
             __syncthreads();
@@ -80,12 +83,12 @@ __device__ void mc_predict(const uint16_t* __restrict__ ref, int64_t plane, int 
             } else if (fx == 0) {
                 int acc = 0;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc += luma_tap(fy, t) * stage[(y + t) * SW + x + 3];
+                for (int t = 0; t < 8; ++t) acc += vtap[t] * stage[(y + t) * SW + x + 3];
                 v = acc >> kShift1;
             } else {
                 int acc = 0;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc += luma_tap(fy, t) * hbuf[(y + t) * N + x];
+                for (int t = 0; t < 8; ++t) acc += vtap[t] * hbuf[(y + t) * N + x];
                 v = acc >> kShift2;
             }
             pred[c * N * N + idx] = (uint16_t)wp_round(v);
@@ -175,6 +178,239 @@ __device__ __forceinline__ void copy_out(const uint16_t* __restrict__ rec, const
     }
 }
 
+// ---------------------------------------------------------------------------
+// Low-latency variant for CUs up to 16: all allowed TU sizes are processed at
+// once (each has its own work/level/recon buffers), so the whole CU takes
+// about seven block barriers instead of three per size.  Same definitions,
+// same results.
+template <int N>
+__host__ __device__ constexpr int tqr_nslots() { return N >= 16 ? 3 : (N >= 8 ? 2 : 1); }
+__host__ __device__ constexpr size_t tqr_conc_off_stage(int N) { return align16((size_t)2 * 3 * N * N * 2); }
+__host__ __device__ constexpr size_t tqr_conc_off_hbuf(int N) { return tqr_conc_off_stage(N) + align16((size_t)3 * (N + 7) * (N + 7) * 2); }
+__host__ __device__ constexpr size_t tqr_conc_off_slots(int N) { return tqr_conc_off_hbuf(N) + align16((size_t)3 * (N + 7) * N * 2); }
+__host__ __device__ constexpr size_t tqr_conc_slot_bytes(int N) { return align16((size_t)3 * 3 * N * N * 2); }
+__host__ __device__ constexpr size_t tqr_conc_off_acc(int N) { return tqr_conc_off_slots(N) + 3 * tqr_conc_slot_bytes(N); }
+__host__ __device__ constexpr size_t tqr_conc_smem_bytes(int N) { return tqr_conc_off_acc(N) + 3 * 8 + 3 * 4 + 16; }
+
+template <int N, int TS>
+__device__ __forceinline__ void conc_row_fwd(int lt, const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
+                                             int16_t* __restrict__ work) {
+    constexpr int L = TS == 4 ? 2 : TS == 8 ? 3 : TS == 16 ? 4 : 5;
+    constexpr int NTU = N / TS;
+    const int c = lt / (N * NTU), rem = lt - c * N * NTU;
+    const int y = rem / NTU, tx = rem - y * NTU;
+    const int base = c * N * N + y * N + tx * TS;
+    int x[TS], yv[TS];
+#pragma unroll
+    for (int i = 0; i < TS; ++i) x[i] = (int)cur[base + i] - (int)pred[base + i];
+    fwd1d<TS>(x, yv);
+#pragma unroll
+    for (int i = 0; i < TS; ++i) work[base + i] = (int16_t)rshift_round(yv[i], L + kBitDepth - 9);
+}
+
+template <int N, int TS>
+__device__ __forceinline__ uint32_t conc_col(int lt, int16_t* __restrict__ work, int16_t* __restrict__ lev, int qp) {
+    constexpr int L = TS == 4 ? 2 : TS == 8 ? 3 : TS == 16 ? 4 : 5;
+    constexpr int NTU = N / TS;
+    const QuantParams q = quant_params(qp, L);
+    const int c = lt / (N * NTU), rem = lt - c * N * NTU;
+    const int ty = rem / N, x = rem - ty * N;
+    const int base = c * N * N + ty * TS * N + x;
+    int col[TS], cf[TS];
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < TS; ++i) col[i] = work[base + i * N];
+    fwd1d<TS>(col, cf);
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+        int lv = quantize(rshift_round(cf[i], L + 6), q);
+        lev[base + i * N] = (int16_t)lv;
+        if (lv != 0) bits += (uint32_t)(2 * L + se_len(lv));
+        col[i] = dequantize(lv, q);
+    }
+    inv1d<TS>(col, cf);
+#pragma unroll
+    for (int i = 0; i < TS; ++i) work[base + i * N] = (int16_t)clip16(rshift_round(cf[i], 7));
+    return bits;
+}
+
+template <int N, int TS>
+__device__ __forceinline__ uint64_t conc_row_inv(int lt, const uint16_t* __restrict__ cur,
+                                                 const uint16_t* __restrict__ pred, const int16_t* __restrict__ work,
+                                                 uint16_t* __restrict__ rec) {
+    constexpr int NTU = N / TS;
+    const int c = lt / (N * NTU), rem = lt - c * N * NTU;
+    const int y = rem / NTU, tx = rem - y * NTU;
+    const int base = c * N * N + y * N + tx * TS;
+    int e[TS], r[TS];
+    uint64_t sse = 0;
+#pragma unroll
+    for (int i = 0; i < TS; ++i) e[i] = work[base + i];
+    inv1d<TS>(e, r);
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+        int v = clip_pix((int)pred[base + i] + rshift_round(r[i], 20 - kBitDepth));
+        rec[base + i] = (uint16_t)v;
+        int d = (int)cur[base + i] - v;
+        sse += (uint64_t)(d * d);
+    }
+    return sse;
+}
+
+template <int N, int NT, bool kCoherent>
+__device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
+                                int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
+                                int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
+                                uint8_t* tu_log2, unsigned char* smem) {
+    constexpr int NS = tqr_nslots<N>();
+    constexpr int SW = N + 7;
+    constexpr int NN = N * N;
+    const int tid = threadIdx.x;
+    uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* s_pred = s_cur + 3 * NN;
+    int16_t* s_stage = reinterpret_cast<int16_t*>(smem + tqr_conc_off_stage(N));
+    int16_t* s_hbuf = reinterpret_cast<int16_t*>(smem + tqr_conc_off_hbuf(N));
+    unsigned char* slots = smem + tqr_conc_off_slots(N);
+    unsigned long long* s_sse = reinterpret_cast<unsigned long long*>(smem + tqr_conc_off_acc(N));
+    unsigned* s_bits = reinterpret_cast<unsigned*>(s_sse + 3);
+    auto work_of = [&](int s) { return reinterpret_cast<int16_t*>(slots + s * tqr_conc_slot_bytes(N)); };
+    auto lev_of = [&](int s) { return work_of(s) + 3 * NN; };
+    auto rec_of = [&](int s) { return reinterpret_cast<uint16_t*>(work_of(s) + 6 * NN); };
+
+    // 1. current samples and the motion-compensation windows of all channels
+    const int ix = mvx >> 2, iy = mvy >> 2, fx = mvx & 3, fy = mvy & 3;
+    for (int idx = tid; idx < 3 * NN; idx += NT) {
+        const int c = idx / NN, rem = idx - c * NN, y = rem / N, x = rem - y * N;
+        s_cur[idx] = __ldg(cur + (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + x);
+        if (!ref) s_pred[idx] = (uint16_t)kFlat;
+    }
+    if (ref) {
+        for (int idx = tid; idx < 3 * SW * SW; idx += NT) {
+            const int c = idx / (SW * SW), rem = idx - c * SW * SW, r = rem / SW, q = rem - r * SW;
+            const int yy = min(max(y0 + iy - 3 + r, 0), Hp - 1), xx = min(max(x0 + ix - 3 + q, 0), Wp - 1);
+            s_stage[idx] = (int16_t)ld_ref<kCoherent>(ref + (size_t)c * plane + (size_t)yy * Wp + xx);
+        }
+    }
+    if (tid < 3) { s_sse[tid] = 0ull; s_bits[tid] = 0u; }
+    __syncthreads();
+    if (ref) {
+        if (fx != 0) {
+            int tap[8];
+            luma_taps(fx, tap);
+            for (int idx = tid; idx < 3 * SW * N; idx += NT) {
+                const int c = idx / (SW * N), rem = idx - c * SW * N, r = rem / N, x = rem - r * N;
+                const int16_t* st = s_stage + c * SW * SW + r * SW + x;
+                int acc = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc += tap[i] * st[i];
+                s_hbuf[idx] = (int16_t)(acc >> kShift1);
+            }
+            __syncthreads();
+        }
+        int vtap[8];
+        luma_taps(fy == 0 ? 2 : fy, vtap);
+        for (int idx = tid; idx < 3 * NN; idx += NT) {
+            const int c = idx / NN, rem = idx - c * NN, y = rem / N, x = rem - y * N;
+            const int16_t* st = s_stage + c * SW * SW;
+            const int16_t* hb = s_hbuf + c * SW * N;
+            int v;
+            if (fx == 0 && fy == 0) {
+                v = st[(y + 3) * SW + x + 3] << kShift3;
+            } else if (fy == 0) {
+                v = hb[(y + 3) * N + x];
+            } else if (fx == 0) {
+                int acc = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc += vtap[t] * st[(y + t) * SW + x + 3];
+                v = acc >> kShift1;
+            } else {
+                int acc = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc += vtap[t] * hb[(y + t) * N + x];
+                v = acc >> kShift2;
+            }
+            s_pred[idx] = (uint16_t)wp_round(v);
+        }
+        __syncthreads();
+    }
+
+    // task ranges of the allowed sizes (slot s: TU size 4 << s)
+    int cum[NS + 1];
+    cum[0] = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) cum[s + 1] = cum[s] + (((tu_mask >> (s + 2)) & 1u) ? 3 * N * (N / (4 << s)) : 0);
+    const int TOT = cum[NS];
+
+    // 2. forward rows, all sizes
+    for (int t = tid; t < TOT; t += NT) {
+        int s = 0;
+        while (s < NS - 1 && t >= cum[s + 1]) ++s;
+        const int lt = t - cum[s];
+        if (s == 0) conc_row_fwd<N, 4>(lt, s_cur, s_pred, work_of(0));
+        if constexpr (NS > 1) if (s == 1) conc_row_fwd<N, 8>(lt, s_cur, s_pred, work_of(1));
+        if constexpr (NS > 2) if (s == 2) conc_row_fwd<N, 16>(lt, s_cur, s_pred, work_of(2));
+    }
+    __syncthreads();
+    // 3. columns: forward, quantise, dequantise, inverse
+    uint32_t bitsS[NS];
+    uint64_t sseS[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { bitsS[s] = 0; sseS[s] = 0; }
+    for (int t = tid; t < TOT; t += NT) {
+        int s = 0;
+        while (s < NS - 1 && t >= cum[s + 1]) ++s;
+        const int lt = t - cum[s];
+        if (s == 0) bitsS[0] += conc_col<N, 4>(lt, work_of(0), lev_of(0), qp);
+        if constexpr (NS > 1) if (s == 1) bitsS[1] += conc_col<N, 8>(lt, work_of(1), lev_of(1), qp);
+        if constexpr (NS > 2) if (s == 2) bitsS[2] += conc_col<N, 16>(lt, work_of(2), lev_of(2), qp);
+    }
+    __syncthreads();
+    // 4. inverse rows, reconstruction, SSE
+    for (int t = tid; t < TOT; t += NT) {
+        int s = 0;
+        while (s < NS - 1 && t >= cum[s + 1]) ++s;
+        const int lt = t - cum[s];
+        if (s == 0) sseS[0] += conc_row_inv<N, 4>(lt, s_cur, s_pred, work_of(0), rec_of(0));
+        if constexpr (NS > 1) if (s == 1) sseS[1] += conc_row_inv<N, 8>(lt, s_cur, s_pred, work_of(1), rec_of(1));
+        if constexpr (NS > 2) if (s == 2) sseS[2] += conc_row_inv<N, 16>(lt, s_cur, s_pred, work_of(2), rec_of(2));
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        uint64_t a = sseS[s];
+        uint32_t b = bitsS[s];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if ((tid & 31) == 0 && (a | b)) {
+            atomicAdd(&s_sse[s], (unsigned long long)a);
+            atomicAdd(&s_bits[s], b);
+        }
+    }
+    __syncthreads();
+    // 5. the size with the least J (ascending, ties to the larger), copied out
+    int64_t bestJ = INT64_MAX;
+    int best = 0;
+    uint32_t bestBits = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (!((tu_mask >> (s + 2)) & 1u)) continue;
+        const int ntu = (N / (4 << s)) * (N / (4 << s));
+        const uint32_t bits = s_bits[s] + 3u * ntu;
+        const int64_t J = (int64_t)(s_sse[s] << 8) + lf8 * (int64_t)bits;
+        if (J <= bestJ) { bestJ = J; best = s; bestBits = bits; }
+    }
+    copy_out<N, NT>(rec_of(best), lev_of(best), recon, levels, plane, Wp, x0, y0);
+    if (tid == 0 && tu_log2) *tu_log2 = (uint8_t)(best + 2);
+    uint32_t mvbits = ref ? (uint32_t)(se_len(mvx) + se_len(mvy)) : 0u;
+    return 2u + mvbits + bestBits;
+}
+
+__host__ __device__ constexpr size_t tqr_smem_bytes(int N) {
+    return N <= 16 ? tqr_conc_smem_bytes(N) : tqr_seq_smem_bytes(N);
+}
+
 // Transform/quantise/reconstruct the CU at (x0, y0).  cur/ref/recon/levels:
 // the group's frame [3][Hp][Wp] (ref == nullptr: first frame).  Returns the
 // CU's rate-proxy bits; writes recon (and levels) and *tu_log2.
@@ -183,6 +419,10 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
                            int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
                            int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
                            uint8_t* tu_log2, unsigned char* smem) {
+    if constexpr (N <= 16) {
+        return tqr_cu_conc<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask, lf8, recon,
+                                             levels, tu_log2, smem);
+    }
     const int tid = threadIdx.x;
     uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
     uint16_t* s_pred = s_cur + 3 * N * N;

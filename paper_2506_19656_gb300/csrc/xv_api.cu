@@ -24,9 +24,15 @@ struct xv_ctx {
     // scratch of the single-cube calls
     DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax;
     // scratch of the batched path
-    DevBuf b_jobs, b_items, b_rowdone, b_ctl, b_bits, b_bandq, b_minmax;
+    DevBuf b_jobs, b_items, b_rowdone, b_depcnt, b_ctl, b_bits, b_bandq, b_minmax;
     long long wait_budget = 4000000000LL;  // cycles per dependency wait (about 2 s)
-    long long stall_item = -1;             // test hook (xv_debug_stall_item)
+    long long stall_row = -1;              // test hook (xv_debug_stall_row)
+    uint64_t launches = 0;                 // kernels launched by this context
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launches
+    double batch_ms = 0.0;
+    int batch_nt = 0;                        // block size of the last persistent launch
+    std::map<std::string, int> tuned_nt;     // autotuner: batch shape -> block size
+    int force_nt = 0;                        // test hook (xv_debug_force_block_size)
 };
 
 namespace xvh {
@@ -125,6 +131,16 @@ bool valid_params(const xv_params* p) {
     return true;
 }
 
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+bool valid_planes(const void* a, const void* b, const void* c, int64_t gstride) {
+    if (!aligned16(a) || !aligned16(b) || !aligned16(c) || gstride % 8 != 0) {
+        set_error("plane pointers must be 16-byte aligned and the group stride a multiple of 8 samples");
+        return false;
+    }
+    return true;
+}
+
 bool valid_frame(int G, int Hp, int Wp, int ctu) {
     if (G < 1 || G > 255) { set_error("G %d: must be in 1..255", G); return false; }
     if (Hp < ctu || Wp < ctu || Hp % ctu || Wp % ctu) {
@@ -150,12 +166,20 @@ xv_status check_launch(cudaError_t e, const char* what) {
     return XV_OK;
 }
 
+// Kernels issued by each launcher (for xv_ctx_launches).
+constexpr int kLaunchMinmax = 3, kLaunchBandq = 1, kLaunchQuant = 1, kLaunchMe = 1, kLaunchTqr = 1, kLaunchPsnr = 2,
+              kLaunchPersist = 1;
+
 // min/max (unless fixed) and the per-band quantiser constants into `bq`.
 xv_status prepare_bands(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, double* minmax,
                         int fixed, BandQ* bq, cudaStream_t st) {
-    if (fixed) return check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants");
+    if (fixed) {
+        c->launches += kLaunchBandq;
+        return check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants");
+    }
     xv_status s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * bands);
     if (s) return s;
+    c->launches += kLaunchMinmax;
     return check_launch(xvh::launch_minmax(src, dt, bands, (int64_t)T * H * W, (unsigned*)c->mm_enc.ptr, minmax, bq, st),
                         "min/max");
 }
@@ -168,6 +192,7 @@ xv_status psnr_into(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, i
     xv_status s = ensure(c, c->psnr_part, sizeof(xvh::PsnrPart) * (size_t)nblk * bands);
     if (s) return s;
     if ((s = ensure(c, c->psnr_out, sizeof(xvh::PsnrPart) * bands))) return s;
+    c->launches += kLaunchPsnr;
     s = check_launch(xvh::launch_psnr(src, dt, bands, T, H, W, planes, recon, Hp, Wp, bq,
                                       (xvh::PsnrPart*)c->psnr_part.ptr, nblk, (xvh::PsnrPart*)c->psnr_out.ptr, st),
                      "psnr");
@@ -213,6 +238,7 @@ bool valid_job(const xv_job* j) {
     if (!valid_cube(j->src, j->dtype, j->bands, j->T, j->H, j->W)) return false;
     if (!valid_params(&j->p)) return false;
     if (!j->planes || !j->recon) { set_error("job planes and recon buffers are required"); return false; }
+    if (!valid_planes(j->planes, j->recon, j->planes, 8)) return false;
     if (j->minmax_fixed && !j->minmax) { set_error("minmax_fixed needs a minmax array"); return false; }
     return true;
 }
@@ -256,8 +282,10 @@ void xv_destroy(xv_ctx* c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax,
-                      &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_ctl, &c->b_bits, &c->b_bandq, &c->b_minmax};
+                      &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq, &c->b_minmax};
     for (DevBuf* b : bufs) release(c, *b);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
 }
 
@@ -313,6 +341,7 @@ xv_status xv_quantize_pack(xv_ctx* c, const void* src, xv_dtype dt, int bands, i
     if (s) return s;
     BandQ* bq = (BandQ*)c->bandq.ptr;
     if ((s = prepare_bands(c, src, dt, bands, T, H, W, minmax, fixed, bq, st))) return s;
+    c->launches += kLaunchQuant;
     return check_launch(xvh::launch_quantize_pack(src, dt, bands, T, H, W, plane_dim(H, ctu), plane_dim(W, ctu), bq,
                                                   planes, st),
                         "quantize_pack");
@@ -324,7 +353,9 @@ xv_status xv_motion_search(xv_ctx* c, const uint16_t* cur, const uint16_t* ref, 
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
     if (!cur || !ref || !mv) { set_error("cur, ref and mv are required"); return XV_EINVAL; }
+    if (!valid_planes(cur, ref, cur, gstride)) return XV_EINVAL;
     DeviceGuard g(c->device);
+    c->launches += kLaunchMe;
     return check_launch(xvh::launch_me_frame(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride,
                                              (cudaStream_t)stream),
                         "motion_search");
@@ -337,7 +368,9 @@ xv_status xv_transform_quant_recon(xv_ctx* c, const uint16_t* cur, const uint16_
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
     if (!cur || !recon || !bits || (ref && !mv)) { set_error("cur, recon, bits (and mv with ref) are required"); return XV_EINVAL; }
+    if (!valid_planes(cur, ref ? ref : cur, recon, gstride)) return XV_EINVAL;
     DeviceGuard g(c->device);
+    c->launches += kLaunchTqr;
     return check_launch(xvh::launch_tqr_frame(cur, ref, mv, G, gstride, Hp, Wp, p, pu_gstride, recon, levels, tu_log2,
                                               bits, bits_gstride, (cudaStream_t)stream),
                         "transform_quant_recon");
@@ -355,6 +388,7 @@ xv_status xv_psnr(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int
     xv_status s = ensure(c, c->bandq, sizeof(BandQ) * bands);
     if (s) return s;
     BandQ* bq = (BandQ*)c->bandq.ptr;
+    c->launches += kLaunchBandq;
     if ((s = check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants"))) return s;
     return psnr_into(c, src, dt, bands, T, H, W, planes, recon, Hp, Wp, bq, psnr, mse, sse10, mean, st);
 }
@@ -386,6 +420,7 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
     if ((s = ensure(c, c->bandq, sizeof(BandQ) * j->bands))) return s;
     BandQ* bq = (BandQ*)c->bandq.ptr;
     if ((s = prepare_bands(c, j->src, j->dtype, j->bands, T, j->H, j->W, minmax, j->minmax_fixed, bq, st))) return s;
+    c->launches += kLaunchQuant;
     if ((s = check_launch(xvh::launch_quantize_pack(j->src, j->dtype, j->bands, T, j->H, j->W, Hp, Wp, bq, j->planes, st),
                           "quantize_pack")))
         return s;
@@ -408,6 +443,7 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
     for (int t = 0; t < T; ++t) {
         const uint16_t* cur = j->planes + t * fsz;
         const uint16_t* ref = t > 0 ? j->recon + (t - 1) * fsz : nullptr;
+        c->launches += kLaunchTqr + (ref ? kLaunchMe : 0);
         if (ref) {
             if ((s = check_launch(xvh::launch_me_frame(cur, ref, G, T * fsz, Hp, Wp, &p, mv + t * npu * 2,
                                                        j->cost ? j->cost + t * npu : nullptr, nullptr, nullptr, T * npu, st),
@@ -450,23 +486,24 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if ((s = ensure(c, c->b_jobs, sizeof(xvh::JobDev) * njobs))) return s;
     if ((s = ensure(c, c->b_bits, sizeof(uint64_t) * nbits))) return s;
     if ((s = ensure(c, c->b_rowdone, sizeof(unsigned) * nrows))) return s;
+    if ((s = ensure(c, c->b_depcnt, sizeof(unsigned) * nrows))) return s;
     if ((s = ensure(c, c->b_bandq, sizeof(BandQ) * XV_MAX_BANDS * njobs))) return s;
     if ((s = ensure(c, c->b_minmax, sizeof(double) * 2 * XV_MAX_BANDS * njobs))) return s;
     // one control block per CTU class (8, 16, 32, 64)
     if ((s = ensure(c, c->b_ctl, sizeof(xvh::BatchCtl) * 4))) return s;
     uint64_t* bits_all = (uint64_t*)c->b_bits.ptr;
     unsigned* rows_all = (unsigned*)c->b_rowdone.ptr;
+    unsigned* deps_all = (unsigned*)c->b_depcnt.ptr;
     BandQ* bq_all = (BandQ*)c->b_bandq.ptr;
     double* mm_all = (double*)c->b_minmax.ptr;
-    cudaError_t e = cudaMemsetAsync(rows_all, 0, sizeof(unsigned) * nrows, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bits_all, 0, sizeof(uint64_t) * nbits, st);
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    cudaError_t e = cudaSuccess;
     for (int i = 0; i < njobs; ++i) {
         const xv_job& j = jobs[i];
         const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
         double* mm = j.minmax ? j.minmax : mm_all + 2 * XV_MAX_BANDS * i;
         BandQ* bq = bq_all + XV_MAX_BANDS * i;
         if ((s = prepare_bands(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, mm, j.minmax_fixed, bq, st))) return s;
+        c->launches += kLaunchQuant;
         if ((s = check_launch(xvh::launch_quantize_pack(j.src, j.dtype, j.bands, j.T, j.H, j.W, Hp, Wp, bq, j.planes, st),
                               "quantize_pack")))
             return s;
@@ -479,59 +516,121 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         d.tu = j.tu_log2;
         d.bits = j.bits ? j.bits : bits_all + bits_off[i];
         d.rowdone = rows_all + row_off[i];
+        d.depcnt = deps_all + row_off[i];
         d.lf8 = j.p.lambda_fp8;
         d.lmv = j.p.lambda_mv_fp16;
         d.G = G; d.T = j.T; d.Hp = Hp; d.Wp = Wp; d.ctu = j.p.ctu; d.R = j.p.search_range; d.qp = j.p.qp;
         d.tu_mask = j.p.tu_mask;
         d.nx = Wp / j.p.ctu;
         d.ny = Hp / j.p.ctu;
-        if (j.bits && (e = cudaMemsetAsync(j.bits, 0, sizeof(uint64_t) * G * j.T, st)) != cudaSuccess)
-            return cuda_fail(e, "memset");
     }
     e = cudaMemcpyAsync(c->b_jobs.ptr, jd.data(), sizeof(xvh::JobDev) * njobs, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "job descriptors");
-    // frame-major work lists, one per CTU class
+    // ready queues, one per CTU class: every item of the class gets one slot;
+    // the first-frame items are queued at each launch, the rest by the kernel
+    // as the rows they read complete
     const int ctus[4] = {8, 16, 32, 64};
-    std::vector<uint64_t> items[4];
-    size_t smem[4] = {0, 0, 0, 0};
-    int maxT = 0;
-    for (int i = 0; i < njobs; ++i) maxT = jobs[i].T > maxT ? jobs[i].T : maxT;
-    for (int t = 0; t < maxT; ++t)
-        for (int i = 0; i < njobs; ++i) {
-            if (t >= jobs[i].T) continue;
-            const xvh::JobDev& d = jd[i];
-            const int k = d.ctu == 8 ? 0 : d.ctu == 16 ? 1 : d.ctu == 32 ? 2 : 3;
-            for (int gi = 0; gi < d.G; ++gi)
-                for (int pu = 0; pu < d.nx * d.ny; ++pu) items[k].push_back(xvh::make_item(i, gi, t, pu));
-            size_t need = xvh::persist_smem_bytes(d.ctu, d.R, jobs[i].T > 1);
-            smem[k] = need > smem[k] ? need : smem[k];
-        }
-    size_t total_items = 0;
-    for (auto& v : items) total_items += v.size();
-    if ((s = ensure(c, c->b_items, sizeof(uint64_t) * total_items))) return s;
-    uint64_t* items_dev = (uint64_t*)c->b_items.ptr;
-    xvh::BatchCtl* ctl = (xvh::BatchCtl*)c->b_ctl.ptr;
-    size_t off = 0;
-    for (int k = 0; k < 4; ++k) {
-        if (items[k].empty()) continue;
-        e = cudaMemcpyAsync(items_dev + off, items[k].data(), sizeof(uint64_t) * items[k].size(), cudaMemcpyHostToDevice, st);
-        xvh::BatchCtl h{0u, 0, c->stall_item >= 0 ? (unsigned)c->stall_item : 0xffffffffu, 0u, c->wait_budget};
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ctl + k, &h, sizeof h, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "work list");
-        const int grid = xvh::persist_grid(ctus[k], smem[k]);
-        if ((s = check_launch(xvh::launch_persist(ctus[k], (const xvh::JobDev*)c->b_jobs.ptr, items_dev + off,
-                                                  (unsigned)items[k].size(), ctl + k, smem[k], grid, st),
-                              "persistent encode")))
-            return s;
-        off += items[k].size();
+    std::vector<uint64_t> first[4];
+    size_t total[4] = {0, 0, 0, 0}, smem[4] = {0, 0, 0, 0};
+    std::string shape[4];
+    for (int i = 0; i < njobs; ++i) {
+        const xvh::JobDev& d = jd[i];
+        const int k = d.ctu == 8 ? 0 : d.ctu == 16 ? 1 : d.ctu == 32 ? 2 : 3;
+        for (int gi = 0; gi < d.G; ++gi)
+            for (int pu = 0; pu < d.nx * d.ny; ++pu) first[k].push_back(xvh::make_item(i, gi, 0, pu));
+        total[k] += (size_t)d.G * d.T * d.nx * d.ny;
+        size_t need = xvh::persist_smem_bytes(d.ctu, d.R, jobs[i].T > 1);
+        smem[k] = need > smem[k] ? need : smem[k];
+        char sh[96];
+        snprintf(sh, sizeof sh, "%d:%d:%d:%d:%d:%d;", d.G, d.T, d.Hp, d.Wp, d.R, jobs[i].T > 1);
+        shape[k] += sh;
     }
+    size_t total_items = 0;
+    for (int k = 0; k < 4; ++k) total_items += total[k];
+    if (total_items > 0xffffffffu) { set_error("too many work items in one batch"); return XV_EINVAL; }
+    if ((s = ensure(c, c->b_items, sizeof(uint64_t) * total_items))) return s;
+    uint64_t* queue_all = (uint64_t*)c->b_items.ptr;
+    xvh::BatchCtl* ctl = (xvh::BatchCtl*)c->b_ctl.ptr;
+    if (!c->ev0 && (e = cudaEventCreate(&c->ev0)) == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) return cuda_fail(e, "events");
+
+    // One complete run of the batch's persistent launches with block sizes
+    // nt[k]: counters, bits and queues reset, then the launches between the
+    // two events.
+    auto run = [&](const int nt[4]) -> xv_status {
+        cudaError_t err = cudaMemsetAsync(rows_all, 0, sizeof(unsigned) * nrows, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(deps_all, 0, sizeof(unsigned) * nrows, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(bits_all, 0, sizeof(uint64_t) * nbits, st);
+        for (int i = 0; i < njobs && err == cudaSuccess; ++i)
+            if (jobs[i].bits) err = cudaMemsetAsync(jobs[i].bits, 0, sizeof(uint64_t) * jd[i].G * jobs[i].T, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(queue_all, 0xff, sizeof(uint64_t) * total_items, st);
+        for (int k = 0, off = 0; k < 4 && err == cudaSuccess; ++k) {
+            if (!total[k]) continue;
+            err = cudaMemcpyAsync(queue_all + off, first[k].data(), sizeof(uint64_t) * first[k].size(),
+                                  cudaMemcpyHostToDevice, st);
+            xvh::BatchCtl h{0u, (unsigned)first[k].size(), (unsigned)total[k], 0, c->wait_budget, c->stall_row};
+            if (err == cudaSuccess) err = cudaMemcpyAsync(ctl + k, &h, sizeof h, cudaMemcpyHostToDevice, st);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(st);  // the host sources are locals
+            off += (int)total[k];
+        }
+        if (err != cudaSuccess) return cuda_fail(err, "ready queue");
+        if ((err = cudaEventRecord(c->ev0, st)) != cudaSuccess) return cuda_fail(err, "event");
+        for (int k = 0, off = 0; k < 4; ++k) {
+            if (!total[k]) continue;
+            const int grid = xvh::persist_grid(ctus[k], nt[k], smem[k]);
+            xv_status r2 = check_launch(xvh::launch_persist(ctus[k], nt[k], (const xvh::JobDev*)c->b_jobs.ptr,
+                                                            queue_all + off, ctl + k, smem[k], grid, st),
+                                        "persistent encode");
+            if (r2) return r2;
+            c->launches += kLaunchPersist;
+            c->batch_nt = nt[k];
+            off += (int)total[k];
+        }
+        if ((err = cudaEventRecord(c->ev1, st)) != cudaSuccess) return cuda_fail(err, "event");
+        return XV_OK;
+    };
+
+    // Autotuner: the first batch of a shape runs once with each block size
+    // (every run gives identical output) and keeps the fastest.
+    int nt[4] = {256, 256, 256, 256};
+    bool tune = false;
+    for (int k = 0; k < 4; ++k) {
+        if (!total[k]) continue;
+        auto it = c->tuned_nt.find(shape[k]);
+        if (it == c->tuned_nt.end()) tune = true;
+        else nt[k] = it->second;
+    }
+    if (c->force_nt) {
+        for (int k = 0; k < 4; ++k) nt[k] = c->force_nt;
+        tune = false;
+    }
+    if (tune && c->stall_row < 0) {
+        float best_ms = 1e30f;
+        int best_nt = 256;
+        for (int cand : xvh::kPersistBlockSizes) {
+            int trial[4] = {cand, cand, cand, cand};
+            if ((s = run(trial))) return s;
+            if ((e = cudaEventSynchronize(c->ev1)) != cudaSuccess) return cuda_fail(e, "autotune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+            if (ms < best_ms) { best_ms = ms; best_nt = cand; }
+        }
+        for (int k = 0; k < 4; ++k) {
+            if (!total[k]) continue;
+            c->tuned_nt[shape[k]] = best_nt;
+            nt[k] = best_nt;
+        }
+    }
+    if ((s = run(nt))) return s;
     // timeouts are reported before any result is read
     xvh::BatchCtl hc[4];
     e = cudaMemcpyAsync(hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "persistent encode");
+    float kms = 0.f;
+    if (cudaEventElapsedTime(&kms, c->ev0, c->ev1) == cudaSuccess) c->batch_ms = kms;
     for (int k = 0; k < 4; ++k)
-        if (!items[k].empty() && hc[k].err) {
+        if (total[k] && hc[k].err) {
             set_error("a dependency wait of the persistent encode (CTU %d) ran out of time", ctus[k]);
             for (int i = 0; i < njobs; ++i) results[i].status = XV_ETIMEOUT;
             return (xv_status)hc[k].err;
@@ -550,6 +649,20 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     return XV_OK;
 }
 
+xv_status xv_last_batch_block_size(const xv_ctx* c, int* nt) {
+    if (!c || !nt) { set_error("ctx and nt are required"); return XV_EINVAL; }
+    *nt = c->batch_nt;
+    return XV_OK;
+}
+
+xv_status xv_last_batch_kernel_ms(const xv_ctx* c, double* ms) {
+    if (!c || !ms) { set_error("ctx and ms are required"); return XV_EINVAL; }
+    *ms = c->batch_ms;
+    return XV_OK;
+}
+
+uint64_t xv_ctx_launches(const xv_ctx* c) { return c ? c->launches : 0; }
+
 // Test hooks for the bounded device waits of the persistent path.
 xv_status xv_debug_set_wait_budget(xv_ctx* c, long long cycles) {
     if (!c || cycles < 1) { set_error("bad wait budget"); return XV_EINVAL; }
@@ -557,9 +670,18 @@ xv_status xv_debug_set_wait_budget(xv_ctx* c, long long cycles) {
     return XV_OK;
 }
 
-xv_status xv_debug_stall_item(xv_ctx* c, long long item) {
+xv_status xv_debug_force_block_size(xv_ctx* c, int nt) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
-    c->stall_item = item;
+    bool ok = nt == 0;
+    for (int v : xvh::kPersistBlockSizes) ok = ok || nt == v;
+    if (!ok) { set_error("block size %d is not one the persistent kernel is built for", nt); return XV_EINVAL; }
+    c->force_nt = nt;
+    return XV_OK;
+}
+
+xv_status xv_debug_stall_row(xv_ctx* c, long long row) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    c->stall_row = row;
     return XV_OK;
 }
 

@@ -118,13 +118,20 @@ __device__ __forceinline__ QuantParams quant_params(int qp, int log2n) {
 }
 
 __device__ __forceinline__ int quantize(int c, const QuantParams& q) {
-    int64_t a = c < 0 ? -(int64_t)c : (int64_t)c;
-    int64_t m = (a * q.qscale + q.offset) >> q.qbits;
+    const unsigned a = c < 0 ? 0u - (unsigned)c : (unsigned)c;
+    int64_t m;
+    if (a < 65536u) {
+        // |c| < 2^16, scale < 2^15, offset < 2^26: the sum fits 32 bits
+        m = (int64_t)((a * (unsigned)q.qscale + (unsigned)q.offset) >> q.qbits);
+    } else {
+        m = ((int64_t)a * q.qscale + q.offset) >> q.qbits;
+    }
     if (m > 32767) m = c < 0 ? 32768 : 32767;  // int16 clip of +/- magnitude
     return c < 0 ? -(int)m : (int)m;
 }
 
 __device__ __forceinline__ int dequantize(int level, const QuantParams& q) {
+    if (level == 0) return 0;  // (0 + 2^(bd-1)) >> bd
     int64_t v = ((int64_t)level * q.dqscale + ((int64_t)1 << (q.bd - 1))) >> q.bd;
     return v < -32768 ? -32768 : (v > 32767 ? 32767 : (int)v);
 }
@@ -151,6 +158,18 @@ __device__ __forceinline__ int luma_tap(int f, int i) {
     return (i == 0 || i == 7) ? -1 : (i == 1 || i == 6) ? 4 : (i == 2 || i == 5) ? -11 : 40;
 }
 
+// All 8 taps of phase f (1..3) in registers, so the filter loops multiply by
+// register values instead of re-deriving each tap.
+__device__ __forceinline__ void luma_taps(int f, int (&t)[8]) {
+    if (f == 2) {
+        t[0] = -1; t[1] = 4; t[2] = -11; t[3] = 40; t[4] = 40; t[5] = -11; t[6] = 4; t[7] = -1;
+    } else if (f == 1) {
+        t[0] = -1; t[1] = 4; t[2] = -10; t[3] = 58; t[4] = 17; t[5] = -5; t[6] = 1; t[7] = 0;
+    } else {
+        t[0] = 0; t[1] = 1; t[2] = -5; t[3] = 17; t[4] = 58; t[5] = -10; t[6] = 4; t[7] = -1;
+    }
+}
+
 // Intermediate shifts for B = 10: shift1 = B - 8, shift2 = 6, full-sample
 // scale 2^(14 - B); weighted-prediction rounding back to B bits.
 constexpr int kShift1 = kBitDepth - 8;
@@ -167,6 +186,11 @@ template <bool kCoherent>
 __device__ __forceinline__ int ld_ref(const uint16_t* p) {
     if constexpr (kCoherent) return (int)__ldcg(p);
     else return (int)__ldg(p);
+}
+template <bool kCoherent>
+__device__ __forceinline__ uint4 ld_ref16(const uint4* p) {
+    if constexpr (kCoherent) return __ldcg(p);
+    else return __ldg(p);
 }
 
 }  // namespace xvd

@@ -67,29 +67,34 @@ struct JobDev {
     uint8_t* tu;             // [G][T][nPU] or null
     uint64_t* bits;          // [G][T]
     unsigned* rowdone;       // [G][T][ny]: finished PUs per CTU row
+    unsigned* depcnt;        // [G][T][ny]: finished rows of the previous frame a row reads
     int64_t lf8, lmv;
     int G, T, Hp, Wp, ctu, R, qp;
     unsigned tu_mask;
     int nx, ny;
 };
 
-// Work-queue control block (device).
+// Ready-queue control block (device).
 struct BatchCtl {
-    unsigned next;         // next ticket
+    unsigned head;         // next queue position to take
+    unsigned tail;         // next queue position to fill
+    unsigned total;        // items in the launch (every item is queued once)
     int err;               // 0, or an xv_status (XV_ETIMEOUT) set by a block
-    unsigned stall_item;   // test hook: this item's dependency can never be met
-    unsigned pad;
     long long budget;      // spin budget per wait, in SM clock cycles
+    long long stall_row;   // test hook: this dependency counter never completes (-1: none)
 };
 
-// Item key: job (8 bits) | group (8) | frame (16) | PU (32), frame-major order.
+// Item key: job (8 bits) | group (8) | frame (16) | PU (32).
+constexpr uint64_t kEmptyItem = ~0ull;
 inline uint64_t make_item(int job, int g, int t, int pu) {
     return ((uint64_t)job << 56) | ((uint64_t)g << 48) | ((uint64_t)t << 32) | (uint32_t)pu;
 }
 
 size_t persist_smem_bytes(int ctu, int R, bool has_me);
-cudaError_t launch_persist(int ctu, const JobDev* jobs, const uint64_t* items, unsigned nitems, BatchCtl* ctl,
-                           size_t smem, int grid, cudaStream_t st);
-int persist_grid(int ctu, size_t smem);
+// Block sizes the persistent kernel is built for (the autotuner picks one).
+constexpr int kPersistBlockSizes[3] = {128, 192, 256};
+cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,
+                           int grid, cudaStream_t st);
+int persist_grid(int ctu, int nt, size_t smem);
 
 }  // namespace xvh

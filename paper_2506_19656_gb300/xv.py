@@ -69,8 +69,12 @@ _SIGS = {
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
     "xv_encode_batch": [_vp, ctypes.POINTER(xv_job), _i, ctypes.POINTER(xv_result), _vp],
+    "xv_last_batch_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_double)],
+    "xv_last_batch_block_size": [_vp, ctypes.POINTER(_i)],
+    "xv_ctx_launches": [_vp],
     "xv_debug_set_wait_budget": [_vp, ctypes.c_longlong],
-    "xv_debug_stall_item": [_vp, ctypes.c_longlong],
+    "xv_debug_force_block_size": [_vp, _i],
+    "xv_debug_stall_row": [_vp, ctypes.c_longlong],
 }
 
 
@@ -88,6 +92,7 @@ def lib():
         L.xv_destroy.restype = None
         L.xv_ctx_bytes.restype = ctypes.c_size_t
         L.xv_job_scratch_bytes.restype = ctypes.c_size_t
+        L.xv_ctx_launches.restype = ctypes.c_uint64
         L.xv_last_error.restype = ctypes.c_char_p
         L.xv_status_string.restype = ctypes.c_char_p
         L.xv_status_string.argtypes = [_i]
@@ -220,12 +225,32 @@ def xv_encode_batch(ctx: Context, jobs, stream=None) -> list:
     return [r.as_dict() for r in res]
 
 
+def xv_last_batch_kernel_ms(ctx: Context) -> float:
+    ms = ctypes.c_double()
+    check(lib().xv_last_batch_kernel_ms(ctx.handle, ctypes.byref(ms)), "xv_last_batch_kernel_ms")
+    return ms.value
+
+
+def xv_last_batch_block_size(ctx: Context) -> int:
+    nt = _i()
+    check(lib().xv_last_batch_block_size(ctx.handle, ctypes.byref(nt)), "xv_last_batch_block_size")
+    return nt.value
+
+
+def xv_ctx_launches(ctx: Context) -> int:
+    return int(lib().xv_ctx_launches(ctx.handle))
+
+
 def xv_debug_set_wait_budget(ctx: Context, cycles: int):
     check(lib().xv_debug_set_wait_budget(ctx.handle, cycles), "xv_debug_set_wait_budget")
 
 
-def xv_debug_stall_item(ctx: Context, item: int):
-    check(lib().xv_debug_stall_item(ctx.handle, item), "xv_debug_stall_item")
+def xv_debug_force_block_size(ctx: Context, block_size: int):
+    check(lib().xv_debug_force_block_size(ctx.handle, block_size), "xv_debug_force_block_size")
+
+
+def xv_debug_stall_row(ctx: Context, row: int):
+    check(lib().xv_debug_stall_row(ctx.handle, row), "xv_debug_stall_row")
 
 
 # ------------------------------------------------------------ tensor helpers

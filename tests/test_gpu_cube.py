@@ -101,6 +101,28 @@ def test_ragged_shapes_and_mixed_batch(xv, ctx):
     assert_matches(b, xv.xv_encode_cube(ctx, j), wants[0])
 
 
+@pytest.mark.parametrize("block_size", [128, 192, 256])
+def test_every_block_size_is_bit_exact(xv, ctx, block_size):
+    """The autotuner's candidates all give the oracle's bytes (mixed CTU sizes)."""
+    specs = [((4, 4, 40, 56), 8, 6, 0b1100, 30), ((5, 3, 37, 53), 16, 9, 0b11100, 22),
+             ((2, 3, 70, 33), 32, 5, 0b111100, 27)]
+    jobs, bufs, wants = [], [], []
+    for i, (shape, ctu, R, mask, qp) in enumerate(specs):
+        cube, _ = synth.tiny_cube(300 + i, T=shape[1], H=shape[2], W=shape[3], bands=shape[0])
+        wants.append(oracle.encode_cube(cube, ctu, R, mask, qp))
+        j, b = gpu_job(xv, cube, ctu, R, mask, qp)
+        jobs.append(j)
+        bufs.append(b)
+    xv.xv_debug_force_block_size(ctx, block_size)
+    try:
+        results = xv.xv_encode_batch(ctx, jobs)
+        assert xv.xv_last_batch_block_size(ctx) == block_size
+    finally:
+        xv.xv_debug_force_block_size(ctx, 0)
+    for b, r, w in zip(bufs, results, wants):
+        assert_matches(b, r, w)
+
+
 def test_uint16_dynamicearthnet_prefix(xv, ctx):
     """Two frames of a DynamicEarthNet-shaped uint16 cube (CTU 64, R 64, TU 4-32),
     with a min/max fixed in advance (as a causal prefix of a longer cube would)."""
@@ -119,11 +141,11 @@ def test_batch_timeout_is_reported_and_context_survives(xv, ctx):
     cube = synth.make_cube(0, T=3)
     job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
     xv.xv_debug_set_wait_budget(ctx, 20_000_000)  # ~10 ms
-    xv.xv_debug_stall_item(ctx, 70)  # an item of frame 1
+    xv.xv_debug_stall_row(ctx, 8 + 3)  # frame 1, CTU row 3 (8 rows per frame)
     with pytest.raises(xv.XvError) as e:
         xv.xv_encode_batch(ctx, [job])
     assert e.value.status == xv.XV_ETIMEOUT
-    xv.xv_debug_stall_item(ctx, -1)
+    xv.xv_debug_stall_row(ctx, -1)
     xv.xv_debug_set_wait_budget(ctx, 4_000_000_000)
     want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27)
     job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
