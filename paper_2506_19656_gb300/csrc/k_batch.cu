@@ -68,30 +68,33 @@ __device__ uint64_t take_item(uint64_t* queue, unsigned pos, BatchCtl* ctl) {
     }
 }
 
-// Thread 0, after the item's writes are fenced: count the PU in its row; if
-// the row is complete, credit the next frame's rows that read it and queue
-// those that become ready.
-__device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, uint64_t* queue, BatchCtl* ctl) {
+// After the item's writes are fenced: thread 0 counts the PU in its row; if
+// the row is complete, one thread per next-frame row that reads it credits
+// that row's dependency counter and queues its items when the count is
+// reached (the credits go out in parallel instead of one after another).
+__device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, uint64_t* queue, BatchCtl* ctl,
+                              int* s_full) {
     const int row = pu / J.nx;
     const int64_t f = (int64_t)g * J.T + t;
-    if (atomicAdd(J.rowdone + f * J.ny + row, 1u) + 1u != (unsigned)J.nx) return;
-    if (t + 1 >= J.T) return;
+    if (threadIdx.x == 0)
+        *s_full = (atomicAdd(J.rowdone + f * J.ny + row, 1u) + 1u == (unsigned)J.nx) && (t + 1 < J.T);
+    __syncthreads();
+    if (!*s_full) return;
     const int reach = (J.R + 4 + J.ctu - 1) / J.ctu + 1;
-    for (int r = row - reach; r <= row + reach; ++r) {
-        if (r < 0 || r >= J.ny) continue;
-        int r0, r1;
-        dep_rows(r, J.ctu, J.R, J.ny, r0, r1);
-        if (row < r0 || row > r1) continue;
-        const int64_t di = (f + 1) * J.ny + r;
-        const unsigned need = (unsigned)(r1 - r0 + 1) + (ctl->stall_row == (long long)di && job == 0 ? 1u : 0u);
-        if (atomicAdd(J.depcnt + di, 1u) + 1u == need) {
-            __threadfence();
-            const unsigned base = atomicAdd(&ctl->tail, (unsigned)J.nx);
-            for (int i = 0; i < J.nx; ++i) {
-                const uint64_t key = ((uint64_t)job << 56) | ((uint64_t)g << 48) | ((uint64_t)(t + 1) << 32) |
-                                     (uint32_t)(r * J.nx + i);
-                asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(queue + base + i), "l"(key) : "memory");
-            }
+    const int r = row - reach + (int)threadIdx.x;
+    if ((int)threadIdx.x > 2 * reach || r < 0 || r >= J.ny) return;
+    int r0, r1;
+    dep_rows(r, J.ctu, J.R, J.ny, r0, r1);
+    if (row < r0 || row > r1) return;
+    const int64_t di = (f + 1) * J.ny + r;
+    const unsigned need = (unsigned)(r1 - r0 + 1) + (ctl->stall_row == (long long)di && job == 0 ? 1u : 0u);
+    if (atomicAdd(J.depcnt + di, 1u) + 1u == need) {
+        __threadfence();
+        const unsigned base = atomicAdd(&ctl->tail, (unsigned)J.nx);
+        for (int i = 0; i < J.nx; ++i) {
+            const uint64_t key = ((uint64_t)job << 56) | ((uint64_t)g << 48) | ((uint64_t)(t + 1) << 32) |
+                                 (uint32_t)(r * J.nx + i);
+            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(queue + base + i), "l"(key) : "memory");
         }
     }
 }
@@ -123,6 +126,7 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_pos, s_next;
     __shared__ uint64_t s_key;
+    __shared__ int s_full;
     const unsigned total = ctl->total;
     if (threadIdx.x == 0) s_next = atomicAdd(&ctl->head, 1u);
     for (;;) {
@@ -144,7 +148,7 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
             item_work<N, kNT>(J, g, t, pu, smem);
             __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0) complete_item(J, job, g, t, pu, queue, ctl);
+            complete_item(J, job, g, t, pu, queue, ctl, &s_full);
         }
         __syncthreads();
     }

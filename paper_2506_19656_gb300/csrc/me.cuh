@@ -156,6 +156,23 @@ __device__ __forceinline__ void row_sad8f(const int* __restrict__ crow_i, const 
     }
 }
 
+// SAD of one candidate over one block row (the last column of candidates
+// when 2R + 1 = 8m + 1).
+template <int W>
+__device__ __forceinline__ uint32_t row_sad1(const int* __restrict__ crow, const int* __restrict__ rrow,
+                                             uint32_t acc) {
+#pragma unroll
+    for (int c = 0; c < W; c += 4) {
+        int4 a = *reinterpret_cast<const int4*>(crow + c);
+        int4 b = *reinterpret_cast<const int4*>(rrow + c);
+        acc = __sad(a.x, b.x, acc);
+        acc = __sad(a.y, b.y, acc);
+        acc = __sad(a.z, b.z, acc);
+        acc = __sad(a.w, b.w, acc);
+    }
+    return acc;
+}
+
 // In-register 8-point Hadamard (Sylvester order) of v.
 __device__ __forceinline__ void hadamard8_row(int (&v)[8]) {
 #pragma unroll
@@ -415,9 +432,15 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     __syncthreads();
 
     // ---- integer full search
+    // Units: (dy, 8 consecutive dx) for the first 8m columns of candidates;
+    // when 2R + 1 = 8m + 1 the last column is a unit of its own (one
+    // candidate per dy), else it is covered by an 8-wide unit that discards
+    // the candidates beyond R.
     const int side = 2 * R + 1;
-    const int ngx = (side + 7) / 8;
-    const int units = side * ngx;
+    const int full = side / 8;
+    const bool lastcol = side - 8 * full == 1;
+    const int ngx = lastcol ? full : (side + 7) / 8;  // 8-wide column groups
+    const int units = side * ngx + (lastcol ? side : 0);
     const int P = me_split(units, NT);      // lanes sharing one unit (rows interleaved)
     const int q = tid & (P - 1);
     const unsigned pmask = P == 1 ? 0u : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
@@ -426,23 +449,36 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         int gx = u / side;
         int dy = u - gx * side - R;
         int dx0 = gx * 8 - R;
+        const int woff = (dy + R + 4) * S + (dx0 + R + 4);
+        const uint32_t rowbase = (uint32_t)((dy + R) * side);
+        const int by = s_bitsd[dy + R];
+        if (gx == ngx) {  // the single last column, dx = R
+            uint32_t sad1 = 0;
+            for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, win + woff + r * S, sad1);
+            for (int o = 1; o < P; o <<= 1) sad1 += __shfl_xor_sync(pmask, sad1, o);
+            if (q == 0) {
+                const uint32_t J = sad1 + s_costb[s_bitsd[2 * R] + by];
+                const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(2 * R));
+                best = key < best ? key : best;
+            }
+            continue;
+        }
         uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         float accf[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int woff = (dy + R + 4) * S + (dx0 + R + 4);
-        // every third row of a lane on the FP32 pipe, the others on the
-        // integer ALU (by iteration, so the lanes of a warp agree)
+        // rows in triples: two on the integer ALU, the third on the FP32 pipe
+        int r = q;
 #pragma unroll 1
-        for (int i = 0, r = q; r < N; ++i, r += P) {
-            if (i % 3 == 2) row_sad8f<N>(blk + r * N, win + woff + r * S, accf);
-            else row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+        for (; r + 2 * P < N; r += 3 * P) {
+            row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+            row_sad8<N>(blk + (r + P) * N, win + woff + (r + P) * S, sad);
+            row_sad8f<N>(blk + (r + 2 * P) * N, win + woff + (r + 2 * P) * S, accf);
         }
+        for (; r < N; r += P) row_sad8<N>(blk + r * N, win + woff + r * S, sad);
 #pragma unroll
         for (int k = 0; k < 8; ++k) sad[k] += (uint32_t)accf[k];
         for (int o = 1; o < P; o <<= 1)
 #pragma unroll
             for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
-        const uint32_t rowbase = (uint32_t)((dy + R) * side);
-        const int by = s_bitsd[dy + R];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int dx = dx0 + k;
