@@ -168,6 +168,28 @@ xv_status xv_psnr(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T
                   double* psnr_band, double* mse_band, uint64_t* sse10_band, double* psnr_mean,
                   void* stream);
 
+/* The same PSNR reduction for callers that cannot allocate device memory:
+ * for example a process whose device memory belongs to another allocator (a
+ * framework's caching pool or a fixed budget that raw cudaMalloc would
+ * bypass), or a code path that must not call cudaMalloc/cudaFree because
+ * those calls can block on the device or fail part-way through a run.  It
+ * takes no context and allocates nothing: its scratch is a fixed device
+ * array of about 129 KB inside the library, which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart; this
+ * is a deployment variant of xv_psnr with identical results.
+ *  - Limits: bands <= XV_MAX_BANDS (16); larger requests return XV_EINVAL.
+ *  - The first call on each device (with that device current) looks up the
+ *    array's device address with cudaGetSymbolAddress and keeps it; make that
+ *    first call before any stream capture.
+ *  - All calls share the array.  Each call rewrites everything it reads, so
+ *    nothing carries over from an earlier call, but calls that overlap on the
+ *    GPU (different streams or threads at the same time) race on it.
+ * Arguments and outputs as xv_psnr (host outputs; synchronous). */
+xv_status xv_psnr_noalloc(const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                          const uint16_t* planes, const uint16_t* recon, int Hp, int Wp,
+                          const double* minmax, double* psnr_band, double* mse_band,
+                          uint64_t* sse10_band, double* psnr_mean, void* stream);
+
 /* ------------------------------------------------------ whole cubes */
 
 /* One cube.  Device buffers, caller-owned: */

@@ -66,6 +66,7 @@ _SIGS = {
     "xv_transform_quant_recon": [_vp, _vp, _vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp,
                                  _vp, _vp, _i64, _vp],
     "xv_psnr": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "xv_psnr_noalloc": [_vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
     "xv_encode_batch": [_vp, ctypes.POINTER(xv_job), _i, ctypes.POINTER(xv_result), _vp],
@@ -200,6 +201,21 @@ def xv_psnr(ctx: Context, src, planes, recon, minmax, stream=None):
     mean = ctypes.c_double()
     check(lib().xv_psnr(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, _ptr(planes), _ptr(recon), Hp, Wp,
                         _ptr(minmax), ps, mse, s10, ctypes.byref(mean), _stream(stream)), "xv_psnr")
+    return dict(psnr_band=list(ps), mse_band=list(mse), sse10_band=list(s10), psnr_mean=mean.value)
+
+
+def xv_psnr_noalloc(src, planes, recon, minmax, stream=None):
+    """xv_psnr without a context or any device allocation (fixed scratch in
+    the library); same results.  Returns dict(psnr_band, mse_band, sse10_band,
+    psnr_mean)."""
+    bands, T, H, W = src.shape
+    Hp, Wp = planes.shape[-2:]
+    ps = (ctypes.c_double * bands)()
+    mse = (ctypes.c_double * bands)()
+    s10 = (ctypes.c_uint64 * bands)()
+    mean = ctypes.c_double()
+    check(lib().xv_psnr_noalloc(_ptr(src), _dtype_code(src), bands, T, H, W, _ptr(planes), _ptr(recon), Hp, Wp,
+                                _ptr(minmax), ps, mse, s10, ctypes.byref(mean), _stream(stream)), "xv_psnr_noalloc")
     return dict(psnr_band=list(ps), mse_band=list(mse), sse10_band=list(s10), psnr_mean=mean.value)
 
 
