@@ -247,6 +247,13 @@ xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result*
  * on this context (CUDA events recorded on the call's stream around the
  * launches), in milliseconds.  Host only. */
 xv_status xv_last_batch_kernel_ms(const xv_ctx* ctx, double* ms);
+/* xv_encode_batch runs a batch as one CUDA graph: captured on the first call
+ * with a given set of jobs (shapes, parameters and buffer pointers) and the
+ * autotuned block size, replayed while the same batch is submitted again.
+ * `enable` = 0 launches the same kernels directly instead.  Host only. */
+xv_status xv_set_batch_graphs(xv_ctx* ctx, int enable);
+/* Graphs captured and graph launches so far on this context.  Host only. */
+xv_status xv_batch_graph_stats(const xv_ctx* ctx, uint64_t* captures, uint64_t* launches);
 /* Threads per block of the last xv_encode_batch persistent launch (the
  * autotuner's choice for that batch shape).  Host only. */
 xv_status xv_last_batch_block_size(const xv_ctx* ctx, int* block_size);

@@ -154,6 +154,53 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
     }
 }
 
+// Batch prologue: block j < njobs handles job j (bits, first-frame items);
+// the others clear the row counters and fill the empty queue slots; block 0
+// also writes the control blocks.
+__global__ void k_batch_prologue(const JobDev* __restrict__ jobs, int njobs, const ClassDev* __restrict__ cls,
+                                 uint64_t* queue, BatchCtl* ctl, unsigned* rows, unsigned* deps, int64_t nrows,
+                                 long long budget, long long stall_row) {
+    const int b = blockIdx.x;
+    if (b < njobs) {
+        const JobDev& J = jobs[b];
+        const int64_t nb = (int64_t)J.G * J.T, npu = (int64_t)J.nx * J.ny;
+        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) J.bits[i] = 0ull;
+        for (int64_t i = threadIdx.x; i < (int64_t)J.G * npu; i += blockDim.x) {
+            const int g = (int)(i / npu), pu = (int)(i - (int64_t)g * npu);
+            queue[J.qfirst + i] = ((uint64_t)b << 56) | ((uint64_t)g << 48) | (uint32_t)pu;
+        }
+        return;
+    }
+    const int64_t stride = (int64_t)(gridDim.x - njobs) * blockDim.x;
+    const int64_t start = (int64_t)(b - njobs) * blockDim.x + threadIdx.x;
+    for (int64_t i = start; i < nrows; i += stride) { rows[i] = 0u; deps[i] = 0u; }
+    for (int k = 0; k < 4; ++k) {
+        const int64_t lo = cls[k].qoff + cls[k].nfirst, hi = cls[k].qoff + cls[k].total;
+        for (int64_t i = lo + start; i < hi; i += stride) queue[i] = kEmptyItem;
+    }
+    if (b == njobs && threadIdx.x < 4) {
+        const int k = threadIdx.x;
+        ctl[k] = BatchCtl{0u, cls[k].nfirst, cls[k].total, 0, budget, stall_row};
+    }
+}
+
+__global__ void k_bits_totals(const JobDev* __restrict__ jobs, unsigned long long* totals) {
+    const JobDev& J = jobs[blockIdx.x];
+    const int64_t nb = (int64_t)J.G * J.T;
+    unsigned long long s = 0;
+    for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) s += J.bits[i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ unsigned long long red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        totals[blockIdx.x] = t;
+    }
+}
+
 using PersistFn = void (*)(const JobDev*, uint64_t*, BatchCtl*);
 template <int NT>
 PersistFn persist_fn_nt(int ctu) {
@@ -176,6 +223,18 @@ PersistFn persist_fn(int ctu, int nt) {
 
 }  // namespace
 
+cudaError_t launch_batch_prologue(const JobDev* jobs, int njobs, const ClassDev* cls, uint64_t* queue,
+                                  BatchCtl* ctl, unsigned* rows, unsigned* deps, int64_t nrows, long long budget,
+                                  long long stall_row, cudaStream_t st) {
+    k_batch_prologue<<<njobs + 64, 256, 0, st>>>(jobs, njobs, cls, queue, ctl, rows, deps, nrows, budget, stall_row);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long* totals, cudaStream_t st) {
+    k_bits_totals<<<njobs, 256, 0, st>>>(jobs, totals);
+    return cudaGetLastError();
+}
+
 size_t persist_smem_bytes(int ctu, int R, bool has_me) {
     size_t a = xvd::tqr_smem_bytes(ctu);
     size_t b = has_me ? xvd::me_smem_bytes(ctu, R) : 0;
@@ -188,8 +247,11 @@ int persist_grid(int ctu, int nt, size_t smem) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nt, smem);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nt, smem) != cudaSuccess) {
+        cudaGetLastError();  // reported by the launch that follows, not left behind
+        per = 1;
+    }
     if (per < 1) per = 1;
     return sms * per;
 }

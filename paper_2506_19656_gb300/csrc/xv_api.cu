@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -33,6 +34,16 @@ struct xv_ctx {
     int batch_nt = 0;                        // block size of the last persistent launch
     std::map<std::string, int> tuned_nt;     // autotuner: batch shape -> block size
     int force_nt = 0;                        // test hook (xv_debug_force_block_size)
+    // batched path: buffers, work stream and the captured graph
+    DevBuf b_cls, b_part, b_out, b_totals;
+    void* h_stage = nullptr;                 // pinned host copy of a batch's results
+    size_t h_stage_bytes = 0;
+    cudaStream_t work = nullptr;             // batches run here (capturable, ordered after the caller's stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // setup, persistent kernels, results
+    std::string graph_key;
+    int use_graph = 1;
+    uint64_t graph_launches = 0, graph_captures = 0;
 };
 
 namespace xvh {
@@ -282,8 +293,15 @@ void xv_destroy(xv_ctx* c) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax,
-                      &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq, &c->b_minmax};
+                      &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
+                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals};
     for (DevBuf* b : bufs) release(c, *b);
+    for (cudaGraphExec_t& gx : c->graph)
+        if (gx) cudaGraphExecDestroy(gx);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->work) cudaStreamDestroy(c->work);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
@@ -469,12 +487,27 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     for (int i = 0; i < njobs; ++i)
         if (!valid_job(&jobs[i])) return XV_EINVAL;
     DeviceGuard g(c->device);
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t caller = (cudaStream_t)stream;
     xv_status s;
-    // per-job device descriptors and internal buffers
+    cudaError_t e = cudaSuccess;
+    if (!c->work) {
+        if ((e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking)) == cudaSuccess &&
+            (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventCreate(&c->ev0)) == cudaSuccess)
+            e = cudaEventCreate(&c->ev1);
+        if (e != cudaSuccess) return cuda_fail(e, "work stream");
+    }
+    cudaStream_t st = c->work;
+
+    // ---- geometry, descriptors, queue layout (host)
+    const int ctus[4] = {8, 16, 32, 64};
     std::vector<xvh::JobDev> jd(njobs);
-    std::vector<int64_t> bits_off(njobs), row_off(njobs);
-    int64_t nbits = 0, nrows = 0;
+    std::vector<int64_t> bits_off(njobs), row_off(njobs), part_off(njobs);
+    std::vector<int> nblk(njobs);
+    int64_t nbits = 0, nrows = 0, nparts = 0;
+    size_t total[4] = {0, 0, 0, 0}, nfirst[4] = {0, 0, 0, 0}, smem[4] = {0, 0, 0, 0};
+    std::string shape[4];
     for (int i = 0; i < njobs; ++i) {
         const xv_job& j = jobs[i];
         const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
@@ -482,32 +515,57 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         nbits += (int64_t)G * j.T;
         row_off[i] = nrows;
         nrows += (int64_t)G * j.T * (Hp / j.p.ctu);
+        nblk[i] = xvh::psnr_blocks_per_band((int64_t)j.T * j.H * j.W);
+        part_off[i] = nparts;
+        nparts += (int64_t)nblk[i] * j.bands;
+        const int k = j.p.ctu == 8 ? 0 : j.p.ctu == 16 ? 1 : j.p.ctu == 32 ? 2 : 3;
+        const int64_t npu = (int64_t)(Hp / j.p.ctu) * (Wp / j.p.ctu);
+        total[k] += (size_t)G * j.T * npu;
+        nfirst[k] += (size_t)G * npu;
+        smem[k] = std::max(smem[k], xvh::persist_smem_bytes(j.p.ctu, j.p.search_range, j.T > 1));
+        char sh[96];
+        snprintf(sh, sizeof sh, "%d:%d:%d:%d:%d:%d;", G, j.T, Hp, Wp, j.p.search_range, j.T > 1);
+        shape[k] += sh;
     }
+    size_t total_items = 0;
+    xvh::ClassDev cls[4];
+    for (int k = 0; k < 4; ++k) {
+        cls[k] = xvh::ClassDev{(int64_t)total_items, (unsigned)total[k], (unsigned)nfirst[k]};
+        total_items += total[k];
+    }
+    if (total_items > 0xffffffffu) { set_error("too many work items in one batch"); return XV_EINVAL; }
     if ((s = ensure(c, c->b_jobs, sizeof(xvh::JobDev) * njobs))) return s;
     if ((s = ensure(c, c->b_bits, sizeof(uint64_t) * nbits))) return s;
     if ((s = ensure(c, c->b_rowdone, sizeof(unsigned) * nrows))) return s;
     if ((s = ensure(c, c->b_depcnt, sizeof(unsigned) * nrows))) return s;
     if ((s = ensure(c, c->b_bandq, sizeof(BandQ) * XV_MAX_BANDS * njobs))) return s;
     if ((s = ensure(c, c->b_minmax, sizeof(double) * 2 * XV_MAX_BANDS * njobs))) return s;
-    // one control block per CTU class (8, 16, 32, 64)
     if ((s = ensure(c, c->b_ctl, sizeof(xvh::BatchCtl) * 4))) return s;
+    if ((s = ensure(c, c->b_cls, sizeof(xvh::ClassDev) * 4))) return s;
+    if ((s = ensure(c, c->b_items, sizeof(uint64_t) * total_items))) return s;
+    if ((s = ensure(c, c->b_part, sizeof(xvh::PsnrPart) * nparts))) return s;
+    if ((s = ensure(c, c->b_out, sizeof(xvh::PsnrPart) * XV_MAX_BANDS * njobs))) return s;
+    if ((s = ensure(c, c->b_totals, sizeof(unsigned long long) * njobs))) return s;
+    if ((s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * XV_MAX_BANDS))) return s;
+    const size_t stage_bytes = sizeof(xvh::BatchCtl) * 4 + sizeof(unsigned long long) * njobs +
+                               (sizeof(xvh::PsnrPart) + sizeof(BandQ)) * XV_MAX_BANDS * njobs;
+    if (c->h_stage_bytes < stage_bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        if ((e = cudaMallocHost(&c->h_stage, stage_bytes)) != cudaSuccess) return cuda_fail(e, "pinned staging");
+        c->h_stage_bytes = stage_bytes;
+    }
     uint64_t* bits_all = (uint64_t*)c->b_bits.ptr;
-    unsigned* rows_all = (unsigned*)c->b_rowdone.ptr;
-    unsigned* deps_all = (unsigned*)c->b_depcnt.ptr;
     BandQ* bq_all = (BandQ*)c->b_bandq.ptr;
     double* mm_all = (double*)c->b_minmax.ptr;
-    cudaError_t e = cudaSuccess;
+    size_t qnext[4];
+    for (int k = 0; k < 4; ++k) qnext[k] = (size_t)cls[k].qoff;
     for (int i = 0; i < njobs; ++i) {
         const xv_job& j = jobs[i];
-        const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
-        double* mm = j.minmax ? j.minmax : mm_all + 2 * XV_MAX_BANDS * i;
-        BandQ* bq = bq_all + XV_MAX_BANDS * i;
-        if ((s = prepare_bands(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, mm, j.minmax_fixed, bq, st))) return s;
-        c->launches += kLaunchQuant;
-        if ((s = check_launch(xvh::launch_quantize_pack(j.src, j.dtype, j.bands, j.T, j.H, j.W, Hp, Wp, bq, j.planes, st),
-                              "quantize_pack")))
-            return s;
         xvh::JobDev& d = jd[i];
+        const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
+        const int k = j.p.ctu == 8 ? 0 : j.p.ctu == 16 ? 1 : j.p.ctu == 32 ? 2 : 3;
         d.planes = j.planes;
         d.recon = j.recon;
         d.mv = j.mv;
@@ -515,83 +573,109 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         d.levels = j.levels;
         d.tu = j.tu_log2;
         d.bits = j.bits ? j.bits : bits_all + bits_off[i];
-        d.rowdone = rows_all + row_off[i];
-        d.depcnt = deps_all + row_off[i];
+        d.rowdone = (unsigned*)c->b_rowdone.ptr + row_off[i];
+        d.depcnt = (unsigned*)c->b_depcnt.ptr + row_off[i];
         d.lf8 = j.p.lambda_fp8;
         d.lmv = j.p.lambda_mv_fp16;
         d.G = G; d.T = j.T; d.Hp = Hp; d.Wp = Wp; d.ctu = j.p.ctu; d.R = j.p.search_range; d.qp = j.p.qp;
         d.tu_mask = j.p.tu_mask;
         d.nx = Wp / j.p.ctu;
         d.ny = Hp / j.p.ctu;
+        d.qfirst = (int64_t)qnext[k];
+        qnext[k] += (size_t)G * d.nx * d.ny;
     }
+    // descriptors go up before (and outside) the captured work
     e = cudaMemcpyAsync(c->b_jobs.ptr, jd.data(), sizeof(xvh::JobDev) * njobs, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "job descriptors");
-    // ready queues, one per CTU class: every item of the class gets one slot;
-    // the first-frame items are queued at each launch, the rest by the kernel
-    // as the rows they read complete
-    const int ctus[4] = {8, 16, 32, 64};
-    std::vector<uint64_t> first[4];
-    size_t total[4] = {0, 0, 0, 0}, smem[4] = {0, 0, 0, 0};
-    std::string shape[4];
-    for (int i = 0; i < njobs; ++i) {
-        const xvh::JobDev& d = jd[i];
-        const int k = d.ctu == 8 ? 0 : d.ctu == 16 ? 1 : d.ctu == 32 ? 2 : 3;
-        for (int gi = 0; gi < d.G; ++gi)
-            for (int pu = 0; pu < d.nx * d.ny; ++pu) first[k].push_back(xvh::make_item(i, gi, 0, pu));
-        total[k] += (size_t)d.G * d.T * d.nx * d.ny;
-        size_t need = xvh::persist_smem_bytes(d.ctu, d.R, jobs[i].T > 1);
-        smem[k] = need > smem[k] ? need : smem[k];
-        char sh[96];
-        snprintf(sh, sizeof sh, "%d:%d:%d:%d:%d:%d;", d.G, d.T, d.Hp, d.Wp, d.R, jobs[i].T > 1);
-        shape[k] += sh;
-    }
-    size_t total_items = 0;
-    for (int k = 0; k < 4; ++k) total_items += total[k];
-    if (total_items > 0xffffffffu) { set_error("too many work items in one batch"); return XV_EINVAL; }
-    if ((s = ensure(c, c->b_items, sizeof(uint64_t) * total_items))) return s;
-    uint64_t* queue_all = (uint64_t*)c->b_items.ptr;
-    xvh::BatchCtl* ctl = (xvh::BatchCtl*)c->b_ctl.ptr;
-    if (!c->ev0 && (e = cudaEventCreate(&c->ev0)) == cudaSuccess) e = cudaEventCreate(&c->ev1);
-    if (e != cudaSuccess) return cuda_fail(e, "events");
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->b_cls.ptr, cls, sizeof cls, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
+    const xvh::JobDev* jobs_dev = (const xvh::JobDev*)c->b_jobs.ptr;
+    unsigned char* hs = (unsigned char*)c->h_stage;
+    xvh::BatchCtl* h_ctl = (xvh::BatchCtl*)hs;
+    unsigned long long* h_tot = (unsigned long long*)(hs + sizeof(xvh::BatchCtl) * 4);
+    xvh::PsnrPart* h_out = (xvh::PsnrPart*)(h_tot + njobs);
+    BandQ* h_bq = (BandQ*)(h_out + XV_MAX_BANDS * njobs);
 
-    // One complete run of the batch's persistent launches with block sizes
-    // nt[k]: counters, bits and queues reset, then the launches between the
-    // two events.
-    auto run = [&](const int nt[4]) -> xv_status {
-        cudaError_t err = cudaMemsetAsync(rows_all, 0, sizeof(unsigned) * nrows, st);
-        if (err == cudaSuccess) err = cudaMemsetAsync(deps_all, 0, sizeof(unsigned) * nrows, st);
-        if (err == cudaSuccess) err = cudaMemsetAsync(bits_all, 0, sizeof(uint64_t) * nbits, st);
-        for (int i = 0; i < njobs && err == cudaSuccess; ++i)
-            if (jobs[i].bits) err = cudaMemsetAsync(jobs[i].bits, 0, sizeof(uint64_t) * jd[i].G * jobs[i].T, st);
-        if (err == cudaSuccess) err = cudaMemsetAsync(queue_all, 0xff, sizeof(uint64_t) * total_items, st);
-        for (int k = 0, off = 0; k < 4 && err == cudaSuccess; ++k) {
-            if (!total[k]) continue;
-            err = cudaMemcpyAsync(queue_all + off, first[k].data(), sizeof(uint64_t) * first[k].size(),
-                                  cudaMemcpyHostToDevice, st);
-            xvh::BatchCtl h{0u, (unsigned)first[k].size(), (unsigned)total[k], 0, c->wait_budget, c->stall_row};
-            if (err == cudaSuccess) err = cudaMemcpyAsync(ctl + k, &h, sizeof h, cudaMemcpyHostToDevice, st);
-            if (err == cudaSuccess) err = cudaStreamSynchronize(st);  // the host sources are locals
-            off += (int)total[k];
+    // ---- the batch as three stream-ordered, capturable parts: setup,
+    // persistent kernels, results; the timing events go between them
+    auto part_setup = [&]() -> xv_status {
+        for (int i = 0; i < njobs; ++i) {
+            const xv_job& j = jobs[i];
+            double* mm = j.minmax ? j.minmax : mm_all + 2 * XV_MAX_BANDS * i;
+            BandQ* bq = bq_all + XV_MAX_BANDS * i;
+            xv_status r = prepare_bands(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, mm, j.minmax_fixed, bq, st);
+            if (r) return r;
+            c->launches += kLaunchQuant;
+            r = check_launch(xvh::launch_quantize_pack(j.src, j.dtype, j.bands, j.T, j.H, j.W, jd[i].Hp, jd[i].Wp, bq,
+                                                       j.planes, st),
+                             "quantize_pack");
+            if (r) return r;
         }
-        if (err != cudaSuccess) return cuda_fail(err, "ready queue");
-        if ((err = cudaEventRecord(c->ev0, st)) != cudaSuccess) return cuda_fail(err, "event");
-        for (int k = 0, off = 0; k < 4; ++k) {
+        c->launches += 1;
+        xv_status r = check_launch(xvh::launch_batch_prologue(jobs_dev, njobs, (const xvh::ClassDev*)c->b_cls.ptr,
+                                                              (uint64_t*)c->b_items.ptr, (xvh::BatchCtl*)c->b_ctl.ptr,
+                                                              (unsigned*)c->b_rowdone.ptr, (unsigned*)c->b_depcnt.ptr,
+                                                              nrows, c->wait_budget, c->stall_row, st),
+                                   "batch prologue");
+        return r;
+    };
+    auto part_kernels = [&](const int nt[4]) -> xv_status {
+        xv_status r = XV_OK;
+        for (int k = 0; k < 4; ++k) {
             if (!total[k]) continue;
             const int grid = xvh::persist_grid(ctus[k], nt[k], smem[k]);
-            xv_status r2 = check_launch(xvh::launch_persist(ctus[k], nt[k], (const xvh::JobDev*)c->b_jobs.ptr,
-                                                            queue_all + off, ctl + k, smem[k], grid, st),
-                                        "persistent encode");
-            if (r2) return r2;
+            r = check_launch(xvh::launch_persist(ctus[k], nt[k], jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
+                                                 (xvh::BatchCtl*)c->b_ctl.ptr + k, smem[k], grid, st),
+                             "persistent encode");
+            if (r) return r;
             c->launches += kLaunchPersist;
             c->batch_nt = nt[k];
-            off += (int)total[k];
         }
-        if ((err = cudaEventRecord(c->ev1, st)) != cudaSuccess) return cuda_fail(err, "event");
+        return r;
+    };
+    auto part_results = [&]() -> xv_status {
+        xv_status r = XV_OK;
+        cudaError_t err = cudaSuccess;
+        for (int i = 0; i < njobs; ++i) {
+            const xv_job& j = jobs[i];
+            c->launches += kLaunchPsnr;
+            r = check_launch(xvh::launch_psnr(j.src, j.dtype, j.bands, j.T, j.H, j.W, j.planes, j.recon, jd[i].Hp,
+                                              jd[i].Wp, bq_all + XV_MAX_BANDS * i,
+                                              (xvh::PsnrPart*)c->b_part.ptr + part_off[i], nblk[i],
+                                              (xvh::PsnrPart*)c->b_out.ptr + XV_MAX_BANDS * i, st),
+                             "psnr");
+            if (r) return r;
+        }
+        c->launches += 1;
+        r = check_launch(xvh::launch_bits_totals(jobs_dev, njobs, (unsigned long long*)c->b_totals.ptr, st),
+                         "bits totals");
+        if (r) return r;
+        err = cudaMemcpyAsync(h_ctl, c->b_ctl.ptr, sizeof(xvh::BatchCtl) * 4, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h_tot, c->b_totals.ptr, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h_out, c->b_out.ptr, sizeof(xvh::PsnrPart) * XV_MAX_BANDS * njobs,
+                                  cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h_bq, bq_all, sizeof(BandQ) * XV_MAX_BANDS * njobs, cudaMemcpyDeviceToHost, st);
+        if (err != cudaSuccess) return cuda_fail(err, "batch results");
         return XV_OK;
     };
+    auto body = [&](const int nt[4]) -> xv_status {
+        xv_status r = part_setup();
+        cudaError_t err;
+        if (!r && (err = cudaEventRecord(c->ev0, st)) != cudaSuccess) r = cuda_fail(err, "event");
+        if (!r) r = part_kernels(nt);
+        if (!r && (err = cudaEventRecord(c->ev1, st)) != cudaSuccess) r = cuda_fail(err, "event");
+        if (!r) r = part_results();
+        return r;
+    };
 
-    // Autotuner: the first batch of a shape runs once with each block size
-    // (every run gives identical output) and keeps the fastest.
+    // order after the caller's stream
+    if ((e = cudaEventRecord(c->ev_in, caller)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c->ev_in, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream order");
+
+    // ---- block size: forced, cached, or tuned now (uncaptured runs)
     int nt[4] = {256, 256, 256, 256};
     bool tune = false;
     for (int k = 0; k < 4; ++k) {
@@ -600,19 +684,20 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         if (it == c->tuned_nt.end()) tune = true;
         else nt[k] = it->second;
     }
+    const bool debug = c->force_nt || c->stall_row >= 0;
     if (c->force_nt) {
         for (int k = 0; k < 4; ++k) nt[k] = c->force_nt;
         tune = false;
     }
-    if (tune && c->stall_row < 0) {
+    if (tune && !debug) {
         float best_ms = 1e30f;
         int best_nt = 256;
         for (int cand : xvh::kPersistBlockSizes) {
             int trial[4] = {cand, cand, cand, cand};
-            if ((s = run(trial))) return s;
-            if ((e = cudaEventSynchronize(c->ev1)) != cudaSuccess) return cuda_fail(e, "autotune");
+            if ((s = body(trial))) return s;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune");
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+            if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) != cudaSuccess) { cudaGetLastError(); ms = 1e30f; }
             if (ms < best_ms) { best_ms = ms; best_nt = cand; }
         }
         for (int k = 0; k < 4; ++k) {
@@ -621,29 +706,97 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
             nt[k] = best_nt;
         }
     }
-    if ((s = run(nt))) return s;
-    // timeouts are reported before any result is read
-    xvh::BatchCtl hc[4];
-    e = cudaMemcpyAsync(hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "persistent encode");
+
+    // ---- run: replay the captured graph of this exact batch, or capture it
+    if (c->use_graph && !debug) {
+        std::string key;
+        char buf[256];
+        for (int i = 0; i < njobs; ++i) {
+            const xv_job& j = jobs[i];
+            snprintf(buf, sizeof buf, "%p,%d,%d,%d,%d,%d,%d,%d,%u,%d,%p,%d,%p,%p,%p,%p,%p,%p,%p;", j.src, (int)j.dtype,
+                     j.bands, j.T, j.H, j.W, j.p.ctu, j.p.search_range, j.p.tu_mask, j.p.qp, (void*)j.minmax,
+                     j.minmax_fixed, (void*)j.planes, (void*)j.recon, (void*)j.mv, (void*)j.cost, (void*)j.levels,
+                     (void*)j.tu_log2, (void*)j.bits);
+            key += buf;
+        }
+        snprintf(buf, sizeof buf, "|%d,%d,%d,%d|%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p|%lld", nt[0], nt[1], nt[2], nt[3],
+                 c->b_jobs.ptr, c->b_bits.ptr, c->b_rowdone.ptr, c->b_depcnt.ptr, c->b_bandq.ptr, c->b_minmax.ptr,
+                 c->b_ctl.ptr, c->b_cls.ptr, c->b_items.ptr, c->b_part.ptr, c->b_out.ptr, c->b_totals.ptr,
+                 c->h_stage, c->wait_budget);
+        key += buf;
+        if (!c->graph[0] || key != c->graph_key) {
+            for (cudaGraphExec_t& gx : c->graph)
+                if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
+            const uint64_t launches_before = c->launches;
+            for (int part = 0; part < 3; ++part) {
+                cudaGraph_t graph = nullptr;
+                if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                    return cuda_fail(e, "begin capture");
+                xv_status r = part == 0 ? part_setup() : part == 1 ? part_kernels(nt) : part_results();
+                e = cudaStreamEndCapture(st, &graph);
+                if (r) { if (graph) cudaGraphDestroy(graph); c->launches = launches_before; return r; }
+                if (e != cudaSuccess) { c->launches = launches_before; return cuda_fail(e, "end capture"); }
+                e = cudaGraphInstantiate(&c->graph[part], graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) { c->graph[part] = nullptr; c->launches = launches_before; return cuda_fail(e, "graph instantiate"); }
+            }
+            c->launches = launches_before;  // counted when the graphs run
+            c->graph_key = key;
+            c->graph_captures++;
+        }
+        if ((e = cudaGraphLaunch(c->graph[0], st)) != cudaSuccess || (e = cudaEventRecord(c->ev0, st)) != cudaSuccess ||
+            (e = cudaGraphLaunch(c->graph[1], st)) != cudaSuccess || (e = cudaEventRecord(c->ev1, st)) != cudaSuccess ||
+            (e = cudaGraphLaunch(c->graph[2], st)) != cudaSuccess)
+            return cuda_fail(e, "graph launch");
+        c->graph_launches++;
+        c->launches += (uint64_t)njobs * (kLaunchMinmax + kLaunchQuant + kLaunchPsnr) + 2;
+        for (int k = 0; k < 4; ++k) if (total[k]) c->launches += kLaunchPersist;
+        for (int i = 0; i < njobs; ++i)
+            if (jobs[i].minmax_fixed) c->launches -= kLaunchMinmax - kLaunchBandq;
+    } else {
+        if ((s = body(nt))) return s;
+    }
+    if ((e = cudaEventRecord(c->ev_out, st)) != cudaSuccess || (e = cudaStreamWaitEvent(caller, c->ev_out, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream order");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "batch");
     float kms = 0.f;
-    if (cudaEventElapsedTime(&kms, c->ev0, c->ev1) == cudaSuccess) c->batch_ms = kms;
+    cudaError_t te = cudaEventElapsedTime(&kms, c->ev0, c->ev1);
+    if (te == cudaSuccess) {
+        c->batch_ms = kms;
+    } else {
+        c->batch_ms = -(double)te;  // timing unavailable; the error is not carried into later calls
+        cudaGetLastError();
+    }
+
+    // ---- results (host)
     for (int k = 0; k < 4; ++k)
-        if (total[k] && hc[k].err) {
+        if (total[k] && h_ctl[k].err) {
             set_error("a dependency wait of the persistent encode (CTU %d) ran out of time", ctus[k]);
             for (int i = 0; i < njobs; ++i) results[i].status = XV_ETIMEOUT;
-            return (xv_status)hc[k].err;
+            return (xv_status)h_ctl[k].err;
         }
     for (int i = 0; i < njobs; ++i) {
         const xv_job& j = jobs[i];
         xv_result* r = &results[i];
         std::memset(r, 0, sizeof *r);
-        const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
-        if ((s = psnr_into(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, j.planes, j.recon, Hp, Wp,
-                           bq_all + XV_MAX_BANDS * i, r->psnr_band, r->mse_band, r->sse10_band, &r->psnr_mean, st)))
-            return s;
-        if ((s = fill_result(&j, jd[i].bits, G, r, st))) return s;
+        double acc = 0.0;
+        bool inf = false;
+        for (int b = 0; b < j.bands; ++b) {
+            const xvh::PsnrPart& o = h_out[XV_MAX_BANDS * i + b];
+            const BandQ& q = h_bq[XV_MAX_BANDS * i + b];
+            const double cnt = (double)o.count;
+            const double m = cnt > 0 ? o.sse / cnt : 0.0;
+            const double peak = q.hi > 0.0 ? q.hi : q.hi - q.lo;
+            const double p = m > 0.0 ? 10.0 * std::log10(peak * peak / m) : INFINITY;
+            r->psnr_band[b] = p;
+            r->mse_band[b] = m;
+            r->sse10_band[b] = o.sse10;
+            if (std::isinf(p)) inf = true; else acc += p;
+        }
+        r->psnr_mean = inf ? INFINITY : acc / j.bands;
+        r->total_bits = h_tot[i];
+        r->bands = j.bands;
+        r->bpppb = (double)h_tot[i] / ((double)j.H * j.W * j.T * j.bands);
         r->status = XV_OK;
     }
     return XV_OK;
@@ -667,6 +820,19 @@ uint64_t xv_ctx_launches(const xv_ctx* c) { return c ? c->launches : 0; }
 xv_status xv_debug_set_wait_budget(xv_ctx* c, long long cycles) {
     if (!c || cycles < 1) { set_error("bad wait budget"); return XV_EINVAL; }
     c->wait_budget = cycles;
+    return XV_OK;
+}
+
+xv_status xv_batch_graph_stats(const xv_ctx* c, uint64_t* captures, uint64_t* launches) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (captures) *captures = c->graph_captures;
+    if (launches) *launches = c->graph_launches;
+    return XV_OK;
+}
+
+xv_status xv_set_batch_graphs(xv_ctx* c, int enable) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    c->use_graph = enable ? 1 : 0;
     return XV_OK;
 }
 

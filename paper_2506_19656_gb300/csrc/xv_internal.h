@@ -72,6 +72,14 @@ struct JobDev {
     int G, T, Hp, Wp, ctu, R, qp;
     unsigned tu_mask;
     int nx, ny;
+    int64_t qfirst;          // queue slot of this job's first first-frame item
+};
+
+// One CTU class of a batch, as the prologue sees it.
+struct ClassDev {
+    int64_t qoff;            // first queue slot of the class
+    unsigned total;          // items of the class
+    unsigned nfirst;         // first-frame items (queued by the prologue)
 };
 
 // Ready-queue control block (device).
@@ -91,6 +99,13 @@ inline uint64_t make_item(int job, int g, int t, int pu) {
 }
 
 size_t persist_smem_bytes(int ctu, int R, bool has_me);
+// Resets the batch's counters and bits, fills the queues (first-frame items,
+// then empty slots) and the control blocks.
+cudaError_t launch_batch_prologue(const JobDev* jobs, int njobs, const ClassDev* cls, uint64_t* queue,
+                                  BatchCtl* ctl, unsigned* rows, unsigned* deps, int64_t nrows, long long budget,
+                                  long long stall_row, cudaStream_t st);
+// totals[j] = sum of job j's per-frame bits.
+cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long* totals, cudaStream_t st);
 // Block sizes the persistent kernel is built for (the autotuner picks one).
 constexpr int kPersistBlockSizes[3] = {128, 192, 256};
 cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,

@@ -73,6 +73,8 @@ _SIGS = {
     "xv_last_batch_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_double)],
     "xv_last_batch_block_size": [_vp, ctypes.POINTER(_i)],
     "xv_ctx_launches": [_vp],
+    "xv_set_batch_graphs": [_vp, _i],
+    "xv_batch_graph_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "xv_debug_set_wait_budget": [_vp, ctypes.c_longlong],
     "xv_debug_force_block_size": [_vp, _i],
     "xv_debug_stall_row": [_vp, ctypes.c_longlong],
@@ -251,6 +253,16 @@ def xv_last_batch_block_size(ctx: Context) -> int:
     nt = _i()
     check(lib().xv_last_batch_block_size(ctx.handle, ctypes.byref(nt)), "xv_last_batch_block_size")
     return nt.value
+
+
+def xv_set_batch_graphs(ctx: Context, enable: bool):
+    check(lib().xv_set_batch_graphs(ctx.handle, int(enable)), "xv_set_batch_graphs")
+
+
+def xv_batch_graph_stats(ctx: Context):
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().xv_batch_graph_stats(ctx.handle, ctypes.byref(a), ctypes.byref(b)), "xv_batch_graph_stats")
+    return a.value, b.value
 
 
 def xv_ctx_launches(ctx: Context) -> int:

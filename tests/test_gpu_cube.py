@@ -150,3 +150,31 @@ def test_batch_timeout_is_reported_and_context_survives(xv, ctx):
     want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27)
     job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
     assert_matches(buf, xv.xv_encode_batch(ctx, [job])[0], want)
+
+
+def test_batch_graph_capture_and_replay(xv):
+    """The second submission of the same batch replays the captured graph; all
+    runs (graph, replay, no graph) give the oracle's bytes."""
+    c = synth.CONFIGS[0]
+    cubes = [synth.tiny_cube(500 + i, T=4)[0] for i in range(2)]
+    wants = [oracle.encode_cube(x, c.ctu, c.R, c.tu_mask, qp) for x, qp in zip(cubes, (22, 32))]
+    ctx = xv.Context(0)
+    try:
+        made = [gpu_job(xv, x, c.ctu, c.R, c.tu_mask, qp) for x, qp in zip(cubes, (22, 32))]
+        jobs = [m[0] for m in made]
+        for _ in range(3):
+            for b in (m[1] for m in made):
+                b["recon"].zero_()
+                b["mv"].zero_()
+            results = xv.xv_encode_batch(ctx, jobs)
+            for (j, b), r, w in zip(made, results, wants):
+                assert_matches(b, r, w)
+        captures, launches = xv.xv_batch_graph_stats(ctx)
+        assert captures == 1 and launches >= 2
+        xv.xv_set_batch_graphs(ctx, False)
+        results = xv.xv_encode_batch(ctx, jobs)
+        for (j, b), r, w in zip(made, results, wants):
+            assert_matches(b, r, w)
+        assert xv.xv_batch_graph_stats(ctx)[0] == 1
+    finally:
+        ctx.close()
