@@ -241,6 +241,50 @@ xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void
  * stays usable). */
 xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
 
+/* ------------------------------------------------------ serving */
+
+/* A compression request for the serving loop.  Unlike xv_job, the cube is in
+ * HOST memory (pinned memory makes the upload asynchronous); the library
+ * allocates the device buffers itself, under the context's memory budget,
+ * and frees them when the request completes.  Every host buffer must stay
+ * valid until xv_serve_poll reports the request done. */
+typedef struct {
+    const void* src;       /* HOST [bands][T][H][W] float32 or uint16 */
+    xv_dtype dtype;
+    int bands, T, H, W;
+    xv_params p;
+    uint16_t* recon_out;   /* HOST [G][T][3][Hp][Wp] reconstruction, or NULL */
+    int16_t* mv_out;       /* HOST [G][T][nPU][2] motion vectors, or NULL */
+} xv_request;
+
+/* Starts the serving loop on the context's device (a library thread).
+ * Requests are admitted in submission order while fewer than `max_slots`
+ * (1..255) are resident and their device buffers fit the memory budget given
+ * to xv_create (0 = no limit); admission uploads and quantises the cube on a
+ * copy stream, overlapping the running work.  Each tick advances every
+ * resident request by up to `frames_per_tick` frames in one persistent launch
+ * (the xv_encode_batch kernel over frame windows), so requests that arrive
+ * while others run join at the next tick: continuous batching at frame
+ * granularity.  Results are bit-identical to xv_encode_cube.  One serving
+ * loop per context; the context's other calls may be used meanwhile. */
+xv_status xv_serve_start(xv_ctx* ctx, int max_slots, int frames_per_tick);
+/* Queues a request; never blocks.  XV_EBUSY when 65536 requests are queued,
+ * XV_EINVAL on a malformed request.  *ticket identifies it. */
+xv_status xv_serve_submit(xv_ctx* ctx, const xv_request* req, uint64_t* ticket);
+/* Non-blocking.  *done = 1 once the request finished (result filled,
+ * including result->status and result->latency_s, the time from submission
+ * to completion); the ticket is then released (later polls: XV_ENOTFOUND). */
+xv_status xv_serve_poll(xv_ctx* ctx, uint64_t ticket, xv_result* result, int* done);
+/* Cancels a queued or resident request; it completes with XV_ECANCELLED at
+ * the next tick boundary (unless it finished first). */
+xv_status xv_serve_cancel(xv_ctx* ctx, uint64_t ticket);
+/* Ticks run, persistent-kernel milliseconds, the largest number of resident
+ * requests and the device bytes requests hold now. */
+xv_status xv_serve_stats(xv_ctx* ctx, uint64_t* ticks, double* kernel_ms, int* peak_resident, size_t* bytes_in_use);
+/* Stops the loop: queued and resident requests are cancelled, the thread is
+ * joined, all serving memory is freed.  Unpolled results are discarded. */
+xv_status xv_serve_stop(xv_ctx* ctx);
+
 /* ------------------------------------------------------ measurement */
 
 /* Device time of the persistent kernel launches of the last xv_encode_batch

@@ -77,7 +77,7 @@ __device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, ui
     const int row = pu / J.nx;
     const int64_t f = (int64_t)g * J.T + t;
     if (threadIdx.x == 0)
-        *s_full = (atomicAdd(J.rowdone + f * J.ny + row, 1u) + 1u == (unsigned)J.nx) && (t + 1 < J.T);
+        *s_full = (atomicAdd(J.rowdone + f * J.ny + row, 1u) + 1u == (unsigned)J.nx) && (t + 1 < J.te);
     __syncthreads();
     if (!*s_full) return;
     const int reach = (J.R + 4 + J.ctu - 1) / J.ctu + 1;
@@ -154,26 +154,34 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
     }
 }
 
-// Batch prologue: block j < njobs handles job j (bits, first-frame items);
-// the others clear the row counters and fill the empty queue slots; block 0
-// also writes the control blocks.
+// Batch prologue: block j < njobs handles job j (its bits and counters over
+// the window, the window's first-frame items); the others fill the empty
+// queue slots; block njobs also writes the control blocks.
 __global__ void k_batch_prologue(const JobDev* __restrict__ jobs, int njobs, const ClassDev* __restrict__ cls,
-                                 uint64_t* queue, BatchCtl* ctl, unsigned* rows, unsigned* deps, int64_t nrows,
-                                 long long budget, long long stall_row) {
+                                 uint64_t* queue, BatchCtl* ctl, long long budget, long long stall_row) {
     const int b = blockIdx.x;
     if (b < njobs) {
         const JobDev& J = jobs[b];
-        const int64_t nb = (int64_t)J.G * J.T, npu = (int64_t)J.nx * J.ny;
-        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) J.bits[i] = 0ull;
+        const int64_t npu = (int64_t)J.nx * J.ny, nw = J.te - J.tb;
+        for (int64_t i = threadIdx.x; i < (int64_t)J.G * nw; i += blockDim.x) {
+            const int g = (int)(i / nw), t = J.tb + (int)(i - (int64_t)g * nw);
+            J.bits[(int64_t)g * J.T + t] = 0ull;
+        }
+        for (int64_t i = threadIdx.x; i < (int64_t)J.G * nw * J.ny; i += blockDim.x) {
+            const int64_t per_g = nw * J.ny;
+            const int g = (int)(i / per_g);
+            const int64_t o = ((int64_t)g * J.T + J.tb) * J.ny + (i - g * per_g);
+            J.rowdone[o] = 0u;
+            J.depcnt[o] = 0u;
+        }
         for (int64_t i = threadIdx.x; i < (int64_t)J.G * npu; i += blockDim.x) {
             const int g = (int)(i / npu), pu = (int)(i - (int64_t)g * npu);
-            queue[J.qfirst + i] = ((uint64_t)b << 56) | ((uint64_t)g << 48) | (uint32_t)pu;
+            queue[J.qfirst + i] = ((uint64_t)b << 56) | ((uint64_t)g << 48) | ((uint64_t)J.tb << 32) | (uint32_t)pu;
         }
         return;
     }
     const int64_t stride = (int64_t)(gridDim.x - njobs) * blockDim.x;
     const int64_t start = (int64_t)(b - njobs) * blockDim.x + threadIdx.x;
-    for (int64_t i = start; i < nrows; i += stride) { rows[i] = 0u; deps[i] = 0u; }
     for (int k = 0; k < 4; ++k) {
         const int64_t lo = cls[k].qoff + cls[k].nfirst, hi = cls[k].qoff + cls[k].total;
         for (int64_t i = lo + start; i < hi; i += stride) queue[i] = kEmptyItem;
@@ -224,9 +232,8 @@ PersistFn persist_fn(int ctu, int nt) {
 }  // namespace
 
 cudaError_t launch_batch_prologue(const JobDev* jobs, int njobs, const ClassDev* cls, uint64_t* queue,
-                                  BatchCtl* ctl, unsigned* rows, unsigned* deps, int64_t nrows, long long budget,
-                                  long long stall_row, cudaStream_t st) {
-    k_batch_prologue<<<njobs + 64, 256, 0, st>>>(jobs, njobs, cls, queue, ctl, rows, deps, nrows, budget, stall_row);
+                                  BatchCtl* ctl, long long budget, long long stall_row, cudaStream_t st) {
+    k_batch_prologue<<<njobs + 64, 256, 0, st>>>(jobs, njobs, cls, queue, ctl, budget, stall_row);
     return cudaGetLastError();
 }
 

@@ -213,6 +213,12 @@ cudaError_t launch_minmax(const void* src, xv_dtype dt, int bands, int64_t n, un
     return cudaGetLastError();
 }
 
+cudaError_t launch_prepare_bands(const void* src, xv_dtype dt, int bands, int64_t n, double* minmax, int fixed,
+                                 unsigned* enc, BandQ* bq, cudaStream_t st) {
+    if (fixed) return launch_bandq(minmax, bands, bq, st);
+    return launch_minmax(src, dt, bands, n, enc, minmax, bq, st);
+}
+
 cudaError_t launch_bandq(const double* minmax, int bands, BandQ* bq, cudaStream_t st) {
     k_bandq<<<(bands + 31) / 32, 32, 0, st>>>(minmax, bands, bq);
     return cudaGetLastError();

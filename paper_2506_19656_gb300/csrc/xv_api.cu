@@ -44,6 +44,7 @@ struct xv_ctx {
     std::string graph_key;
     int use_graph = 1;
     uint64_t graph_launches = 0, graph_captures = 0;
+    xvh::ServeState* serve = nullptr;
 };
 
 namespace xvh {
@@ -291,6 +292,7 @@ xv_status xv_create(xv_ctx** out, int device, size_t budget) {
 void xv_destroy(xv_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    if (c->serve) { xvh::serve_destroy(c->serve); c->serve = nullptr; }
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax,
                       &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
@@ -582,6 +584,8 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         d.nx = Wp / j.p.ctu;
         d.ny = Hp / j.p.ctu;
         d.qfirst = (int64_t)qnext[k];
+        d.tb = 0;
+        d.te = j.T;
         qnext[k] += (size_t)G * d.nx * d.ny;
     }
     // descriptors go up before (and outside) the captured work
@@ -614,8 +618,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         c->launches += 1;
         xv_status r = check_launch(xvh::launch_batch_prologue(jobs_dev, njobs, (const xvh::ClassDev*)c->b_cls.ptr,
                                                               (uint64_t*)c->b_items.ptr, (xvh::BatchCtl*)c->b_ctl.ptr,
-                                                              (unsigned*)c->b_rowdone.ptr, (unsigned*)c->b_depcnt.ptr,
-                                                              nrows, c->wait_budget, c->stall_row, st),
+                                                              c->wait_budget, c->stall_row, st),
                                    "batch prologue");
         return r;
     };
@@ -820,6 +823,53 @@ uint64_t xv_ctx_launches(const xv_ctx* c) { return c ? c->launches : 0; }
 xv_status xv_debug_set_wait_budget(xv_ctx* c, long long cycles) {
     if (!c || cycles < 1) { set_error("bad wait budget"); return XV_EINVAL; }
     c->wait_budget = cycles;
+    return XV_OK;
+}
+
+xv_status xv_serve_start(xv_ctx* c, int max_slots, int frames_per_tick) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (c->serve) { set_error("serving already started on this context"); return XV_EINVAL; }
+    if (max_slots < 1 || max_slots > 255 || frames_per_tick < 1) {
+        set_error("max_slots %d (1..255) / frames_per_tick %d (>= 1)", max_slots, frames_per_tick);
+        return XV_EINVAL;
+    }
+    DeviceGuard g(c->device);
+    xv_status st = XV_OK;
+    xvh::ServeState* s = xvh::serve_create(c->device, max_slots, frames_per_tick, c->budget, c->wait_budget, &st);
+    if (st) { xvh::serve_destroy(s); return st; }
+    c->serve = s;
+    return XV_OK;
+}
+
+xv_status xv_serve_submit(xv_ctx* c, const xv_request* r, uint64_t* ticket) {
+    if (!c || !c->serve) { set_error("serving not started"); return XV_EINVAL; }
+    if (!r || !ticket) { set_error("request and ticket are required"); return XV_EINVAL; }
+    if (!valid_cube(r->src, r->dtype, r->bands, r->T, r->H, r->W) || !valid_params(&r->p)) return XV_EINVAL;
+    return xvh::serve_submit(c->serve, r, ticket);
+}
+
+xv_status xv_serve_poll(xv_ctx* c, uint64_t ticket, xv_result* res, int* done) {
+    if (!c || !c->serve) { set_error("serving not started"); return XV_EINVAL; }
+    if (!done) { set_error("done is required"); return XV_EINVAL; }
+    return xvh::serve_poll(c->serve, ticket, res, done);
+}
+
+xv_status xv_serve_cancel(xv_ctx* c, uint64_t ticket) {
+    if (!c || !c->serve) { set_error("serving not started"); return XV_EINVAL; }
+    return xvh::serve_cancel(c->serve, ticket);
+}
+
+xv_status xv_serve_stats(xv_ctx* c, uint64_t* ticks, double* kernel_ms, int* peak, size_t* bytes) {
+    if (!c || !c->serve) { set_error("serving not started"); return XV_EINVAL; }
+    xvh::serve_stats(c->serve, ticks, kernel_ms, peak, bytes);
+    return XV_OK;
+}
+
+xv_status xv_serve_stop(xv_ctx* c) {
+    if (!c || !c->serve) { set_error("serving not started"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    xvh::serve_destroy(c->serve);
+    c->serve = nullptr;
     return XV_OK;
 }
 

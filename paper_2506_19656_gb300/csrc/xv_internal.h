@@ -72,14 +72,15 @@ struct JobDev {
     int G, T, Hp, Wp, ctu, R, qp;
     unsigned tu_mask;
     int nx, ny;
-    int64_t qfirst;          // queue slot of this job's first first-frame item
+    int64_t qfirst;          // queue slot of this job's first window item
+    int tb, te;              // frames [tb, te) are encoded by this launch (frame tb-1 is complete)
 };
 
 // One CTU class of a batch, as the prologue sees it.
 struct ClassDev {
     int64_t qoff;            // first queue slot of the class
     unsigned total;          // items of the class
-    unsigned nfirst;         // first-frame items (queued by the prologue)
+    unsigned nfirst;         // items of the jobs' first window frames (queued by the prologue)
 };
 
 // Ready-queue control block (device).
@@ -99,11 +100,15 @@ inline uint64_t make_item(int job, int g, int t, int pu) {
 }
 
 size_t persist_smem_bytes(int ctu, int R, bool has_me);
-// Resets the batch's counters and bits, fills the queues (first-frame items,
-// then empty slots) and the control blocks.
+// Resets each job's counters and bits over its frame window, fills the
+// queues (the window's first-frame items, then empty slots) and the control
+// blocks.
 cudaError_t launch_batch_prologue(const JobDev* jobs, int njobs, const ClassDev* cls, uint64_t* queue,
-                                  BatchCtl* ctl, unsigned* rows, unsigned* deps, int64_t nrows, long long budget,
-                                  long long stall_row, cudaStream_t st);
+                                  BatchCtl* ctl, long long budget, long long stall_row, cudaStream_t st);
+// min/max (unless fixed) and the per-band quantiser constants; `enc` is
+// 2 * bands words of scratch.
+cudaError_t launch_prepare_bands(const void* src, xv_dtype dt, int bands, int64_t n_per_band, double* minmax,
+                                 int fixed, unsigned* enc, BandQ* bq, cudaStream_t st);
 // totals[j] = sum of job j's per-frame bits.
 cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long* totals, cudaStream_t st);
 // Block sizes the persistent kernel is built for (the autotuner picks one).
@@ -111,5 +116,19 @@ constexpr int kPersistBlockSizes[3] = {128, 192, 256};
 cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,
                            int grid, cudaStream_t st);
 int persist_grid(int ctu, int nt, size_t smem);
+
+}  // namespace xvh
+
+namespace xvh {
+
+// Serving (csrc/xv_serve.cu).
+struct ServeState;
+ServeState* serve_create(int device, int max_slots, int frames_per_tick, size_t budget, long long wait_budget,
+                         xv_status* st);
+void serve_destroy(ServeState* s);
+xv_status serve_submit(ServeState* s, const xv_request* r, uint64_t* ticket);
+xv_status serve_poll(ServeState* s, uint64_t ticket, xv_result* res, int* done);
+xv_status serve_cancel(ServeState* s, uint64_t ticket);
+void serve_stats(ServeState* s, uint64_t* ticks, double* kernel_ms, int* peak_active, size_t* bytes_in_use);
 
 }  // namespace xvh

@@ -33,6 +33,11 @@ class xv_job(ctypes.Structure):
                 ("mv", _vp), ("cost", _vp), ("levels", _vp), ("tu_log2", _vp), ("bits", _vp)]
 
 
+class xv_request(ctypes.Structure):
+    _fields_ = [("src", _vp), ("dtype", _i), ("bands", _i), ("T", _i), ("H", _i), ("W", _i), ("p", xv_params),
+                ("recon_out", _vp), ("mv_out", _vp)]
+
+
 class xv_result(ctypes.Structure):
     _fields_ = [("status", _i), ("bands", _i), ("psnr_mean", ctypes.c_double), ("bpppb", ctypes.c_double),
                 ("total_bits", ctypes.c_uint64), ("psnr_band", ctypes.c_double * XV_MAX_BANDS),
@@ -70,6 +75,13 @@ _SIGS = {
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
     "xv_encode_batch": [_vp, ctypes.POINTER(xv_job), _i, ctypes.POINTER(xv_result), _vp],
+    "xv_serve_start": [_vp, _i, _i],
+    "xv_serve_submit": [_vp, ctypes.POINTER(xv_request), ctypes.POINTER(ctypes.c_uint64)],
+    "xv_serve_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(xv_result), ctypes.POINTER(_i)],
+    "xv_serve_cancel": [_vp, ctypes.c_uint64],
+    "xv_serve_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i),
+                       ctypes.POINTER(ctypes.c_size_t)],
+    "xv_serve_stop": [_vp],
     "xv_last_batch_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_double)],
     "xv_last_batch_block_size": [_vp, ctypes.POINTER(_i)],
     "xv_ctx_launches": [_vp],
@@ -241,6 +253,46 @@ def xv_encode_batch(ctx: Context, jobs, stream=None) -> list:
     res = (xv_result * n)()
     check(lib().xv_encode_batch(ctx.handle, arr, n, res, _stream(stream)), "xv_encode_batch")
     return [r.as_dict() for r in res]
+
+
+def xv_serve_start(ctx: Context, max_slots: int, frames_per_tick: int):
+    check(lib().xv_serve_start(ctx.handle, max_slots, frames_per_tick), "xv_serve_start")
+
+
+def make_request(src_host, p: xv_params, recon_out=None, mv_out=None) -> xv_request:
+    """src_host: a CPU torch tensor [bands, T, H, W] (pin it for an asynchronous upload)."""
+    bands, T, H, W = src_host.shape
+    return xv_request(src=_ptr(src_host), dtype=_dtype_code(src_host), bands=bands, T=T, H=H, W=W, p=p,
+                      recon_out=_ptr(recon_out), mv_out=_ptr(mv_out))
+
+
+def xv_serve_submit(ctx: Context, req: xv_request) -> int:
+    t = ctypes.c_uint64()
+    check(lib().xv_serve_submit(ctx.handle, ctypes.byref(req), ctypes.byref(t)), "xv_serve_submit")
+    return t.value
+
+
+def xv_serve_poll(ctx: Context, ticket: int):
+    """(done, result dict or None)."""
+    r = xv_result()
+    done = _i()
+    check(lib().xv_serve_poll(ctx.handle, ticket, ctypes.byref(r), ctypes.byref(done)), "xv_serve_poll")
+    return (True, r.as_dict()) if done.value else (False, None)
+
+
+def xv_serve_cancel(ctx: Context, ticket: int):
+    check(lib().xv_serve_cancel(ctx.handle, ticket), "xv_serve_cancel")
+
+
+def xv_serve_stats(ctx: Context):
+    t, ms, pk, b = ctypes.c_uint64(), ctypes.c_double(), _i(), ctypes.c_size_t()
+    check(lib().xv_serve_stats(ctx.handle, ctypes.byref(t), ctypes.byref(ms), ctypes.byref(pk), ctypes.byref(b)),
+          "xv_serve_stats")
+    return dict(ticks=t.value, kernel_ms=ms.value, peak_resident=pk.value, bytes_in_use=b.value)
+
+
+def xv_serve_stop(ctx: Context):
+    check(lib().xv_serve_stop(ctx.handle), "xv_serve_stop")
 
 
 def xv_last_batch_kernel_ms(ctx: Context) -> float:
