@@ -178,3 +178,25 @@ def test_batch_graph_capture_and_replay(xv):
         assert xv.xv_batch_graph_stats(ctx)[0] == 1
     finally:
         ctx.close()
+
+
+def test_full_resolution_dynamicearthnet_and_era5_prefixes(xv, ctx):
+    """Full-size frames of the DynamicEarthNet-shaped (1024x1024 uint16, CTU 64,
+    R 64, TU 4-32) and ERA5-shaped (721x1440 float32, padded to 736, CTU 32,
+    R 16) workloads, on causal prefixes the oracle finishes: plain path, and
+    both together in one batch (two CTU classes, one launch each)."""
+    c2, c3 = synth.CONFIGS[2], synth.CONFIGS[3]
+    den = synth.make_cube(2, T=2)
+    era = synth.make_cube(3, T=3)
+    w2 = oracle.encode_cube(den, c2.ctu, c2.R, c2.tu_mask, 27)
+    w3 = oracle.encode_cube(era, c3.ctu, c3.R, c3.tu_mask, 22)
+    j2, b2 = gpu_job(xv, den, c2.ctu, c2.R, c2.tu_mask, 27)
+    assert_matches(b2, xv.xv_encode_cube(ctx, j2), w2)
+    j3, b3 = gpu_job(xv, era, c3.ctu, c3.R, c3.tu_mask, 22)
+    assert_matches(b3, xv.xv_encode_cube(ctx, j3), w3)
+    for b in (b2, b3):
+        b["recon"].zero_()
+        b["mv"].zero_()
+    r2, r3 = xv.xv_encode_batch(ctx, [j2, j3])
+    assert_matches(b2, r2, w2)
+    assert_matches(b3, r3, w3)
