@@ -109,6 +109,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, dist_mod=None, device=None):
+    """The timed region's length as the slowest rank saw it (no-op on one rank)."""
+    if dist_mod is None or not dist_mod.is_available() or not dist_mod.is_initialized() \
+            or dist_mod.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(work_per_rank, steps, world_size, max_total_ms):
+    """Units all ranks processed / the slowest rank's time (weak scaling: every
+    rank runs its own replica of the workload)."""
+    return world_size * work_per_rank * steps / (max_total_ms / 1e3)
+
+
 def algorithmic_ad(cfg, T):
     """Integer-search abs-diffs of one encode: N^2 (2R+1)^2 per PU and P-frame."""
     G = (cfg.bands + 2) // 3
@@ -398,12 +415,8 @@ def main():
     clk = clocks.stop()
     block_size = xv.xv_last_batch_block_size(ctx)
 
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * work_mpx * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist if ws > 1 else None, dev)
+    value = whole_job_value(work_mpx, args.steps, ws, total_ms)
 
     # plain per-frame path, same work
     plain = None
