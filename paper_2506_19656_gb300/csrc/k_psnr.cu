@@ -26,23 +26,33 @@ k_psnr(const T* __restrict__ src, int bands, int T_, int H, int W, const uint16_
     const int g = b / 3, c = b % 3;
     const BandQ q = bq[b];
     const int64_t n = (int64_t)T_ * H * W;
+    (void)n;
     const T* p = src + (int64_t)b * n;
     double sse = 0.0;
     unsigned long long sse10 = 0, count = 0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        int64_t ty = i / W;
-        int x = (int)(i - ty * W);
-        int t = (int)(ty / H), y = (int)(ty - (int64_t)t * H);
-        int64_t pi = (((int64_t)g * T_ + t) * 3 + c) * Hp * Wp + (int64_t)y * Wp + x;
-        int rq = recon[pi];
-        int e10 = (int)planes[pi] - rq;
-        sse10 += (unsigned long long)(e10 * e10);
-        double xv = (double)p[i];
-        if (isfinite(xv)) {
-            double xh = __dadd_rn(q.lo, __dmul_rn((double)rq, q.delta));
-            double e = __dsub_rn(xv, xh);
-            sse = __dadd_rn(sse, __dmul_rn(e, e));
-            ++count;
+    // one warp per image row: the row's frame and y are derived once, the
+    // lanes stride along x
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)gridDim.x * (kThreads / 32);
+    const int64_t rows = (int64_t)T_ * H;
+    const int64_t cstride = (int64_t)Hp * Wp;
+    for (int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const int t = (int)(row / H), y = (int)(row - (int64_t)t * H);
+        const T* xr = p + row * W;
+        const int64_t base = (((int64_t)g * T_ + t) * 3 + c) * cstride + (int64_t)y * Wp;
+        const uint16_t* rr = recon + base;
+        const uint16_t* qr = planes + base;
+        for (int x = lane; x < W; x += 32) {
+            const int rq = rr[x];
+            const int e10 = (int)qr[x] - rq;
+            sse10 += (unsigned long long)(e10 * e10);
+            const double xv = (double)xr[x];
+            if (isfinite(xv)) {
+                const double xh = __dadd_rn(q.lo, __dmul_rn((double)rq, q.delta));
+                const double e = __dsub_rn(xv, xh);
+                sse = __dadd_rn(sse, __dmul_rn(e, e));
+                ++count;
+            }
         }
     }
 #pragma unroll

@@ -42,7 +42,9 @@ __host__ __device__ constexpr int me_stride(int N, int R) {
 __host__ __device__ constexpr size_t me_align16(size_t b) { return (b + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t me_off_blk(int N, int R) { return me_align16((size_t)me_win(N, R) * me_stride(N, R) * 4); }
 __host__ __device__ constexpr size_t me_off_hp(int N, int R) { return me_off_blk(N, R) + me_align16((size_t)N * N * 4); }
-__host__ __device__ constexpr size_t me_off_red(int N, int R) { return me_off_hp(N, R) + me_align16((size_t)3 * (N + 8) * N * 2); }
+__host__ __device__ constexpr size_t me_off_red(int N, int R) {
+    return me_off_hp(N, R) + me_align16((size_t)3 * (N + 8) * N * (N <= 32 ? 4 : 2));
+}
 __host__ __device__ constexpr size_t me_off_satd(int N, int R) { return me_off_red(N, R) + 64 * 8; }
 // motion-cost tables: |se(4d)| for d in [-R, R] (129 at most) and the
 // rounded cost of b bits, b < 64
@@ -278,7 +280,7 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
 // absolute sums before the block's (S + 2) >> 2.
 template <int N, int NT>
 __device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const int* __restrict__ blk,
-                                int16_t* __restrict__ hp, int16_t* __restrict__ had, int cx, int cy, int s,
+                                int* __restrict__ hp, int16_t* __restrict__ had, int cx, int cy, int s,
                                 const int* cand_x, const int* cand_y, int ncand, uint32_t* satd) {
     const int tid = threadIdx.x;
     const int iy_min = (cy - s) >> 2, iy_max = (cy + s) >> 2;
@@ -301,7 +303,7 @@ __device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const
             for (int i = 0; i < 8; ++i) acc += tap[i] * dec_sample(wr[i - 3]);
             v = acc >> kShift1;
         }
-        hp[(j * (N + 8) + r) * N + x] = (int16_t)v;
+        hp[(j * (N + 8) + r) * N + x] = v;
     }
     for (int k = tid; k < ncand; k += NT) satd[k] = 0;
     __syncthreads();
@@ -312,26 +314,35 @@ __device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const
         const int mvx = cand_x[k], mvy = cand_y[k];
         const int j = (mvx - cx) / s + 1;
         const int hx = mvx & 3, fy = mvy & 3, iy = mvy >> 2;
-        const int16_t* col = hp + (size_t)j * (N + 8) * N + bx;
+        const int* col = hp + (size_t)j * (N + 8) * N + bx;
         const int r0 = y + iy - 3 - rbase;
+        int cb[8];
+        {
+            const int4 a = *reinterpret_cast<const int4*>(blk + y * N + bx);
+            const int4 b = *reinterpret_cast<const int4*>(blk + y * N + bx + 4);
+            cb[0] = a.x; cb[1] = a.y; cb[2] = a.z; cb[3] = a.w; cb[4] = b.x; cb[5] = b.y; cb[6] = b.z; cb[7] = b.w;
+        }
         int d[8];
         if (fy == 0) {
+            const int4 a = *reinterpret_cast<const int4*>(col + (r0 + 3) * N);
+            const int4 b = *reinterpret_cast<const int4*>(col + (r0 + 3) * N + 4);
+            const int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const int a = col[(r0 + 3) * N + x];
-                d[x] = dec_sample(blk[y * N + bx + x]) - wp_round(hx == 0 ? a << kShift3 : a);
-            }
+            for (int x = 0; x < 8; ++x) d[x] = dec_sample(cb[x]) - wp_round(hx == 0 ? v[x] << kShift3 : v[x]);
         } else {
             int tap[8];
             luma_taps(fy, tap);
             const int sh = hx == 0 ? kShift1 : kShift2;
+            int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                int acc = 0;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc += tap[t] * (int)col[(r0 + t) * N + x];
-                d[x] = dec_sample(blk[y * N + bx + x]) - wp_round(acc >> sh);
+            for (int t = 0; t < 8; ++t) {
+                const int4 a = *reinterpret_cast<const int4*>(col + (r0 + t) * N);
+                const int4 b = *reinterpret_cast<const int4*>(col + (r0 + t) * N + 4);
+                acc[0] += tap[t] * a.x; acc[1] += tap[t] * a.y; acc[2] += tap[t] * a.z; acc[3] += tap[t] * a.w;
+                acc[4] += tap[t] * b.x; acc[5] += tap[t] * b.y; acc[6] += tap[t] * b.z; acc[7] += tap[t] * b.w;
             }
+#pragma unroll
+            for (int x = 0; x < 8; ++x) d[x] = dec_sample(cb[x]) - wp_round(acc[x] >> sh);
         }
         hadamard8_row(d);
         uint4 pk;
@@ -445,10 +456,12 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     const int q = tid & (P - 1);
     const unsigned pmask = P == 1 ? 0u : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
     uint64_t best = ~0ull;
-    for (int u = tid / P; u < units; u += NT / P) {
-        int gx = u / side;
-        int dy = u - gx * side - R;
-        int dx0 = gx * 8 - R;
+    // (gx, dy) of unit u = gx * side + dy + R, advanced without division
+    int gx = (tid / P) / side, dyi = (tid / P) - gx * side;
+    const int ustep = NT / P, gstep = ustep / side, dstep = ustep - gstep * side;
+    for (int u = tid / P; u < units; u += ustep) {
+        const int dy = dyi - R;
+        const int dx0 = gx * 8 - R;
         const int woff = (dy + R + 4) * S + (dx0 + R + 4);
         const uint32_t rowbase = (uint32_t)((dy + R) * side);
         const int by = s_bitsd[dy + R];
@@ -461,6 +474,9 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
                 const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(2 * R));
                 best = key < best ? key : best;
             }
+            gx += gstep;
+            dyi += dstep;
+            if (dyi >= side) { dyi -= side; ++gx; }
             continue;
         }
         uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -475,7 +491,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         }
         for (; r < N; r += P) row_sad8<N>(blk + r * N, win + woff + r * S, sad);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sad[k] += (uint32_t)accf[k];
+        for (int k = 0; k < 8; ++k)  // exact integer below 2^23: read it through the 2^23 bias
+            sad[k] += __float_as_uint(accf[k] + 8388608.0f) - 0x4B000000u;
         for (int o = 1; o < P; o <<= 1)
 #pragma unroll
             for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
@@ -488,6 +505,9 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
                 best = key < best ? key : best;
             }
         }
+        gx += gstep;
+        dyi += dstep;
+        if (dyi >= side) { dyi -= side; ++gx; }
     }
     best = block_min_u64<NT>(best, red);
     MeResult res;
@@ -506,7 +526,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     cand_x[0] = cx; cand_y[0] = cy;
 #pragma unroll
     for (int k = 0; k < 8; ++k) { cand_x[k + 1] = cx + 2 * ring_x[k]; cand_y[k + 1] = cy + 2 * ring_y[k]; }
-    if constexpr (N <= 32) satd_stage_smem<N, NT>(win, S, R, blk, hp, had, cx, cy, 2, cand_x, cand_y, 9, satd);
+    if constexpr (N <= 32)
+        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 2, cand_x, cand_y, 9, satd);
     else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 2, cand_x, cand_y, 9, satd);
     uint32_t bJ = satd[0] + mv_cost(cx, cy, lmv);
     int bx = cx, by = cy;
@@ -519,7 +540,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     cx = bx; cy = by;
 #pragma unroll
     for (int k = 0; k < 8; ++k) { cand_x[k] = cx + ring_x[k]; cand_y[k] = cy + ring_y[k]; }
-    if constexpr (N <= 32) satd_stage_smem<N, NT>(win, S, R, blk, hp, had, cx, cy, 1, cand_x, cand_y, 8, satd);
+    if constexpr (N <= 32)
+        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 1, cand_x, cand_y, 8, satd);
     else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 1, cand_x, cand_y, 8, satd);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {

@@ -188,7 +188,9 @@ __host__ __device__ constexpr int tqr_nslots() { return N >= 16 ? 3 : (N >= 8 ? 
 __host__ __device__ constexpr size_t tqr_conc_off_stage(int N) { return align16((size_t)2 * 3 * N * N * 2); }
 __host__ __device__ constexpr size_t tqr_conc_off_hbuf(int N) { return tqr_conc_off_stage(N) + align16((size_t)3 * (N + 7) * (N + 7) * 2); }
 __host__ __device__ constexpr size_t tqr_conc_off_slots(int N) { return tqr_conc_off_hbuf(N) + align16((size_t)3 * (N + 7) * N * 2); }
-__host__ __device__ constexpr size_t tqr_conc_slot_bytes(int N) { return align16((size_t)3 * 3 * N * N * 2); }
+__host__ __device__ constexpr size_t tqr_conc_slot_bytes(int N) {
+    return align16((size_t)3 * 3 * N * N * 2) + align16((size_t)3 * N * N * 4);
+}
 __host__ __device__ constexpr size_t tqr_conc_off_acc(int N) { return tqr_conc_off_slots(N) + 3 * tqr_conc_slot_bytes(N); }
 __host__ __device__ constexpr size_t tqr_conc_smem_bytes(int N) { return tqr_conc_off_acc(N) + 3 * 8 + 3 * 4 + 16; }
 
@@ -208,30 +210,36 @@ __device__ __forceinline__ void conc_row_fwd(int lt, const uint16_t* __restrict_
     for (int i = 0; i < TS; ++i) work[base + i] = (int16_t)rshift_round(yv[i], L + kBitDepth - 9);
 }
 
+// Forward column transform of one TU column: coefficients C = rs(T Y, log2N + 6).
 template <int N, int TS>
-__device__ __forceinline__ uint32_t conc_col(int lt, int16_t* __restrict__ work, int16_t* __restrict__ lev, int qp) {
+__device__ __forceinline__ void conc_col_fwd(int lt, const int16_t* __restrict__ work, int* __restrict__ coef) {
     constexpr int L = TS == 4 ? 2 : TS == 8 ? 3 : TS == 16 ? 4 : 5;
     constexpr int NTU = N / TS;
-    const QuantParams q = quant_params(qp, L);
     const int c = lt / (N * NTU), rem = lt - c * N * NTU;
     const int ty = rem / N, x = rem - ty * N;
     const int base = c * N * N + ty * TS * N + x;
     int col[TS], cf[TS];
-    uint32_t bits = 0;
 #pragma unroll
     for (int i = 0; i < TS; ++i) col[i] = work[base + i * N];
     fwd1d<TS>(col, cf);
 #pragma unroll
-    for (int i = 0; i < TS; ++i) {
-        int lv = quantize(rshift_round(cf[i], L + 6), q);
-        lev[base + i * N] = (int16_t)lv;
-        if (lv != 0) bits += (uint32_t)(2 * L + se_len(lv));
-        col[i] = dequantize(lv, q);
-    }
-    inv1d<TS>(col, cf);
+    for (int i = 0; i < TS; ++i) coef[base + i * N] = rshift_round(cf[i], L + 6);
+}
+
+// Inverse column transform of one TU column of dequantised coefficients:
+// E = clip16(rs(T^T D, 7)).
+template <int N, int TS>
+__device__ __forceinline__ void conc_col_inv(int lt, const int* __restrict__ coef, int16_t* __restrict__ work) {
+    constexpr int NTU = N / TS;
+    const int c = lt / (N * NTU), rem = lt - c * N * NTU;
+    const int ty = rem / N, x = rem - ty * N;
+    const int base = c * N * N + ty * TS * N + x;
+    int col[TS], r[TS];
 #pragma unroll
-    for (int i = 0; i < TS; ++i) work[base + i * N] = (int16_t)clip16(rshift_round(cf[i], 7));
-    return bits;
+    for (int i = 0; i < TS; ++i) col[i] = coef[base + i * N];
+    inv1d<TS>(col, r);
+#pragma unroll
+    for (int i = 0; i < TS; ++i) work[base + i * N] = (int16_t)clip16(rshift_round(r[i], 7));
 }
 
 template <int N, int TS>
@@ -276,6 +284,9 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
     auto work_of = [&](int s) { return reinterpret_cast<int16_t*>(slots + s * tqr_conc_slot_bytes(N)); };
     auto lev_of = [&](int s) { return work_of(s) + 3 * NN; };
     auto rec_of = [&](int s) { return reinterpret_cast<uint16_t*>(work_of(s) + 6 * NN); };
+    auto coef_of = [&](int s) {
+        return reinterpret_cast<int*>(slots + s * tqr_conc_slot_bytes(N) + align16((size_t)3 * 3 * NN * 2));
+    };
 
     // 1. current samples and the motion-compensation windows of all channels
     const int ix = mvx >> 2, iy = mvy >> 2, fx = mvx & 3, fy = mvy & 3;
@@ -351,7 +362,9 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
         if constexpr (NS > 2) if (s == 2) conc_row_fwd<N, 16>(lt, s_cur, s_pred, work_of(2));
     }
     __syncthreads();
-    // 3. columns: forward, quantise, dequantise, inverse
+    // 3. columns: forward transform; then quantise / dequantise element by
+    // element over every coefficient of every size (balanced over the block);
+    // then the inverse column transform
     uint32_t bitsS[NS];
     uint64_t sseS[NS];
 #pragma unroll
@@ -360,9 +373,40 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
         int s = 0;
         while (s < NS - 1 && t >= cum[s + 1]) ++s;
         const int lt = t - cum[s];
-        if (s == 0) bitsS[0] += conc_col<N, 4>(lt, work_of(0), lev_of(0), qp);
-        if constexpr (NS > 1) if (s == 1) bitsS[1] += conc_col<N, 8>(lt, work_of(1), lev_of(1), qp);
-        if constexpr (NS > 2) if (s == 2) bitsS[2] += conc_col<N, 16>(lt, work_of(2), lev_of(2), qp);
+        if (s == 0) conc_col_fwd<N, 4>(lt, work_of(0), coef_of(0));
+        if constexpr (NS > 1) if (s == 1) conc_col_fwd<N, 8>(lt, work_of(1), coef_of(1));
+        if constexpr (NS > 2) if (s == 2) conc_col_fwd<N, 16>(lt, work_of(2), coef_of(2));
+    }
+    __syncthreads();
+    {
+        QuantParams qs[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) qs[s] = quant_params(qp, s + 2);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (!((tu_mask >> (s + 2)) & 1u)) continue;
+            int* cf = coef_of(s);
+            int16_t* lv = lev_of(s);
+            for (int i = tid; i < 3 * NN; i += NT) {
+                const int l = quantize(cf[i], qs[s]);
+                lv[i] = (int16_t)l;
+                if (l != 0) {
+                    bitsS[s] += (uint32_t)(2 * (s + 2) + se_len(l));
+                    cf[i] = dequantize(l, qs[s]);
+                } else {
+                    cf[i] = 0;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < TOT; t += NT) {
+        int s = 0;
+        while (s < NS - 1 && t >= cum[s + 1]) ++s;
+        const int lt = t - cum[s];
+        if (s == 0) conc_col_inv<N, 4>(lt, coef_of(0), work_of(0));
+        if constexpr (NS > 1) if (s == 1) conc_col_inv<N, 8>(lt, coef_of(1), work_of(1));
+        if constexpr (NS > 2) if (s == 2) conc_col_inv<N, 16>(lt, coef_of(2), work_of(2));
     }
     __syncthreads();
     // 4. inverse rows, reconstruction, SSE
