@@ -309,7 +309,7 @@ uint64_t xv_ctx_launches(const xv_ctx* ctx);
 /* Spin budget (SM clock cycles, default 4e9, about 2 s) of each dependency
  * wait in xv_encode_batch.  Host only. */
 xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
-/* Run xv_encode_batch with this block size (128, 192 or 256) instead of the
+/* Run xv_encode_batch with this block size (128, 192, 256 or 512) instead of the
  * autotuner's choice; 0 restores the autotuner.  Host only. */
 xv_status xv_debug_force_block_size(xv_ctx* ctx, int block_size);
 /* Make one dependency counter of xv_encode_batch impossible to complete: the

@@ -112,7 +112,7 @@ cudaError_t launch_prepare_bands(const void* src, xv_dtype dt, int bands, int64_
 // totals[j] = sum of job j's per-frame bits.
 cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long* totals, cudaStream_t st);
 // Block sizes the persistent kernel is built for (the autotuner picks one).
-constexpr int kPersistBlockSizes[3] = {128, 192, 256};
+constexpr int kPersistBlockSizes[4] = {128, 192, 256, 512};
 cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,
                            int grid, cudaStream_t st);
 int persist_grid(int ctu, int nt, size_t smem);
