@@ -117,6 +117,10 @@ xv_status xv_quantize_pack(xv_ctx* ctx, const void* src, xv_dtype dtype, int ban
  *  best, each J = SATD(8x8 Hadamard) + mvcost, replacing the best only when
  *  strictly lower.  mvcost(mx, my) = (lambda_mv_fp16 (|se(mx)| + |se(my)|)
  *  + 2^15) >> 16 with |se| the signed Exp-Golomb code length.
+ *  The kernels skip candidates whose lower bound (sum over sub-blocks of
+ *  |sum cur - sum ref|, plus mvcost) exceeds the J of a candidate already
+ *  evaluated; such a candidate can neither win nor tie, so the result is
+ *  that of the full search.
  * cur/ref: device uint16, group g's frame at cur + g * plane_gstride, layout
  *   [3][Hp][Wp] (only channel 0 is read).
  * mv: int16 [G][nPU][2] quarter-sample (x, y); cost: uint32 [G][nPU] (final
@@ -301,6 +305,14 @@ xv_status xv_batch_graph_stats(const xv_ctx* ctx, uint64_t* captures, uint64_t* 
 /* Threads per block of the last xv_encode_batch persistent launch (the
  * autotuner's choice for that batch shape).  Host only. */
 xv_status xv_last_batch_block_size(const xv_ctx* ctx, int* block_size);
+/* Integer-search work of the last xv_encode_batch on this context.
+ * `full_candidates`: the candidates of the integer full search defined at
+ * xv_motion_search, (2R + 1)^2 per PU of every frame after the first.
+ * `exact_candidates`: those whose SAD the kernels computed exactly (8 per
+ * 8-wide unit of vectors, 1 per single last-column unit); the others were
+ * excluded by the sub-block sum bound and cannot be the minimum.  Either
+ * pointer may be NULL.  Host only. */
+xv_status xv_last_batch_search_stats(const xv_ctx* ctx, uint64_t* exact_candidates, uint64_t* full_candidates);
 /* Number of kernels this context has launched so far.  Host only. */
 uint64_t xv_ctx_launches(const xv_ctx* ctx);
 

@@ -89,14 +89,15 @@ __device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, ui
     }
 }
 
+// Encodes one PU; returns the integer-search candidates evaluated exactly.
 template <int N, int kNT>
-__device__ void item_work(const JobDev& J, int g, int t, int pu, unsigned char* smem) {
+__device__ uint32_t item_work(const JobDev& J, int g, int t, int pu, unsigned char* smem) {
     const int64_t plane = (int64_t)J.Hp * J.Wp, fsz = 3 * plane;
     const int64_t f = (int64_t)g * J.T + t;
     const uint16_t* cur = J.planes + f * fsz;
     const uint16_t* ref = t > 0 ? J.recon + (f - 1) * fsz : nullptr;
     const int x0 = (pu % J.nx) * N, y0 = (pu / J.nx) * N;
-    xvd::MeResult m{0, 0, 0u, 0, 0, 0u};
+    xvd::MeResult m{0, 0, 0u, 0, 0, 0u, 0u};
     if (ref) m = xvd::me_pu<N, kNT, true>(cur, ref, J.Hp, J.Wp, x0, y0, J.R, J.lmv, smem);
     const int64_t npu = (int64_t)J.nx * J.ny;
     uint32_t b = xvd::tqr_cu<N, kNT, true>(cur, ref, plane, J.Hp, J.Wp, x0, y0, m.mvx, m.mvy, J.qp, J.tu_mask,
@@ -108,6 +109,7 @@ __device__ void item_work(const JobDev& J, int g, int t, int pu, unsigned char* 
         if (J.cost) J.cost[o] = m.cost;
         atomicAdd(reinterpret_cast<unsigned long long*>(J.bits + f), (unsigned long long)b);
     }
+    return m.exact_cand;
 }
 
 template <int N, int kNT>
@@ -118,6 +120,7 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
     __shared__ uint64_t s_key;
     __shared__ int s_full;
     const unsigned total = ctl->total;
+    unsigned long long exact = 0;  // thread 0: this block's exactly evaluated candidates
     if (threadIdx.x == 0) s_next = atomicAdd(&ctl->head, 1u);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -135,13 +138,14 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
             const int job = (int)(key >> 56);
             const JobDev& J = jobs[job];
             const int g = (int)((key >> 48) & 0xff), t = (int)((key >> 32) & 0xffff), pu = (int)(uint32_t)key;
-            item_work<N, kNT>(J, g, t, pu, smem);
+            exact += item_work<N, kNT>(J, g, t, pu, smem);
             __threadfence();
             __syncthreads();
             complete_item(J, job, g, t, pu, queue, ctl, &s_full);
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && exact) atomicAdd(&ctl->exact_cand, exact);
 }
 
 

@@ -66,7 +66,7 @@ __global__ void k_batch_prologue(const JobDev* __restrict__ jobs, int njobs, con
     }
     if (b == njobs && threadIdx.x < 4) {
         const int k = threadIdx.x;
-        ctl[k] = BatchCtl{0u, cls[k].nfirst, cls[k].total, 0, budget, stall_row};
+        ctl[k] = BatchCtl{0u, cls[k].nfirst, cls[k].total, 0, budget, stall_row, 0ull};
     }
 }
 

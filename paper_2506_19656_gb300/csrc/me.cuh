@@ -32,27 +32,70 @@ struct MeResult {
     uint32_t cost_int;
     int mvx, mvy;          // final vector (quarter samples)
     uint32_t cost;
+    uint32_t exact_cand;   // integer candidates whose SAD was computed exactly
 };
 
 __host__ __device__ constexpr int me_win(int N, int R) { return N + 2 * R + 8; }
 __host__ __device__ constexpr int me_stride(int N, int R) {
     return ((me_win(N, R) + 3) / 8) * 8 + 4;  // smallest S >= WW with S % 8 == 4
 }
+
+// Exact pruning of the integer search.  For a candidate, split the PU into
+// SB x SB sub-blocks; by the triangle inequality the SAD is at least the sum
+// over sub-blocks of |sum of current samples - sum of reference samples|.
+// A candidate whose bound plus motion cost exceeds the J of a candidate
+// already evaluated exactly cannot be the minimum (nor tie with it), so only
+// the rest need the exact SAD and the result is that of the full search.
+// The reference sums come from a table of SB x SB box sums at every window
+// position.  For CTU 16 and 64 it is built and used K row classes at a time
+// (box rows y with y - 4 = m mod K, m = 0..K-1): CTU 64 for the whole table
+// would not fit next to the window, and at CTU 16 the smaller table keeps
+// five blocks per SM resident.
+__host__ __device__ constexpr int me_sb(int N) { return N <= 16 ? 4 : (N == 32 ? 8 : 16); }
+__host__ __device__ constexpr int me_kcls(int N) { return N == 64 || N == 16 ? 4 : 1; }
+__host__ __device__ constexpr int me_side(int R) { return 2 * R + 1; }
+__host__ __device__ constexpr bool me_lastcol(int R) { return me_side(R) % 8 == 1; }
+// 8-wide column groups of candidates, plus the single last column when
+// 2R + 1 = 8m + 1
+__host__ __device__ constexpr int me_ngx(int R) { return me_lastcol(R) ? me_side(R) / 8 : (me_side(R) + 7) / 8; }
+__host__ __device__ constexpr int me_ngxa(int R) { return me_ngx(R) + (me_lastcol(R) ? 1 : 0); }
+__host__ __device__ constexpr int me_units(int R) { return me_side(R) * me_ngxa(R); }
+// box-sum table: row stride (a multiple of 8) and rows of one class
+__host__ __device__ constexpr int me_tab_stride(int N, int R) { return (8 * me_ngxa(R) + N - me_sb(N) + 7) / 8 * 8; }
+__host__ __device__ constexpr int me_tab_rows(int N, int R) {
+    return (2 * R + N - me_sb(N) + me_kcls(N)) / me_kcls(N);
+}
+
 // Byte offsets of the shared-memory regions (every region 16-byte aligned).
+// The scratch region holds the pruning tables during the integer search and
+// the refinement's filtered columns afterwards.
 __host__ __device__ constexpr size_t me_align16(size_t b) { return (b + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t me_off_blk(int N, int R) { return me_align16((size_t)me_win(N, R) * me_stride(N, R) * 4); }
-__host__ __device__ constexpr size_t me_off_hp(int N, int R) { return me_off_blk(N, R) + me_align16((size_t)N * N * 4); }
-__host__ __device__ constexpr size_t me_off_red(int N, int R) {
-    return me_off_hp(N, R) + me_align16((size_t)3 * (N + 8) * N * (N <= 32 ? 4 : 2));
-}
+__host__ __device__ constexpr size_t me_off_red(int N, int R) { return me_off_blk(N, R) + me_align16((size_t)N * N * 4); }
 __host__ __device__ constexpr size_t me_off_satd(int N, int R) { return me_off_red(N, R) + 64 * 8; }
 // motion-cost tables: |se(4d)| for d in [-R, R] (129 at most) and the
 // rounded cost of b bits, b < 64
 __host__ __device__ constexpr size_t me_off_cost(int N, int R) { return me_off_satd(N, R) + 16 * 4; }
-__host__ __device__ constexpr size_t me_off_had(int N, int R) { return me_off_cost(N, R) + me_align16((129 + 64) * 4); }
+__host__ __device__ constexpr size_t me_off_scr(int N, int R) { return me_off_cost(N, R) + me_align16((129 + 64) * 4); }
+// refinement view of the scratch region
+__host__ __device__ constexpr size_t me_hp_bytes(int N) { return me_align16((size_t)3 * (N + 8) * N * (N <= 32 ? 4 : 2)); }
+__host__ __device__ constexpr size_t me_off_hp(int N, int R) { return me_off_scr(N, R); }
+__host__ __device__ constexpr size_t me_off_had(int N, int R) { return me_off_scr(N, R) + me_hp_bytes(N); }
 // Candidates' horizontally transformed differences (PUs up to 32 only).
 __host__ __device__ constexpr size_t me_had_bytes(int N) { return N <= 32 ? me_align16((size_t)9 * N * N * 2) : 0; }
-__host__ __device__ constexpr size_t me_smem_bytes(int N, int R) { return me_off_had(N, R) + me_had_bytes(N); }
+// pruning view: box table (later the survivor list), sub-block sums of the
+// PU, per-unit bounds
+__host__ __device__ constexpr size_t me_max(size_t a, size_t b) { return a > b ? a : b; }
+__host__ __device__ constexpr size_t me_tab_bytes(int N, int R) {
+    return me_align16(me_max((size_t)me_tab_rows(N, R) * me_tab_stride(N, R) * 4, (size_t)me_units(R) * 2));
+}
+__host__ __device__ constexpr size_t me_off_bsub(int N, int R) { return me_off_scr(N, R) + me_tab_bytes(N, R); }
+__host__ __device__ constexpr size_t me_off_ulb(int N, int R) {
+    return me_off_bsub(N, R) + me_align16((size_t)(N / me_sb(N)) * (N / me_sb(N)) * 4);
+}
+__host__ __device__ constexpr size_t me_smem_bytes(int N, int R) {
+    return me_max(me_off_had(N, R) + me_had_bytes(N), me_off_ulb(N, R) + me_align16((size_t)me_units(R) * 4));
+}
 
 // Samples in the window and block are stored as the float 2^23 + v (v <= 1023).
 // Its bit pattern is 0x4B000000 | v, so the integer path's __sad on the raw
@@ -440,74 +483,256 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         if (i < 2 * R + 1) s_bitsd[i] = se_len(4 * (i - R));
         else s_costb[i - (2 * R + 1)] = (uint32_t)((lmv * (int64_t)(i - (2 * R + 1)) + 32768) >> 16);
     }
+    {  // sub-block sums, the seed unit's sums and the survivor count start at 0
+        int* bs = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
+        constexpr int nsb = (N / me_sb(N)) * (N / me_sb(N));
+        for (int i = tid; i < nsb + 10; i += NT) {
+            if (i < nsb) bs[i] = 0;
+            else satd[i - nsb] = 0;
+        }
+    }
     __syncthreads();
 
-    // ---- integer full search
+    // ---- integer search, exact pruning (see me_sb above)
     // Units: (dy, 8 consecutive dx) for the first 8m columns of candidates;
     // when 2R + 1 = 8m + 1 the last column is a unit of its own (one
-    // candidate per dy), else it is covered by an 8-wide unit that discards
-    // the candidates beyond R.
-    const int side = 2 * R + 1;
-    const int full = side / 8;
-    const bool lastcol = side - 8 * full == 1;
-    const int ngx = lastcol ? full : (side + 7) / 8;  // 8-wide column groups
-    const int units = side * ngx + (lastcol ? side : 0);
-    const int P = me_split(units, NT);      // lanes sharing one unit (rows interleaved)
-    const int q = tid & (P - 1);
-    const unsigned pmask = P == 1 ? 0u : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
-    uint64_t best = ~0ull;
-    // (gx, dy) of unit u = gx * side + dy + R, advanced without division
-    int gx = (tid / P) / side, dyi = (tid / P) - gx * side;
-    const int ustep = NT / P, gstep = ustep / side, dstep = ustep - gstep * side;
-    for (int u = tid / P; u < units; u += ustep) {
-        const int dy = dyi - R;
-        const int dx0 = gx * 8 - R;
-        const int woff = (dy + R + 4) * S + (dx0 + R + 4);
-        const uint32_t rowbase = (uint32_t)((dy + R) * side);
-        const int by = s_bitsd[dy + R];
-        if (gx == ngx) {  // the single last column, dx = R
-            uint32_t sad1 = 0;
-            for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, win + woff + r * S, sad1);
-            for (int o = 1; o < P; o <<= 1) sad1 += __shfl_xor_sync(pmask, sad1, o);
-            if (q == 0) {
-                const uint32_t J = sad1 + s_costb[s_bitsd[2 * R] + by];
-                const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(2 * R));
-                best = key < best ? key : best;
-            }
-            gx += gstep;
-            dyi += dstep;
-            if (dyi >= side) { dyi -= side; ++gx; }
-            continue;
+    // candidate per dy, column group gx = ngx), else it is covered by an
+    // 8-wide unit that discards the candidates beyond R.  Unit u = gx * side
+    // + dy + R.
+    constexpr int SB = me_sb(N), NS = N / SB, K = me_kcls(N);
+    const int side = me_side(R);
+    const int ngx = me_ngx(R), ngxa = me_ngxa(R);
+    const int units = side * ngxa;
+    const int TS = me_tab_stride(N, R);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem + me_off_scr(N, R));
+    uint16_t* list = reinterpret_cast<uint16_t*>(smem + me_off_scr(N, R));  // after the bounds
+    int* bsub = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
+    uint32_t* ulb = reinterpret_cast<uint32_t*>(smem + me_off_ulb(N, R));
+
+    // sub-block sums of the PU: one task per (sub-block, row), summing SB
+    // biased words (the bias cancels modulo 2^32)
+    for (int task = tid; task < NS * NS * SB; task += NT) {
+        const int sbk = task / SB, r = task - sbk * SB;
+        const int i = sbk / NS, j = sbk - i * NS;
+        const int* row = blk + (i * SB + r) * N + j * SB;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int c = 0; c < SB; c += 4) {
+            const int4 v = *reinterpret_cast<const int4*>(row + c);
+            acc += (uint32_t)v.x + (uint32_t)v.y + (uint32_t)v.z + (uint32_t)v.w;
         }
-        uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        float accf[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        // rows in triples: two on the integer ALU, the third on the FP32 pipe
-        int r = q;
+        atomicAdd(bsub + sbk, (int)(acc - (uint32_t)SB * (uint32_t)kSampleBias));
+    }
+    // Box table of row class m: entry (t, tx) = sum of the SB x SB window
+    // samples with top-left corner (4 + m + K t, 4 + tx).  One task per 8
+    // consecutive entries: horizontal running sums over SB window rows.
+    auto build_tab = [&](int m) {
+        const int nr = (2 * R + N - SB - m) / K + 1;
+        const int nch = TS / 8;
+        for (int task = tid; task < nr * nch; task += NT) {
+            const int t = task / nch, c = task - t * nch;
+            const int* w0 = win + (4 + m + K * t) * S + 8 * c + 4;
+            uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 1
-        for (; r + 2 * P < N; r += 3 * P) {
-            row_sad8<N>(blk + r * N, win + woff + r * S, sad);
-            row_sad8<N>(blk + (r + P) * N, win + woff + (r + P) * S, sad);
-            row_sad8f<N>(blk + (r + 2 * P) * N, win + woff + (r + 2 * P) * S, accf);
+            for (int r = 0; r < SB; ++r) {
+                uint32_t v[8 + SB];
+#pragma unroll
+                for (int i = 0; i < 8 + SB; i += 4) {
+                    const int4 q4 = *reinterpret_cast<const int4*>(w0 + r * S + i);
+                    v[i] = (uint32_t)q4.x; v[i + 1] = (uint32_t)q4.y; v[i + 2] = (uint32_t)q4.z; v[i + 3] = (uint32_t)q4.w;
+                }
+                uint32_t h = 0;
+#pragma unroll
+                for (int i = 0; i < SB; ++i) h += v[i];
+                acc[0] += h;
+#pragma unroll
+                for (int k = 1; k < 8; ++k) {
+                    h += v[k + SB - 1] - v[k - 1];
+                    acc[k] += h;
+                }
+            }
+            uint4 o0, o1;
+            const uint32_t bias = (uint32_t)(SB * SB) * (uint32_t)kSampleBias;
+            o0.x = acc[0] - bias; o0.y = acc[1] - bias; o0.z = acc[2] - bias; o0.w = acc[3] - bias;
+            o1.x = acc[4] - bias; o1.y = acc[5] - bias; o1.z = acc[6] - bias; o1.w = acc[7] - bias;
+            *reinterpret_cast<uint4*>(tab + t * TS + 8 * c) = o0;
+            *reinterpret_cast<uint4*>(tab + t * TS + 8 * c + 4) = o1;
         }
-        for (; r < N; r += P) row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+    };
+    build_tab(0);
+    __syncthreads();
+
+    // bound pass: per unit the smallest bound + motion cost of its valid
+    // candidates (dx <= R) into ulb[u]; the unit with the smallest one is the
+    // seed
+    uint64_t lbbest = ~0ull;
+#pragma unroll 1
+    for (int m = 0; m < K; ++m) {
+        if (m > 0) {
+            __syncthreads();
+            build_tab(m);
+            __syncthreads();
+        }
+        const int nd = m <= 2 * R ? (2 * R - m) / K + 1 : 0;  // dy + R = m, m + K, ...
+        const int ncu = nd * ngxa;
+        int P = me_split(ncu, NT);
+        P = P < NS ? P : NS;
+        const int q = tid & (P - 1);
+        const unsigned pmask = P == 1 ? 0u : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
+        for (int v = tid / P; v < ncu; v += NT / P) {
+            const int gx = v / nd;
+            const int dyi = m + K * (v - gx * nd);
+            const uint32_t* trow = tab + ((dyi - m) / K) * TS + 8 * gx;
+            uint32_t lb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i = q; i < NS; i += P) {
+                const uint32_t* tr = trow + i * (SB / K) * TS;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)  // exact integer below 2^23: read it through the 2^23 bias
-            sad[k] += __float_as_uint(accf[k] + 8388608.0f) - 0x4B000000u;
-        for (int o = 1; o < P; o <<= 1)
+                for (int j = 0; j < NS; ++j) {
+                    const uint4 b0 = *reinterpret_cast<const uint4*>(tr + SB * j);
+                    const uint4 b1 = *reinterpret_cast<const uint4*>(tr + SB * j + 4);
+                    const int cs = bsub[i * NS + j];
+                    lb[0] = __sad(cs, (int)b0.x, lb[0]); lb[1] = __sad(cs, (int)b0.y, lb[1]);
+                    lb[2] = __sad(cs, (int)b0.z, lb[2]); lb[3] = __sad(cs, (int)b0.w, lb[3]);
+                    lb[4] = __sad(cs, (int)b1.x, lb[4]); lb[5] = __sad(cs, (int)b1.y, lb[5]);
+                    lb[6] = __sad(cs, (int)b1.z, lb[6]); lb[7] = __sad(cs, (int)b1.w, lb[7]);
+                }
+            }
+            for (int o = 1; o < P; o <<= 1)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
+                for (int k = 0; k < 8; ++k) lb[k] += __shfl_xor_sync(pmask, lb[k], o);
+            if (q == 0) {
+                const int by = s_bitsd[dyi];
+                uint32_t mn = ~0u;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int dx = gx * 8 - R + k;
+                    if (dx <= R) {
+                        const uint32_t J = lb[k] + s_costb[s_bitsd[dx + R] + by];
+                        mn = J < mn ? J : mn;
+                    }
+                }
+                const int u = gx * side + dyi;
+                ulb[u] = mn;
+                const uint64_t key = ((uint64_t)mn << 32) | (uint32_t)u;
+                lbbest = key < lbbest ? key : lbbest;
+            }
+        }
+    }
+    lbbest = block_min_u64<NT>(lbbest, red);  // its barriers also end the bound pass
+    const int useed = (int)(lbbest & 0xffffffffu);
+
+    // exact SAD of the seed unit: one block row per thread, reduced per warp
+    {
+        const int gx = useed / side, dyi = useed - gx * side;
+        const int woff = (dyi + 4) * S + gx * 8 + 4;
+        const bool single = gx == ngx;  // the last column: dx = R only
+        for (int r = tid; r < ((N + 31) & ~31); r += NT) {
+            uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (r < N) {
+                if (single) sad[0] = row_sad1<N>(blk + r * N, win + woff + r * S, 0u);
+                else row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(0xffffffffu, sad[k], o);
+            if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) atomicAdd(satd + k, sad[k]);
+        }
+    }
+    __syncthreads();
+    uint64_t best = ~0ull;
+    uint32_t thr;
+    {
+        const int gx = useed / side, dyi = useed - gx * side;
+        const int by = s_bitsd[dyi];
+        const uint32_t rowbase = (uint32_t)(dyi * side);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int dx = dx0 + k;
-            if ((k & (P - 1)) == q && dx <= R) {  // the P lanes share the candidates
-                const uint32_t J = sad[k] + s_costb[s_bitsd[dx + R] + by];
+            const int dx = gx * 8 - R + k;
+            if (dx <= R) {
+                const uint32_t J = satd[k] + s_costb[s_bitsd[dx + R] + by];
                 const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(dx + R));
                 best = key < best ? key : best;
             }
         }
-        gx += gstep;
-        dyi += dstep;
-        if (dyi >= side) { dyi -= side; ++gx; }
+        thr = (uint32_t)(best >> 32);
+    }
+    // survivors: units (other than the seed) whose bound does not exceed
+    // the seed's J; warp-aggregated appends (satd[9] counts the single-column
+    // ones, for the executed-work statistic)
+    {
+        const int lane = threadIdx.x & 31;
+        for (int u0 = tid - lane; u0 < units; u0 += NT) {
+            const int u = u0 + lane;
+            const bool keep = u < units && u != useed && ulb[u] <= thr;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (!bal) continue;
+            const unsigned bal1 = __ballot_sync(0xffffffffu, keep && u >= ngx * side);
+            unsigned base = 0;
+            if (lane == 0) {
+                base = atomicAdd(satd + 8, (uint32_t)__popc(bal));
+                if (bal1) atomicAdd(satd + 9, (uint32_t)__popc(bal1));
+            }
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) list[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)u;
+        }
+    }
+    __syncthreads();
+    const int M = (int)satd[8];
+    const uint32_t exact_cand = 8u * (uint32_t)(M - (int)satd[9]) + satd[9] + (useed >= ngx * side ? 1u : 8u);
+    // exact search over the survivors, P lanes per unit (rows interleaved)
+    {
+        int P = 1;
+        while (P < 32 && 2 * P <= N && M * 2 * P <= NT) P *= 2;
+        const int q = tid & (P - 1);
+        const unsigned pmask = P == 1 ? 0u : (P == 32 ? 0xffffffffu : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1)));
+        for (int i = tid / P; i < M; i += NT / P) {
+            const int u = list[i];
+            const int gx = u / side, dyi = u - gx * side;
+            const int dx0 = gx * 8 - R;
+            const int woff = (dyi + 4) * S + gx * 8 + 4;
+            const uint32_t rowbase = (uint32_t)(dyi * side);
+            const int by = s_bitsd[dyi];
+            if (gx == ngx) {  // the single last column, dx = R
+                uint32_t sad1 = 0;
+                for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, win + woff + r * S, sad1);
+                for (int o = 1; o < P; o <<= 1) sad1 += __shfl_xor_sync(pmask, sad1, o);
+                if (q == 0) {
+                    const uint32_t J = sad1 + s_costb[s_bitsd[2 * R] + by];
+                    const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(2 * R));
+                    best = key < best ? key : best;
+                }
+                continue;
+            }
+            uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float accf[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            // rows in triples: two on the integer ALU, the third on the FP32 pipe
+            int r = q;
+#pragma unroll 1
+            for (; r + 2 * P < N; r += 3 * P) {
+                row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+                row_sad8<N>(blk + (r + P) * N, win + woff + (r + P) * S, sad);
+                row_sad8f<N>(blk + (r + 2 * P) * N, win + woff + (r + 2 * P) * S, accf);
+            }
+            for (; r < N; r += P) row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)  // exact integer below 2^23: read it through the 2^23 bias
+                sad[k] += __float_as_uint(accf[k] + 8388608.0f) - 0x4B000000u;
+            for (int o = 1; o < P; o <<= 1)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int dx = dx0 + k;
+                if ((k & (P - 1)) == q && dx <= R) {  // the P lanes share the candidates
+                    const uint32_t J = sad[k] + s_costb[s_bitsd[dx + R] + by];
+                    const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(dx + R));
+                    best = key < best ? key : best;
+                }
+            }
+        }
     }
     best = block_min_u64<NT>(best, red);
     MeResult res;
@@ -516,6 +741,7 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         res.mvy_int = idx / side - R;
         res.mvx_int = idx - (idx / side) * side - R;
         res.cost_int = (uint32_t)(best >> 32);
+        res.exact_cand = exact_cand;
     }
 
     // ---- quarter-sample refinement: centre + 8 half-sample, then 8 quarter

@@ -32,6 +32,7 @@ struct xv_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launches
     double batch_ms = 0.0;
     int batch_nt = 0;                        // block size of the last persistent launch
+    uint64_t batch_exact = 0, batch_full = 0;  // integer-search candidates: evaluated exactly / defined
     std::map<std::string, int> tuned_nt;     // autotuner: batch shape -> block size
     int force_nt = 0;                        // test hook (xv_debug_force_block_size)
     // batched path: buffers, work stream and the captured graph
@@ -772,6 +773,14 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     }
 
     // ---- results (host)
+    c->batch_exact = 0;
+    c->batch_full = 0;
+    for (int k = 0; k < 4; ++k)
+        if (total[k]) c->batch_exact += h_ctl[k].exact_cand;
+    for (int i = 0; i < njobs; ++i) {
+        const uint64_t side = 2 * (uint64_t)jobs[i].p.search_range + 1;
+        c->batch_full += (uint64_t)jd[i].G * (uint64_t)(jobs[i].T - 1) * jd[i].nx * jd[i].ny * side * side;
+    }
     for (int k = 0; k < 4; ++k)
         if (total[k] && h_ctl[k].err) {
             set_error("a dependency wait of the persistent encode (CTU %d) ran out of time", ctus[k]);
@@ -808,6 +817,13 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
 xv_status xv_last_batch_block_size(const xv_ctx* c, int* nt) {
     if (!c || !nt) { set_error("ctx and nt are required"); return XV_EINVAL; }
     *nt = c->batch_nt;
+    return XV_OK;
+}
+
+xv_status xv_last_batch_search_stats(const xv_ctx* c, uint64_t* exact_candidates, uint64_t* full_candidates) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (exact_candidates) *exact_candidates = c->batch_exact;
+    if (full_candidates) *full_candidates = c->batch_full;
     return XV_OK;
 }
 

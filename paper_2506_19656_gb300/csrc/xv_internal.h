@@ -91,6 +91,7 @@ struct BatchCtl {
     int err;               // 0, or an xv_status (XV_ETIMEOUT) set by a block
     long long budget;      // spin budget per wait, in SM clock cycles
     long long stall_row;   // test hook: this dependency counter never completes (-1: none)
+    unsigned long long exact_cand;  // integer-search candidates whose SAD was computed exactly
 };
 
 // Item key: job (8 bits) | group (8) | frame (16) | PU (32).

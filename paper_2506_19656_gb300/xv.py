@@ -84,6 +84,7 @@ _SIGS = {
     "xv_serve_stop": [_vp],
     "xv_last_batch_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_double)],
     "xv_last_batch_block_size": [_vp, ctypes.POINTER(_i)],
+    "xv_last_batch_search_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "xv_ctx_launches": [_vp],
     "xv_set_batch_graphs": [_vp, _i],
     "xv_batch_graph_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -305,6 +306,15 @@ def xv_last_batch_block_size(ctx: Context) -> int:
     nt = _i()
     check(lib().xv_last_batch_block_size(ctx.handle, ctypes.byref(nt)), "xv_last_batch_block_size")
     return nt.value
+
+
+def xv_last_batch_search_stats(ctx: Context) -> tuple[int, int]:
+    """(candidates evaluated exactly, candidates of the full search) of the
+    last xv_encode_batch."""
+    ex, full = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().xv_last_batch_search_stats(ctx.handle, ctypes.byref(ex), ctypes.byref(full)),
+          "xv_last_batch_search_stats")
+    return ex.value, full.value
 
 
 def xv_set_batch_graphs(ctx: Context, enable: bool):

@@ -75,6 +75,14 @@ def test_deepextremecubes_prefix_plain_and_batched(xv, ctx, qp):
     assert_matches(buf, xv.xv_encode_cube(ctx, job), want)
     job2, buf2 = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, qp)
     assert_matches(buf2, xv.xv_encode_batch(ctx, [job2])[0], want)
+    # the search statistics: every P-frame PU's (2R+1)^2 candidates defined,
+    # at least one unit of them evaluated exactly
+    exact, full = xv.xv_last_batch_search_stats(ctx)
+    G, npu = (c.bands + 2) // 3, (c.H // c.ctu) * (c.W // c.ctu)
+    assert full == G * (6 - 1) * npu * (2 * c.R + 1) ** 2
+    side = 2 * c.R + 1
+    units = side * (side // 8 + 1 if side % 8 == 1 else (side + 7) // 8)
+    assert G * 5 * npu * 8 <= exact <= G * 5 * npu * units * 8
 
 
 def test_ragged_shapes_and_mixed_batch(xv, ctx):

@@ -109,6 +109,65 @@ def test_motion_search(xv, ctx, ctu, R, Hp, Wp, G):
         assert np.array_equal(to_np(cost)[g].astype(np.uint32), wc)
 
 
+def pruning_case(kind, Hp, Wp, seed):
+    """Frames on which the sub-block bound of the integer search is weak,
+    tight or tied everywhere: (cur, ref) channel-0 planes as [1, 3, Hp, Wp]."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:Hp, 0:Wp]
+    if kind == "flat":  # every SAD is 0: the motion cost alone decides
+        ref = np.full((Hp, Wp), 300)
+        cur = ref.copy()
+    elif kind == "flat_offset":  # every SAD is the same non-zero value
+        ref = np.full((Hp, Wp), 310)
+        cur = np.full((Hp, Wp), 300)
+    elif kind == "noise":  # independent noise: weak bounds, most units survive
+        ref = rng.integers(0, 1024, (Hp, Wp))
+        cur = rng.integers(0, 1024, (Hp, Wp))
+    elif kind == "stripes8":  # period 8: equal SADs at vectors 8 apart
+        ref = np.where(x % 8 < 4, 800, 100)
+        cur = np.roll(ref, 3, axis=1)
+    elif kind == "zero_sum_tiles":  # every 4x4 box sum equal: every bound is 0
+        a = rng.integers(-200, 201, (4, 4))
+        a -= a.sum() // 16
+        a[3, 3] -= a.sum()
+        ref = 512 + a[y % 4, x % 4]
+        cur = np.clip(np.roll(ref, (1, 2), axis=(0, 1)) + rng.integers(-3, 4, (Hp, Wp)), 0, 1023)
+    else:  # "checker": period 2 in both axes
+        ref = np.where((x + y) % 2 == 0, 900, 50)
+        cur = np.roll(ref, (1, 0), axis=(0, 1))
+    out = []
+    for pl in (cur, ref):
+        f = np.zeros((1, 3, Hp, Wp), np.uint16)
+        f[0, 0] = pl
+        f[0, 1] = pl[::-1]
+        f[0, 2] = 512
+        out.append(f)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["flat", "flat_offset", "noise", "stripes8", "zero_sum_tiles", "checker"])
+@pytest.mark.parametrize("ctu,R,Hp,Wp", [(8, 16, 24, 32), (8, 4, 16, 24), (16, 32, 48, 32), (16, 5, 32, 48),
+                                         (32, 16, 64, 96), (32, 12, 64, 64), (64, 64, 128, 128), (64, 9, 64, 128)])
+def test_motion_search_pruning_adversarial(xv, ctx, kind, ctu, R, Hp, Wp):
+    """The integer search skips candidates by an exact bound: on ties, weak
+    bounds and periodic textures its result is still the full search's."""
+    cur, ref = pruning_case(kind, Hp, Wp, ctu * 1000 + R)
+    p = xv.xv_params_init(ctu, R, 1 << 3, 27)
+    npu = (Hp // ctu) * (Wp // ctu)
+    mv = torch.zeros((1, npu, 2), dtype=torch.int16, device="cuda")
+    cost = torch.zeros((1, npu), dtype=torch.int32, device="cuda")
+    mvi = torch.zeros_like(mv)
+    costi = torch.zeros_like(cost)
+    xv.xv_motion_search(ctx, to_dev(cur), to_dev(ref), 1, 3 * Hp * Wp, Hp, Wp, p, mv, cost, mvi, costi, npu)
+    torch.cuda.synchronize()
+    wmi, wci = oracle.me_int(cur[0, 0], ref[0, 0], ctu, R, p.lambda_mv_fp16)
+    wm, wc = oracle.me_qpel(cur[0, 0], ref[0, 0], ctu, p.lambda_mv_fp16, wmi)
+    assert np.array_equal(to_np(mvi)[0], wmi)
+    assert np.array_equal(to_np(costi)[0].astype(np.uint32), wci)
+    assert np.array_equal(to_np(mv)[0], wm)
+    assert np.array_equal(to_np(cost)[0].astype(np.uint32), wc)
+
+
 @pytest.mark.parametrize("ctu,mask,qp", [(8, 0b1000, 27), (16, 0b11100, 22), (32, 0b111100, 32),
                                          (64, 0b111100, 27), (16, 0b10000, -12), (32, 0b100, 51)])
 @pytest.mark.parametrize("first", [True, False])
