@@ -13,13 +13,17 @@
 //                       consecutive lanes fall in distinct 16-byte bank
 //                       groups for 128-bit loads.
 //   blk  int32 [N][N]   the PU's channel-0 samples.
-//   hp   int16 [3][N+8][N]  horizontally filtered columns for the three
-//                       x-vectors of one refinement stage.
+//   scratch             during the integer search: the box-sum table, the
+//                       PU's sub-block sums, per-unit bounds, the survivor
+//                       list; during refinement: horizontally filtered
+//                       columns for the three x-vectors of one stage and the
+//                       candidates' row-transformed differences.
 // Work split of the integer search: a unit is one candidate row dy and 8
-// consecutive dx; consecutive lanes take consecutive dy (distinct window
-// rows), so the reference loads are conflict-free and the current-block loads
-// are warp-wide broadcasts.  Each lane keeps its best 64-bit key
-// (J << 32 | raster index); a block-wide min gives the winner and the
+// consecutive dx.  Bound pass: every unit, one lane (or a few) per unit, the
+// 8 bounds from 2 x 128-bit table loads per sub-block.  Exact pass: the
+// surviving units, P lanes per unit interleaving the block rows; the current
+// block's loads are warp-wide broadcasts.  Each lane keeps its best 64-bit
+// key (J << 32 | raster index); a block-wide min gives the winner and the
 // tie-break of the definition.
 #pragma once
 #include <cstdint>
@@ -104,20 +108,6 @@ __host__ __device__ constexpr size_t me_smem_bytes(int N, int R) {
 constexpr int kSampleBias = 0x4B000000;
 __device__ __forceinline__ int enc_sample(int v) { return kSampleBias | v; }
 __device__ __forceinline__ int dec_sample(int bits) { return bits - kSampleBias; }
-
-// Lanes per integer-search unit: the smallest P in {1, 2, 4} whose split of
-// units * P over NT threads wastes least (all P lanes of a unit sit in one
-// warp and interleave the block rows).
-__host__ __device__ inline int me_split(int units, int NT) {
-    // efficiency work / (iters * NT), compared as cross products
-    int bestP = 1;
-    long long bw = units, bd = (long long)((units + NT - 1) / NT) * NT;
-    for (int P = 2; P <= 4; P *= 2) {
-        const long long w = (long long)units * P, d = ((w + NT - 1) / NT) * NT;
-        if (w * bd > bw * d) { bw = w; bd = d; bestP = P; }
-    }
-    return bestP;
-}
 
 template <int NT>
 __device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
@@ -440,37 +430,40 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     const int wx0 = x0 - R - 4, wy0 = y0 - R - 4;
     const int xa = wx0 - (((wx0 % 8) + 8) % 8);  // 8-aligned start at or left of wx0
     const int nch = (wx0 + WW - xa + 7) / 8;
-    constexpr int kILP = 2;
-    for (int base = tid; base < WW * nch; base += NT * kILP) {
-        uint16_t v[kILP][8];
+    const int ntask = WW * nch;
+    constexpr int kILP = 4;  // loads in flight per thread before the first store
+    for (int base = tid; base < ntask; base += NT * kILP) {
+        uint4 v[kILP];
 #pragma unroll
         for (int j = 0; j < kILP; ++j) {
             const int task = base + j * NT;
-            if (task < WW * nch) {
+            if (task < ntask) {
                 const int r = task / nch, ch = task - r * nch;
                 const int yy = min(max(wy0 + r, 0), Hp - 1), xs = xa + 8 * ch;
                 const uint16_t* rowp = ref0 + (size_t)yy * Wp;
                 if (xs >= 0 && xs + 8 <= Wp) {
-                    uint4 w = ld_ref16<kCoherent>(reinterpret_cast<const uint4*>(rowp + xs));
-                    const uint16_t* e = reinterpret_cast<const uint16_t*>(&w);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) v[j][i] = e[i];
+                    v[j] = ld_ref16<kCoherent>(reinterpret_cast<const uint4*>(rowp + xs));
                 } else {
+                    uint32_t w[4];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) v[j][i] = (uint16_t)ld_ref<kCoherent>(rowp + min(max(xs + i, 0), Wp - 1));
+                    for (int i = 0; i < 4; ++i)
+                        w[i] = (uint32_t)ld_ref<kCoherent>(rowp + min(max(xs + 2 * i, 0), Wp - 1)) |
+                               ((uint32_t)ld_ref<kCoherent>(rowp + min(max(xs + 2 * i + 1, 0), Wp - 1)) << 16);
+                    v[j] = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
         }
 #pragma unroll
         for (int j = 0; j < kILP; ++j) {
             const int task = base + j * NT;
-            if (task < WW * nch) {
+            if (task < ntask) {
                 const int r = task / nch, ch = task - r * nch;
                 const int c0 = xa + 8 * ch - wx0;
+                const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int c = c0 + i;
-                    if (c >= 0 && c < WW) win[r * S + c] = enc_sample(v[j][i]);
+                    if (c >= 0 && c < WW) win[r * S + c] = enc_sample((int)((w[i >> 1] >> (16 * (i & 1))) & 0xffffu));
                 }
             }
         }
@@ -575,8 +568,11 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         }
         const int nd = m <= 2 * R ? (2 * R - m) / K + 1 : 0;  // dy + R = m, m + K, ...
         const int ncu = nd * ngxa;
-        int P = me_split(ncu, NT);
-        P = P < NS ? P : NS;
+        // lanes per unit: the most (up to NS) that still cover every unit in
+        // one round; one when even that is impossible (latency: a single
+        // lane per unit needs no reduction and no shared epilogue)
+        int P = 1;
+        while (2 * P <= NS && ncu * 2 * P <= NT) P *= 2;
         const int q = tid & (P - 1);
         const unsigned pmask = P == 1 ? 0u : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1));
         for (int v = tid / P; v < ncu; v += NT / P) {
