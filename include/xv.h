@@ -18,6 +18,9 @@
  *    message is available from xv_last_error() (thread-local).
  *  - Plane layout: uint16 [G][T][3][Hp][Wp] holding 10-bit samples, G =
  *    ceil(bands / 3) groups, Hp/Wp = H/W rounded up to the CTU size.
+ *    Plane pointers (planes, recon, levels, cur, ref) must be 16-byte
+ *    aligned and group strides multiples of 8 samples (the kernels move
+ *    16-byte chunks); otherwise the call returns XV_EINVAL.
  *  - Signed right shifts are arithmetic.  Bit depth B = 10.
  */
 #ifndef XV_H

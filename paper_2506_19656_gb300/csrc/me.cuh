@@ -134,14 +134,14 @@ __device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
     return v;
 }
 
-// SAD of 8 horizontally adjacent candidates over one block row, 16 columns at
+// SAD of 8 horizontally adjacent candidates over one block row, 8 columns at
 // a time: cur[c] against ref[c + k], k = 0..7.
 template <int W>
 __device__ __forceinline__ void row_sad8(const int* __restrict__ crow, const int* __restrict__ rrow,
                                          uint32_t (&sad)[8]) {
 #pragma unroll
-    for (int c0 = 0; c0 < W; c0 += 16) {
-        constexpr int CW = W < 16 ? W : 16;
+    for (int c0 = 0; c0 < W; c0 += 8) {
+        constexpr int CW = 8;
         int cv[CW], rv[CW + 8];
 #pragma unroll
         for (int i = 0; i < CW; i += 4) {
@@ -171,8 +171,8 @@ __device__ __forceinline__ void row_sad8f(const int* __restrict__ crow_i, const 
     const float* crow = reinterpret_cast<const float*>(crow_i);
     const float* rrow = reinterpret_cast<const float*>(rrow_i);
 #pragma unroll
-    for (int c0 = 0; c0 < W; c0 += 16) {
-        constexpr int CW = W < 16 ? W : 16;
+    for (int c0 = 0; c0 < W; c0 += 8) {
+        constexpr int CW = 8;
         float cv[CW], rv[CW + 8];
 #pragma unroll
         for (int i = 0; i < CW; i += 4) {
@@ -208,6 +208,17 @@ __device__ __forceinline__ uint32_t row_sad1(const int* __restrict__ crow, const
     return acc;
 }
 
+// Candidate k of a refinement stage around (cx, cy) with step s.  The ring
+// of 8 neighbours is taken in raster order (-1,-1), (0,-1), (1,-1), (-1,0),
+// (1,0), (-1,1), (0,1), (1,1); with `centre` set, candidate 0 is (cx, cy)
+// itself and the ring follows.
+__device__ __forceinline__ void stage_cand(int k, int cx, int cy, int s, bool centre, int& mx, int& my) {
+    const int r = centre ? k - 1 : k;            // ring index, -1 = the centre
+    const int g = r < 0 ? 4 : (r < 4 ? r : r + 1);  // position in the 3 x 3 grid
+    mx = cx + (g % 3 - 1) * s;
+    my = cy + (g / 3 - 1) * s;
+}
+
 // In-register 8-point Hadamard (Sylvester order) of v.
 __device__ __forceinline__ void hadamard8_row(int (&v)[8]) {
 #pragma unroll
@@ -222,12 +233,12 @@ __device__ __forceinline__ void hadamard8_row(int (&v)[8]) {
 }
 
 // Refinement stage: evaluate `ncand` quarter-sample candidates around
-// (cx, cy) with step s (their vectors in cand_x/cand_y, all within one
+// (cx, cy) with step s (candidate k as stage_cand gives it, all within one
 // column-set of three x-vectors cx - s, cx, cx + s), SATD summed into satd[].
 template <int N, int NT>
 __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int* __restrict__ blk,
-                           int16_t* __restrict__ hp, int cx, int cy, int s, const int* cand_x,
-                           const int* cand_y, int ncand, uint32_t* satd) {
+                           int16_t* __restrict__ hp, int cx, int cy, int s, bool centre, int ncand,
+                           uint32_t* satd) {
     const int tid = threadIdx.x;
     const int iy_min = (cy - s) >> 2, iy_max = (cy + s) >> 2;
     const int rbase = iy_min - 3;          // block-relative row of hp row 0
@@ -261,7 +272,8 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
     for (int task = tid >> 3; task < ncand * NB; task += NT / 8) {
         int k = task / NB, b = task - k * NB;
         int by = (b / (N / 8)) * 8, bx = (b % (N / 8)) * 8;
-        int mvx = cand_x[k], mvy = cand_y[k];
+        int mvx, mvy;
+        stage_cand(k, cx, cy, s, centre, mvx, mvy);
         int j = (mvx - cx) / s + 1;
         int hx = mvx & 3, fy = mvy & 3, iy = mvy >> 2;
         int y = by + lane8;
@@ -314,7 +326,7 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
 template <int N, int NT>
 __device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const int* __restrict__ blk,
                                 int* __restrict__ hp, int16_t* __restrict__ had, int cx, int cy, int s,
-                                const int* cand_x, const int* cand_y, int ncand, uint32_t* satd) {
+                                bool centre, int ncand, uint32_t* satd) {
     const int tid = threadIdx.x;
     const int iy_min = (cy - s) >> 2, iy_max = (cy + s) >> 2;
     const int rbase = iy_min - 3;
@@ -344,7 +356,8 @@ __device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const
     for (int task = tid; task < ncand * N * NBX; task += NT) {
         const int k = task / (N * NBX), rem = task - k * N * NBX;
         const int y = rem / NBX, bx = (rem - y * NBX) * 8;
-        const int mvx = cand_x[k], mvy = cand_y[k];
+        int mvx, mvy;
+        stage_cand(k, cx, cy, s, centre, mvx, mvy);
         const int j = (mvx - cx) / s + 1;
         const int hx = mvx & 3, fy = mvy & 3, iy = mvy >> 2;
         const int* col = hp + (size_t)j * (N + 8) * N + bx;
@@ -741,34 +754,30 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     }
 
     // ---- quarter-sample refinement: centre + 8 half-sample, then 8 quarter
-    const int ring_x[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
-    const int ring_y[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
     int cx = 4 * res.mvx_int, cy = 4 * res.mvy_int;
-    int cand_x[9], cand_y[9];
-    cand_x[0] = cx; cand_y[0] = cy;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) { cand_x[k + 1] = cx + 2 * ring_x[k]; cand_y[k + 1] = cy + 2 * ring_y[k]; }
     if constexpr (N <= 32)
-        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 2, cand_x, cand_y, 9, satd);
-    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 2, cand_x, cand_y, 9, satd);
+        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 2, true, 9, satd);
+    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 2, true, 9, satd);
     uint32_t bJ = satd[0] + mv_cost(cx, cy, lmv);
     int bx = cx, by = cy;
 #pragma unroll
     for (int k = 1; k < 9; ++k) {
-        uint32_t J = satd[k] + mv_cost(cand_x[k], cand_y[k], lmv);
-        if (J < bJ) { bJ = J; bx = cand_x[k]; by = cand_y[k]; }
+        int mx, my;
+        stage_cand(k, cx, cy, 2, true, mx, my);
+        const uint32_t J = satd[k] + mv_cost(mx, my, lmv);
+        if (J < bJ) { bJ = J; bx = mx; by = my; }
     }
     __syncthreads();
     cx = bx; cy = by;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) { cand_x[k] = cx + ring_x[k]; cand_y[k] = cy + ring_y[k]; }
     if constexpr (N <= 32)
-        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 1, cand_x, cand_y, 8, satd);
-    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 1, cand_x, cand_y, 8, satd);
+        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 1, false, 8, satd);
+    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 1, false, 8, satd);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        uint32_t J = satd[k] + mv_cost(cand_x[k], cand_y[k], lmv);
-        if (J < bJ) { bJ = J; bx = cand_x[k]; by = cand_y[k]; }
+        int mx, my;
+        stage_cand(k, cx, cy, 1, false, mx, my);
+        const uint32_t J = satd[k] + mv_cost(mx, my, lmv);
+        if (J < bJ) { bJ = J; bx = mx; by = my; }
     }
     __syncthreads();
     res.mvx = bx;

@@ -12,8 +12,8 @@
 //
 // Shared memory (all [3][N][N] unless noted):
 //   cur u16, pred u16, work int16 (Y, then E), lev int16, rec u16,
-//   stage int16 [(N+7)*(N+7)] (the motion-compensation window of one
-//   channel; reused as the horizontal-pass buffer), reductions.
+//   stage int16 [3][N+7][N+7] (the motion-compensation windows),
+//   hbuf int16 [3][N+7][N] (their horizontal pass), reductions.
 #pragma once
 #include <cstdint>
 #include "xv_dev.cuh"
@@ -23,8 +23,8 @@ namespace xvd {
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 // Byte offsets of the shared-memory regions (every region 16-byte aligned).
 __host__ __device__ constexpr size_t tqr_off_stage(int N) { return align16((size_t)5 * 3 * N * N * 2); }
-__host__ __device__ constexpr size_t tqr_off_hbuf(int N) { return tqr_off_stage(N) + align16((size_t)(N + 7) * (N + 7) * 2); }
-__host__ __device__ constexpr size_t tqr_off_red(int N) { return tqr_off_hbuf(N) + align16((size_t)(N + 7) * (N + 7) * 2); }
+__host__ __device__ constexpr size_t tqr_off_hbuf(int N) { return tqr_off_stage(N) + align16((size_t)3 * (N + 7) * (N + 7) * 2); }
+__host__ __device__ constexpr size_t tqr_off_red(int N) { return tqr_off_hbuf(N) + align16((size_t)3 * (N + 7) * N * 2); }
 __host__ __device__ constexpr size_t tqr_seq_smem_bytes(int N) { return tqr_off_red(N) + 64 * 8; }
 
 template <int NT>
@@ -43,58 +43,118 @@ __device__ __forceinline__ void block_sum2(uint64_t& a, uint32_t& b, uint64_t* r
     __syncthreads();
 }
 
-// Motion-compensated prediction of the CU for all 3 channels.
+// Loads the CU's current samples (s_cur) and, with a reference, the motion-
+// compensation windows of all three channels (s_stage [3][N+7][N+7]: rows
+// y0+iy-3 .. y0+iy+N+3, columns likewise, coordinates clamped to the plane),
+// as 16-byte chunks with every load of a thread in flight before its
+// stores.  Then predicts the CU (s_pred; flat 512 without a reference):
+// HEVC 8-tap luma filter, horizontal pass into s_hbuf [3][N+7][N], vertical
+// pass, default weighted rounding.  Ends with a block barrier.
 template <int N, int NT, bool kCoherent>
-__device__ void mc_predict(const uint16_t* __restrict__ ref, int64_t plane, int Hp, int Wp, int x0, int y0,
-                           int mvx, int mvy, uint16_t* __restrict__ pred, int16_t* __restrict__ stage,
-                           int16_t* __restrict__ hbuf) {
-    const int tid = threadIdx.x;
+__device__ void load_and_predict(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
+                                 int Hp, int Wp, int x0, int y0, int mvx, int mvy, uint16_t* __restrict__ s_cur,
+                                 uint16_t* __restrict__ s_pred, int16_t* __restrict__ s_stage,
+                                 int16_t* __restrict__ s_hbuf) {
     constexpr int SW = N + 7;
+    constexpr int NN = N * N;
+    constexpr int CCH = N / 8;  // 16-byte chunks per current row
+    const int tid = threadIdx.x;
     const int ix = mvx >> 2, iy = mvy >> 2, fx = mvx & 3, fy = mvy & 3;
-    for (int c = 0; c < 3; ++c) {
-        const uint16_t* rp = ref + c * plane;
-        // window rows y0+iy-3 .. +N+3, columns x0+ix-3 .. +N+3, clamped
-        for (int idx = tid; idx < SW * SW; idx += NT) {
-            int r = idx / SW, q = idx - r * SW;
-            int yy = min(max(y0 + iy - 3 + r, 0), Hp - 1), xx = min(max(x0 + ix - 3 + q, 0), Wp - 1);
-            stage[idx] = (int16_t)ld_ref<kCoherent>(rp + (size_t)yy * Wp + xx);
+    const int wx = x0 + ix - 3, wy = y0 + iy - 3;   // window origin
+    const int xa = wx - (((wx % 8) + 8) % 8);       // 8-aligned start at or left of wx
+    const int mch = (wx + SW - xa + 7) / 8;         // chunks per window row
+    const int ncur = 3 * N * CCH;
+    const int ntask = ncur + (ref ? 3 * SW * mch : 0);
+    constexpr int kILP = 2;
+    for (int base = tid; base < ntask; base += NT * kILP) {
+        uint4 v[kILP];
+#pragma unroll
+        for (int j = 0; j < kILP; ++j) {
+            const int task = base + j * NT;
+            if (task < ncur) {
+                const int c = task / (N * CCH), rem = task - c * N * CCH, y = rem / CCH, ch = rem - y * CCH;
+                v[j] = __ldg(reinterpret_cast<const uint4*>(cur + (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + 8 * ch));
+            } else if (task < ntask) {
+                const int t2 = task - ncur;
+                const int c = t2 / (SW * mch), rem = t2 - c * SW * mch, r = rem / mch, ch = rem - r * mch;
+                const int yy = min(max(wy + r, 0), Hp - 1), xs = xa + 8 * ch;
+                const uint16_t* rowp = ref + (size_t)c * plane + (size_t)yy * Wp;
+                if (xs >= 0 && xs + 8 <= Wp) {
+                    v[j] = ld_ref16<kCoherent>(reinterpret_cast<const uint4*>(rowp + xs));
+                } else {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        w[i] = (uint32_t)ld_ref<kCoherent>(rowp + min(max(xs + 2 * i, 0), Wp - 1)) |
+                               ((uint32_t)ld_ref<kCoherent>(rowp + min(max(xs + 2 * i + 1, 0), Wp - 1)) << 16);
+                    v[j] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
         }
+#pragma unroll
+        for (int j = 0; j < kILP; ++j) {
+            const int task = base + j * NT;
+            if (task < ncur) {
+                const int c = task / (N * CCH), rem = task - c * N * CCH, y = rem / CCH, ch = rem - y * CCH;
+                *reinterpret_cast<uint4*>(s_cur + c * NN + y * N + 8 * ch) = v[j];
+            } else if (task < ntask) {
+                const int t2 = task - ncur;
+                const int c = t2 / (SW * mch), rem = t2 - c * SW * mch, r = rem / mch, ch = rem - r * mch;
+                const int q0 = xa + 8 * ch - wx;
+                const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+                int16_t* srow = s_stage + c * SW * SW + r * SW;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int q = q0 + i;
+                    if (q >= 0 && q < SW) srow[q] = (int16_t)((w[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+                }
+            }
+        }
+    }
+    if (!ref) {
+        for (int idx = tid; idx < 3 * NN; idx += NT) s_pred[idx] = (uint16_t)kFlat;
         __syncthreads();
-        int htap[8], vtap[8];
-        luma_taps(fx == 0 ? 2 : fx, htap);
-        luma_taps(fy == 0 ? 2 : fy, vtap);
-        if (fx != 0) {  // horizontal pass over all SW rows
-            for (int idx = tid; idx < SW * N; idx += NT) {
-                int r = idx / N, x = idx - r * N;
-                int acc = 0;
+        return;
+    }
+    __syncthreads();
+    if (fx != 0) {
+        int tap[8];
+        luma_taps(fx, tap);
+        for (int idx = tid; idx < 3 * SW * N; idx += NT) {
+            const int c = idx / (SW * N), rem = idx - c * SW * N, r = rem / N, x = rem - r * N;
+            const int16_t* st = s_stage + c * SW * SW + r * SW + x;
+            int acc = 0;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) acc += htap[i] * stage[r * SW + x + i];
-                hbuf[idx] = (int16_t)(acc >> kShift1);
-            }
-            __syncthreads();
-        }
-        for (int idx = tid; idx < N * N; idx += NT) {
-            int y = idx / N, x = idx - y * N;
-            int v;
-            if (fx == 0 && fy == 0) {
-                v = stage[(y + 3) * SW + x + 3] << kShift3;
-            } else if (fy == 0) {
-                v = hbuf[(y + 3) * N + x];
-            } else if (fx == 0) {
-                int acc = 0;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc += vtap[t] * stage[(y + t) * SW + x + 3];
-                v = acc >> kShift1;
-            } else {
-                int acc = 0;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc += vtap[t] * hbuf[(y + t) * N + x];
-                v = acc >> kShift2;
-            }
-            pred[c * N * N + idx] = (uint16_t)wp_round(v);
+            for (int i = 0; i < 8; ++i) acc += tap[i] * st[i];
+            s_hbuf[idx] = (int16_t)(acc >> kShift1);
         }
         __syncthreads();
     }
+    int vtap[8];
+    luma_taps(fy == 0 ? 2 : fy, vtap);
+    for (int idx = tid; idx < 3 * NN; idx += NT) {
+        const int c = idx / NN, rem = idx - c * NN, y = rem / N, x = rem - y * N;
+        const int16_t* st = s_stage + c * SW * SW;
+        const int16_t* hb = s_hbuf + c * SW * N;
+        int v;
+        if (fx == 0 && fy == 0) {
+            v = st[(y + 3) * SW + x + 3] << kShift3;
+        } else if (fy == 0) {
+            v = hb[(y + 3) * N + x];
+        } else if (fx == 0) {
+            int acc = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc += vtap[t] * st[(y + t) * SW + x + 3];
+            v = acc >> kShift1;
+        } else {
+            int acc = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc += vtap[t] * hb[(y + t) * N + x];
+            v = acc >> kShift2;
+        }
+        s_pred[idx] = (uint16_t)wp_round(v);
+    }
+    __syncthreads();
 }
 
 // One TU size over the whole CU; returns (SSE, bits) through the reduction.
@@ -165,16 +225,18 @@ __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __rest
     bits_out = bits + 3u * NTU * NTU;  // one coded-block flag per TU and channel
 }
 
+// Writes the kept reconstruction (and levels) of the CU, 16 bytes per store.
 template <int N, int NT>
 __device__ __forceinline__ void copy_out(const uint16_t* __restrict__ rec, const int16_t* __restrict__ lev,
                                          uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
                                          int64_t plane, int Wp, int x0, int y0) {
-    for (int idx = threadIdx.x; idx < 3 * N * N; idx += NT) {
-        int c = idx / (N * N), rem = idx - c * N * N;
-        int y = rem / N, x = rem - y * N;
-        size_t o = (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + x;
-        recon[o] = rec[idx];
-        if (levels) levels[o] = lev[idx];
+    constexpr int CCH = N / 8;
+    for (int t = threadIdx.x; t < 3 * N * CCH; t += NT) {
+        const int c = t / (N * CCH), rem = t - c * N * CCH, y = rem / CCH, ch = rem - y * CCH;
+        const int si = c * N * N + y * N + 8 * ch;
+        const size_t o = (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + 8 * ch;
+        *reinterpret_cast<uint4*>(recon + o) = *reinterpret_cast<const uint4*>(rec + si);
+        if (levels) *reinterpret_cast<uint4*>(levels + o) = *reinterpret_cast<const uint4*>(lev + si);
     }
 }
 
@@ -271,7 +333,6 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
                                 int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
                                 uint8_t* tu_log2, unsigned char* smem) {
     constexpr int NS = tqr_nslots<N>();
-    constexpr int SW = N + 7;
     constexpr int NN = N * N;
     const int tid = threadIdx.x;
     uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
@@ -288,62 +349,9 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
         return reinterpret_cast<int*>(slots + s * tqr_conc_slot_bytes(N) + align16((size_t)3 * 3 * NN * 2));
     };
 
-    // 1. current samples and the motion-compensation windows of all channels
-    const int ix = mvx >> 2, iy = mvy >> 2, fx = mvx & 3, fy = mvy & 3;
-    for (int idx = tid; idx < 3 * NN; idx += NT) {
-        const int c = idx / NN, rem = idx - c * NN, y = rem / N, x = rem - y * N;
-        s_cur[idx] = __ldg(cur + (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + x);
-        if (!ref) s_pred[idx] = (uint16_t)kFlat;
-    }
-    if (ref) {
-        for (int idx = tid; idx < 3 * SW * SW; idx += NT) {
-            const int c = idx / (SW * SW), rem = idx - c * SW * SW, r = rem / SW, q = rem - r * SW;
-            const int yy = min(max(y0 + iy - 3 + r, 0), Hp - 1), xx = min(max(x0 + ix - 3 + q, 0), Wp - 1);
-            s_stage[idx] = (int16_t)ld_ref<kCoherent>(ref + (size_t)c * plane + (size_t)yy * Wp + xx);
-        }
-    }
+    // 1. current samples, motion-compensated prediction
     if (tid < 3) { s_sse[tid] = 0ull; s_bits[tid] = 0u; }
-    __syncthreads();
-    if (ref) {
-        if (fx != 0) {
-            int tap[8];
-            luma_taps(fx, tap);
-            for (int idx = tid; idx < 3 * SW * N; idx += NT) {
-                const int c = idx / (SW * N), rem = idx - c * SW * N, r = rem / N, x = rem - r * N;
-                const int16_t* st = s_stage + c * SW * SW + r * SW + x;
-                int acc = 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc += tap[i] * st[i];
-                s_hbuf[idx] = (int16_t)(acc >> kShift1);
-            }
-            __syncthreads();
-        }
-        int vtap[8];
-        luma_taps(fy == 0 ? 2 : fy, vtap);
-        for (int idx = tid; idx < 3 * NN; idx += NT) {
-            const int c = idx / NN, rem = idx - c * NN, y = rem / N, x = rem - y * N;
-            const int16_t* st = s_stage + c * SW * SW;
-            const int16_t* hb = s_hbuf + c * SW * N;
-            int v;
-            if (fx == 0 && fy == 0) {
-                v = st[(y + 3) * SW + x + 3] << kShift3;
-            } else if (fy == 0) {
-                v = hb[(y + 3) * N + x];
-            } else if (fx == 0) {
-                int acc = 0;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc += vtap[t] * st[(y + t) * SW + x + 3];
-                v = acc >> kShift1;
-            } else {
-                int acc = 0;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc += vtap[t] * hb[(y + t) * N + x];
-                v = acc >> kShift2;
-            }
-            s_pred[idx] = (uint16_t)wp_round(v);
-        }
-        __syncthreads();
-    }
+    load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
 
     // task ranges of the allowed sizes (slot s: TU size 4 << s)
     int cum[NS + 1];
@@ -477,18 +485,7 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
     int16_t* s_hbuf = reinterpret_cast<int16_t*>(smem + tqr_off_hbuf(N));
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + tqr_off_red(N));
 
-    for (int idx = tid; idx < 3 * N * N; idx += NT) {
-        int c = idx / (N * N), rem = idx - c * N * N;
-        int y = rem / N, x = rem - y * N;
-        s_cur[idx] = __ldg(cur + (size_t)c * plane + (size_t)(y0 + y) * Wp + x0 + x);
-        if (!ref) s_pred[idx] = (uint16_t)kFlat;
-    }
-    if (ref) {
-        __syncthreads();
-        mc_predict<N, NT, kCoherent>(ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_pred, s_stage, s_hbuf);
-    } else {
-        __syncthreads();
-    }
+    load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
 
     int64_t bestJ = INT64_MAX;
     int bestL = 0;

@@ -251,7 +251,7 @@ bool valid_job(const xv_job* j) {
     if (!valid_cube(j->src, j->dtype, j->bands, j->T, j->H, j->W)) return false;
     if (!valid_params(&j->p)) return false;
     if (!j->planes || !j->recon) { set_error("job planes and recon buffers are required"); return false; }
-    if (!valid_planes(j->planes, j->recon, j->planes, 8)) return false;
+    if (!valid_planes(j->planes, j->recon, j->levels ? (const void*)j->levels : j->planes, 8)) return false;
     if (j->minmax_fixed && !j->minmax) { set_error("minmax_fixed needs a minmax array"); return false; }
     return true;
 }
@@ -390,6 +390,7 @@ xv_status xv_transform_quant_recon(xv_ctx* c, const uint16_t* cur, const uint16_
     if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
     if (!cur || !recon || !bits || (ref && !mv)) { set_error("cur, recon, bits (and mv with ref) are required"); return XV_EINVAL; }
     if (!valid_planes(cur, ref ? ref : cur, recon, gstride)) return XV_EINVAL;
+    if (levels && !valid_planes(levels, levels, levels, gstride)) return XV_EINVAL;
     DeviceGuard g(c->device);
     c->launches += kLaunchTqr;
     return check_launch(xvh::launch_tqr_frame(cur, ref, mv, G, gstride, Hp, Wp, p, pu_gstride, recon, levels, tu_log2,
