@@ -19,7 +19,7 @@ namespace {  // each including file gets its own copies
 
 
 // Resident blocks per SM the register allocation aims for, per CTU size and
-// block size (64 registers per thread at most where shared memory allows
+// block size (64 to 80 registers per thread where shared memory allows
 // several blocks; the CTU-64 window leaves room for one).
 template <int N, int NT>
 constexpr int kMinBlocks = NT == 512 ? (N == 64 ? 1 : 2)

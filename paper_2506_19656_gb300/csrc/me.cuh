@@ -5,14 +5,16 @@
 // definitions are those of xv_motion_search in include/xv.h.
 //
 // Layout in shared memory:
-//   win  int32 [WW][S]  reference window, WW = N + 2R + 8 rows/columns around
+//   win  u16 [WW][S]    reference window, WW = N + 2R + 8 rows/columns around
 //                       the PU (margin R + 4: the 8-tap filter at vectors up
 //                       to +-(R + 3/4)), coordinates clamped to the plane when
 //                       loaded -- so the search itself never branches on
-//                       borders.  S >= WW with S = 4 (mod 8): rows of
-//                       consecutive lanes fall in distinct 16-byte bank
-//                       groups for 128-bit loads.
-//   blk  int32 [N][N]   the PU's channel-0 samples.
+//                       borders.  Window column c of row y is element
+//                       y * S + 4 + c, so the first column of every 8-wide
+//                       unit of vectors (c = 8 gx + 4) starts a 16-byte word;
+//                       S = 8 (mod 16) spreads the rows of consecutive lanes
+//                       over distinct bank groups for 128-bit loads.
+//   blk  int32 [N][N]   the PU's channel-0 samples as biased floats (below).
 //   scratch             during the integer search: the box-sum table, the
 //                       PU's sub-block sums, per-unit bounds, the survivor
 //                       list; during refinement: horizontally filtered
@@ -41,7 +43,7 @@ struct MeResult {
 
 __host__ __device__ constexpr int me_win(int N, int R) { return N + 2 * R + 8; }
 __host__ __device__ constexpr int me_stride(int N, int R) {
-    return ((me_win(N, R) + 3) / 8) * 8 + 4;  // smallest S >= WW with S % 8 == 4
+    return (me_win(N, R) + 4 + 7) / 16 * 16 + 8;  // smallest S >= WW + 4 with S % 16 == 8
 }
 
 // Exact pruning of the integer search.  For a candidate, split the PU into
@@ -64,8 +66,11 @@ __host__ __device__ constexpr bool me_lastcol(int R) { return me_side(R) % 8 == 
 __host__ __device__ constexpr int me_ngx(int R) { return me_lastcol(R) ? me_side(R) / 8 : (me_side(R) + 7) / 8; }
 __host__ __device__ constexpr int me_ngxa(int R) { return me_ngx(R) + (me_lastcol(R) ? 1 : 0); }
 __host__ __device__ constexpr int me_units(int R) { return me_side(R) * me_ngxa(R); }
-// box-sum table: row stride (a multiple of 8) and rows of one class
+// box-sum table: entries per row (a multiple of 8), row pitch (= 4 mod 32
+// words: the rows that 8 consecutive lanes read fall in distinct 16-byte
+// bank groups) and rows of one class
 __host__ __device__ constexpr int me_tab_stride(int N, int R) { return (8 * me_ngxa(R) + N - me_sb(N) + 7) / 8 * 8; }
+__host__ __device__ constexpr int me_tab_pitch(int N, int R) { return (me_tab_stride(N, R) - 4 + 31) / 32 * 32 + 4; }
 __host__ __device__ constexpr int me_tab_rows(int N, int R) {
     return (2 * R + N - me_sb(N) + me_kcls(N)) / me_kcls(N);
 }
@@ -74,7 +79,11 @@ __host__ __device__ constexpr int me_tab_rows(int N, int R) {
 // The scratch region holds the pruning tables during the integer search and
 // the refinement's filtered columns afterwards.
 __host__ __device__ constexpr size_t me_align16(size_t b) { return (b + 15) / 16 * 16; }
-__host__ __device__ constexpr size_t me_off_blk(int N, int R) { return me_align16((size_t)me_win(N, R) * me_stride(N, R) * 4); }
+// (32 elements of slack after the last row: the box-table build and the
+// 8-wide SADs read a few elements past the end of a row)
+__host__ __device__ constexpr size_t me_off_blk(int N, int R) {
+    return me_align16(((size_t)me_win(N, R) * me_stride(N, R) + 32) * 2);
+}
 __host__ __device__ constexpr size_t me_off_red(int N, int R) { return me_off_blk(N, R) + me_align16((size_t)N * N * 4); }
 __host__ __device__ constexpr size_t me_off_satd(int N, int R) { return me_off_red(N, R) + 64 * 8; }
 // motion-cost tables: |se(4d)| for d in [-R, R] (129 at most) and the
@@ -91,7 +100,7 @@ __host__ __device__ constexpr size_t me_had_bytes(int N) { return N <= 32 ? me_a
 // PU, per-unit bounds
 __host__ __device__ constexpr size_t me_max(size_t a, size_t b) { return a > b ? a : b; }
 __host__ __device__ constexpr size_t me_tab_bytes(int N, int R) {
-    return me_align16(me_max((size_t)me_tab_rows(N, R) * me_tab_stride(N, R) * 4, (size_t)me_units(R) * 2));
+    return me_align16(me_max((size_t)me_tab_rows(N, R) * me_tab_pitch(N, R) * 4, (size_t)me_units(R) * 2));
 }
 __host__ __device__ constexpr size_t me_off_bsub(int N, int R) { return me_off_scr(N, R) + me_tab_bytes(N, R); }
 __host__ __device__ constexpr size_t me_off_ulb(int N, int R) {
@@ -108,102 +117,96 @@ __host__ __device__ constexpr size_t me_smem_bytes(int N, int R) {
 constexpr int kSampleBias = 0x4B000000;
 __device__ __forceinline__ int enc_sample(int v) { return kSampleBias | v; }
 __device__ __forceinline__ int dec_sample(int bits) { return bits - kSampleBias; }
+// The two 16-bit samples of a word as biased floats' bit patterns, one byte
+// permute each: bytes (v.lo, v.hi, 0x00, 0x4B).
+__device__ __forceinline__ int enc_lo(uint32_t w) { return (int)__byte_perm(w, (uint32_t)kSampleBias, 0x7410); }
+__device__ __forceinline__ int enc_hi(uint32_t w) { return (int)__byte_perm(w, (uint32_t)kSampleBias, 0x7432); }
+// 8 window samples (one 16-byte word) as biased values
+__device__ __forceinline__ void enc8(const uint16_t* p, int* out) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    out[0] = enc_lo(q.x); out[1] = enc_hi(q.x); out[2] = enc_lo(q.y); out[3] = enc_hi(q.y);
+    out[4] = enc_lo(q.z); out[5] = enc_hi(q.z); out[6] = enc_lo(q.w); out[7] = enc_hi(q.w);
+}
 
-template <int NT>
-__device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Block-wide minimum of v with one barrier: a warp-level minimum, then one
+// shared-memory atomicMin per warp into *slot, which must hold ~0 (set
+// before an earlier barrier) and is not written again until the caller's
+// next item.
+__device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* slot) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+        const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
         v = w < v ? w : v;
     }
-    if (lane == 0) red[warp] = v;
+    if ((threadIdx.x & 31) == 0 && v != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(slot), v);
     __syncthreads();
-    if (warp == 0) {
-        v = lane < NT / 32 ? red[lane] : ~0ull;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
-            v = w < v ? w : v;
-        }
-        if (lane == 0) red[0] = v;
-    }
-    __syncthreads();
-    v = red[0];
-    __syncthreads();
-    return v;
+    return *slot;
 }
 
 // SAD of 8 horizontally adjacent candidates over one block row, 8 columns at
-// a time: cur[c] against ref[c + k], k = 0..7.
+// a time: cur[c] against ref[c + k], k = 0..7.  crow: biased int32 samples;
+// rrow: window samples, 16-byte aligned.
 template <int W>
-__device__ __forceinline__ void row_sad8(const int* __restrict__ crow, const int* __restrict__ rrow,
+__device__ __forceinline__ void row_sad8(const int* __restrict__ crow, const uint16_t* __restrict__ rrow,
                                          uint32_t (&sad)[8]) {
 #pragma unroll
     for (int c0 = 0; c0 < W; c0 += 8) {
-        constexpr int CW = 8;
-        int cv[CW], rv[CW + 8];
-#pragma unroll
-        for (int i = 0; i < CW; i += 4) {
-            int4 t = *reinterpret_cast<const int4*>(crow + c0 + i);
-            cv[i] = t.x; cv[i + 1] = t.y; cv[i + 2] = t.z; cv[i + 3] = t.w;
+        int cv[8], rv[16];
+        {
+            const int4 a = *reinterpret_cast<const int4*>(crow + c0);
+            const int4 b = *reinterpret_cast<const int4*>(crow + c0 + 4);
+            cv[0] = a.x; cv[1] = a.y; cv[2] = a.z; cv[3] = a.w; cv[4] = b.x; cv[5] = b.y; cv[6] = b.z; cv[7] = b.w;
         }
-#pragma unroll
-        for (int i = 0; i < CW + 8; i += 4) {
-            int4 t = *reinterpret_cast<const int4*>(rrow + c0 + i);
-            rv[i] = t.x; rv[i + 1] = t.y; rv[i + 2] = t.z; rv[i + 3] = t.w;
-        }
+        enc8(rrow + c0, rv);
+        enc8(rrow + c0 + 8, rv + 8);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
-            for (int c = 0; c < CW; ++c) sad[k] = __sad(cv[c], rv[c + k], sad[k]);
+            for (int c = 0; c < 8; ++c) sad[k] = __sad(cv[c], rv[c + k], sad[k]);
     }
 }
 
-// The same through the FP32 pipe: the words read as floats, |a - b|
+// The same through the FP32 pipe: the biased words read as floats, |a - b|
 // accumulated in float32, exact because every partial sum is an integer
 // below 2^24.  Running a third of the rows through this path keeps both the
 // integer ALU pipe (one __sad per abs-diff at half the issue rate) and the
 // FP32 pipe busy.
 template <int W>
-__device__ __forceinline__ void row_sad8f(const int* __restrict__ crow_i, const int* __restrict__ rrow_i,
+__device__ __forceinline__ void row_sad8f(const int* __restrict__ crow, const uint16_t* __restrict__ rrow,
                                           float (&acc)[8]) {
-    const float* crow = reinterpret_cast<const float*>(crow_i);
-    const float* rrow = reinterpret_cast<const float*>(rrow_i);
 #pragma unroll
     for (int c0 = 0; c0 < W; c0 += 8) {
-        constexpr int CW = 8;
-        float cv[CW], rv[CW + 8];
-#pragma unroll
-        for (int i = 0; i < CW; i += 4) {
-            float4 t = *reinterpret_cast<const float4*>(crow + c0 + i);
-            cv[i] = t.x; cv[i + 1] = t.y; cv[i + 2] = t.z; cv[i + 3] = t.w;
+        float cv[8];
+        int rv[16];
+        {
+            const float4 a = *reinterpret_cast<const float4*>(crow + c0);
+            const float4 b = *reinterpret_cast<const float4*>(crow + c0 + 4);
+            cv[0] = a.x; cv[1] = a.y; cv[2] = a.z; cv[3] = a.w; cv[4] = b.x; cv[5] = b.y; cv[6] = b.z; cv[7] = b.w;
         }
-#pragma unroll
-        for (int i = 0; i < CW + 8; i += 4) {
-            float4 t = *reinterpret_cast<const float4*>(rrow + c0 + i);
-            rv[i] = t.x; rv[i + 1] = t.y; rv[i + 2] = t.z; rv[i + 3] = t.w;
-        }
+        enc8(rrow + c0, rv);
+        enc8(rrow + c0 + 8, rv + 8);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
-            for (int c = 0; c < CW; ++c) acc[k] += fabsf(cv[c] - rv[c + k]);
+            for (int c = 0; c < 8; ++c) acc[k] += fabsf(cv[c] - __int_as_float(rv[c + k]));
     }
 }
 
 // SAD of one candidate over one block row (the last column of candidates
-// when 2R + 1 = 8m + 1).
+// when 2R + 1 = 8m + 1); rrow 16-byte aligned.
 template <int W>
-__device__ __forceinline__ uint32_t row_sad1(const int* __restrict__ crow, const int* __restrict__ rrow,
+__device__ __forceinline__ uint32_t row_sad1(const int* __restrict__ crow, const uint16_t* __restrict__ rrow,
                                              uint32_t acc) {
 #pragma unroll
-    for (int c = 0; c < W; c += 4) {
-        int4 a = *reinterpret_cast<const int4*>(crow + c);
-        int4 b = *reinterpret_cast<const int4*>(rrow + c);
-        acc = __sad(a.x, b.x, acc);
-        acc = __sad(a.y, b.y, acc);
-        acc = __sad(a.z, b.z, acc);
-        acc = __sad(a.w, b.w, acc);
+    for (int c = 0; c < W; c += 8) {
+        int rv[8];
+        enc8(rrow + c, rv);
+        const int4 a = *reinterpret_cast<const int4*>(crow + c);
+        const int4 b = *reinterpret_cast<const int4*>(crow + c + 4);
+        acc = __sad(a.x, rv[0], acc); acc = __sad(a.y, rv[1], acc);
+        acc = __sad(a.z, rv[2], acc); acc = __sad(a.w, rv[3], acc);
+        acc = __sad(b.x, rv[4], acc); acc = __sad(b.y, rv[5], acc);
+        acc = __sad(b.z, rv[6], acc); acc = __sad(b.w, rv[7], acc);
     }
     return acc;
 }
@@ -236,7 +239,7 @@ __device__ __forceinline__ void hadamard8_row(int (&v)[8]) {
 // (cx, cy) with step s (candidate k as stage_cand gives it, all within one
 // column-set of three x-vectors cx - s, cx, cx + s), SATD summed into satd[].
 template <int N, int NT>
-__device__ void satd_stage(const int* __restrict__ win, int S, int R, const int* __restrict__ blk,
+__device__ void satd_stage(const uint16_t* __restrict__ wb, int S, int R, const int* __restrict__ blk,
                            int16_t* __restrict__ hp, int cx, int cy, int s, bool centre, int ncand,
                            uint32_t* satd) {
     const int tid = threadIdx.x;
@@ -249,16 +252,16 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
         int r = rem / N, x = rem - r * N;
         int m = cx + (j - 1) * s;
         int hx = m & 3, ix = m >> 2;
-        const int* wr = win + (rbase + r + R + 4) * S + (x + ix + R + 4);
+        const uint16_t* wr = wb + (rbase + r + R + 4) * S + (x + ix + R + 4);
         int v;
         if (hx == 0) {
-            v = dec_sample(wr[0]);
+            v = wr[0];
         } else {
             int tap[8];
             luma_taps(hx, tap);
             int acc = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc += tap[i] * dec_sample(wr[i - 3]);
+            for (int i = 0; i < 8; ++i) acc += tap[i] * (int)wr[i - 3];
             v = acc >> kShift1;
         }
         hp[(j * (N + 8) + r) * N + x] = (int16_t)v;
@@ -324,7 +327,7 @@ __device__ void satd_stage(const int* __restrict__ win, int S, int R, const int*
 // Hadamard; the 8 column tasks of a block are adjacent lanes and add their
 // absolute sums before the block's (S + 2) >> 2.
 template <int N, int NT>
-__device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const int* __restrict__ blk,
+__device__ void satd_stage_smem(const uint16_t* __restrict__ wb, int S, int R, const int* __restrict__ blk,
                                 int* __restrict__ hp, int16_t* __restrict__ had, int cx, int cy, int s,
                                 bool centre, int ncand, uint32_t* satd) {
     const int tid = threadIdx.x;
@@ -336,16 +339,16 @@ __device__ void satd_stage_smem(const int* __restrict__ win, int S, int R, const
         int r = rem / N, x = rem - r * N;
         int m = cx + (j - 1) * s;
         int hx = m & 3, ix = m >> 2;
-        const int* wr = win + (rbase + r + R + 4) * S + (x + ix + R + 4);
+        const uint16_t* wr = wb + (rbase + r + R + 4) * S + (x + ix + R + 4);
         int v;
         if (hx == 0) {
-            v = dec_sample(wr[0]);
+            v = wr[0];
         } else {
             int tap[8];
             luma_taps(hx, tap);
             int acc = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc += tap[i] * dec_sample(wr[i - 3]);
+            for (int i = 0; i < 8; ++i) acc += tap[i] * (int)wr[i - 3];
             v = acc >> kShift1;
         }
         hp[(j * (N + 8) + r) * N + x] = v;
@@ -429,7 +432,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     static_assert(N % 8 == 0, "PU size must be a multiple of 8");
     const int tid = threadIdx.x;
     const int WW = me_win(N, R), S = me_stride(N, R);
-    int* win = reinterpret_cast<int*>(smem);
+    uint16_t* win = reinterpret_cast<uint16_t*>(smem);
+    const uint16_t* wb = win + 4;  // window column 0 of row 0
     int* blk = reinterpret_cast<int*>(smem + me_off_blk(N, R));
     int16_t* hp = reinterpret_cast<int16_t*>(smem + me_off_hp(N, R));
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + me_off_red(N, R));
@@ -443,14 +447,16 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     const int wx0 = x0 - R - 4, wy0 = y0 - R - 4;
     const int xa = wx0 - (((wx0 % 8) + 8) % 8);  // 8-aligned start at or left of wx0
     const int nch = (wx0 + WW - xa + 7) / 8;
-    const int ntask = WW * nch;
-    constexpr int kILP = 4;  // loads in flight per thread before the first store
+    const int nwin = WW * nch;
+    constexpr int BCH = N / 8;                 // 16-byte chunks per block row
+    const int ntask = nwin + N * BCH;          // window chunks, then the PU's
+    constexpr int kILP = 5;  // loads in flight per thread before the first store
     for (int base = tid; base < ntask; base += NT * kILP) {
         uint4 v[kILP];
 #pragma unroll
         for (int j = 0; j < kILP; ++j) {
             const int task = base + j * NT;
-            if (task < ntask) {
+            if (task < nwin) {
                 const int r = task / nch, ch = task - r * nch;
                 const int yy = min(max(wy0 + r, 0), Hp - 1), xs = xa + 8 * ch;
                 const uint16_t* rowp = ref0 + (size_t)yy * Wp;
@@ -464,37 +470,53 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
                                ((uint32_t)ld_ref<kCoherent>(rowp + min(max(xs + 2 * i + 1, 0), Wp - 1)) << 16);
                     v[j] = make_uint4(w[0], w[1], w[2], w[3]);
                 }
+            } else if (task < ntask) {
+                const int t2 = task - nwin, r = t2 / BCH, ch = t2 - r * BCH;
+                v[j] = __ldg(reinterpret_cast<const uint4*>(cur0 + (size_t)(y0 + r) * Wp + x0 + 8 * ch));
             }
         }
 #pragma unroll
         for (int j = 0; j < kILP; ++j) {
             const int task = base + j * NT;
-            if (task < ntask) {
+            const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+            if (task < nwin) {
                 const int r = task / nch, ch = task - r * nch;
                 const int c0 = xa + 8 * ch - wx0;
-                const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+                if (wx0 - xa == 4) {
+                    // plane chunk ch is element 8 ch of the row (the columns
+                    // outside the window land in the row's padding)
+                    *reinterpret_cast<uint4*>(win + r * S + 8 * ch) = v[j];
+                } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int c = c0 + i;
-                    if (c >= 0 && c < WW) win[r * S + c] = enc_sample((int)((w[i >> 1] >> (16 * (i & 1))) & 0xffffu));
+                    for (int i = 0; i < 8; ++i) {
+                        const int c = c0 + i;
+                        if (c >= 0 && c < WW) win[r * S + 4 + c] = (uint16_t)(w[i >> 1] >> (16 * (i & 1)));
+                    }
                 }
+            } else if (task < ntask) {
+                const int t2 = task - nwin, r = t2 / BCH, ch = t2 - r * BCH;
+                int4 lo, hi;
+                lo.x = enc_sample((int)(w[0] & 0xffffu)); lo.y = enc_sample((int)(w[0] >> 16));
+                lo.z = enc_sample((int)(w[1] & 0xffffu)); lo.w = enc_sample((int)(w[1] >> 16));
+                hi.x = enc_sample((int)(w[2] & 0xffffu)); hi.y = enc_sample((int)(w[2] >> 16));
+                hi.z = enc_sample((int)(w[3] & 0xffffu)); hi.w = enc_sample((int)(w[3] >> 16));
+                *reinterpret_cast<int4*>(blk + r * N + 8 * ch) = lo;
+                *reinterpret_cast<int4*>(blk + r * N + 8 * ch + 4) = hi;
             }
         }
-    }
-    for (int idx = tid; idx < N * N; idx += NT) {
-        int r = idx / N, c = idx - r * N;
-        blk[idx] = enc_sample(__ldg(cur0 + (size_t)(y0 + r) * Wp + x0 + c));
     }
     for (int i = tid; i < 2 * R + 1 + 64; i += NT) {
         if (i < 2 * R + 1) s_bitsd[i] = se_len(4 * (i - R));
         else s_costb[i - (2 * R + 1)] = (uint32_t)((lmv * (int64_t)(i - (2 * R + 1)) + 32768) >> 16);
     }
-    {  // sub-block sums, the seed unit's sums and the survivor count start at 0
+    {  // sub-block sums, the seed unit's sums, the survivor counts start at 0;
+       // the two block-minimum slots at ~0
         int* bs = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
         constexpr int nsb = (N / me_sb(N)) * (N / me_sb(N));
-        for (int i = tid; i < nsb + 10; i += NT) {
+        for (int i = tid; i < nsb + 12; i += NT) {
             if (i < nsb) bs[i] = 0;
-            else satd[i - nsb] = 0;
+            else if (i < nsb + 10) satd[i - nsb] = 0;
+            else red[i - nsb - 10] = ~0ull;
         }
     }
     __syncthreads();
@@ -509,7 +531,7 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     const int side = me_side(R);
     const int ngx = me_ngx(R), ngxa = me_ngxa(R);
     const int units = side * ngxa;
-    const int TS = me_tab_stride(N, R);
+    const int TS = me_tab_stride(N, R), TP = me_tab_pitch(N, R);
     uint32_t* tab = reinterpret_cast<uint32_t*>(smem + me_off_scr(N, R));
     uint16_t* list = reinterpret_cast<uint16_t*>(smem + me_off_scr(N, R));  // after the bounds
     int* bsub = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
@@ -531,21 +553,23 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     }
     // Box table of row class m: entry (t, tx) = sum of the SB x SB window
     // samples with top-left corner (4 + m + K t, 4 + tx).  One task per 8
-    // consecutive entries: horizontal running sums over SB window rows.
+    // consecutive entries: horizontal running sums over SB window rows (the
+    // 16-byte loads start at window column 8 c + 4, a word boundary).
     auto build_tab = [&](int m) {
         const int nr = (2 * R + N - SB - m) / K + 1;
         const int nch = TS / 8;
         for (int task = tid; task < nr * nch; task += NT) {
             const int t = task / nch, c = task - t * nch;
-            const int* w0 = win + (4 + m + K * t) * S + 8 * c + 4;
+            const uint16_t* w0 = wb + (4 + m + K * t) * S + 8 * c + 4;
             uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 1
             for (int r = 0; r < SB; ++r) {
-                uint32_t v[8 + SB];
+                uint32_t v[(8 + SB + 7) / 8 * 8];
 #pragma unroll
-                for (int i = 0; i < 8 + SB; i += 4) {
-                    const int4 q4 = *reinterpret_cast<const int4*>(w0 + r * S + i);
-                    v[i] = (uint32_t)q4.x; v[i + 1] = (uint32_t)q4.y; v[i + 2] = (uint32_t)q4.z; v[i + 3] = (uint32_t)q4.w;
+                for (int i = 0; i < 8 + SB; i += 8) {
+                    const uint4 q4 = *reinterpret_cast<const uint4*>(w0 + r * S + i);
+                    v[i] = q4.x & 0xffffu; v[i + 1] = q4.x >> 16; v[i + 2] = q4.y & 0xffffu; v[i + 3] = q4.y >> 16;
+                    v[i + 4] = q4.z & 0xffffu; v[i + 5] = q4.z >> 16; v[i + 6] = q4.w & 0xffffu; v[i + 7] = q4.w >> 16;
                 }
                 uint32_t h = 0;
 #pragma unroll
@@ -557,12 +581,10 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
                     acc[k] += h;
                 }
             }
-            uint4 o0, o1;
-            const uint32_t bias = (uint32_t)(SB * SB) * (uint32_t)kSampleBias;
-            o0.x = acc[0] - bias; o0.y = acc[1] - bias; o0.z = acc[2] - bias; o0.w = acc[3] - bias;
-            o1.x = acc[4] - bias; o1.y = acc[5] - bias; o1.z = acc[6] - bias; o1.w = acc[7] - bias;
-            *reinterpret_cast<uint4*>(tab + t * TS + 8 * c) = o0;
-            *reinterpret_cast<uint4*>(tab + t * TS + 8 * c + 4) = o1;
+            const uint4 o0 = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+            const uint4 o1 = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+            *reinterpret_cast<uint4*>(tab + t * TP + 8 * c) = o0;
+            *reinterpret_cast<uint4*>(tab + t * TP + 8 * c + 4) = o1;
         }
     };
     build_tab(0);
@@ -591,10 +613,10 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         for (int v = tid / P; v < ncu; v += NT / P) {
             const int gx = v / nd;
             const int dyi = m + K * (v - gx * nd);
-            const uint32_t* trow = tab + ((dyi - m) / K) * TS + 8 * gx;
+            const uint32_t* trow = tab + ((dyi - m) / K) * TP + 8 * gx;
             uint32_t lb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int i = q; i < NS; i += P) {
-                const uint32_t* tr = trow + i * (SB / K) * TS;
+                const uint32_t* tr = trow + i * (SB / K) * TP;
 #pragma unroll
                 for (int j = 0; j < NS; ++j) {
                     const uint4 b0 = *reinterpret_cast<const uint4*>(tr + SB * j);
@@ -627,7 +649,7 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
             }
         }
     }
-    lbbest = block_min_u64<NT>(lbbest, red);  // its barriers also end the bound pass
+    lbbest = block_min_u64(lbbest, red);  // its barrier also ends the bound pass
     const int useed = (int)(lbbest & 0xffffffffu);
 
     // exact SAD of the seed unit: one block row per thread, reduced per warp
@@ -638,8 +660,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         for (int r = tid; r < ((N + 31) & ~31); r += NT) {
             uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (r < N) {
-                if (single) sad[0] = row_sad1<N>(blk + r * N, win + woff + r * S, 0u);
-                else row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+                if (single) sad[0] = row_sad1<N>(blk + r * N, wb + woff + r * S, 0u);
+                else row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
             }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1)
@@ -706,7 +728,7 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
             const int by = s_bitsd[dyi];
             if (gx == ngx) {  // the single last column, dx = R
                 uint32_t sad1 = 0;
-                for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, win + woff + r * S, sad1);
+                for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, wb + woff + r * S, sad1);
                 for (int o = 1; o < P; o <<= 1) sad1 += __shfl_xor_sync(pmask, sad1, o);
                 if (q == 0) {
                     const uint32_t J = sad1 + s_costb[s_bitsd[2 * R] + by];
@@ -721,11 +743,11 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
             int r = q;
 #pragma unroll 1
             for (; r + 2 * P < N; r += 3 * P) {
-                row_sad8<N>(blk + r * N, win + woff + r * S, sad);
-                row_sad8<N>(blk + (r + P) * N, win + woff + (r + P) * S, sad);
-                row_sad8f<N>(blk + (r + 2 * P) * N, win + woff + (r + 2 * P) * S, accf);
+                row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
+                row_sad8<N>(blk + (r + P) * N, wb + woff + (r + P) * S, sad);
+                row_sad8f<N>(blk + (r + 2 * P) * N, wb + woff + (r + 2 * P) * S, accf);
             }
-            for (; r < N; r += P) row_sad8<N>(blk + r * N, win + woff + r * S, sad);
+            for (; r < N; r += P) row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
 #pragma unroll
             for (int k = 0; k < 8; ++k)  // exact integer below 2^23: read it through the 2^23 bias
                 sad[k] += __float_as_uint(accf[k] + 8388608.0f) - 0x4B000000u;
@@ -743,7 +765,7 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
             }
         }
     }
-    best = block_min_u64<NT>(best, red);
+    best = block_min_u64(best, red + 1);
     MeResult res;
     {
         int idx = (int)(best & 0xffffffffu);
@@ -756,8 +778,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     // ---- quarter-sample refinement: centre + 8 half-sample, then 8 quarter
     int cx = 4 * res.mvx_int, cy = 4 * res.mvy_int;
     if constexpr (N <= 32)
-        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 2, true, 9, satd);
-    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 2, true, 9, satd);
+        satd_stage_smem<N, NT>(wb, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 2, true, 9, satd);
+    else satd_stage<N, NT>(wb, S, R, blk, hp, cx, cy, 2, true, 9, satd);
     uint32_t bJ = satd[0] + mv_cost(cx, cy, lmv);
     int bx = cx, by = cy;
 #pragma unroll
@@ -770,8 +792,8 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     __syncthreads();
     cx = bx; cy = by;
     if constexpr (N <= 32)
-        satd_stage_smem<N, NT>(win, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 1, false, 8, satd);
-    else satd_stage<N, NT>(win, S, R, blk, hp, cx, cy, 1, false, 8, satd);
+        satd_stage_smem<N, NT>(wb, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 1, false, 8, satd);
+    else satd_stage<N, NT>(wb, S, R, blk, hp, cx, cy, 1, false, 8, satd);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         int mx, my;
