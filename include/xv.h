@@ -165,8 +165,9 @@ xv_status xv_transform_quant_recon(xv_ctx* ctx, const uint16_t* cur, const uint1
 
 /* PSNR per real band (paper Sec. 2.3: peak = the maximum of the original
  * sequence for that band; max - min when max <= 0).  Band b is read from
- * group b/3, channel b%3 of `recon`, de-quantised as min + q (max-min)/1023,
- * and compared with the finite samples of `src` over the valid H x W region.
+ * group b/3, channel b%3 of `recon`, de-quantised as min + q (max-min)/1023
+ * (q: the sample's low 10 bits; planes hold 10-bit samples), and compared
+ * with the finite samples of `src` over the valid H x W region.
  * Also the exact 10-bit SSE against `planes`.  psnr_band, mse_band,
  * sse10_band: HOST arrays [bands] (any may be NULL); psnr_mean: HOST, the
  * mean of the per-band PSNR (+inf when any band is exact).  Synchronous. */

@@ -5,6 +5,18 @@
 // is de-quantised as min + q (max - min)/1023 (one double multiply, one
 // double add, as in the definition) and compared with the original; the
 // exact 10-bit error against the quantised planes is accumulated alongside.
+//
+// FP64 issue is scarce on this part, so the per-sample loop runs in FP32:
+// the 1024 possible de-quantised doubles of the band are tabulated in shared
+// memory, each split exactly into three floats (h + l + l2: 24 + 24 + 5
+// significant bits); e = x - (h + l + l2) is formed in float-float with
+// TwoSum steps, squared with an FMA-exact product and accumulated in
+// float-float per thread, and only the thread totals are summed in double.
+// The error of a term is about u^2 |e| + u^3 |x^| (u = 2^-24), far below the
+// double rounding of the definition itself.  Bands with max(|min|, |max|)
+// outside [2^-30, 2^50] take the plain double path: below, float subnormals
+// could cost the split its exactness; above, a thread's float sum of squares
+// could overflow.
 // Per-block partials go to context scratch and are summed in a fixed order
 // (Kahan) by a second kernel, so the result does not depend on scheduling.
 #include <cuda_runtime.h>
@@ -18,6 +30,14 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// s + err = a + b exactly (Knuth's TwoSum; explicit roundings so that
+// nothing is contracted or reassociated)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_psnr(const T* __restrict__ src, int bands, int T_, int H, int W, const uint16_t* __restrict__ planes,
@@ -26,9 +46,21 @@ k_psnr(const T* __restrict__ src, int bands, int T_, int H, int W, const uint16_
     const int g = b / 3, c = b % 3;
     const BandQ q = bq[b];
     const int64_t n = (int64_t)T_ * H * W;
-    (void)n;
     const T* p = src + (int64_t)b * n;
+    const double mag = fmax(fabs(q.lo), fabs(q.hi));
+    const bool ff = mag >= 0x1p-30 && mag <= 0x1p50;  // the FP32 path (see above)
+    __shared__ float4 s_xh[1024];  // (h, l, l2, unused) of each 10-bit level's de-quantised value
+    for (int v = threadIdx.x; v < 1024; v += kThreads) {
+        const double xh = __dadd_rn(q.lo, __dmul_rn((double)v, q.delta));
+        const float h = __double2float_rn(xh);
+        const double r = xh - (double)h;  // exact
+        const float l = __double2float_rn(r);
+        const float l2 = __double2float_rn(r - (double)l);  // exact: at most 5 significant bits remain
+        s_xh[v] = make_float4(h, l, l2, 0.f);
+    }
+    __syncthreads();
     double sse = 0.0;
+    float acc_hi = 0.f, acc_lo = 0.f;  // float-float running sum of e^2
     unsigned long long sse10 = 0, count = 0;
     // one warp per image row: the row's frame and y are derived once, the
     // lanes stride along x
@@ -46,15 +78,33 @@ k_psnr(const T* __restrict__ src, int bands, int T_, int H, int W, const uint16_
             const int rq = rr[x];
             const int e10 = (int)qr[x] - rq;
             sse10 += (unsigned long long)(e10 * e10);
-            const double xv = (double)xr[x];
-            if (isfinite(xv)) {
+            const float xf = (float)xr[x];  // exact for float and uint16 sources
+            if (!isfinite(xf)) continue;
+            ++count;
+            const float4 tv = s_xh[rq & 1023];
+            if (ff) {
+                // e = xf - h - l - l2 in float-float
+                float s1, e1, t1, e2, eh, el;
+                two_sum(xf, -tv.x, s1, e1);
+                two_sum(e1, -tv.y, t1, e2);
+                two_sum(s1, t1, eh, el);
+                el = __fadd_rn(el, __fsub_rn(e2, tv.z));
+                // e^2 = p + pe + 2 eh el (+ el^2, negligible)
+                const float pr = __fmul_rn(eh, eh);
+                const float pe = __fmaf_rn(eh, eh, -pr);
+                const float qq = __fmaf_rn(__fmul_rn(2.f, eh), el, pe);
+                float sh, se;
+                two_sum(acc_hi, pr, sh, se);
+                acc_lo = __fadd_rn(acc_lo, __fadd_rn(se, qq));
+                acc_hi = sh;
+            } else {
                 const double xh = __dadd_rn(q.lo, __dmul_rn((double)rq, q.delta));
-                const double e = __dsub_rn(xv, xh);
-                sse = __dadd_rn(sse, __dmul_rn(e, e));
-                ++count;
+                const double e = __dsub_rn((double)xr[x], xh);
+                sse = __fma_rn(e, e, sse);
             }
         }
     }
+    sse += (double)acc_hi + (double)acc_lo;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         sse += __shfl_xor_sync(0xffffffffu, sse, o);
@@ -73,19 +123,30 @@ k_psnr(const T* __restrict__ src, int bands, int T_, int H, int W, const uint16_
     }
 }
 
+// Per band: the block partials summed in block order (Kahan).  The warp
+// first stages the partials in shared memory (nblk <= 256), so the serial
+// sum reads no global memory.
 __global__ void k_psnr_final(const PsnrPart* part, int nblk, PsnrPart* out) {
     const int b = blockIdx.x;
+    __shared__ double s_sse[256];
+    __shared__ unsigned long long s_10[256], s_n[256];
+    for (int k = threadIdx.x; k < nblk; k += 32) {
+        const PsnrPart r = part[(int64_t)b * nblk + k];
+        s_sse[k] = r.sse;
+        s_10[k] = r.sse10;
+        s_n[k] = r.count;
+    }
+    __syncwarp();
     if (threadIdx.x != 0) return;
     double sum = 0.0, comp = 0.0;
     unsigned long long s10 = 0, cnt = 0;
     for (int k = 0; k < nblk; ++k) {
-        const PsnrPart& r = part[(int64_t)b * nblk + k];
-        double y = r.sse - comp;  // Kahan summation in block order
+        double y = s_sse[k] - comp;  // Kahan summation in block order
         double t = sum + y;
         comp = (t - sum) - y;
         sum = t;
-        s10 += r.sse10;
-        cnt += r.count;
+        s10 += s_10[k];
+        cnt += s_n[k];
     }
     out[b] = PsnrPart{sum, s10, cnt, 0.0};
 }

@@ -215,3 +215,24 @@ def test_psnr(xv, ctx, dtype):
         else:
             assert abs(g["psnr_band"][b] - w["psnr_band"][b]) <= 1e-9 * abs(w["psnr_band"][b])
         assert g["sse10_band"][b] == int(w["sse10_band"][b])
+
+
+def test_psnr_magnitudes(xv, ctx):
+    """The FP32 (float-float) accumulation against the oracle's double
+    definition on awkward bands: tiny and huge magnitudes (the latter on the
+    double path), values around zero, and a large offset with a small range
+    (heavy cancellation in x - x^)."""
+    rng = np.random.default_rng(11)
+    shape = (3, 17, 33)
+    bands = [rng.uniform(-1e-12, 3e-12, shape), rng.uniform(1e20, 4e20, shape),
+             rng.uniform(-1e-3, 1e-3, shape), 1e6 + rng.uniform(0, 1, shape),
+             rng.uniform(-7e14, 7e14, shape), rng.uniform(0, 1, shape)]
+    cube = np.stack(bands).astype(np.float32)
+    mm, _ = oracle.minmax(cube)
+    planes = oracle.quantize_pack(cube, 16, mm)
+    recon = np.clip(planes.astype(int) + rng.integers(-2, 3, planes.shape), 0, 1023).astype(np.uint16)
+    w = oracle.psnr(cube, planes, recon, mm)
+    g = xv.xv_psnr(ctx, to_dev(cube), to_dev(planes), to_dev(recon), to_dev(mm))
+    for b in range(len(bands)):
+        assert abs(g["psnr_band"][b] - w["psnr_band"][b]) <= 1e-9 * abs(w["psnr_band"][b]), b
+        assert g["sse10_band"][b] == int(w["sse10_band"][b])
