@@ -357,6 +357,9 @@ def main():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--frames-per-tick", type=int, default=8)
+    ap.add_argument("--block-size", type=int, default=0,
+                    help="persistent-kernel block size (128/192/256/512) instead of the autotuner's choice, e.g. to "
+                         "profile the variant an uninstrumented run picks")
     args = ap.parse_args()
     globals()["QPS"] = tuple(int(q) for q in args.qps.split(","))
     if args.config != 1 and args.qps == ",".join(str(q) for q in (22, 27, 32)):
@@ -390,6 +393,8 @@ def main():
         cfg = dataclasses.replace(cfg, T=args.frames)
     dev = torch.device("cuda", local)
     ctx = xv.Context(local)
+    if args.block_size:
+        xv.xv_debug_force_block_size(ctx, args.block_size)
     # one encode per (sub-cube, QP); the ERA5-shaped workload is six sub-cubes
     # of uneven length (causal prefixes of one generated cube, copied to their
     # own contiguous buffers)
@@ -514,7 +519,7 @@ def main():
         "gpu_launches": int(launches),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=16 if args.config == 1 else 4)
+        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=192 if args.config == 1 else 4)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
