@@ -85,6 +85,10 @@ def lib():
             L.xvo_tqr_frame.restype = ctypes.c_uint64
             L.xvo_encode_planes.argtypes = [vp, i, i, i, i, i, i, u, i, vp, vp, vp, vp, vp, vp, vp, vp]
             L.xvo_psnr.argtypes = [vp, i, i, i, i, i, vp, vp, i, i, vp, vp, vp, vp, vp]
+            L.xvo_decode_frame.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
+            L.xvo_decode_frame.restype = ctypes.c_uint64
+            L.xvo_decode_planes.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
+            L.xvo_unpack.argtypes = [vp, i, i, i, i, i, i, vp, vp]
             L.xvo_max_threads.restype = i
             L.xvo_set_threads.argtypes = [i]
             _lib = L
@@ -279,6 +283,41 @@ def encode_planes(planes: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, w
                             _p(out["mv"]), _p(out["cost"]), _p(out["mv_int"]), _p(out["cost_int"]),
                             _p(out["levels"]), _p(out["tu_log2"]), _p(out["bits"]))
     return out
+
+
+# ------------------------------------------------------------------ decoder
+def decode_frame(levels: np.ndarray, ref, mv: np.ndarray, tu_log2: np.ndarray, ctu: int, qp: int):
+    """One frame [3,Hp,Wp] of one group from its levels, vectors and TU sizes
+    (ref None: frame 0).  Returns (recon, bits)."""
+    levels = np.ascontiguousarray(levels, np.int16)
+    _, Hp, Wp = levels.shape
+    recon = np.zeros(levels.shape, np.uint16)
+    r = None if ref is None else np.ascontiguousarray(ref, np.uint16)
+    bits = lib().xvo_decode_frame(_p(levels), _p(r), _p(np.ascontiguousarray(mv, np.int16)),
+                                  _p(np.ascontiguousarray(tu_log2, np.uint8)), Hp, Wp, ctu, qp, _p(recon))
+    return recon, int(bits)
+
+
+def decode_planes(levels: np.ndarray, mv: np.ndarray, tu_log2: np.ndarray, ctu: int, qp: int):
+    """The whole chain [G,T,3,Hp,Wp]: frames in order per group.  Returns
+    dict(recon, bits[G,T])."""
+    levels = np.ascontiguousarray(levels, np.int16)
+    G, T, _, Hp, Wp = levels.shape
+    recon = np.zeros(levels.shape, np.uint16)
+    bits = np.zeros((G, T), np.uint64)
+    lib().xvo_decode_planes(_p(levels), _p(np.ascontiguousarray(mv, np.int16)),
+                            _p(np.ascontiguousarray(tu_log2, np.uint8)), G, T, Hp, Wp, ctu, qp, _p(recon),
+                            _p(bits))
+    return dict(recon=recon, bits=bits)
+
+
+def unpack(recon: np.ndarray, mm: np.ndarray, bands: int, H: int, W: int) -> np.ndarray:
+    """The reconstruction in the cube's units: float32 [bands,T,H,W]."""
+    recon = np.ascontiguousarray(recon, np.uint16)
+    G, T, _, Hp, Wp = recon.shape
+    dst = np.zeros((bands, T, H, W), np.float32)
+    lib().xvo_unpack(_p(recon), bands, T, H, W, Hp, Wp, _p(np.ascontiguousarray(mm, np.float64)), _p(dst))
+    return dst
 
 
 # ----------------------------------------------------------------- C14 / C13

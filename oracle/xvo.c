@@ -542,6 +542,89 @@ int xvo_encode_planes(const uint16_t* planes, int G, int T, int Hp, int Wp, int 
     return 0;
 }
 
+/* ======================= Decoder (the inverse of C4..C13) ===================== */
+
+/* One frame of one group from its coded data: per CU the same prediction as
+ * the encoder (C4: flat 2^(B-1) in frame 0, else channel 0's vector applied
+ * to all three channels of the previous reconstruction, C5/C6), then per TU
+ * of the CU's chosen size the dequantised levels (C11), the inverse
+ * transform (C10) and recon = clip(pred + r, 0, 1023).  Returns the frame's
+ * rate proxy recomputed from the levels (C13), which must equal the
+ * encoder's. */
+uint64_t xvo_decode_frame(const int16_t* levels, const uint16_t* ref, const int16_t* mv,
+                          const uint8_t* tu_log2, int Hp, int Wp, int ctu, int qp, uint16_t* recon) {
+    int nx = Wp / ctu, ny = Hp / ctu, ncu = nx * ny;
+    int64_t plane = (int64_t)Hp * Wp;
+    uint64_t* bits_per_cu = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)ncu);
+#pragma omp parallel for schedule(dynamic)
+    for (int cu = 0; cu < ncu; ++cu) {
+        int x0 = (cu % nx) * ctu, y0 = (cu / nx) * ctu;
+        int mvx = ref ? mv[2 * cu] : 0, mvy = ref ? mv[2 * cu + 1] : 0;
+        int L = tu_log2[cu], N = 1 << L;
+        uint64_t bits = 2 + (ref ? (uint64_t)xvo_mv_bits(mvx, mvy) : 0);
+        int32_t D[32 * 32], Rr[32 * 32];
+        for (int c = 0; c < 3; ++c)
+            for (int ty = 0; ty < ctu; ty += N)
+                for (int tx = 0; tx < ctu; tx += N) {
+                    uint64_t tb = 1; /* coded-block flag */
+                    for (int y = 0; y < N; ++y)
+                        for (int x = 0; x < N; ++x) {
+                            int lv = levels[c * plane + (int64_t)(y0 + ty + y) * Wp + x0 + tx + x];
+                            if (lv != 0) tb += (uint64_t)(2 * L + xvo_ue_len_se(lv));
+                            D[y * N + x] = xvo_dequant(lv, qp, L);
+                        }
+                    bits += tb;
+                    xvo_inv_transform(N, D, Rr);
+                    for (int y = 0; y < N; ++y)
+                        for (int x = 0; x < N; ++x) {
+                            int xs = x0 + tx + x, ys = y0 + ty + y;
+                            int pred = ref ? interp_sample(ref + c * plane, Hp, Wp, xs, ys, mvx, mvy)
+                                           : (1 << (BITDEPTH - 1));
+                            recon[c * plane + (int64_t)ys * Wp + xs] =
+                                (uint16_t)clampi(pred + Rr[y * N + x], 0, PIXMAX);
+                        }
+                }
+        bits_per_cu[cu] = bits;
+    }
+    uint64_t total = 0;
+    for (int cu = 0; cu < ncu; ++cu) total += bits_per_cu[cu];
+    free(bits_per_cu);
+    return total;
+}
+
+int xvo_decode_planes(const int16_t* levels, const int16_t* mv, const uint8_t* tu_log2, int G, int T,
+                      int Hp, int Wp, int ctu, int qp, uint16_t* recon, uint64_t* bits) {
+    int npu = (Hp / ctu) * (Wp / ctu);
+    int64_t fsz = 3 * (int64_t)Hp * Wp;
+    for (int g = 0; g < G; ++g)
+        for (int t = 0; t < T; ++t) {
+            int64_t f = (int64_t)g * T + t;
+            bits[f] = xvo_decode_frame(levels + f * fsz, t > 0 ? recon + (f - 1) * fsz : NULL,
+                                       mv + f * 2 * npu, tu_log2 + f * npu, Hp, Wp, ctu, qp,
+                                       recon + f * fsz);
+        }
+    return 0;
+}
+
+/* The reconstruction back in the cube's units (the inverse of C1/C2): band b
+ * (group b/3, channel b%3) over the valid H x W region, x^ = min + q
+ * (max - min)/1023 in double (multiply, then add), rounded to float32. */
+void xvo_unpack(const uint16_t* recon, int bands, int T, int H, int W, int Hp, int Wp, const double* mm,
+                float* dst) {
+    for (int b = 0; b < bands; ++b) {
+        int g = b / 3, c = b % 3;
+        double lo = mm[2 * b], hi = mm[2 * b + 1];
+        double delta = (hi - lo) / (double)PIXMAX;
+        for (int t = 0; t < T; ++t)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    int q = recon[((((int64_t)g * T + t) * 3 + c) * Hp + y) * Wp + x];
+                    double xh = lo + (double)q * delta;
+                    dst[(((int64_t)b * T + t) * H + y) * W + x] = (float)xh;
+                }
+    }
+}
+
 /* ============================== C14: PSNR ==================================== */
 
 /* Per real band b (slot: group b/3, channel b%3): x^ = min + q^ (max-min)/1023,

@@ -80,6 +80,16 @@ int xvo_encode_planes(const uint16_t* planes /*[G][T][3][Hp][Wp]*/, int G, int T
                       uint32_t* cost_int /*or NULL*/, int16_t* levels /*or NULL*/,
                       uint8_t* tu_log2 /*[G][T][nCU] or NULL*/, uint64_t* bits /*[G][T]*/);
 
+/* ---- decoder: coded data -> reconstruction -> cube units ---------------------- */
+uint64_t xvo_decode_frame(const int16_t* levels /*[3][Hp][Wp]*/, const uint16_t* ref /*NULL: frame 0*/,
+                          const int16_t* mv /*[nCU][2]*/, const uint8_t* tu_log2 /*[nCU]*/,
+                          int Hp, int Wp, int ctu, int qp, uint16_t* recon /*[3][Hp][Wp]*/);
+int xvo_decode_planes(const int16_t* levels /*[G][T][3][Hp][Wp]*/, const int16_t* mv /*[G][T][nPU][2]*/,
+                      const uint8_t* tu_log2 /*[G][T][nCU]*/, int G, int T, int Hp, int Wp, int ctu,
+                      int qp, uint16_t* recon /*[G][T][3][Hp][Wp]*/, uint64_t* bits /*[G][T]*/);
+void xvo_unpack(const uint16_t* recon /*[G][T][3][Hp][Wp]*/, int bands, int T, int H, int W, int Hp,
+                int Wp, const double* mm /*[bands][2]*/, float* dst /*[bands][T][H][W]*/);
+
 /* ---- C14/C13: PSNR and bits per pixel per band ------------------------------- */
 void xvo_psnr(const void* src, int dtype, int bands, int T, int H, int W,
               const uint16_t* planes, const uint16_t* recon, int Hp, int Wp, const double* mm,
