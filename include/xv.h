@@ -249,6 +249,63 @@ xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void
  * stays usable). */
 xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
 
+/* ------------------------------------------------------ decoder */
+
+/* The decoder (the paper's video2xarray step, Sec. 2.1, below the codec): a
+ * frame is rebuilt from its coded data exactly as the encoder reconstructed
+ * it.  Per CU: the encoder's prediction (ref == NULL, frame 0: flat 512;
+ * else the CU's quarter-sample vector on all three channels of the previous
+ * reconstruction, as at xv_transform_quant_recon), then per TU of the CU's
+ * size the dequantised levels, the inverse transform and
+ * recon = clip(pred + r, 0, 1023).  The rate proxy of
+ * xv_transform_quant_recon is recomputed from the levels and vectors, so
+ * decoding an encoder's output reproduces its recon and bits bit for bit.
+ * Decoding one frame for G groups; layouts as xv_transform_quant_recon:
+ * levels: int16 plane layout (group g at + g * plane_gstride, [3][Hp][Wp]);
+ * ref/recon: uint16 the same; mv: int16 [G][nCU][2] at + g * pu_gstride * 2
+ * (ignored when ref == NULL); tu_log2: uint8 [G][nCU] at + g * pu_gstride
+ * (values outside 2..log2 ctu are clamped into it); bits: uint64, group g's
+ * frame total is ADDED to bits[g * bits_gstride] (zero it first).  Only
+ * p->ctu and p->qp are used. */
+xv_status xv_decode_frame(xv_ctx* ctx, const int16_t* levels, const uint16_t* ref, const int16_t* mv,
+                          const uint8_t* tu_log2, int G, int64_t plane_gstride, int Hp, int Wp,
+                          const xv_params* p, int64_t pu_gstride, uint16_t* recon, uint64_t* bits,
+                          int64_t bits_gstride, void* stream);
+
+/* One coded cube for xv_decode_batch (device pointers). */
+typedef struct {
+    xv_params p;            /* ctu, qp, and search_range: every vector lies within
+                               +-(4 search_range + 3) quarter samples (the frame
+                               dependency is scheduled from it) */
+    int G, T, Hp, Wp;       /* planes: G groups of T frames of [3][Hp][Wp] */
+    const int16_t* levels;  /* [G][T][3][Hp][Wp] */
+    const int16_t* mv;      /* [G][T][nCU][2] quarter samples (frame 0 ignored) */
+    const uint8_t* tu_log2; /* [G][T][nCU] */
+    uint16_t* recon;        /* [G][T][3][Hp][Wp], written */
+    uint64_t* bits;         /* [G][T] rate proxy per frame, written; or NULL */
+    /* the reconstruction in the cube's units (optional, as xv_unpack) */
+    int bands, H, W;        /* 1 <= bands <= 3G, H <= Hp, W <= Wp */
+    const double* minmax;   /* [bands][2] */
+    float* dst;             /* [bands][T][H][W]; NULL: not written */
+} xv_djob;
+
+/* Decodes whole cubes in ONE persistent launch per CTU size, scheduled like
+ * xv_encode_batch (an item runs once the previous frame's reconstruction rows
+ * its vectors can reach are complete); each job's recon equals
+ * xv_decode_frame applied frame by frame.  total_bits: HOST [njobs] (the
+ * jobs' rate proxies) or NULL.  Synchronous.  XV_ETIMEOUT if a bounded
+ * device wait ran out of time; XV_EINVAL on a malformed job (njobs 1..255,
+ * 16-byte-aligned levels/recon). */
+xv_status xv_decode_batch(xv_ctx* ctx, const xv_djob* jobs, int njobs, uint64_t* total_bits, void* stream);
+
+/* The reconstruction in the cube's units (the inverse of xv_quantize_pack):
+ * band b from group b/3, channel b%3 of recon [G][T][3][Hp][Wp] over the valid
+ * H x W region, x^ = min + q (max - min)/1023 evaluated in double (multiply,
+ * then add) and rounded to float32.  minmax: device [bands][2]; dst: device
+ * float32 [bands][T][H][W]. */
+xv_status xv_unpack(xv_ctx* ctx, const uint16_t* recon, int bands, int T, int H, int W, int Hp, int Wp,
+                    const double* minmax, float* dst, void* stream);
+
 /* ------------------------------------------------------ serving */
 
 /* A compression request for the serving loop.  Unlike xv_job, the cube is in

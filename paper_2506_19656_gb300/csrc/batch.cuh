@@ -6,6 +6,7 @@
 
 #include <cstdint>
 
+#include "dec.cuh"
 #include "me.cuh"
 #include "tqr.cuh"
 #include "xv_internal.h"
@@ -89,14 +90,23 @@ __device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, ui
     }
 }
 
-// Encodes one PU; returns the integer-search candidates evaluated exactly.
+// Encodes (or decodes) one PU; returns the integer-search candidates
+// evaluated exactly.
 template <int N, int kNT>
 __device__ uint32_t item_work(const JobDev& J, int g, int t, int pu, unsigned char* smem) {
     const int64_t plane = (int64_t)J.Hp * J.Wp, fsz = 3 * plane;
     const int64_t f = (int64_t)g * J.T + t;
-    const uint16_t* cur = J.planes + f * fsz;
     const uint16_t* ref = t > 0 ? J.recon + (f - 1) * fsz : nullptr;
     const int x0 = (pu % J.nx) * N, y0 = (pu / J.nx) * N;
+    if (J.decode) {
+        const int64_t o = f * (int64_t)J.nx * J.ny + pu;
+        const int mvx = ref ? J.mv[2 * o] : 0, mvy = ref ? J.mv[2 * o + 1] : 0;
+        const uint32_t b = xvd::dec_cu<N, kNT, true>(J.levels + f * fsz, ref, plane, J.Hp, J.Wp, x0, y0, mvx, mvy,
+                                                     J.tu[o], J.qp, J.recon + f * fsz, smem);
+        if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(J.bits + f), (unsigned long long)b);
+        return 0u;
+    }
+    const uint16_t* cur = J.planes + f * fsz;
     xvd::MeResult m{0, 0, 0u, 0, 0, 0u, 0u};
     if (ref) m = xvd::me_pu<N, kNT, true>(cur, ref, J.Hp, J.Wp, x0, y0, J.R, J.lmv, smem);
     const int64_t npu = (int64_t)J.nx * J.ny;

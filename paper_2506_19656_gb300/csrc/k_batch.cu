@@ -111,6 +111,11 @@ cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long
     return cudaGetLastError();
 }
 
+size_t decode_smem_bytes(int ctu) {
+    size_t a = xvd::dec_smem_bytes(ctu), b = xvd::tqr_smem_bytes(ctu);
+    return a > b ? a : b;
+}
+
 size_t persist_smem_bytes(int ctu, int R, bool has_me) {
     size_t a = xvd::tqr_smem_bytes(ctu);
     size_t b = has_me ? xvd::me_smem_bytes(ctu, R) : 0;

@@ -485,6 +485,47 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
     return fill_result(j, bits, G, r, st);
 }
 
+}  // extern "C"
+
+namespace {
+
+// The batched paths' work stream and events (created on first use).
+xv_status ensure_work_stream(xv_ctx* c) {
+    if (c->work) return XV_OK;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) == cudaSuccess &&
+        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) == cudaSuccess &&
+        (e = cudaEventCreate(&c->ev0)) == cudaSuccess)
+        e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) return cuda_fail(e, "work stream");
+    return XV_OK;
+}
+
+bool valid_djob(const xv_djob* j) {
+    if (!j) { set_error("job is NULL"); return false; }
+    if (!valid_params(&j->p) || !valid_frame(j->G, j->Hp, j->Wp, j->p.ctu)) return false;
+    if (j->T < 1 || j->T > 65535) { set_error("T %d: must be in 1..65535", j->T); return false; }
+    if (!j->levels || !j->mv || !j->tu_log2 || !j->recon) {
+        set_error("levels, mv, tu_log2 and recon are required");
+        return false;
+    }
+    if (!valid_planes(j->levels, j->recon, j->levels, 8)) return false;
+    if (j->dst) {
+        if (j->bands < 1 || j->bands > 3 * j->G || j->bands > XV_MAX_BANDS || j->H < 1 || j->W < 1 || j->H > j->Hp ||
+            j->W > j->Wp || !j->minmax) {
+            set_error("unpack: bands %d (1..min(3G, %d)), cube %dx%d inside %dx%d, and minmax are required", j->bands,
+                      XV_MAX_BANDS, j->H, j->W, j->Hp, j->Wp);
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* results, void* stream) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (njobs < 1 || njobs > 255 || !jobs || !results) { set_error("njobs %d: must be 1..255 with jobs and results", njobs); return XV_EINVAL; }
@@ -494,14 +535,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     cudaStream_t caller = (cudaStream_t)stream;
     xv_status s;
     cudaError_t e = cudaSuccess;
-    if (!c->work) {
-        if ((e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking)) == cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) == cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) == cudaSuccess &&
-            (e = cudaEventCreate(&c->ev0)) == cudaSuccess)
-            e = cudaEventCreate(&c->ev1);
-        if (e != cudaSuccess) return cuda_fail(e, "work stream");
-    }
+    if ((s = ensure_work_stream(c))) return s;
     cudaStream_t st = c->work;
 
     // ---- geometry, descriptors, queue layout (host)
@@ -812,6 +846,179 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         r->bpppb = (double)h_tot[i] / ((double)j.H * j.W * j.T * j.bands);
         r->status = XV_OK;
     }
+    return XV_OK;
+}
+
+xv_status xv_decode_frame(xv_ctx* c, const int16_t* levels, const uint16_t* ref, const int16_t* mv,
+                          const uint8_t* tu_log2, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
+                          int64_t pu_gstride, uint16_t* recon, uint64_t* bits, int64_t bits_gstride, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    if (!levels || !tu_log2 || !recon || !bits || (ref && !mv)) {
+        set_error("levels, tu_log2, recon, bits (and mv with ref) are required");
+        return XV_EINVAL;
+    }
+    if (!valid_planes(levels, ref ? ref : recon, recon, gstride)) return XV_EINVAL;
+    DeviceGuard g(c->device);
+    c->launches += 1;
+    return check_launch(xvh::launch_dec_frame(levels, ref, mv, tu_log2, G, gstride, Hp, Wp, p, pu_gstride, recon, bits,
+                                              bits_gstride, (cudaStream_t)stream),
+                        "decode_frame");
+}
+
+xv_status xv_unpack(xv_ctx* c, const uint16_t* recon, int bands, int T, int H, int W, int Hp, int Wp,
+                    const double* minmax, float* dst, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!recon || !minmax || !dst) { set_error("recon, minmax and dst are required"); return XV_EINVAL; }
+    if (bands < 1 || bands > XV_MAX_BANDS || T < 1 || H < 1 || W < 1 || Hp < H || Wp < W) {
+        set_error("unpack: bands %d (1..%d), cube %dx%dx%d inside planes %dx%d", bands, XV_MAX_BANDS, T, H, W, Hp, Wp);
+        return XV_EINVAL;
+    }
+    DeviceGuard g(c->device);
+    c->launches += 1;
+    return check_launch(xvh::launch_unpack(recon, bands, T, H, W, Hp, Wp, minmax, dst, (cudaStream_t)stream), "unpack");
+}
+
+xv_status xv_decode_batch(xv_ctx* c, const xv_djob* jobs, int njobs, uint64_t* total_bits, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (njobs < 1 || njobs > 255 || !jobs) { set_error("njobs %d: must be 1..255 with jobs", njobs); return XV_EINVAL; }
+    for (int i = 0; i < njobs; ++i)
+        if (!valid_djob(&jobs[i])) return XV_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t caller = (cudaStream_t)stream;
+    xv_status s;
+    cudaError_t e = cudaSuccess;
+    if ((s = ensure_work_stream(c))) return s;
+    cudaStream_t st = c->work;
+
+    // ---- descriptors and queue layout (host), as xv_encode_batch
+    std::vector<xvh::JobDev> jd(njobs);
+    std::vector<int64_t> bits_off(njobs), row_off(njobs);
+    int64_t nbits = 0, nrows = 0;
+    size_t total[4] = {0, 0, 0, 0}, nfirst[4] = {0, 0, 0, 0};
+    const int ctus[4] = {8, 16, 32, 64};
+    for (int i = 0; i < njobs; ++i) {
+        const xv_djob& j = jobs[i];
+        bits_off[i] = nbits;
+        nbits += (int64_t)j.G * j.T;
+        row_off[i] = nrows;
+        nrows += (int64_t)j.G * j.T * (j.Hp / j.p.ctu);
+        const int k = j.p.ctu == 8 ? 0 : j.p.ctu == 16 ? 1 : j.p.ctu == 32 ? 2 : 3;
+        const int64_t npu = (int64_t)(j.Hp / j.p.ctu) * (j.Wp / j.p.ctu);
+        total[k] += (size_t)j.G * j.T * npu;
+        nfirst[k] += (size_t)j.G * npu;
+    }
+    size_t total_items = 0;
+    xvh::ClassDev cls[4];
+    for (int k = 0; k < 4; ++k) {
+        cls[k] = xvh::ClassDev{(int64_t)total_items, (unsigned)total[k], (unsigned)nfirst[k]};
+        total_items += total[k];
+    }
+    if (total_items > 0xffffffffu) { set_error("too many work items in one batch"); return XV_EINVAL; }
+    if ((s = ensure(c, c->b_jobs, sizeof(xvh::JobDev) * njobs))) return s;
+    if ((s = ensure(c, c->b_bits, sizeof(uint64_t) * nbits))) return s;
+    if ((s = ensure(c, c->b_rowdone, sizeof(unsigned) * nrows))) return s;
+    if ((s = ensure(c, c->b_depcnt, sizeof(unsigned) * nrows))) return s;
+    if ((s = ensure(c, c->b_ctl, sizeof(xvh::BatchCtl) * 4))) return s;
+    if ((s = ensure(c, c->b_cls, sizeof(xvh::ClassDev) * 4))) return s;
+    if ((s = ensure(c, c->b_items, sizeof(uint64_t) * total_items))) return s;
+    if ((s = ensure(c, c->b_totals, sizeof(unsigned long long) * njobs))) return s;
+    const size_t stage_bytes = sizeof(xvh::BatchCtl) * 4 + sizeof(unsigned long long) * njobs;
+    if (c->h_stage_bytes < stage_bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        if ((e = cudaMallocHost(&c->h_stage, stage_bytes)) != cudaSuccess) return cuda_fail(e, "pinned staging");
+        c->h_stage_bytes = stage_bytes;
+    }
+    size_t qnext[4];
+    for (int k = 0; k < 4; ++k) qnext[k] = (size_t)cls[k].qoff;
+    for (int i = 0; i < njobs; ++i) {
+        const xv_djob& j = jobs[i];
+        xvh::JobDev& d = jd[i];
+        const int k = j.p.ctu == 8 ? 0 : j.p.ctu == 16 ? 1 : j.p.ctu == 32 ? 2 : 3;
+        d.planes = nullptr;
+        d.recon = j.recon;
+        d.mv = const_cast<int16_t*>(j.mv);
+        d.cost = nullptr;
+        d.levels = const_cast<int16_t*>(j.levels);
+        d.tu = const_cast<uint8_t*>(j.tu_log2);
+        d.bits = j.bits ? j.bits : (uint64_t*)c->b_bits.ptr + bits_off[i];
+        d.rowdone = (unsigned*)c->b_rowdone.ptr + row_off[i];
+        d.depcnt = (unsigned*)c->b_depcnt.ptr + row_off[i];
+        d.lf8 = 0;
+        d.lmv = 0;
+        d.G = j.G; d.T = j.T; d.Hp = j.Hp; d.Wp = j.Wp; d.ctu = j.p.ctu; d.R = j.p.search_range; d.qp = j.p.qp;
+        d.tu_mask = j.p.tu_mask;
+        d.nx = j.Wp / j.p.ctu;
+        d.ny = j.Hp / j.p.ctu;
+        d.qfirst = (int64_t)qnext[k];
+        d.tb = 0;
+        d.te = j.T;
+        d.decode = 1;
+        qnext[k] += (size_t)j.G * d.nx * d.ny;
+    }
+    e = cudaMemcpyAsync(c->b_jobs.ptr, jd.data(), sizeof(xvh::JobDev) * njobs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->b_cls.ptr, cls, sizeof cls, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "decode descriptors");
+    const xvh::JobDev* jobs_dev = (const xvh::JobDev*)c->b_jobs.ptr;
+    xvh::BatchCtl* h_ctl = (xvh::BatchCtl*)c->h_stage;
+    unsigned long long* h_tot = (unsigned long long*)((unsigned char*)c->h_stage + sizeof(xvh::BatchCtl) * 4);
+
+    if ((e = cudaEventRecord(c->ev_in, caller)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c->ev_in, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream order");
+    c->launches += 1;
+    if ((s = check_launch(xvh::launch_batch_prologue(jobs_dev, njobs, (const xvh::ClassDev*)c->b_cls.ptr,
+                                                     (uint64_t*)c->b_items.ptr, (xvh::BatchCtl*)c->b_ctl.ptr,
+                                                     c->wait_budget, c->stall_row, st),
+                          "decode prologue")))
+        return s;
+    if ((e = cudaEventRecord(c->ev0, st)) != cudaSuccess) return cuda_fail(e, "event");
+    for (int k = 0; k < 4; ++k) {
+        if (!total[k]) continue;
+        const int nt = c->force_nt ? c->force_nt : 256;
+        const size_t smem = xvh::decode_smem_bytes(ctus[k]);
+        const int grid = xvh::persist_grid(ctus[k], nt, smem);
+        if ((s = check_launch(xvh::launch_persist(ctus[k], nt, jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
+                                                  (xvh::BatchCtl*)c->b_ctl.ptr + k, smem, grid, st),
+                              "persistent decode")))
+            return s;
+        c->launches += kLaunchPersist;
+        c->batch_nt = nt;
+    }
+    if ((e = cudaEventRecord(c->ev1, st)) != cudaSuccess) return cuda_fail(e, "event");
+    c->launches += 1;
+    if ((s = check_launch(xvh::launch_bits_totals(jobs_dev, njobs, (unsigned long long*)c->b_totals.ptr, st),
+                          "bits totals")))
+        return s;
+    for (int i = 0; i < njobs; ++i) {
+        const xv_djob& j = jobs[i];
+        if (!j.dst) continue;
+        c->launches += 1;
+        if ((s = check_launch(xvh::launch_unpack(j.recon, j.bands, j.T, j.H, j.W, j.Hp, j.Wp, j.minmax, j.dst, st),
+                              "unpack")))
+            return s;
+    }
+    e = cudaMemcpyAsync(h_ctl, c->b_ctl.ptr, sizeof(xvh::BatchCtl) * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_tot, c->b_totals.ptr, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_out, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, c->ev_out, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "decode batch");
+    float kms = 0.f;
+    if (cudaEventElapsedTime(&kms, c->ev0, c->ev1) == cudaSuccess) c->batch_ms = kms;
+    else { c->batch_ms = -1.0; cudaGetLastError(); }
+    c->batch_exact = 0;
+    c->batch_full = 0;
+    for (int k = 0; k < 4; ++k)
+        if (total[k] && h_ctl[k].err) {
+            set_error("a dependency wait of the persistent decode (CTU %d) ran out of time", ctus[k]);
+            return (xv_status)h_ctl[k].err;
+        }
+    if (total_bits)
+        for (int i = 0; i < njobs; ++i) total_bits[i] = h_tot[i];
     return XV_OK;
 }
 

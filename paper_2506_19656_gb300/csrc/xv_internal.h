@@ -36,6 +36,12 @@ cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T,
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
                             uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st);
+cudaError_t launch_dec_frame(const int16_t* levels, const uint16_t* ref, const int16_t* mv, const uint8_t* tu_log2,
+                             int G, int64_t gstride, int Hp, int Wp, const xv_params* p, int64_t pu_gstride,
+                             uint16_t* recon, uint64_t* bits, int64_t bits_gstride, cudaStream_t st);
+cudaError_t launch_unpack(const uint16_t* recon, int bands, int T, int H, int W, int Hp, int Wp, const double* minmax,
+                          float* dst, cudaStream_t st);
+size_t decode_smem_bytes(int ctu);
 cudaError_t launch_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, int G, int64_t gstride,
                              int Hp, int Wp, const xv_params* p, int64_t pu_gstride, uint16_t* recon,
                              int16_t* levels, uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride,
@@ -74,6 +80,7 @@ struct JobDev {
     int nx, ny;
     int64_t qfirst;          // queue slot of this job's first window item
     int tb, te;              // frames [tb, te) are encoded by this launch (frame tb-1 is complete)
+    int decode = 0;          // 1: decode (levels, mv, tu are inputs; recon and bits outputs)
 };
 
 // One CTU class of a batch, as the prologue sees it.

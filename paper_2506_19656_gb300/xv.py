@@ -38,6 +38,12 @@ class xv_request(ctypes.Structure):
                 ("recon_out", _vp), ("mv_out", _vp)]
 
 
+class xv_djob(ctypes.Structure):
+    _fields_ = [("p", xv_params), ("G", _i), ("T", _i), ("Hp", _i), ("Wp", _i), ("levels", _vp), ("mv", _vp),
+                ("tu_log2", _vp), ("recon", _vp), ("bits", _vp), ("bands", _i), ("H", _i), ("W", _i),
+                ("minmax", _vp), ("dst", _vp)]
+
+
 class xv_result(ctypes.Structure):
     _fields_ = [("status", _i), ("bands", _i), ("psnr_mean", ctypes.c_double), ("bpppb", ctypes.c_double),
                 ("total_bits", ctypes.c_uint64), ("psnr_band", ctypes.c_double * XV_MAX_BANDS),
@@ -71,6 +77,10 @@ _SIGS = {
     "xv_transform_quant_recon": [_vp, _vp, _vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp,
                                  _vp, _vp, _i64, _vp],
     "xv_psnr": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+    "xv_decode_frame": [_vp, _vp, _vp, _vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp, _i64,
+                        _vp],
+    "xv_decode_batch": [_vp, ctypes.POINTER(xv_djob), _i, ctypes.POINTER(ctypes.c_uint64), _vp],
+    "xv_unpack": [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp],
     "xv_psnr_noalloc": [_vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
@@ -204,6 +214,37 @@ def xv_transform_quant_recon(ctx: Context, cur, ref, mv, G: int, plane_gstride: 
     check(lib().xv_transform_quant_recon(ctx.handle, _ptr(cur), _ptr(ref), _ptr(mv), G, plane_gstride, Hp, Wp,
                                          ctypes.byref(p), pu_gstride, _ptr(recon), _ptr(levels), _ptr(tu_log2),
                                          _ptr(bits), bits_gstride, _stream(stream)), "xv_transform_quant_recon")
+
+
+def xv_decode_frame(ctx: Context, levels, ref, mv, tu_log2, G: int, plane_gstride: int, Hp: int, Wp: int,
+                    p: xv_params, pu_gstride: int, recon, bits, bits_gstride: int, stream=None):
+    check(lib().xv_decode_frame(ctx.handle, _ptr(levels), _ptr(ref), _ptr(mv), _ptr(tu_log2), G, plane_gstride, Hp,
+                                Wp, ctypes.byref(p), pu_gstride, _ptr(recon), _ptr(bits), bits_gstride,
+                                _stream(stream)), "xv_decode_frame")
+
+
+def make_djob(p: xv_params, levels, mv, tu_log2, recon, bits=None, minmax=None, dst=None, bands=0, H=0,
+              W=0) -> xv_djob:
+    """levels [G,T,3,Hp,Wp] int16, mv [G,T,nCU,2] int16, tu_log2 [G,T,nCU] uint8, recon like levels (uint16);
+    with dst ([bands,T,H,W] float32) and minmax the reconstruction is also written in the cube's units."""
+    G, T, _, Hp, Wp = levels.shape
+    return xv_djob(p=p, G=G, T=T, Hp=Hp, Wp=Wp, levels=_ptr(levels), mv=_ptr(mv), tu_log2=_ptr(tu_log2),
+                   recon=_ptr(recon), bits=_ptr(bits), bands=bands, H=H, W=W, minmax=_ptr(minmax), dst=_ptr(dst))
+
+
+def xv_decode_batch(ctx: Context, djobs, stream=None) -> list:
+    """Decodes the jobs in one persistent launch per CTU size; returns each job's total rate-proxy bits."""
+    n = len(djobs)
+    arr = (xv_djob * n)(*djobs)
+    tot = (ctypes.c_uint64 * n)()
+    check(lib().xv_decode_batch(ctx.handle, arr, n, tot, _stream(stream)), "xv_decode_batch")
+    return list(tot)
+
+
+def xv_unpack(ctx: Context, recon, bands: int, H: int, W: int, minmax, dst, stream=None):
+    G, T, _, Hp, Wp = recon.shape
+    check(lib().xv_unpack(ctx.handle, _ptr(recon), bands, T, H, W, Hp, Wp, _ptr(minmax), _ptr(dst), _stream(stream)),
+          "xv_unpack")
 
 
 def xv_psnr(ctx: Context, src, planes, recon, minmax, stream=None):
