@@ -231,6 +231,157 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_decode(args):
+    """Decode run: the workload's encodes (QP 22/27/32 for the DeepExtremeCubes
+    shape) are encoded once, untimed; each timed step decodes all of them in
+    one xv_decode_batch, writing the reconstruction planes and the cube in its
+    own units (float32), checked equal to the encoder's reconstruction."""
+    import dataclasses
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2506_19656_gb300 import build, synth, xv
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg = synth.CONFIGS[args.config]
+    if args.frames:
+        cfg = dataclasses.replace(cfg, T=args.frames)
+    lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
+    cube = synth.make_cube(args.config, T=max(lengths))
+    ctx = xv.Context(0)
+    if args.block_size:
+        xv.xv_debug_force_block_size(ctx, args.block_size)
+    jobs, djobs, bufs, outs = [], [], [], []
+    for T in lengths:
+        src = torch.from_numpy(np.ascontiguousarray(cube[:, :T])).to(dev)
+        for qp in QPS:
+            p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
+            b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=dev)
+            b["src"] = src
+            jobs.append(xv.make_job(src, p, b["planes"], b["recon"], minmax=b["minmax"], mv=b["mv"], cost=b["cost"],
+                                    levels=b["levels"], tu_log2=b["tu_log2"], bits=b["bits"]))
+            G, Tn = b["levels"].shape[:2]
+            o = dict(recon=torch.empty_like(b["recon"]), bits=torch.zeros((G, Tn), dtype=torch.int64, device=dev),
+                     dst=torch.empty((cfg.bands, T, cfg.H, cfg.W), dtype=torch.float32, device=dev))
+            djobs.append(xv.make_djob(p, b["levels"], b["mv"], b["tu_log2"], o["recon"], bits=o["bits"],
+                                      minmax=b["minmax"], dst=o["dst"], bands=cfg.bands, H=cfg.H, W=cfg.W))
+            bufs.append(b)
+            outs.append(o)
+    enc = xv.xv_encode_batch(ctx, jobs)  # untimed: the coded data to decode
+    work_mpx = len(QPS) * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(step, k):
+        ms, extra = [], []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            extra.append(out)
+        return ms, extra
+
+    def batched():
+        xv.xv_decode_batch(ctx, djobs)
+        return xv.xv_last_batch_kernel_ms(ctx)
+
+    for _ in range(args.warmup):
+        batched()
+    torch.cuda.synchronize()
+    for b, o, r in zip(bufs, outs, enc):  # bit-exact before anything is timed
+        assert torch.equal(o["recon"].view(torch.int16), b["recon"].view(torch.int16)), "decode != encoder recon"
+        assert torch.equal(o["bits"], b["bits"]) and int(o["bits"].sum()) == r["total_bits"], "decoded rate differs"
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = xv.xv_ctx_launches(ctx)
+    torch.cuda.synchronize()
+    step_ms, kern_ms = timed(batched, args.steps)
+    torch.cuda.synchronize()
+    launches = xv.xv_ctx_launches(ctx) - launches0
+    clk = clocks.stop()
+    value = work_mpx / (sum(step_ms) / args.steps / 1e3)
+
+    # plain: per-frame decode launches, then unpack, per encode
+    def plain_step():
+        for dj, b, o in zip(djobs, bufs, outs):
+            G, Tn, _, Hp, Wp = b["levels"].shape
+            fsz = 3 * Hp * Wp
+            ncu = b["tu_log2"].shape[2]
+            o["bits"].zero_()
+            for t in range(Tn):
+                xv.xv_decode_frame(ctx, b["levels"][:, t], o["recon"][:, t - 1] if t else None, b["mv"][:, t],
+                                   b["tu_log2"][:, t], G, Tn * fsz, Hp, Wp, dj.p, Tn * ncu, o["recon"][:, t],
+                                   o["bits"][:, t], Tn)
+            xv.xv_unpack(ctx, o["recon"], cfg.bands, cfg.H, cfg.W, b["minmax"], o["dst"])
+    plain = None
+    if not args.no_plain:
+        plain_step()
+        pm, _ = timed(plain_step, max(3, min(args.steps, 5)))
+        for b, o in zip(bufs, outs):
+            assert torch.equal(o["recon"].view(torch.int16), b["recon"].view(torch.int16))
+        plain = {"value": work_mpx / (statistics.mean(pm) / 1e3), "ms_per_step": statistics.mean(pm),
+                 "path": "xv_decode_frame per frame (one launch for all groups) + xv_unpack, per encode"}
+
+    # end to end: the coded data from pinned host memory, the float cube back to the host
+    hosts = [{k: b[k].cpu().pin_memory() for k in ("levels", "mv", "tu_log2")} for b in bufs]
+    backs = [torch.empty(o["dst"].shape, dtype=torch.float32).pin_memory() for o in outs]
+
+    def e2e_step():
+        for h, b in zip(hosts, bufs):
+            for k in ("levels", "mv", "tu_log2"):
+                b[k].copy_(h[k], non_blocking=True)
+        xv.xv_decode_batch(ctx, djobs)
+        for o, bk in zip(outs, backs):
+            bk.copy_(o["dst"], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_step()
+    em, _ = timed(e2e_step, max(3, min(args.steps, 5)))
+    h2d = sum(sum(h[k].numel() * h[k].element_size() for k in h) for h in hosts)
+    d2h = sum(bk.numel() * bk.element_size() for bk in backs)
+    e2e = {"value": work_mpx / (statistics.mean(em) / 1e3), "unit": "Mpx·band/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    # HBM roofline of the persistent decode: per plane sample the levels read
+    # (2 B), the reference read by motion compensation (2 B) and the
+    # reconstruction written (2 B); vectors and TU sizes are negligible
+    samples = sum(b["levels"].numel() for b in bufs)
+    algo = 6 * samples
+    kms = statistics.mean(kern_ms)
+    peak = 6660.3
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    achieved = algo / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"k_persist<{cfg.ctu}> in decode mode", "kernel_ms": kms,
+                "work_per_launch": f"{algo:.4g} B (levels read, reference read, recon written: 6 B per plane sample)",
+                "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    line = {
+        "metric": "Mpx·band/s of decode (levels, vectors, TU sizes -> recon -> cube units; bit-exact)",
+        "value": value, "unit": "Mpx·band/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": cfg.name, "qps": list(QPS), "ctu": cfg.ctu, "frames": lengths if len(lengths) > 1 else cfg.T,
+                   "bands": cfg.bands, "path": "xv_decode_batch (persistent kernel, decode mode) + unpack",
+                   "block_size": xv.xv_last_batch_block_size(ctx),
+                   "l2": "flushed before every step (256 MB write)", "parallelism": "replicas1"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "plain": plain, "e2e": e2e, "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving run: a stream of requests with Poisson arrivals, kinds drawn
     uniformly from the four workloads, through xv_serve_*; against the plain
@@ -354,6 +505,7 @@ def main():
                     help="workload: 0 tiny, 1 DeepExtremeCubes-shaped (default), 2 DynamicEarthNet-shaped, "
                          "3 ERA5-shaped sub-cubes")
     ap.add_argument("--serve", action="store_true", help="the serving run (request stream) instead")
+    ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--frames-per-tick", type=int, default=8)
@@ -371,6 +523,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.decode:
+        return run_decode(args)
 
     import numpy as np
     import torch
