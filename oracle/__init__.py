@@ -89,6 +89,12 @@ def lib():
             L.xvo_decode_frame.restype = ctypes.c_uint64
             L.xvo_decode_planes.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
             L.xvo_unpack.argtypes = [vp, i, i, i, i, i, i, vp, vp]
+            L.xvo_ssim_window.argtypes = [vp]
+            L.xvo_ssim_image.argtypes = [vp, vp, i, i, ctypes.c_double, vp]
+            L.xvo_ssim_image.restype = ctypes.c_double
+            L.xvo_ssim.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
+            L.xvo_sa.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
+            L.xvo_sa.restype = ctypes.c_double
             L.xvo_max_threads.restype = i
             L.xvo_set_threads.argtypes = [i]
             _lib = L
@@ -318,6 +324,44 @@ def unpack(recon: np.ndarray, mm: np.ndarray, bands: int, H: int, W: int) -> np.
     dst = np.zeros((bands, T, H, W), np.float32)
     lib().xvo_unpack(_p(recon), bands, T, H, W, Hp, Wp, _p(np.ascontiguousarray(mm, np.float64)), _p(dst))
     return dst
+
+
+# ------------------------------------------------------------ SSIM and SA
+def ssim_window() -> np.ndarray:
+    w = np.zeros(11)
+    lib().xvo_ssim_window(_p(w))
+    return w
+
+
+def ssim_image(X: np.ndarray, Y: np.ndarray, L: float):
+    """(sum of the SSIM map over the valid windows, windows counted) of one image pair."""
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    n = np.zeros(1, np.int64)
+    s = lib().xvo_ssim_image(_p(X), _p(Y), X.shape[0], X.shape[1], float(L), _p(n))
+    return s, int(n[0])
+
+
+def ssim(src: np.ndarray, recon: np.ndarray, mm: np.ndarray) -> np.ndarray:
+    """Mean SSIM per band between the cube and the de-quantised reconstruction."""
+    src, dt = _src(src)
+    bands, T, H, W = src.shape
+    Hp, Wp = recon.shape[-2:]
+    out = np.zeros(bands)
+    lib().xvo_ssim(_p(src), dt, bands, T, H, W, _p(np.ascontiguousarray(recon, np.uint16)), Hp, Wp,
+                   _p(np.ascontiguousarray(mm, np.float64)), _p(out))
+    return out
+
+
+def sa(src: np.ndarray, recon: np.ndarray, mm: np.ndarray):
+    """(mean spectral angle in radians, pixels counted)."""
+    src, dt = _src(src)
+    bands, T, H, W = src.shape
+    Hp, Wp = recon.shape[-2:]
+    n = np.zeros(1, np.int64)
+    v = lib().xvo_sa(_p(src), dt, bands, T, H, W, _p(np.ascontiguousarray(recon, np.uint16)), Hp, Wp,
+                     _p(np.ascontiguousarray(mm, np.float64)), _p(n))
+    return float(v), int(n[0])
 
 
 # ----------------------------------------------------------------- C14 / C13

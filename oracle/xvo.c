@@ -625,6 +625,133 @@ void xvo_unpack(const uint16_t* recon, int bands, int T, int H, int W, int Hp, i
     }
 }
 
+/* ============================ SSIM and spectral angle ========================== */
+
+/* The 11-tap Gaussian window of SSIM (sigma 1.5), normalised to sum 1; the 2-D
+ * window is the outer product. */
+void xvo_ssim_window(double* w) {
+    double s = 0.0;
+    for (int k = 0; k < 11; ++k) {
+        w[k] = exp(-(double)((k - 5) * (k - 5)) / (2.0 * 1.5 * 1.5));
+        s += w[k];
+    }
+    for (int k = 0; k < 11; ++k) w[k] /= s;
+}
+
+/* Sum of the SSIM map of one image pair over its valid window positions
+ * (every 11 x 11 window inside the H x W image), skipping windows with a
+ * non-finite sample of X; *nwin += the windows counted.  Local statistics
+ * are Gaussian-weighted: mu = sum w x, sigma_x^2 = sum w (x - mu_x)^2,
+ * sigma_xy = sum w (x - mu_x)(y - mu_y); C1 = (0.01 L)^2, C2 = (0.03 L)^2. */
+double xvo_ssim_image(const double* X, const double* Y, int H, int W, double L, int64_t* nwin) {
+    double w[11];
+    xvo_ssim_window(w);
+    const double C1 = (0.01 * L) * (0.01 * L), C2 = (0.03 * L) * (0.03 * L);
+    double sum = 0.0, comp = 0.0;
+    for (int i = 0; i + 11 <= H; ++i)
+        for (int j = 0; j + 11 <= W; ++j) {
+            double mx = 0.0, my = 0.0;
+            int finite = 1;
+            for (int u = 0; u < 11; ++u)
+                for (int v = 0; v < 11; ++v) {
+                    double x = X[(int64_t)(i + u) * W + j + v];
+                    if (!isfinite(x)) finite = 0;
+                    mx += w[u] * w[v] * x;
+                    my += w[u] * w[v] * Y[(int64_t)(i + u) * W + j + v];
+                }
+            if (!finite) continue;
+            double sxx = 0.0, syy = 0.0, sxy = 0.0;
+            for (int u = 0; u < 11; ++u)
+                for (int v = 0; v < 11; ++v) {
+                    double dx = X[(int64_t)(i + u) * W + j + v] - mx;
+                    double dy = Y[(int64_t)(i + u) * W + j + v] - my;
+                    sxx += w[u] * w[v] * dx * dx;
+                    syy += w[u] * w[v] * dy * dy;
+                    sxy += w[u] * w[v] * dx * dy;
+                }
+            double v = ((2.0 * mx * my + C1) * (2.0 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2));
+            double yk = v - comp, t = sum + yk; /* Kahan */
+            comp = (t - sum) - yk;
+            sum = t;
+            ++*nwin;
+        }
+    return sum;
+}
+
+/* Mean SSIM per real band between the cube and its reconstruction
+ * x^ = min + q (max - min)/1023, over every frame; L = max - min of the band
+ * (a constant band, L = 0, counts as 1).  NaN when no window fits. */
+void xvo_ssim(const void* src, int dtype, int bands, int T, int H, int W, const uint16_t* recon, int Hp, int Wp,
+              const double* mm, double* ssim_band) {
+    double* X = (double*)malloc(sizeof(double) * (size_t)H * W);
+    double* Y = (double*)malloc(sizeof(double) * (size_t)H * W);
+    for (int b = 0; b < bands; ++b) {
+        int g = b / 3, c = b % 3;
+        double lo = mm[2 * b], hi = mm[2 * b + 1], L = hi - lo;
+        double delta = L / (double)PIXMAX;
+        double sum = 0.0;
+        int64_t n = 0;
+        for (int t = 0; t < T; ++t) {
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    X[(int64_t)y * W + x] = src_value(src, dtype, (((int64_t)b * T + t) * H + y) * W + x);
+                    int q = recon[((((int64_t)g * T + t) * 3 + c) * Hp + y) * Wp + x];
+                    Y[(int64_t)y * W + x] = lo + (double)q * delta;
+                }
+            if (L > 0.0) sum += xvo_ssim_image(X, Y, H, W, L, &n);
+        }
+        if (L <= 0.0) ssim_band[b] = (H >= 11 && W >= 11) ? 1.0 : NAN;
+        else ssim_band[b] = n > 0 ? sum / (double)n : NAN;
+    }
+    free(X); free(Y);
+}
+
+/* Mean spectral angle (radians) over the pixels (t, y, x) of the valid
+ * region: the angle between s = (x_b) and s^ = (x^_b) over all bands.  It is
+ * evaluated as atan2(|s ^ s^|, <s, s^>) with |s ^ s^|^2 = sum over band pairs
+ * i < j of (s_i s^_j - s_j s^_i)^2 (Lagrange's identity), which equals
+ * acos(<s, s^> / (|s| |s^|)) and stays accurate for small angles.  Pixels
+ * with a non-finite sample or a zero spectrum are skipped; *npix = the pixels
+ * counted. */
+double xvo_sa(const void* src, int dtype, int bands, int T, int H, int W, const uint16_t* recon, int Hp, int Wp,
+              const double* mm, int64_t* npix) {
+    double sum = 0.0, comp = 0.0;
+    int64_t n = 0;
+    double s[64], sh[64];
+    if (bands > 64) { if (npix) *npix = 0; return NAN; }
+    for (int t = 0; t < T; ++t)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double dot = 0.0, n1 = 0.0, n2 = 0.0;
+                int ok = 1;
+                for (int b = 0; b < bands; ++b) {
+                    int g = b / 3, c = b % 3;
+                    double lo = mm[2 * b], hi = mm[2 * b + 1];
+                    s[b] = src_value(src, dtype, (((int64_t)b * T + t) * H + y) * W + x);
+                    int q = recon[((((int64_t)g * T + t) * 3 + c) * Hp + y) * Wp + x];
+                    sh[b] = lo + (double)q * ((hi - lo) / (double)PIXMAX);
+                    if (!isfinite(s[b])) ok = 0;
+                    dot += s[b] * sh[b];
+                    n1 += s[b] * s[b];
+                    n2 += sh[b] * sh[b];
+                }
+                if (!ok || n1 <= 0.0 || n2 <= 0.0) continue;
+                double cr = 0.0;
+                for (int i = 0; i < bands; ++i)
+                    for (int j = i + 1; j < bands; ++j) {
+                        double m = s[i] * sh[j] - s[j] * sh[i];
+                        cr += m * m;
+                    }
+                double a = atan2(sqrt(cr), dot);
+                double yk = a - comp, tt = sum + yk; /* Kahan */
+                comp = (tt - sum) - yk;
+                sum = tt;
+                ++n;
+            }
+    if (npix) *npix = n;
+    return n > 0 ? sum / (double)n : NAN;
+}
+
 /* ============================== C14: PSNR ==================================== */
 
 /* Per real band b (slot: group b/3, channel b%3): x^ = min + q^ (max-min)/1023,

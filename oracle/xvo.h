@@ -90,6 +90,14 @@ int xvo_decode_planes(const int16_t* levels /*[G][T][3][Hp][Wp]*/, const int16_t
 void xvo_unpack(const uint16_t* recon /*[G][T][3][Hp][Wp]*/, int bands, int T, int H, int W, int Hp,
                 int Wp, const double* mm /*[bands][2]*/, float* dst /*[bands][T][H][W]*/);
 
+/* ---- SSIM (Wang et al. 2004) and spectral angle (Kruse et al. 1993) ---------- */
+void   xvo_ssim_window(double* w /*[11]*/);
+double xvo_ssim_image(const double* X, const double* Y, int H, int W, double L, int64_t* nwin);
+void   xvo_ssim(const void* src, int dtype, int bands, int T, int H, int W, const uint16_t* recon, int Hp,
+                int Wp, const double* mm, double* ssim_band /*[bands]*/);
+double xvo_sa(const void* src, int dtype, int bands, int T, int H, int W, const uint16_t* recon, int Hp,
+              int Wp, const double* mm, int64_t* npix);
+
 /* ---- C14/C13: PSNR and bits per pixel per band ------------------------------- */
 void xvo_psnr(const void* src, int dtype, int bands, int T, int H, int W,
               const uint16_t* planes, const uint16_t* recon, int Hp, int Wp, const double* mm,
