@@ -249,6 +249,33 @@ xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void
  * stays usable). */
 xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
 
+/* SSIM per real band (the paper's Sec. 2.3 quality metric, Wang et al.
+ * 2004): band b against its reconstruction x^ = min + q (max - min)/1023
+ * (group b/3, channel b%3 of recon), per frame over every 11 x 11 window
+ * inside the H x W region with Gaussian weights (sigma 1.5, normalised),
+ * local means mu, variances sum w (x - mu)^2 and covariance,
+ * SSIM = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_x^2 + s_y^2 + C2)),
+ * C1 = (0.01 L)^2, C2 = (0.03 L)^2, L = max - min of the band; windows with a
+ * non-finite original sample are skipped; the band's value is the mean over
+ * its frames' windows (1 for a constant band, NaN when no window fits).
+ * Evaluated in FP32 on (x - min)/L (the index is invariant to it).
+ * ssim_band: HOST [bands] or NULL; ssim_mean: HOST, the mean over bands, or
+ * NULL.  Synchronous. */
+xv_status xv_ssim(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                  const uint16_t* recon, int Hp, int Wp, const double* minmax, double* ssim_band,
+                  double* ssim_mean, void* stream);
+
+/* Mean spectral angle (the paper's Sec. 2.3, Kruse et al. 1993), radians:
+ * per pixel (t, y, x) of the valid region, the angle between the original
+ * spectrum s = (x_b) and the reconstructed one s^ = (x^_b) over all bands,
+ * atan2(|s ^ s^|, <s, s^>) with |s ^ s^|^2 = sum over i < j of
+ * (s_i s^_j - s_j s^_i)^2 (= acos of the normalised dot product, accurate
+ * for small angles); pixels with a non-finite sample or a zero spectrum are
+ * skipped.  sa, npix: HOST.  Synchronous. */
+xv_status xv_sa(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                const uint16_t* recon, int Hp, int Wp, const double* minmax, double* sa, int64_t* npix,
+                void* stream);
+
 /* ------------------------------------------------------ decoder */
 
 /* The decoder (the paper's video2xarray step, Sec. 2.1, below the codec): a

@@ -23,7 +23,7 @@ struct xv_ctx {
     size_t budget = 0;  // 0 = unlimited
     size_t held = 0;
     // scratch of the single-cube calls
-    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax;
+    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax, met_part, met_out;
     // scratch of the batched path
     DevBuf b_jobs, b_items, b_rowdone, b_depcnt, b_ctl, b_bits, b_bandq, b_minmax;
     long long wait_budget = 4000000000LL;  // cycles per dependency wait (about 2 s)
@@ -413,6 +413,73 @@ xv_status xv_psnr(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int
     c->launches += kLaunchBandq;
     if ((s = check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants"))) return s;
     return psnr_into(c, src, dt, bands, T, H, W, planes, recon, Hp, Wp, bq, psnr, mse, sse10, mean, st);
+}
+
+xv_status xv_ssim(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* recon,
+                  int Hp, int Wp, const double* minmax, double* ssim_band, double* ssim_mean, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (!recon || !minmax) { set_error("recon and minmax are required"); return XV_EINVAL; }
+    if (Hp < H || Wp < W) { set_error("plane %dx%d smaller than the cube %dx%d", Hp, Wp, H, W); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = xvh::ssim_blocks_per_band(T, H, W);
+    xv_status s;
+    if ((s = ensure(c, c->bandq, sizeof(BandQ) * bands))) return s;
+    if ((s = ensure(c, c->met_part, sizeof(xvh::MetricPart) * (size_t)nblk * bands))) return s;
+    if ((s = ensure(c, c->met_out, sizeof(xvh::MetricPart) * bands))) return s;
+    BandQ* bq = (BandQ*)c->bandq.ptr;
+    c->launches += kLaunchBandq + 2;
+    if ((s = check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants"))) return s;
+    if ((s = check_launch(xvh::launch_ssim(src, dt, bands, T, H, W, recon, Hp, Wp, bq, (xvh::MetricPart*)c->met_part.ptr,
+                                           nblk, (xvh::MetricPart*)c->met_out.ptr, st),
+                          "ssim")))
+        return s;
+    std::vector<xvh::MetricPart> out(bands);
+    std::vector<BandQ> hq(bands);
+    cudaError_t e = cudaMemcpyAsync(out.data(), c->met_out.ptr, sizeof(xvh::MetricPart) * bands, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), bq, sizeof(BandQ) * bands, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "ssim read-back");
+    double acc = 0.0;
+    for (int b = 0; b < bands; ++b) {
+        double v;
+        if (hq[b].hi - hq[b].lo <= 0.0) v = (H >= 11 && W >= 11) ? 1.0 : NAN;  // a constant band
+        else v = out[b].n > 0 ? out[b].sum / (double)out[b].n : NAN;
+        if (ssim_band) ssim_band[b] = v;
+        acc += v;
+    }
+    if (ssim_mean) *ssim_mean = acc / bands;
+    return XV_OK;
+}
+
+xv_status xv_sa(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* recon,
+                int Hp, int Wp, const double* minmax, double* sa, int64_t* npix, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (!recon || !minmax) { set_error("recon and minmax are required"); return XV_EINVAL; }
+    if (Hp < H || Wp < W) { set_error("plane %dx%d smaller than the cube %dx%d", Hp, Wp, H, W); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = xvh::sa_blocks((int64_t)T * H * W);
+    xv_status s;
+    if ((s = ensure(c, c->bandq, sizeof(BandQ) * bands))) return s;
+    if ((s = ensure(c, c->met_part, sizeof(xvh::MetricPart) * (size_t)nblk))) return s;
+    if ((s = ensure(c, c->met_out, sizeof(xvh::MetricPart) * bands))) return s;
+    BandQ* bq = (BandQ*)c->bandq.ptr;
+    c->launches += kLaunchBandq + 2;
+    if ((s = check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants"))) return s;
+    if ((s = check_launch(xvh::launch_sa(src, dt, bands, T, H, W, recon, Hp, Wp, bq, (xvh::MetricPart*)c->met_part.ptr,
+                                         nblk, (xvh::MetricPart*)c->met_out.ptr, st),
+                          "spectral angle")))
+        return s;
+    xvh::MetricPart out;
+    cudaError_t e = cudaMemcpyAsync(&out, c->met_out.ptr, sizeof out, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "spectral angle read-back");
+    if (sa) *sa = out.n > 0 ? out.sum / (double)out.n : NAN;
+    if (npix) *npix = (int64_t)out.n;
+    return XV_OK;
 }
 
 size_t xv_job_scratch_bytes(const xv_job* j) {

@@ -36,6 +36,17 @@ cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T,
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
                             uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st);
+// SSIM / spectral-angle partial sums (k_metrics.cu).
+struct MetricPart {
+    double sum;
+    unsigned long long n;
+};
+int ssim_blocks_per_band(int T, int H, int W);
+int sa_blocks(int64_t npix);
+cudaError_t launch_ssim(const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* recon, int Hp,
+                        int Wp, const BandQ* bq, MetricPart* part, int nblk, MetricPart* out, cudaStream_t st);
+cudaError_t launch_sa(const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* recon, int Hp,
+                      int Wp, const BandQ* bq, MetricPart* part, int nblk, MetricPart* out, cudaStream_t st);
 cudaError_t launch_dec_frame(const int16_t* levels, const uint16_t* ref, const int16_t* mv, const uint8_t* tu_log2,
                              int G, int64_t gstride, int Hp, int Wp, const xv_params* p, int64_t pu_gstride,
                              uint16_t* recon, uint64_t* bits, int64_t bits_gstride, cudaStream_t st);

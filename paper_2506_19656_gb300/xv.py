@@ -81,6 +81,8 @@ _SIGS = {
                         _vp],
     "xv_decode_batch": [_vp, ctypes.POINTER(xv_djob), _i, ctypes.POINTER(ctypes.c_uint64), _vp],
     "xv_unpack": [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp],
+    "xv_ssim": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp],
+    "xv_sa": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
     "xv_psnr_noalloc": [_vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
@@ -245,6 +247,27 @@ def xv_unpack(ctx: Context, recon, bands: int, H: int, W: int, minmax, dst, stre
     G, T, _, Hp, Wp = recon.shape
     check(lib().xv_unpack(ctx.handle, _ptr(recon), bands, T, H, W, Hp, Wp, _ptr(minmax), _ptr(dst), _stream(stream)),
           "xv_unpack")
+
+
+def xv_ssim(ctx: Context, src, recon, minmax, stream=None) -> dict:
+    """SSIM per band and their mean; src [bands,T,H,W] (float32/uint16), recon [G,T,3,Hp,Wp]."""
+    bands, T, H, W = src.shape
+    Hp, Wp = recon.shape[-2:]
+    band = (ctypes.c_double * bands)()
+    mean = ctypes.c_double()
+    check(lib().xv_ssim(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, _ptr(recon), Hp, Wp, _ptr(minmax),
+                        band, ctypes.byref(mean), _stream(stream)), "xv_ssim")
+    return dict(ssim_band=list(band), ssim_mean=mean.value)
+
+
+def xv_sa(ctx: Context, src, recon, minmax, stream=None):
+    """(mean spectral angle in radians, pixels counted)."""
+    bands, T, H, W = src.shape
+    Hp, Wp = recon.shape[-2:]
+    v, n = ctypes.c_double(), ctypes.c_int64()
+    check(lib().xv_sa(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, _ptr(recon), Hp, Wp, _ptr(minmax),
+                      ctypes.byref(v), ctypes.byref(n), _stream(stream)), "xv_sa")
+    return v.value, n.value
 
 
 def xv_psnr(ctx: Context, src, planes, recon, minmax, stream=None):
