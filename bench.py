@@ -382,6 +382,103 @@ def run_decode(args):
     ctx.close()
 
 
+def run_metrics(args):
+    """Quality-metric run: the workload's encodes are made once, untimed; each
+    timed step computes SSIM per band (xv_ssim) and the mean spectral angle
+    (xv_sa) of every encode's reconstruction against the cube."""
+    import dataclasses
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2506_19656_gb300 import build, synth, xv
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg = synth.CONFIGS[args.config]
+    if args.frames:
+        cfg = dataclasses.replace(cfg, T=args.frames)
+    lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
+    cube = synth.make_cube(args.config, T=max(lengths))
+    ctx = xv.Context(0)
+    jobs, bufs, srcs = [], [], []
+    for T in lengths:
+        src = torch.from_numpy(np.ascontiguousarray(cube[:, :T])).to(dev)
+        for qp in QPS:
+            p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
+            b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=dev)
+            jobs.append(xv.make_job(src, p, b["planes"], b["recon"], minmax=b["minmax"], mv=b["mv"], cost=b["cost"],
+                                    levels=b["levels"], tu_log2=b["tu_log2"], bits=b["bits"]))
+            bufs.append(b)
+            srcs.append(src)
+    xv.xv_encode_batch(ctx, jobs)  # untimed: the reconstructions to score
+    work_mpx = len(QPS) * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
+    windows = len(QPS) * sum(cfg.bands * T * max(cfg.H - 10, 0) * max(cfg.W - 10, 0) for T in lengths)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        out = []
+        for src, b in zip(srcs, bufs):
+            s = xv.xv_ssim(ctx, src, b["recon"], b["minmax"])
+            a, _ = xv.xv_sa(ctx, src, b["recon"], b["minmax"])
+            out.append((s["ssim_mean"], a))
+        return out
+
+    def ssim_only():
+        for src, b in zip(srcs, bufs):
+            xv.xv_ssim(ctx, src, b["recon"], b["minmax"])
+
+    def timed(fn, k):
+        ms, res = [], None
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, res
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = xv.xv_ctx_launches(ctx)
+    step_ms, res = timed(step, args.steps)
+    launches = xv.xv_ctx_launches(ctx) - launches0
+    clk = clocks.stop()
+    ssim_ms, _ = timed(ssim_only, max(3, min(args.steps, 5)))
+    value = work_mpx / (statistics.mean(step_ms) / 1e3)
+    # SSIM kernel: per window 121 taps x 9 FP32 operations (3 deviations and
+    # their weighted products, 3 accumulations) plus about 100 for the means
+    # and the index; the FP32 peak is 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz
+    flops = windows * (121 * 9 + 100)
+    peak = 152 * 128 * 2 * 2.07e9
+    ach = flops / (statistics.mean(ssim_ms) / 1e3)
+    roofline = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "k_ssim (FP32)", "kernel_ms": statistics.mean(ssim_ms),
+                "work_per_launch": f"{flops:.4g} FP32 operations over {windows:.4g} windows (all encodes)",
+                "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"}
+    line = {
+        "metric": "Mpx·band/s of SSIM per band + mean spectral angle of the reconstructions",
+        "value": value, "unit": "Mpx·band/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "qps": list(QPS), "frames": lengths if len(lengths) > 1 else cfg.T,
+                   "bands": cfg.bands, "path": "xv_ssim + xv_sa per encode",
+                   "l2": "flushed before every step (256 MB write)", "parallelism": "replicas1"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "ssim_mean_by_qp": [r[0] for r in res], "sa_rad_by_qp": [r[1] for r in res],
+        "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving run: a stream of requests with Poisson arrivals, kinds drawn
     uniformly from the four workloads, through xv_serve_*; against the plain
@@ -506,6 +603,7 @@ def main():
                          "3 ERA5-shaped sub-cubes")
     ap.add_argument("--serve", action="store_true", help="the serving run (request stream) instead")
     ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
+    ap.add_argument("--metrics", action="store_true", help="the SSIM / spectral-angle run instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--frames-per-tick", type=int, default=8)
@@ -525,6 +623,8 @@ def main():
         return run_serve(args)
     if args.decode:
         return run_decode(args)
+    if args.metrics:
+        return run_metrics(args)
 
     import numpy as np
     import torch
