@@ -364,6 +364,47 @@ def sa(src: np.ndarray, recon: np.ndarray, mm: np.ndarray):
     return float(v), int(n[0])
 
 
+# --------------------------------------------------------------------- PCA
+def pca_fit(src: np.ndarray):
+    """PCA over the bands (the paper's optional transform before packing,
+    Sec. 2.1): every pixel (t, y, x) with all bands finite is a sample.
+    Returns (mean [bands], components [bands, bands], variance [bands]):
+    mean = the sample mean, covariance = (1/n) sum (x - mean)(x - mean)^T,
+    components = its eigenvectors as rows in order of decreasing eigenvalue
+    (ties: lower index first), each signed so that its entry of largest
+    magnitude (the first such) is positive; variance = the eigenvalues."""
+    x = np.asarray(src, np.float64).reshape(src.shape[0], -1)
+    x = x[:, np.all(np.isfinite(x), axis=0)]
+    mean = x.mean(axis=1)
+    xc = x - mean[:, None]
+    cov = xc @ xc.T / x.shape[1]
+    w, v = np.linalg.eigh(cov)
+    order = sorted(range(len(w)), key=lambda i: (-w[i], i))
+    comps = v[:, order].T.copy()
+    for k in range(comps.shape[0]):
+        j = int(np.argmax(np.abs(comps[k])))
+        if comps[k, j] < 0:
+            comps[k] = -comps[k]
+    return mean, comps, w[order]
+
+
+def pca_project(src: np.ndarray, mean: np.ndarray, comps: np.ndarray, npc: int) -> np.ndarray:
+    """z_k = sum_b comps[k, b] (x_b - mean_b) for k < npc, in float64, stored
+    as float32 [npc, T, H, W] (NaN where a band is non-finite)."""
+    bands = src.shape[0]
+    x = np.asarray(src, np.float64).reshape(bands, -1)
+    z = comps[:npc] @ (x - mean[:, None])
+    return z.reshape((npc,) + src.shape[1:]).astype(np.float32)
+
+
+def pca_inverse(z: np.ndarray, mean: np.ndarray, comps: np.ndarray) -> np.ndarray:
+    """x_b = mean_b + sum_k comps[k, b] z_k over the kept components, float32."""
+    npc = z.shape[0]
+    zz = np.asarray(z, np.float64).reshape(npc, -1)
+    x = mean[:, None] + comps[:npc].T @ zz
+    return x.reshape((comps.shape[1],) + z.shape[1:]).astype(np.float32)
+
+
 # ----------------------------------------------------------------- C14 / C13
 def psnr(src: np.ndarray, planes: np.ndarray, recon: np.ndarray, mm: np.ndarray):
     src, dt = _src(src)
