@@ -276,6 +276,33 @@ xv_status xv_sa(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, 
                 const uint16_t* recon, int Hp, int Wp, const double* minmax, double* sa, int64_t* npix,
                 void* stream);
 
+/* ------------------------------------------------------ PCA over bands */
+
+/* The paper's optional transform before packing (Sec. 2.1: keep the first
+ * nPC principal components of a video's bands; Sec. 3 compresses them as
+ * bands, later components at lower quality or not at all).  Every pixel
+ * (t, y, x) whose bands are all finite is a sample: mean = the sample mean,
+ * covariance = (1/n) sum (x - mean)(x - mean)^T (in double), eigenvectors by
+ * cyclic Jacobi rotations in double on the host.  mean: HOST [bands];
+ * components: HOST [bands][bands], rows = eigenvectors in order of
+ * decreasing eigenvalue (ties: lower index first), each signed so that its
+ * first entry of largest magnitude is positive; variance: HOST [bands], the
+ * eigenvalues.  XV_EINVAL when no pixel has all bands finite.  Synchronous. */
+xv_status xv_pca_fit(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                     double* mean, double* components, double* variance, void* stream);
+
+/* z_k = sum_b components[k][b] (x_b - mean_b) for k < npc, in FP32: src
+ * device [bands][T][H][W]; mean, components: HOST (as xv_pca_fit returns
+ * them, the first npc rows used); dst: device float32 [npc][T][H][W] (a pixel
+ * with a non-finite band gives non-finite components). */
+xv_status xv_pca_project(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands, int T, int H, int W,
+                         const double* mean, const double* components, int npc, float* dst, void* stream);
+
+/* The inverse: x_b = mean_b + sum_{k < npc} components[k][b] z_k, FP32.
+ * z: device float32 [npc][T][H][W]; dst: device float32 [bands][T][H][W]. */
+xv_status xv_pca_inverse(xv_ctx* ctx, const float* z, int npc, int bands, int T, int H, int W,
+                         const double* mean, const double* components, float* dst, void* stream);
+
 /* ------------------------------------------------------ decoder */
 
 /* The decoder (the paper's video2xarray step, Sec. 2.1, below the codec): a

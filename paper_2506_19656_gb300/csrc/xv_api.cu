@@ -23,7 +23,7 @@ struct xv_ctx {
     size_t budget = 0;  // 0 = unlimited
     size_t held = 0;
     // scratch of the single-cube calls
-    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax, met_part, met_out;
+    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax, met_part, met_out, pca_part;
     // scratch of the batched path
     DevBuf b_jobs, b_items, b_rowdone, b_depcnt, b_ctl, b_bits, b_bandq, b_minmax;
     long long wait_budget = 4000000000LL;  // cycles per dependency wait (about 2 s)
@@ -480,6 +480,87 @@ xv_status xv_sa(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H
     if (sa) *sa = out.n > 0 ? out.sum / (double)out.n : NAN;
     if (npix) *npix = (int64_t)out.n;
     return XV_OK;
+}
+
+xv_status xv_pca_fit(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, double* mean,
+                     double* components, double* variance, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (!mean || !components || !variance) { set_error("mean, components and variance are required"); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t npix = (int64_t)T * H * W;
+    const int nblk = xvh::pca_fit_blocks(npix);
+    xv_status s;
+    if ((s = ensure(c, c->pca_part, sizeof(double) * 136 * (size_t)nblk))) return s;
+    double* part = (double*)c->pca_part.ptr;
+    std::vector<double> h((size_t)136 * nblk);
+    c->launches += 1;
+    if ((s = check_launch(xvh::launch_pca_sums(src, dt, bands, npix, part, nblk, st), "pca sums"))) return s;
+    cudaError_t e = cudaMemcpyAsync(h.data(), part, sizeof(double) * (XV_MAX_BANDS + 1) * nblk, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pca sums read-back");
+    double cnt = 0.0, m[XV_MAX_BANDS] = {0};
+    for (int k = 0; k < nblk; ++k) {  // in block order
+        for (int b = 0; b < bands; ++b) m[b] += h[(size_t)k * (XV_MAX_BANDS + 1) + b];
+        cnt += h[(size_t)k * (XV_MAX_BANDS + 1) + XV_MAX_BANDS];
+    }
+    if (cnt < 1.0) { set_error("no pixel has all bands finite"); return XV_EINVAL; }
+    for (int b = 0; b < bands; ++b) m[b] /= cnt;
+    c->launches += 1;
+    if ((s = check_launch(xvh::launch_pca_cov(src, dt, bands, npix, m, part, nblk, st), "pca covariance"))) return s;
+    e = cudaMemcpyAsync(h.data(), part, sizeof(double) * 136 * nblk, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pca covariance read-back");
+    std::vector<double> cov((size_t)bands * bands, 0.0);
+    const int npair = bands * (bands + 1) / 2;
+    for (int k = 0; k < nblk; ++k) {
+        int pi = 0, pj = 0;
+        for (int q = 0; q < npair; ++q) {
+            const double v = h[(size_t)k * 136 + q];
+            cov[(size_t)pi * bands + pj] += v;
+            if (++pj == bands) { ++pi; pj = pi; }
+        }
+    }
+    for (int i = 0; i < bands; ++i)
+        for (int j = i; j < bands; ++j) {
+            cov[(size_t)i * bands + j] /= cnt;
+            cov[(size_t)j * bands + i] = cov[(size_t)i * bands + j];
+        }
+    for (int b = 0; b < bands; ++b) mean[b] = m[b];
+    xvh::pca_eigen(bands, cov.data(), variance, components);
+    return XV_OK;
+}
+
+xv_status xv_pca_project(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, const double* mean,
+                         const double* components, int npc, float* dst, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_cube(src, dt, bands, T, H, W)) return XV_EINVAL;
+    if (!mean || !components || !dst || npc < 1 || npc > bands) {
+        set_error("mean, components, dst and 1 <= npc (%d) <= bands (%d) are required", npc, bands);
+        return XV_EINVAL;
+    }
+    DeviceGuard g(c->device);
+    c->launches += 1;
+    return check_launch(xvh::launch_pca_project(src, dt, bands, npc, (int64_t)T * H * W, mean, components, dst,
+                                                (cudaStream_t)stream),
+                        "pca project");
+}
+
+xv_status xv_pca_inverse(xv_ctx* c, const float* z, int npc, int bands, int T, int H, int W, const double* mean,
+                         const double* components, float* dst, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!z || !mean || !components || !dst || bands < 1 || bands > XV_MAX_BANDS || npc < 1 || npc > bands || T < 1 ||
+        H < 1 || W < 1) {
+        set_error("pca inverse: z, mean, components, dst, 1 <= npc (%d) <= bands (%d) <= %d and a cube are required",
+                  npc, bands, XV_MAX_BANDS);
+        return XV_EINVAL;
+    }
+    DeviceGuard g(c->device);
+    c->launches += 1;
+    return check_launch(xvh::launch_pca_inverse(z, npc, bands, (int64_t)T * H * W, mean, components, dst,
+                                                (cudaStream_t)stream),
+                        "pca inverse");
 }
 
 size_t xv_job_scratch_bytes(const xv_job* j) {

@@ -36,6 +36,17 @@ cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T,
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
                             uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st);
+// PCA over bands (k_pca.cu).
+int pca_fit_blocks(int64_t npix);
+cudaError_t launch_pca_sums(const void* src, xv_dtype dt, int bands, int64_t npix, double* part, int nblk,
+                            cudaStream_t st);
+cudaError_t launch_pca_cov(const void* src, xv_dtype dt, int bands, int64_t npix, const double* mean, double* part,
+                           int nblk, cudaStream_t st);
+cudaError_t launch_pca_project(const void* src, xv_dtype dt, int bands, int npc, int64_t npix, const double* mean,
+                               const double* comps, float* dst, cudaStream_t st);
+cudaError_t launch_pca_inverse(const float* z, int npc, int bands, int64_t npix, const double* mean, const double* comps,
+                               float* dst, cudaStream_t st);
+void pca_eigen(int n, const double* a, double* vals, double* vecs);
 // SSIM / spectral-angle partial sums (k_metrics.cu).
 struct MetricPart {
     double sum;

@@ -81,6 +81,9 @@ _SIGS = {
                         _vp],
     "xv_decode_batch": [_vp, ctypes.POINTER(xv_djob), _i, ctypes.POINTER(ctypes.c_uint64), _vp],
     "xv_unpack": [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp],
+    "xv_pca_fit": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp],
+    "xv_pca_project": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _vp, _vp],
+    "xv_pca_inverse": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp],
     "xv_ssim": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _vp],
     "xv_sa": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
     "xv_psnr_noalloc": [_vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -247,6 +250,37 @@ def xv_unpack(ctx: Context, recon, bands: int, H: int, W: int, minmax, dst, stre
     G, T, _, Hp, Wp = recon.shape
     check(lib().xv_unpack(ctx.handle, _ptr(recon), bands, T, H, W, Hp, Wp, _ptr(minmax), _ptr(dst), _stream(stream)),
           "xv_unpack")
+
+
+def xv_pca_fit(ctx: Context, src, stream=None):
+    """(mean [bands], components [bands, bands], variance [bands]) as numpy float64."""
+    import numpy as np
+    bands, T, H, W = src.shape
+    mean = np.zeros(bands)
+    comps = np.zeros((bands, bands))
+    var = np.zeros(bands)
+    check(lib().xv_pca_fit(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, mean.ctypes.data,
+                           comps.ctypes.data, var.ctypes.data, _stream(stream)), "xv_pca_fit")
+    return mean, comps, var
+
+
+def xv_pca_project(ctx: Context, src, mean, comps, npc: int, dst, stream=None):
+    import numpy as np
+    bands, T, H, W = src.shape
+    m = np.ascontiguousarray(mean, np.float64)
+    cmp = np.ascontiguousarray(comps, np.float64)
+    check(lib().xv_pca_project(ctx.handle, _ptr(src), _dtype_code(src), bands, T, H, W, m.ctypes.data,
+                               cmp.ctypes.data, npc, _ptr(dst), _stream(stream)), "xv_pca_project")
+
+
+def xv_pca_inverse(ctx: Context, z, mean, comps, dst, stream=None):
+    import numpy as np
+    npc, T, H, W = z.shape
+    bands = dst.shape[0]
+    m = np.ascontiguousarray(mean, np.float64)
+    cmp = np.ascontiguousarray(comps, np.float64)
+    check(lib().xv_pca_inverse(ctx.handle, _ptr(z), npc, bands, T, H, W, m.ctypes.data, cmp.ctypes.data, _ptr(dst),
+                               _stream(stream)), "xv_pca_inverse")
 
 
 def xv_ssim(ctx: Context, src, recon, minmax, stream=None) -> dict:
