@@ -479,6 +479,102 @@ def run_metrics(args):
     ctx.close()
 
 
+def run_pca(args):
+    """PCA run on the workload's cube: each timed step fits the PCA over its
+    bands (xv_pca_fit), projects it onto all but the last component (the
+    paper's "PCA - 9 bands" packing of ten bands into three videos) and
+    inverts the projection; the round trip is checked against the cube."""
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2506_19656_gb300 import build, synth, xv
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg = synth.CONFIGS[args.config]
+    T = args.frames or cfg.T
+    cube = synth.make_cube(args.config, T=T)
+    src = torch.from_numpy(np.ascontiguousarray(cube)).to(dev)
+    bands = cube.shape[0]
+    npc = max(1, bands - 1)
+    ctx = xv.Context(0)
+    z = torch.empty((npc,) + cube.shape[1:], dtype=torch.float32, device=dev)
+    back = torch.empty(cube.shape, dtype=torch.float32, device=dev)
+    npix = int(np.prod(cube.shape[1:]))
+    work_mpx = bands * npix / 1e6
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    state = {}
+
+    def step():
+        m, c, v = xv.xv_pca_fit(ctx, src)
+        xv.xv_pca_project(ctx, src, m, c, npc, z)
+        xv.xv_pca_inverse(ctx, z, m, c, back)
+        state.update(m=m, c=c, v=v)
+
+    def proj_inv():
+        xv.xv_pca_project(ctx, src, state["m"], state["c"], npc, z)
+        xv.xv_pca_inverse(ctx, z, state["m"], state["c"], back)
+
+    def timed(fn, k):
+        ms = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # the dropped component's variance is the round trip's mean square error per pixel
+    err = (back.double() - src.double()).pow(2).sum(dim=0).mean().item()
+    assert abs(err - state["v"][-1]) <= 1e-3 * state["v"][-1] + 1e-9 * state["v"][0], (err, state["v"][-1])
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = xv.xv_ctx_launches(ctx)
+    step_ms = timed(step, args.steps)
+    launches = xv.xv_ctx_launches(ctx) - launches0
+    clk = clocks.stop()
+    pi_ms = timed(proj_inv, max(3, min(args.steps, 5)))
+    esz = src.element_size()
+    algo = npix * (bands * esz + npc * 4) + npix * (npc * 4 + bands * 4)  # project, then inverse
+    kms = statistics.mean(pi_ms)
+    peak = 6660.3
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    ach = algo / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "kernel": "k_pca_project + k_pca_inverse", "kernel_ms": kms,
+                "work_per_launch": f"{algo:.4g} B (bands and components read and written once each)",
+                "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    line = {
+        "metric": "Mpx·band/s of PCA over bands (fit + project to bands-1 components + inverse)",
+        "value": work_mpx / (statistics.mean(step_ms) / 1e3), "unit": "Mpx·band/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 fit, f32 transform",
+        "data": "synthetic",
+        "config": {"workload": cfg.name, "frames": T, "bands": bands, "components_kept": npc,
+                   "path": "xv_pca_fit + xv_pca_project + xv_pca_inverse",
+                   "l2": "flushed before every step (256 MB write)", "parallelism": "replicas1"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "variance_kept": float(sum(state["v"][:npc]) / sum(state["v"])), "roundtrip_mse": err,
+        "roofline": roofline, "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving run: a stream of requests with Poisson arrivals, kinds drawn
     uniformly from the four workloads, through xv_serve_*; against the plain
@@ -604,6 +700,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="the serving run (request stream) instead")
     ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
     ap.add_argument("--metrics", action="store_true", help="the SSIM / spectral-angle run instead")
+    ap.add_argument("--pca", action="store_true", help="the PCA (fit, project, inverse) run instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--frames-per-tick", type=int, default=8)
@@ -625,6 +722,8 @@ def main():
         return run_decode(args)
     if args.metrics:
         return run_metrics(args)
+    if args.pca:
+        return run_pca(args)
 
     import numpy as np
     import torch
