@@ -134,23 +134,42 @@ __device__ __forceinline__ int quantize_sample(float x, const BandQ& q) {
     return (int)f;
 }
 
-// One thread: 8 consecutive output samples of one plane row.
+// Mixed-radix position of an item: (g, t, c, y, xv) with item index
+// (((g T + t) 3 + c) Hp + y) wv + xv.
+struct QPos {
+    int64_t g;
+    int t, c, y, xv;
+};
+
+__device__ __forceinline__ QPos qpos(int64_t it, int wv, int Hp, int T_) {
+    QPos p;
+    const int64_t row = it / wv;
+    p.xv = (int)(it - row * wv);
+    const int64_t f = row / Hp;
+    p.y = (int)(row - f * Hp);
+    const int64_t gt = f / 3;
+    p.c = (int)(f - gt * 3);
+    p.g = gt / T_;
+    p.t = (int)(gt - p.g * T_);
+    return p;
+}
+
+// One thread: 8 consecutive output samples of one plane row.  The grid
+// stride's position is added to the item's position digit by digit with
+// carries, so the loop divides only once.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_quant_pack(const T* __restrict__ src, int bands, int T_, int H, int W, int Hp, int Wp,
              const BandQ* __restrict__ bq, uint16_t* __restrict__ planes, int64_t items) {
     const int wv = Wp / 8;
-    for (int64_t it = (int64_t)blockIdx.x * kThreads + threadIdx.x; it < items;
-         it += (int64_t)gridDim.x * kThreads) {
-        int64_t row = it / wv;
-        int xv = (int)(it - row * wv);
-        int y = (int)(row % Hp);
-        int64_t f = row / Hp;  // ((g*T + t)*3 + c)
-        int c = (int)(f % 3);
-        int64_t gt = f / 3;
-        int t = (int)(gt % T_);
-        int g = (int)(gt / T_);
-        int b = 3 * g + c;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t it = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    QPos p = qpos(it, wv, Hp, T_);
+    const QPos d = qpos(stride, wv, Hp, T_);
+    for (; it < items; it += stride) {
+        const int xv = p.xv, y = p.y, c = p.c, t = p.t;
+        const int64_t row = ((p.g * T_ + t) * 3 + c) * Hp + y;
+        int b = (int)(3 * p.g + c);
         if (b >= bands) b = bands - 1;
         const BandQ q = bq[b];
         const int sy = y < H ? y : H - 1;
@@ -180,6 +199,13 @@ k_quant_pack(const T* __restrict__ src, int bands, int T_, int H, int W, int Hp,
 #pragma unroll
         for (int k = 0; k < 8; ++k) o[k] = (uint16_t)quantize_sample(v[k], q);
         *reinterpret_cast<uint4*>(planes + row * Wp + x0) = out;
+        // advance the position by the stride
+        int carry;
+        p.xv += d.xv; carry = p.xv >= wv; if (carry) p.xv -= wv;
+        p.y += d.y + carry; carry = p.y >= Hp; if (carry) p.y -= Hp;
+        p.c += d.c + carry; carry = p.c >= 3; if (carry) p.c -= 3;
+        p.t += d.t + carry; carry = p.t >= T_; if (carry) p.t -= T_;
+        p.g += d.g + carry;
     }
 }
 
