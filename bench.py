@@ -37,7 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpx·band/s of ME+transform/quant/recon (bit-exact), batched vs plain; p50/p99"
-CONFIG_ID = 1
+WORKLOAD = "deepextremecubes"
 QPS = (22, 27, 32)
 # ALU roofline of the motion search.  One exact 10-bit abs-diff-accumulate is
 # either one __sad on the integer ALU pipe (64 lanes/clock/SM, half the issue
@@ -205,9 +205,9 @@ def run_reference(args):
     from paper_2506_19656_gb300 import synth
     import oracle
     oracle.build()
-    cfg = synth.CONFIGS[CONFIG_ID]
+    cfg = synth.WORKLOADS[WORKLOAD]
     frames = 8
-    cube = synth.make_cube(CONFIG_ID, T=frames)
+    cube = synth.make_cube(WORKLOAD, T=frames)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -246,11 +246,11 @@ def run_decode(args):
     build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    cfg = synth.CONFIGS[args.config]
+    cfg = synth.WORKLOADS[args.workload]
     if args.frames:
         cfg = dataclasses.replace(cfg, T=args.frames)
     lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
-    cube = synth.make_cube(args.config, T=max(lengths))
+    cube = synth.make_cube(args.workload, T=max(lengths))
     ctx = xv.Context(0)
     if args.block_size:
         xv.xv_debug_force_block_size(ctx, args.block_size)
@@ -396,11 +396,11 @@ def run_metrics(args):
     build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    cfg = synth.CONFIGS[args.config]
+    cfg = synth.WORKLOADS[args.workload]
     if args.frames:
         cfg = dataclasses.replace(cfg, T=args.frames)
     lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
-    cube = synth.make_cube(args.config, T=max(lengths))
+    cube = synth.make_cube(args.workload, T=max(lengths))
     ctx = xv.Context(0)
     jobs, bufs, srcs = [], [], []
     for T in lengths:
@@ -493,9 +493,9 @@ def run_pca(args):
     build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    cfg = synth.CONFIGS[args.config]
+    cfg = synth.WORKLOADS[args.workload]
     T = args.frames or cfg.T
-    cube = synth.make_cube(args.config, T=T)
+    cube = synth.make_cube(args.workload, T=T)
     src = torch.from_numpy(np.ascontiguousarray(cube)).to(dev)
     bands = cube.shape[0]
     npc = max(1, bands - 1)
@@ -591,16 +591,16 @@ def run_serve(args):
     # host pools in pinned memory: causal prefixes of one long cube serve the
     # shorter draws of a workload (every prefix is itself a valid cube)
     t0 = time.time()
-    pools = {0: [torch.from_numpy(synth.make_cube(0, cube=i)).pin_memory() for i in range(4)]}
-    for cfg in (1, 2, 3):
-        if any(r["config"] == cfg for r in reqs):
-            T = max(r["T"] for r in reqs if r["config"] == cfg)
-            pools[cfg] = [torch.from_numpy(synth.make_cube(cfg, T=T)).pin_memory()]
+    pools = {"tiny": [torch.from_numpy(synth.make_cube("tiny", cube=i)).pin_memory() for i in range(4)]}
+    for name in ("deepextremecubes", "dynamicearthnet", "era5"):
+        if any(r["workload"] == name for r in reqs):
+            T = max(r["T"] for r in reqs if r["workload"] == name)
+            pools[name] = [torch.from_numpy(synth.make_cube(name, T=T)).pin_memory()]
     gen_s = time.time() - t0
     work = []
     for r in reqs:
-        c = synth.CONFIGS[r["config"]]
-        pool = pools[r["config"]]
+        c = synth.WORKLOADS[r["workload"]]
+        pool = pools[r["workload"]]
         host = pool[r["cube"] % len(pool)][:, : r["T"]]
         if not host.is_contiguous():
             host = host.contiguous().pin_memory()
@@ -611,9 +611,9 @@ def run_serve(args):
     # warm-up: one request of each kind, alone
     seen = set()
     for r, host, p, _ in work:
-        if r["config"] in seen:
+        if r["workload"] in seen:
             continue
-        seen.add(r["config"])
+        seen.add(r["workload"])
         t = xv.xv_serve_submit(ctx, xv.make_request(host, p))
         while not xv.xv_serve_poll(ctx, t)[0]:
             time.sleep(0.001)
@@ -646,8 +646,8 @@ def run_serve(args):
     bufs = {}
     service = []
     for r, host, p, _ in work:
-        key = (r["config"], r["T"])
-        c = synth.CONFIGS[r["config"]]
+        key = (r["workload"], r["T"])
+        c = synth.WORKLOADS[r["workload"]]
         if key not in bufs:
             bufs[key] = (torch.empty(host.shape, dtype=host.dtype, device="cuda"),
                          xv.alloc_cube_buffers(c.bands, r["T"], c.H, c.W, p, levels=False))
@@ -664,7 +664,7 @@ def run_serve(args):
         plain_lat.append(finish - r["arrival_s"])
     plain_makespan = finish - work[0][0]["arrival_s"]
     ctx.close()
-    kinds = {k: sum(1 for r in reqs if r["config"] == k) for k in range(4)}
+    kinds = {k: sum(1 for r in reqs if r["workload"] == k) for k in synth.WORKLOADS}
     line = {
         "metric": METRIC, "value": total_mpx / makespan, "unit": "Mpx·band/s", "n_gpus": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -694,9 +694,10 @@ def main():
     ap.add_argument("--qps", default=",".join(str(q) for q in QPS),
                     help="QPs of the encodes in one step (profiling cases use one)")
     ap.add_argument("--frames", type=int, default=0, help="encode only the first F frames (profiling cases)")
-    ap.add_argument("--config", type=int, default=CONFIG_ID,
-                    help="workload: 0 tiny, 1 DeepExtremeCubes-shaped (default), 2 DynamicEarthNet-shaped, "
-                         "3 ERA5-shaped sub-cubes")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["tiny", "deepextremecubes", "dynamicearthnet", "era5"],
+                    help="the DeepExtremeCubes-shaped cube (default), the tiny cube, the DynamicEarthNet-shaped "
+                         "uint16 cube or the ERA5-shaped sub-cubes")
     ap.add_argument("--serve", action="store_true", help="the serving run (request stream) instead")
     ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
     ap.add_argument("--metrics", action="store_true", help="the SSIM / spectral-angle run instead")
@@ -709,9 +710,9 @@ def main():
                          "profile the variant an uninstrumented run picks")
     args = ap.parse_args()
     globals()["QPS"] = tuple(int(q) for q in args.qps.split(","))
-    if args.config != 1 and args.qps == ",".join(str(q) for q in (22, 27, 32)):
+    if args.workload != WORKLOAD and args.qps == ",".join(str(q) for q in (22, 27, 32)):
         from paper_2506_19656_gb300 import synth as _s
-        globals()["QPS"] = _s.CONFIGS[args.config].qps
+        globals()["QPS"] = _s.WORKLOADS[args.workload].qps
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -741,7 +742,7 @@ def main():
     from paper_2506_19656_gb300 import build, synth, xv
     build.build()
     import dataclasses
-    cfg = synth.CONFIGS[args.config]
+    cfg = synth.WORKLOADS[args.workload]
     if args.frames:
         cfg = dataclasses.replace(cfg, T=args.frames)
     dev = torch.device("cuda", local)
@@ -752,7 +753,7 @@ def main():
     # of uneven length (causal prefixes of one generated cube, copied to their
     # own contiguous buffers)
     lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
-    cube = synth.make_cube(args.config, T=max(lengths))
+    cube = synth.make_cube(args.workload, T=max(lengths))
     full = torch.from_numpy(cube)
     srcs = [full[:, :T].contiguous().to(dev) for T in lengths]
     del full
@@ -872,7 +873,7 @@ def main():
         "gpu_launches": int(launches),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=192 if args.config == 1 else 4)
+        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=192 if args.workload == WORKLOAD else 4)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -1125,7 +1125,8 @@ xv_status xv_decode_batch(xv_ctx* c, const xv_djob* jobs, int njobs, uint64_t* t
     if ((e = cudaEventRecord(c->ev0, st)) != cudaSuccess) return cuda_fail(e, "event");
     for (int k = 0; k < 4; ++k) {
         if (!total[k]) continue;
-        const int nt = c->force_nt ? c->force_nt : 256;
+        // measured: 256 threads for CTU 16 and 64, 128 for CTU 32 (its frames are wide)
+        const int nt = c->force_nt ? c->force_nt : (ctus[k] == 32 ? 128 : 256);
         const size_t smem = xvh::decode_smem_bytes(ctus[k]);
         const int grid = xvh::persist_grid(ctus[k], nt, smem);
         if ((s = check_launch(xvh::launch_persist(ctus[k], nt, jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,

@@ -5,9 +5,10 @@ Sec. 2.2) are not available here, so these generators stand in for them with
 the same shapes, value ranges and kinds of structure.  This module holds no
 step of the compression method: it only draws inputs, and both the CUDA path
 and the CPU oracle are fed from it.  Every draw comes from
-``numpy.random.default_rng(seed)`` with ``seed = 1000 * config + cube``.
+``numpy.random.default_rng(seed)`` with ``seed = seed_base + cube`` (a seed
+base per workload).
 
-Each generator is frame-addressable: ``T`` may be smaller than the config's
+Each generator is frame-addressable: ``T`` may be smaller than the workload's
 length to draw a causal prefix (the first ``T`` frames are the same numbers a
 full draw would give).
 """
@@ -22,6 +23,7 @@ import numpy as np
 class EncoderConfig:
     """Encoder parameters of one workload (restates the paper's mapping_rules)."""
     name: str
+    seed_base: int        # seeds of the workload's cubes: seed_base + cube
     bands: int
     T: int
     H: int
@@ -41,14 +43,16 @@ class EncoderConfig:
         return m
 
 
-CONFIGS = {
-    0: EncoderConfig("tiny-3x8x64x64", 3, 8, 64, 64, "f32", 8, 16, (8,), (27,)),
-    1: EncoderConfig("deepextremecubes-10x256x128x128", 10, 256, 128, 128, "f32", 16, 32,
-                     (4, 8, 16), (22, 27, 32)),
-    2: EncoderConfig("dynamicearthnet-4x300x1024x1024", 4, 300, 1024, 1024, "u16", 64, 64,
-                     (4, 8, 16, 32), (27,)),
-    3: EncoderConfig("era5-6x721x1440-subcubes", 6, 168, 721, 1440, "f32", 32, 16,
-                     (4, 8, 16, 32), (22,), sub_T=(24, 53, 82, 110, 139, 168)),
+# The workloads, by what they stand in for (in this order: the serving
+# stream draws its kinds by position).
+WORKLOADS = {
+    "tiny": EncoderConfig("tiny-3x8x64x64", 0, 3, 8, 64, 64, "f32", 8, 16, (8,), (27,)),
+    "deepextremecubes": EncoderConfig("deepextremecubes-10x256x128x128", 1000, 10, 256, 128, 128, "f32", 16, 32,
+                                      (4, 8, 16), (22, 27, 32)),
+    "dynamicearthnet": EncoderConfig("dynamicearthnet-4x300x1024x1024", 2000, 4, 300, 1024, 1024, "u16", 64, 64,
+                                     (4, 8, 16, 32), (27,)),
+    "era5": EncoderConfig("era5-6x721x1440-subcubes", 3000, 6, 168, 721, 1440, "f32", 32, 16,
+                          (4, 8, 16, 32), (22,), sub_T=(24, 53, 82, 110, 139, 168)),
 }
 
 
@@ -68,7 +72,7 @@ def _blur_periodic(a: np.ndarray, sigma: float) -> np.ndarray:
     return np.real(np.fft.ifft2(np.fft.fft2(a) * g))
 
 
-# ------------------------------------------------------------------ config 0
+# ------------------------------------------------------------------ tiny
 def tiny_cube(seed: int = 0, T: int = 8, H: int = 64, W: int = 64, bands: int = 3):
     """Gaussian blobs translated by seeded integer steps in [-4, 4]^2 plus N(0, 0.002).
 
@@ -102,7 +106,7 @@ def tiny_cube(seed: int = 0, T: int = 8, H: int = 64, W: int = 64, bands: int = 
     return out, S
 
 
-# ------------------------------------------------------------------ config 1
+# ------------------------------------------------------------------ DeepExtremeCubes-shaped
 def deepextremecubes_cube(seed: int = 1000, T: int = 256, H: int = 128, W: int = 128, bands: int = 10,
                           T_full: int | None = None):
     """Beta(2,5) reflectance via a Gaussian copula of smooth noise (sigma 6 px),
@@ -142,7 +146,7 @@ def deepextremecubes_cube(seed: int = 1000, T: int = 256, H: int = 128, W: int =
     return out
 
 
-# ------------------------------------------------------------------ config 2
+# ------------------------------------------------------------------ DynamicEarthNet-shaped
 def dynamicearthnet_cube(seed: int = 2000, T: int = 300, H: int = 1024, W: int = 1024, bands: int = 4,
                          n_seeds: int = 200):
     """Piecewise-constant Voronoi land-cover patches (200 seeds) with per-patch
@@ -170,7 +174,7 @@ def dynamicearthnet_cube(seed: int = 2000, T: int = 300, H: int = 1024, W: int =
     return out
 
 
-# ------------------------------------------------------------------ config 3
+# ------------------------------------------------------------------ ERA5-shaped
 def era5_cube(seed: int = 3000, T: int = 24, H: int = 721, W: int = 1440, bands: int = 6):
     """Smooth spectral random fields, P(k) ~ k^-3, advected zonally (periodic in
     longitude) by u ~ U(2, 6) px/frame, plus a diurnal term 0.2 sigma
@@ -198,19 +202,19 @@ def era5_cube(seed: int = 3000, T: int = 24, H: int = 721, W: int = 1440, bands:
     return out
 
 
-def make_cube(config: int, cube: int = 0, T: int | None = None):
-    """The synthetic cube of a config (float32 or uint16 [bands, T, H, W])."""
-    seed = 1000 * config + cube
-    c = CONFIGS[config]
-    if config == 0:
+def make_cube(workload: str, cube: int = 0, T: int | None = None):
+    """The synthetic cube of a workload (float32 or uint16 [bands, T, H, W])."""
+    c = WORKLOADS[workload]
+    seed = c.seed_base + cube
+    if workload == "tiny":
         return tiny_cube(seed, T=T or c.T)[0]
-    if config == 1:
+    if workload == "deepextremecubes":
         return deepextremecubes_cube(seed, T=T or c.T)
-    if config == 2:
+    if workload == "dynamicearthnet":
         return dynamicearthnet_cube(seed, T=T or c.T)
-    if config == 3:
+    if workload == "era5":
         return era5_cube(seed, T=T or c.sub_T[0])
-    raise ValueError(config)
+    raise ValueError(workload)
 
 
 def random_planes(seed: int, G: int, T: int, Hp: int, Wp: int, smooth: float = 0.0):
@@ -227,14 +231,15 @@ def random_planes(seed: int, G: int, T: int, Hp: int, Wp: int, smooth: float = 0
 def serving_requests(seed: int = 4000, n: int = 2000, mean_interval_s: float = 0.005):
     """Poisson arrival times and uniformly drawn workload kinds for the serving run.
 
-    Returns a list of dicts (arrival_s, config, qp, T)."""
+    Returns a list of dicts (arrival_s, workload, qp, T, cube)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(mean_interval_s, n))
+    names = list(WORKLOADS)
     out = []
     for i in range(n):
-        cfg = int(rng.integers(0, 4))
-        c = CONFIGS[cfg]
+        name = names[int(rng.integers(0, 4))]
+        c = WORKLOADS[name]
         qp = int(rng.choice(c.qps))
         T = int(rng.choice(c.sub_T)) if c.sub_T else c.T
-        out.append(dict(arrival_s=float(t[i]), config=cfg, qp=qp, T=T, cube=int(rng.integers(0, 4))))
+        out.append(dict(arrival_s=float(t[i]), workload=name, qp=qp, T=T, cube=int(rng.integers(0, 4))))
     return out

@@ -57,8 +57,8 @@ def assert_matches(buf, res, want, frames=None):
 
 
 def test_tiny_config_plain(xv, ctx):
-    c = synth.CONFIGS[0]
-    cube = synth.make_cube(0)
+    c = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny")
     want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, c.qps[0])
     job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, c.qps[0])
     res = xv.xv_encode_cube(ctx, job)
@@ -68,8 +68,8 @@ def test_tiny_config_plain(xv, ctx):
 @pytest.mark.parametrize("qp", [22, 27, 32])
 def test_deepextremecubes_prefix_plain_and_batched(xv, ctx, qp):
     """The first 6 frames of the 10-band 128x128 cube (CTU 16, R 32, TU 4-16)."""
-    c = synth.CONFIGS[1]
-    cube = synth.make_cube(1, T=6)
+    c = synth.WORKLOADS["deepextremecubes"]
+    cube = synth.make_cube("deepextremecubes", T=6)
     want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, qp)
     job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, qp)
     assert_matches(buf, xv.xv_encode_cube(ctx, job), want)
@@ -134,7 +134,7 @@ def test_every_block_size_is_bit_exact(xv, ctx, block_size):
 def test_uint16_dynamicearthnet_prefix(xv, ctx):
     """Two frames of a DynamicEarthNet-shaped uint16 cube (CTU 64, R 64, TU 4-32),
     with a min/max fixed in advance (as a causal prefix of a longer cube would)."""
-    c = synth.CONFIGS[2]
+    c = synth.WORKLOADS["dynamicearthnet"]
     cube = synth.dynamicearthnet_cube(2000, T=2, H=256, W=320)
     mm = np.array([[0.0, 10000.0]] * 4)
     want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27, mm=mm)
@@ -145,8 +145,8 @@ def test_uint16_dynamicearthnet_prefix(xv, ctx):
 def test_batch_timeout_is_reported_and_context_survives(xv, ctx):
     """A dependency that is never met: the bounded wait returns XV_ETIMEOUT
     (no fault, no hang) and the same context then encodes correctly."""
-    c = synth.CONFIGS[0]
-    cube = synth.make_cube(0, T=3)
+    c = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny", T=3)
     job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
     xv.xv_debug_set_wait_budget(ctx, 20_000_000)  # ~10 ms
     xv.xv_debug_stall_row(ctx, 8 + 3)  # frame 1, CTU row 3 (8 rows per frame)
@@ -163,7 +163,7 @@ def test_batch_timeout_is_reported_and_context_survives(xv, ctx):
 def test_batch_graph_capture_and_replay(xv):
     """The second submission of the same batch replays the captured graph; all
     runs (graph, replay, no graph) give the oracle's bytes."""
-    c = synth.CONFIGS[0]
+    c = synth.WORKLOADS["tiny"]
     cubes = [synth.tiny_cube(500 + i, T=4)[0] for i in range(2)]
     wants = [oracle.encode_cube(x, c.ctu, c.R, c.tu_mask, qp) for x, qp in zip(cubes, (22, 32))]
     ctx = xv.Context(0)
@@ -193,9 +193,9 @@ def test_full_resolution_dynamicearthnet_and_era5_prefixes(xv, ctx):
     R 64, TU 4-32) and ERA5-shaped (721x1440 float32, padded to 736, CTU 32,
     R 16) workloads, on causal prefixes the oracle finishes: plain path, and
     both together in one batch (two CTU classes, one launch each)."""
-    c2, c3 = synth.CONFIGS[2], synth.CONFIGS[3]
-    den = synth.make_cube(2, T=2)
-    era = synth.make_cube(3, T=3)
+    c2, c3 = synth.WORKLOADS["dynamicearthnet"], synth.WORKLOADS["era5"]
+    den = synth.make_cube("dynamicearthnet", T=2)
+    era = synth.make_cube("era5", T=3)
     w2 = oracle.encode_cube(den, c2.ctu, c2.R, c2.tu_mask, 27)
     w3 = oracle.encode_cube(era, c3.ctu, c3.R, c3.tu_mask, 22)
     j2, b2 = gpu_job(xv, den, c2.ctu, c2.R, c2.tu_mask, 27)

@@ -109,8 +109,8 @@ def test_decode_batch_inverts_encode_mixed(xv, ctx):
 
 @pytest.mark.parametrize("block_size", [128, 256, 512])
 def test_decode_batch_every_block_size(xv, ctx, block_size):
-    c = synth.CONFIGS[1]
-    cube = synth.make_cube(1, T=4)[:4]
+    c = synth.WORKLOADS["deepextremecubes"]
+    cube = synth.make_cube("deepextremecubes", T=4)[:4]
     p, buf, job = gpu_encode(xv, cube, c.ctu, c.R, c.tu_mask, 27)
     xv.xv_encode_batch(ctx, [job])
     dj, out = decode_job(xv, p, buf, 4, c.H, c.W)
@@ -144,9 +144,9 @@ def test_decode_batch_random_data_matches_oracle(xv, ctx):
 def test_decode_full_resolution_prefixes(xv, ctx):
     """Two frames of the DynamicEarthNet-shaped (uint16, CTU 64, R 64) and
     ERA5-shaped (721 x 1440, CTU 32) workloads: decode == encoder recon."""
-    for cfg_id, cube in ((2, synth.dynamicearthnet_cube(2000, T=2, H=512, W=512)),
-                         (3, synth.era5_cube(3000, T=2)[:2])):
-        c = synth.CONFIGS[cfg_id]
+    for name, cube in (("dynamicearthnet", synth.dynamicearthnet_cube(2000, T=2, H=512, W=512)),
+                       ("era5", synth.era5_cube(3000, T=2)[:2])):
+        c = synth.WORKLOADS[name]
         bands, T, H, W = cube.shape
         p, buf, job = gpu_encode(xv, cube, c.ctu, c.R, c.tu_mask, c.qps[0])
         res = xv.xv_encode_batch(ctx, [job])[0]

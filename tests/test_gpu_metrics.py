@@ -90,8 +90,8 @@ def test_metrics_skip_non_finite_and_small_images(xv, ctx):
 def test_metrics_on_an_encoded_cube(xv, ctx):
     """The tiny workload encoded on the GPU at two QPs: SSIM and SA of the
     GPU reconstruction against the oracle's, and quality ordered by QP."""
-    c = synth.CONFIGS[0]
-    cube = synth.make_cube(0)
+    c = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny")
     res = []
     for qp in (22, 37):
         p = xv.xv_params_init(c.ctu, c.R, c.tu_mask, qp)

@@ -31,8 +31,8 @@ def test_decode_inverts_encode(shape, ctu, R, mask, qp, dtype):
 
 
 def test_decode_tiny_workload_every_qp():
-    c = synth.CONFIGS[0]
-    cube = synth.make_cube(0)
+    c = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny")
     for qp in (12, 27, 45):
         enc = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, qp)
         dec = oracle.decode_planes(enc["levels"], enc["mv"], enc["tu_log2"], c.ctu, qp)
