@@ -10,10 +10,11 @@
 // 2 m_x m_y + C1 = (m_x^2 + m_y^2 + C1) - (m_x - m_y)^2, i.e.
 // 1 - (mu'_x - mu'_y)^2 / (m_x^2 + m_y^2 + C1), where the difference comes
 // from the shifted means (no cancellation however large the offset).  A
-// block takes a tile of 32 x 16 window positions of one frame: the Gaussian
+// block takes a tile of 32 x 32 window positions of one frame: the Gaussian
 // means by a separable pass through shared memory, then the variances and
 // the covariance directly over each 11 x 11 window (deviations from the
-// local mean, so nothing cancels).  The spectral angle takes the
+// local mean, so nothing cancels), each thread taking four vertically
+// adjacent windows so that every sample load serves up to four of them.  The spectral angle takes the
 // per-band differences d = x^ - x in double, the wedge terms
 // s_i d_j - s_j d_i (= s_i s^_j - s_j s^_i) and the dot product in FP32, and
 // atan2.  Per-block partials are summed in a fixed order by a final kernel.
@@ -27,12 +28,14 @@
 namespace xvh {
 namespace {
 
-constexpr int kSsimTX = 32, kSsimTY = 16;                  // window positions per tile
+constexpr int kSsimTX = 32, kSsimTY = 32;                  // window positions per tile
 constexpr int kSsimIX = kSsimTX + 10, kSsimIY = kSsimTY + 10;  // input tile
 constexpr int kSsimThreads = 256;
+constexpr int kSsimRows = 4;  // vertically adjacent windows per thread (they share sample loads)
 
 struct Gauss11 {
     float w[11];
+    float w2[121];  // w[u] w[v]: kernel parameters are free FMA operands
 };
 
 template <typename T>
@@ -106,33 +109,47 @@ k_ssim(const T* __restrict__ src, int T_, int H, int W, const uint16_t* __restri
                 s_my[r][c] = ay;
             }
             __syncthreads();
-            for (int i = tid; i < kSsimTY * kSsimTX; i += kSsimThreads) {
-                const int r = i / kSsimTX, c = i - r * kSsimTX;
-                if (y0 + r >= oy_n || x0 + c >= ox_n) continue;
-                unsigned char bad = 0;
+            {
+                // thread: column c, windows r0 .. r0 + 3; every sample of the 14
+                // input rows is loaded once and used by the windows covering it
+                const int c = tid % kSsimTX, r0 = (tid / kSsimTX) * kSsimRows;
+                float mx[kSsimRows], my[kSsimRows], sxx[kSsimRows], syy[kSsimRows], sxy[kSsimRows];
 #pragma unroll
-                for (int u = 0; u < 11; ++u) bad |= s_hbad[r + u][c];
-                if (bad) continue;
-                const float mx = s_mx[r][c], my = s_my[r][c];
-                float sxx = 0.f, syy = 0.f, sxy = 0.f;
+                for (int j = 0; j < kSsimRows; ++j) {
+                    mx[j] = s_mx[r0 + j][c];
+                    my[j] = s_my[r0 + j][c];
+                    sxx[j] = syy[j] = sxy[j] = 0.f;
+                }
 #pragma unroll
-                for (int u = 0; u < 11; ++u) {
-                    float rxx = 0.f, ryy = 0.f, rxy = 0.f;
+                for (int k = 0; k < 10 + kSsimRows; ++k) {
 #pragma unroll
                     for (int v = 0; v < 11; ++v) {
-                        const float dx = s_x[r + u][c + v] - mx, dy = s_y[r + u][c + v] - my;
-                        rxx = fmaf(g.w[v] * dx, dx, rxx);
-                        ryy = fmaf(g.w[v] * dy, dy, ryy);
-                        rxy = fmaf(g.w[v] * dx, dy, rxy);
+                        const float x = s_x[r0 + k][c + v], y = s_y[r0 + k][c + v];
+#pragma unroll
+                        for (int j = 0; j < kSsimRows; ++j) {
+                            const int u = k - j;
+                            if (u < 0 || u > 10) continue;  // resolved at compile time
+                            const float dx = x - mx[j], dy = y - my[j];
+                            const float wdx = g.w2[u * 11 + v] * dx;
+                            sxx[j] = fmaf(wdx, dx, sxx[j]);
+                            sxy[j] = fmaf(wdx, dy, sxy[j]);
+                            syy[j] = fmaf(g.w2[u * 11 + v] * dy, dy, syy[j]);
+                        }
                     }
-                    sxx = fmaf(g.w[u], rxx, sxx);
-                    syy = fmaf(g.w[u], ryy, syy);
-                    sxy = fmaf(g.w[u], rxy, sxy);
                 }
-                const float ax = off + mx, ay = off + my, dm = mx - my;
-                const float lum = 1.f - dm * dm / (ax * ax + ay * ay + C1);
-                sum += (double)(lum * (2.f * sxy + C2) / (sxx + syy + C2));
-                ++n;
+#pragma unroll
+                for (int j = 0; j < kSsimRows; ++j) {
+                    const int r = r0 + j;
+                    if (y0 + r >= oy_n || x0 + c >= ox_n) continue;
+                    unsigned char bad = 0;
+#pragma unroll
+                    for (int u = 0; u < 11; ++u) bad |= s_hbad[r + u][c];
+                    if (bad) continue;
+                    const float ax = off + mx[j], ay = off + my[j], dm = mx[j] - my[j];
+                    const float lum = 1.f - dm * dm / (ax * ax + ay * ay + C1);
+                    sum += (double)(lum * (2.f * sxy[j] + C2) / (sxx[j] + syy[j] + C2));
+                    ++n;
+                }
             }
         }
     }
@@ -260,6 +277,8 @@ cudaError_t launch_ssim(const void* src, xv_dtype dt, int bands, int T, int H, i
         s += w[k];
     }
     for (int k = 0; k < 11; ++k) g.w[k] = (float)(w[k] / s);
+    for (int u = 0; u < 11; ++u)
+        for (int v = 0; v < 11; ++v) g.w2[u * 11 + v] = (float)((w[u] / s) * (w[v] / s));
     dim3 grid(nblk, bands);
     if (H >= 11 && W >= 11) {
         if (dt == XV_F32)
