@@ -53,3 +53,28 @@ def test_params_validation_without_gpu(libxv):
             xv.xv_params_init(*bad)
         assert e.value.status == xv.XV_EINVAL
     assert xv.xv_plane_geometry(10, 721, 1440, 32) == (4, 736, 1440)
+
+
+def test_widened_entry_points_reject_bad_arguments_without_gpu(libxv):
+    """The decoder, metric and PCA calls validate before touching the device:
+    a NULL context or malformed shapes return XV_EINVAL (-1) with a message."""
+    lib = libxv
+    vp, i, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.xv_decode_frame.restype = i
+    lib.xv_unpack.restype = i
+    lib.xv_ssim.restype = i
+    lib.xv_sa.restype = i
+    lib.xv_pca_fit.restype = i
+    lib.xv_pca_project.restype = i
+    lib.xv_pca_inverse.restype = i
+    lib.xv_decode_batch.restype = i
+    null = vp(0)
+    assert lib.xv_decode_frame(null, null, null, null, null, i(1), i64(0), i(16), i(16), null, i64(1), null, null,
+                               i64(1), null) == -1
+    assert lib.xv_decode_batch(null, null, i(1), null, null) == -1
+    assert lib.xv_unpack(null, null, i(3), i(1), i(8), i(8), i(8), i(8), null, null, null) == -1
+    assert lib.xv_ssim(null, null, i(0), i(3), i(1), i(8), i(8), null, i(8), i(8), null, null, null, null) == -1
+    assert lib.xv_sa(null, null, i(0), i(3), i(1), i(8), i(8), null, i(8), i(8), null, null, null, null) == -1
+    assert lib.xv_pca_fit(null, null, i(0), i(3), i(1), i(8), i(8), null, null, null, null) == -1
+    assert lib.xv_pca_project(null, null, i(0), i(3), i(1), i(8), i(8), null, null, i(2), null, null) == -1
+    assert lib.xv_pca_inverse(null, null, i(2), i(3), i(1), i(8), i(8), null, null, null, null) == -1
