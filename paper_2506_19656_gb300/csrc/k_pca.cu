@@ -63,18 +63,22 @@ struct PcaMean {
 };
 
 // Pass 2: per block, sum over valid pixels of c_i c_j (c = x - mean) for
-// i <= j: a tile of 256 pixels' centred values (double) in shared memory,
-// one thread per pair accumulating in double.  The covariance is the
-// accurate part of the fit: the smallest principal components sit in tiny
-// eigenvalue gaps.  part: [nblk][136].
+// i <= j: a tile of 256 pixels' centred values (double) in shared memory;
+// each pair is summed by 256 / npair threads over interleaved pixels (all
+// threads busy however few the bands), the parts combined in a fixed order
+// at the end.  The covariance is the accurate part of the fit: the smallest
+// principal components sit in tiny eigenvalue gaps.  part: [nblk][136].
 template <typename T>
 __global__ void __launch_bounds__(kPcaThreads)
 k_pca_cov(const T* __restrict__ src, int bands, int64_t npix, PcaMean mean, double* part) {
     __shared__ double s_c[kMaxB][kPcaThreads];
     const int npair = bands * (bands + 1) / 2;
+    const int nsplit = kPcaThreads / npair;  // threads per pair
+    const int pr = (int)threadIdx.x % npair, part_of = (int)threadIdx.x / npair;
+    const bool active = part_of < nsplit;
     int pi = 0, pj = 0;
-    if ((int)threadIdx.x < npair) {  // pair index -> (i, j), i <= j, row by row
-        int k = threadIdx.x;
+    {  // pair index -> (i, j), i <= j, row by row
+        int k = pr;
         while (k >= bands - pi) { k -= bands - pi; ++pi; }
         pj = pi + k;
     }
@@ -92,10 +96,19 @@ k_pca_cov(const T* __restrict__ src, int bands, int64_t npix, PcaMean mean, doub
 #pragma unroll
         for (int b = 0; b < kMaxB; ++b) s_c[b][threadIdx.x] = ok ? v[b] : 0.0;
         __syncthreads();
-        if ((int)threadIdx.x < npair)
-            for (int q = 0; q < kPcaThreads; ++q) acc = fma(s_c[pi][q], s_c[pj][q], acc);
+        if (active)
+            for (int q = part_of; q < kPcaThreads; q += nsplit) acc = fma(s_c[pi][q], s_c[pj][q], acc);
     }
-    if ((int)threadIdx.x < npair) part[(int64_t)blockIdx.x * 136 + threadIdx.x] = acc;
+    // combine the parts of each pair in part order
+    __syncthreads();
+    double* s_acc = &s_c[0][0];  // kMaxB * 256 doubles >= 256 partial sums
+    s_acc[threadIdx.x] = active ? acc : 0.0;
+    __syncthreads();
+    if ((int)threadIdx.x < npair) {
+        double t = 0.0;
+        for (int k = 0; k < nsplit; ++k) t += s_acc[k * npair + threadIdx.x];
+        part[(int64_t)blockIdx.x * 136 + threadIdx.x] = t;
+    }
 }
 
 struct PcaBasis {
@@ -103,39 +116,91 @@ struct PcaBasis {
     float v[kMaxB][kMaxB];  // [component][band]
 };
 
+// 4 consecutive pixels of one band (16-byte float or 8-byte uint16 load).
 template <typename T>
+__device__ __forceinline__ float4 load4(const T* p) {
+    if constexpr (sizeof(T) == 4) {
+        return *reinterpret_cast<const float4*>(p);
+    } else {
+        const uint2 w = *reinterpret_cast<const uint2*>(p);
+        return make_float4((float)(w.x & 0xffffu), (float)(w.x >> 16), (float)(w.y & 0xffffu), (float)(w.y >> 16));
+    }
+}
+
+// kVec: 4 pixels per thread with vector loads and stores (npix % 4 == 0 and
+// aligned arrays, chosen by the host), else one.
+template <typename T, int kVec>
 __global__ void __launch_bounds__(kPcaThreads)
 k_pca_project(const T* __restrict__ src, int bands, int npc, int64_t npix, PcaBasis B, float* __restrict__ dst) {
-    for (int64_t p = (int64_t)blockIdx.x * kPcaThreads + threadIdx.x; p < npix; p += (int64_t)gridDim.x * kPcaThreads) {
-        float c[kMaxB];
+    const int64_t nq = npix / kVec;
+    for (int64_t q = (int64_t)blockIdx.x * kPcaThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kPcaThreads) {
+        const int64_t p = q * kVec;
+        float c[kMaxB][kVec];
 #pragma unroll
-        for (int b = 0; b < kMaxB; ++b) c[b] = b < bands ? (float)src[(int64_t)b * npix + p] - B.m[b] : 0.f;
+        for (int b = 0; b < kMaxB; ++b) {
+            if (b < bands) {
+                if constexpr (kVec == 4) {
+                    const float4 v = load4(src + (int64_t)b * npix + p);
+                    c[b][0] = v.x - B.m[b]; c[b][1] = v.y - B.m[b]; c[b][2] = v.z - B.m[b]; c[b][3] = v.w - B.m[b];
+                } else {
+                    c[b][0] = (float)src[(int64_t)b * npix + p] - B.m[b];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kVec; ++e) c[b][e] = 0.f;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < kMaxB; ++k) {
             if (k >= npc) break;
-            float z = 0.f;
+            float z[kVec];
+#pragma unroll
+            for (int e = 0; e < kVec; ++e) z[e] = 0.f;
 #pragma unroll
             for (int b = 0; b < kMaxB; ++b)
-                if (b < bands) z = fmaf(B.v[k][b], c[b], z);
-            dst[(int64_t)k * npix + p] = z;
+                if (b < bands)
+#pragma unroll
+                    for (int e = 0; e < kVec; ++e) z[e] = fmaf(B.v[k][b], c[b][e], z[e]);
+            if constexpr (kVec == 4) *reinterpret_cast<float4*>(dst + (int64_t)k * npix + p) = make_float4(z[0], z[1], z[2], z[3]);
+            else dst[(int64_t)k * npix + p] = z[0];
         }
     }
 }
 
+template <int kVec>
 __global__ void __launch_bounds__(kPcaThreads)
 k_pca_inverse(const float* __restrict__ z, int npc, int bands, int64_t npix, PcaBasis B, float* __restrict__ dst) {
-    for (int64_t p = (int64_t)blockIdx.x * kPcaThreads + threadIdx.x; p < npix; p += (int64_t)gridDim.x * kPcaThreads) {
-        float zz[kMaxB];
+    const int64_t nq = npix / kVec;
+    for (int64_t q = (int64_t)blockIdx.x * kPcaThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kPcaThreads) {
+        const int64_t p = q * kVec;
+        float zz[kMaxB][kVec];
 #pragma unroll
-        for (int k = 0; k < kMaxB; ++k) zz[k] = k < npc ? z[(int64_t)k * npix + p] : 0.f;
+        for (int k = 0; k < kMaxB; ++k) {
+            if (k < npc) {
+                if constexpr (kVec == 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(z + (int64_t)k * npix + p);
+                    zz[k][0] = v.x; zz[k][1] = v.y; zz[k][2] = v.z; zz[k][3] = v.w;
+                } else {
+                    zz[k][0] = z[(int64_t)k * npix + p];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kVec; ++e) zz[k][e] = 0.f;
+            }
+        }
 #pragma unroll
         for (int b = 0; b < kMaxB; ++b) {
             if (b >= bands) break;
-            float x = B.m[b];
+            float x[kVec];
+#pragma unroll
+            for (int e = 0; e < kVec; ++e) x[e] = B.m[b];
 #pragma unroll
             for (int k = 0; k < kMaxB; ++k)
-                if (k < npc) x = fmaf(B.v[k][b], zz[k], x);
-            dst[(int64_t)b * npix + p] = x;
+                if (k < npc)
+#pragma unroll
+                    for (int e = 0; e < kVec; ++e) x[e] = fmaf(B.v[k][b], zz[k][e], x[e]);
+            if constexpr (kVec == 4) *reinterpret_cast<float4*>(dst + (int64_t)b * npix + p) = make_float4(x[0], x[1], x[2], x[3]);
+            else dst[(int64_t)b * npix + p] = x[0];
         }
     }
 }
@@ -231,17 +296,26 @@ cudaError_t launch_pca_project(const void* src, xv_dtype dt, int bands, int npc,
                                const double* comps, float* dst, cudaStream_t st) {
     const PcaBasis B = to_basis(bands, npc, mean, comps);
     const int nblk = pca_blocks(npix);
-    if (dt == XV_F32)
-        k_pca_project<float><<<nblk, kPcaThreads, 0, st>>>(static_cast<const float*>(src), bands, npc, npix, B, dst);
-    else
-        k_pca_project<uint16_t><<<nblk, kPcaThreads, 0, st>>>(static_cast<const uint16_t*>(src), bands, npc, npix, B, dst);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
+    const bool vec = npix % 4 == 0 && a % 16 == 0;
+    if (dt == XV_F32) {
+        const float* s = static_cast<const float*>(src);
+        if (vec) k_pca_project<float, 4><<<nblk, kPcaThreads, 0, st>>>(s, bands, npc, npix, B, dst);
+        else k_pca_project<float, 1><<<nblk, kPcaThreads, 0, st>>>(s, bands, npc, npix, B, dst);
+    } else {
+        const uint16_t* s = static_cast<const uint16_t*>(src);
+        if (vec) k_pca_project<uint16_t, 4><<<nblk, kPcaThreads, 0, st>>>(s, bands, npc, npix, B, dst);
+        else k_pca_project<uint16_t, 1><<<nblk, kPcaThreads, 0, st>>>(s, bands, npc, npix, B, dst);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pca_inverse(const float* z, int npc, int bands, int64_t npix, const double* mean, const double* comps,
                                float* dst, cudaStream_t st) {
     const PcaBasis B = to_basis(bands, npc, mean, comps);
-    k_pca_inverse<<<pca_blocks(npix), kPcaThreads, 0, st>>>(z, npc, bands, npix, B, dst);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(dst);
+    if (npix % 4 == 0 && a % 16 == 0) k_pca_inverse<4><<<pca_blocks(npix), kPcaThreads, 0, st>>>(z, npc, bands, npix, B, dst);
+    else k_pca_inverse<1><<<pca_blocks(npix), kPcaThreads, 0, st>>>(z, npc, bands, npix, B, dst);
     return cudaGetLastError();
 }
 
