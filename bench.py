@@ -197,6 +197,37 @@ def cpu_baseline(cube, cfg, frames=16):
                       f"{dt:.1f} s"}
 
 
+def workload_jobs(workload, frames=0, device=None):
+    """The encodes one step runs: for each sub-cube (the ERA5-shaped workload is
+    six causal prefixes of one generated cube, each in its own contiguous
+    buffer) and each QP of QPS, device buffers and an xv_job.  Returns (cfg,
+    lengths, cube, srcs, jobs, bufs): cube = the generated host cube, srcs =
+    the device sub-cubes, bufs[i] = job i's buffers plus "src", "qp" and "T"."""
+    import dataclasses
+
+    import torch
+
+    from paper_2506_19656_gb300 import synth, xv
+    cfg = synth.WORKLOADS[workload]
+    if frames:
+        cfg = dataclasses.replace(cfg, T=frames)
+    lengths = list(cfg.sub_T) if cfg.sub_T and not frames else [cfg.T]
+    cube = synth.make_cube(workload, T=max(lengths))
+    full = torch.from_numpy(cube)
+    srcs = [full[:, :T].contiguous().to(device) for T in lengths]
+    del full
+    jobs, bufs = [], []
+    for T, src in zip(lengths, srcs):
+        for qp in QPS:
+            p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
+            b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=device)
+            b.update(src=src, qp=qp, T=T)
+            jobs.append(xv.make_job(src, p, b["planes"], b["recon"], minmax=b["minmax"], mv=b["mv"], cost=b["cost"],
+                                    levels=b["levels"], tu_log2=b["tu_log2"], bits=b["bits"]))
+            bufs.append(b)
+    return cfg, lengths, cube, srcs, jobs, bufs
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on bounded samples of the workload."""
     ws, rank, _ = dist_env()
@@ -236,40 +267,28 @@ def run_decode(args):
     shape) are encoded once, untimed; each timed step decodes all of them in
     one xv_decode_batch, writing the reconstruction planes and the cube in its
     own units (float32), checked equal to the encoder's reconstruction."""
-    import dataclasses
     import statistics
 
     import numpy as np
     import torch
 
-    from paper_2506_19656_gb300 import build, synth, xv
+    from paper_2506_19656_gb300 import build, xv
     build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    cfg = synth.WORKLOADS[args.workload]
-    if args.frames:
-        cfg = dataclasses.replace(cfg, T=args.frames)
-    lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
-    cube = synth.make_cube(args.workload, T=max(lengths))
+    cfg, lengths, _, _, jobs, bufs = workload_jobs(args.workload, args.frames, dev)
     ctx = xv.Context(0)
     if args.block_size:
         xv.xv_debug_force_block_size(ctx, args.block_size)
-    jobs, djobs, bufs, outs = [], [], [], []
-    for T in lengths:
-        src = torch.from_numpy(np.ascontiguousarray(cube[:, :T])).to(dev)
-        for qp in QPS:
-            p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
-            b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=dev)
-            b["src"] = src
-            jobs.append(xv.make_job(src, p, b["planes"], b["recon"], minmax=b["minmax"], mv=b["mv"], cost=b["cost"],
-                                    levels=b["levels"], tu_log2=b["tu_log2"], bits=b["bits"]))
-            G, Tn = b["levels"].shape[:2]
-            o = dict(recon=torch.empty_like(b["recon"]), bits=torch.zeros((G, Tn), dtype=torch.int64, device=dev),
-                     dst=torch.empty((cfg.bands, T, cfg.H, cfg.W), dtype=torch.float32, device=dev))
-            djobs.append(xv.make_djob(p, b["levels"], b["mv"], b["tu_log2"], o["recon"], bits=o["bits"],
-                                      minmax=b["minmax"], dst=o["dst"], bands=cfg.bands, H=cfg.H, W=cfg.W))
-            bufs.append(b)
-            outs.append(o)
+    djobs, outs = [], []
+    for b in bufs:
+        p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, b["qp"])
+        G, Tn = b["levels"].shape[:2]
+        o = dict(recon=torch.empty_like(b["recon"]), bits=torch.zeros((G, Tn), dtype=torch.int64, device=dev),
+                 dst=torch.empty((cfg.bands, b["T"], cfg.H, cfg.W), dtype=torch.float32, device=dev))
+        djobs.append(xv.make_djob(p, b["levels"], b["mv"], b["tu_log2"], o["recon"], bits=o["bits"],
+                                  minmax=b["minmax"], dst=o["dst"], bands=cfg.bands, H=cfg.H, W=cfg.W))
+        outs.append(o)
     enc = xv.xv_encode_batch(ctx, jobs)  # untimed: the coded data to decode
     work_mpx = len(QPS) * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -386,32 +405,18 @@ def run_metrics(args):
     """Quality-metric run: the workload's encodes are made once, untimed; each
     timed step computes SSIM per band (xv_ssim) and the mean spectral angle
     (xv_sa) of every encode's reconstruction against the cube."""
-    import dataclasses
     import statistics
 
     import numpy as np
     import torch
 
-    from paper_2506_19656_gb300 import build, synth, xv
+    from paper_2506_19656_gb300 import build, xv
     build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    cfg = synth.WORKLOADS[args.workload]
-    if args.frames:
-        cfg = dataclasses.replace(cfg, T=args.frames)
-    lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
-    cube = synth.make_cube(args.workload, T=max(lengths))
+    cfg, lengths, _, _, jobs, bufs = workload_jobs(args.workload, args.frames, dev)
+    srcs = [b["src"] for b in bufs]
     ctx = xv.Context(0)
-    jobs, bufs, srcs = [], [], []
-    for T in lengths:
-        src = torch.from_numpy(np.ascontiguousarray(cube[:, :T])).to(dev)
-        for qp in QPS:
-            p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
-            b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=dev)
-            jobs.append(xv.make_job(src, p, b["planes"], b["recon"], minmax=b["minmax"], mv=b["mv"], cost=b["cost"],
-                                    levels=b["levels"], tu_log2=b["tu_log2"], bits=b["bits"]))
-            bufs.append(b)
-            srcs.append(src)
     xv.xv_encode_batch(ctx, jobs)  # untimed: the reconstructions to score
     work_mpx = len(QPS) * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
     windows = len(QPS) * sum(cfg.bands * T * max(cfg.H - 10, 0) * max(cfg.W - 10, 0) for T in lengths)
@@ -579,7 +584,6 @@ def run_serve(args):
     """Serving run: a stream of requests with Poisson arrivals, kinds drawn
     uniformly from the four workloads, through xv_serve_*; against the plain
     per-request path (xv_encode_cube on each request in arrival order)."""
-    import dataclasses
 
     import numpy as np
     import torch
@@ -739,32 +743,13 @@ def main():
         if ws > 1:
             dist.barrier()
 
-    from paper_2506_19656_gb300 import build, synth, xv
+    from paper_2506_19656_gb300 import build, xv
     build.build()
-    import dataclasses
-    cfg = synth.WORKLOADS[args.workload]
-    if args.frames:
-        cfg = dataclasses.replace(cfg, T=args.frames)
     dev = torch.device("cuda", local)
     ctx = xv.Context(local)
     if args.block_size:
         xv.xv_debug_force_block_size(ctx, args.block_size)
-    # one encode per (sub-cube, QP); the ERA5-shaped workload is six sub-cubes
-    # of uneven length (causal prefixes of one generated cube, copied to their
-    # own contiguous buffers)
-    lengths = list(cfg.sub_T) if cfg.sub_T and not args.frames else [cfg.T]
-    cube = synth.make_cube(args.workload, T=max(lengths))
-    full = torch.from_numpy(cube)
-    srcs = [full[:, :T].contiguous().to(dev) for T in lengths]
-    del full
-    jobs, bufs = [], []
-    for T, src in zip(lengths, srcs):
-        for qp in QPS:
-            p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
-            b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=dev)
-            jobs.append(xv.make_job(src, p, b["planes"], b["recon"], minmax=b["minmax"], mv=b["mv"], cost=b["cost"],
-                                    levels=b["levels"], tu_log2=b["tu_log2"], bits=b["bits"]))
-            bufs.append(b)
+    cfg, lengths, cube, srcs, jobs, bufs = workload_jobs(args.workload, args.frames, dev)
     src = srcs[0] if len(srcs) == 1 else None
     work_mpx = len(QPS) * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2

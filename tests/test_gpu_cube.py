@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import to_dev, to_np
+from gpu_util import assert_matches, to_dev, to_np
 from paper_2506_19656_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -38,22 +38,6 @@ def gpu_job(xv, cube, ctu, R, mask, qp, minmax=None):
                       minmax_fixed=minmax is not None, mv=buf["mv"], cost=buf["cost"], levels=buf["levels"],
                       tu_log2=buf["tu_log2"], bits=buf["bits"])
     return job, buf
-
-
-def assert_matches(buf, res, want, frames=None):
-    sl = slice(None) if frames is None else slice(0, frames)
-    assert np.array_equal(to_np(buf["planes"])[:, sl], want["planes"][:, sl])
-    assert np.array_equal(to_np(buf["mv"])[:, sl], want["mv"][:, sl])
-    assert np.array_equal(to_np(buf["cost"])[:, sl].astype(np.uint32), want["cost"][:, sl])
-    assert np.array_equal(to_np(buf["recon"])[:, sl], want["recon"][:, sl])
-    assert np.array_equal(to_np(buf["levels"])[:, sl], want["levels"][:, sl])
-    assert np.array_equal(to_np(buf["tu_log2"])[:, sl], want["tu_log2"][:, sl])
-    assert np.array_equal(to_np(buf["bits"])[:, sl].astype(np.uint64), want["bits"][:, sl])
-    if frames is None:
-        assert res["total_bits"] == want["total_bits"]
-        for g, w in zip(res["psnr_band"], want["psnr_band"]):
-            assert (np.isinf(g) and np.isinf(w)) or abs(g - w) <= 1e-9 * abs(w)
-        assert res["sse10_band"] == [int(v) for v in want["sse10_band"]]
 
 
 def test_tiny_config_plain(xv, ctx):
