@@ -197,12 +197,20 @@ def cpu_baseline(cube, cfg, frames=16):
                       f"{dt:.1f} s"}
 
 
-def workload_jobs(workload, frames=0, device=None):
+def default_qps(workload):
+    """The QPs one step encodes when --qps is not given: 22, 27 and 32 for the
+    DeepExtremeCubes-shaped cube, the workload's own QPs otherwise."""
+    from paper_2506_19656_gb300 import synth
+    return (22, 27, 32) if workload == WORKLOAD else tuple(synth.WORKLOADS[workload].qps)
+
+
+def workload_jobs(workload, frames=0, device=None, qps=None):
     """The encodes one step runs: for each sub-cube (the ERA5-shaped workload is
     six causal prefixes of one generated cube, each in its own contiguous
-    buffer) and each QP of QPS, device buffers and an xv_job.  Returns (cfg,
-    lengths, cube, srcs, jobs, bufs): cube = the generated host cube, srcs =
-    the device sub-cubes, bufs[i] = job i's buffers plus "src", "qp" and "T"."""
+    buffer) and each QP (default: QPS, which main() sets from --qps or
+    default_qps), device buffers and an xv_job.  Returns (cfg, lengths, cube,
+    srcs, jobs, bufs): cube = the generated host cube, srcs = the device
+    sub-cubes, bufs[i] = job i's buffers plus "src", "qp" and "T"."""
     import dataclasses
 
     import torch
@@ -218,7 +226,7 @@ def workload_jobs(workload, frames=0, device=None):
     del full
     jobs, bufs = [], []
     for T, src in zip(lengths, srcs):
-        for qp in QPS:
+        for qp in (QPS if qps is None else qps):
             p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qp)
             b = xv.alloc_cube_buffers(cfg.bands, T, cfg.H, cfg.W, p, device=device)
             b.update(src=src, qp=qp, T=T)
@@ -695,8 +703,9 @@ def main():
     ap.add_argument("--impl", default="xv", choices=["xv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--qps", default=",".join(str(q) for q in QPS),
-                    help="QPs of the encodes in one step (profiling cases use one)")
+    ap.add_argument("--qps", default="",
+                    help="QPs of the encodes in one step (default: 22,27,32 for the DeepExtremeCubes-shaped cube, "
+                         "the workload's own otherwise)")
     ap.add_argument("--frames", type=int, default=0, help="encode only the first F frames (profiling cases)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["tiny", "deepextremecubes", "dynamicearthnet", "era5"],
@@ -713,10 +722,7 @@ def main():
                     help="persistent-kernel block size (128/192/256/512) instead of the autotuner's choice, e.g. to "
                          "profile the variant an uninstrumented run picks")
     args = ap.parse_args()
-    globals()["QPS"] = tuple(int(q) for q in args.qps.split(","))
-    if args.workload != WORKLOAD and args.qps == ",".join(str(q) for q in (22, 27, 32)):
-        from paper_2506_19656_gb300 import synth as _s
-        globals()["QPS"] = _s.WORKLOADS[args.workload].qps
+    globals()["QPS"] = tuple(int(q) for q in args.qps.split(",")) if args.qps else default_qps(args.workload)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -392,7 +392,9 @@ xv_status xv_serve_start(xv_ctx* ctx, int max_slots, int frames_per_tick);
 xv_status xv_serve_submit(xv_ctx* ctx, const xv_request* req, uint64_t* ticket);
 /* Non-blocking.  *done = 1 once the request finished (result filled,
  * including result->status and result->latency_s, the time from submission
- * to completion); the ticket is then released (later polls: XV_ENOTFOUND). */
+ * to completion); the ticket is then released (later polls: XV_ENOTFOUND).
+ * When the request failed (result->status != XV_OK), xv_last_error on the
+ * polling thread returns its message. */
 xv_status xv_serve_poll(xv_ctx* ctx, uint64_t ticket, xv_result* result, int* done);
 /* Cancels a queued or resident request; it completes with XV_ECANCELLED at
  * the next tick boundary (unless it finished first). */

@@ -90,39 +90,41 @@ __device__ void complete_item(const JobDev& J, int job, int g, int t, int pu, ui
     }
 }
 
-// Encodes (or decodes) one PU; returns the integer-search candidates
-// evaluated exactly.
-template <int N, int kNT>
+// Encodes (kDecode: decodes) one PU; returns the integer-search candidates
+// evaluated exactly.  Decoding is a separate instantiation so that the
+// encoder's code carries none of it (smaller code, fewer spills).
+template <int N, int kNT, bool kDecode>
 __device__ uint32_t item_work(const JobDev& J, int g, int t, int pu, unsigned char* smem) {
     const int64_t plane = (int64_t)J.Hp * J.Wp, fsz = 3 * plane;
     const int64_t f = (int64_t)g * J.T + t;
     const uint16_t* ref = t > 0 ? J.recon + (f - 1) * fsz : nullptr;
     const int x0 = (pu % J.nx) * N, y0 = (pu / J.nx) * N;
-    if (J.decode) {
+    if constexpr (kDecode) {
         const int64_t o = f * (int64_t)J.nx * J.ny + pu;
         const int mvx = ref ? J.mv[2 * o] : 0, mvy = ref ? J.mv[2 * o + 1] : 0;
         const uint32_t b = xvd::dec_cu<N, kNT, true>(J.levels + f * fsz, ref, plane, J.Hp, J.Wp, x0, y0, mvx, mvy,
                                                      J.tu[o], J.qp, J.recon + f * fsz, smem);
         if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(J.bits + f), (unsigned long long)b);
         return 0u;
+    } else {
+        const uint16_t* cur = J.planes + f * fsz;
+        xvd::MeResult m{0, 0, 0u, 0, 0, 0u, 0u};
+        if (ref) m = xvd::me_pu<N, kNT, true>(cur, ref, J.Hp, J.Wp, x0, y0, J.R, J.lmv, smem);
+        const int64_t npu = (int64_t)J.nx * J.ny;
+        uint32_t b = xvd::tqr_cu<N, kNT, true>(cur, ref, plane, J.Hp, J.Wp, x0, y0, m.mvx, m.mvy, J.qp, J.tu_mask,
+                                               J.lf8, J.recon + f * fsz, J.levels ? J.levels + f * fsz : nullptr,
+                                               J.tu ? J.tu + f * npu + pu : nullptr, smem);
+        if (threadIdx.x == 0) {
+            const int64_t o = f * npu + pu;
+            if (J.mv) { J.mv[2 * o] = (int16_t)m.mvx; J.mv[2 * o + 1] = (int16_t)m.mvy; }
+            if (J.cost) J.cost[o] = m.cost;
+            atomicAdd(reinterpret_cast<unsigned long long*>(J.bits + f), (unsigned long long)b);
+        }
+        return m.exact_cand;
     }
-    const uint16_t* cur = J.planes + f * fsz;
-    xvd::MeResult m{0, 0, 0u, 0, 0, 0u, 0u};
-    if (ref) m = xvd::me_pu<N, kNT, true>(cur, ref, J.Hp, J.Wp, x0, y0, J.R, J.lmv, smem);
-    const int64_t npu = (int64_t)J.nx * J.ny;
-    uint32_t b = xvd::tqr_cu<N, kNT, true>(cur, ref, plane, J.Hp, J.Wp, x0, y0, m.mvx, m.mvy, J.qp, J.tu_mask,
-                                           J.lf8, J.recon + f * fsz, J.levels ? J.levels + f * fsz : nullptr,
-                                           J.tu ? J.tu + f * npu + pu : nullptr, smem);
-    if (threadIdx.x == 0) {
-        const int64_t o = f * npu + pu;
-        if (J.mv) { J.mv[2 * o] = (int16_t)m.mvx; J.mv[2 * o + 1] = (int16_t)m.mvy; }
-        if (J.cost) J.cost[o] = m.cost;
-        atomicAdd(reinterpret_cast<unsigned long long*>(J.bits + f), (unsigned long long)b);
-    }
-    return m.exact_cand;
 }
 
-template <int N, int kNT>
+template <int N, int kNT, bool kDecode>
 __global__ void __launch_bounds__(kNT, (kMinBlocks<N, kNT>))
 k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -148,7 +150,7 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
             const int job = (int)(key >> 56);
             const JobDev& J = jobs[job];
             const int g = (int)((key >> 48) & 0xff), t = (int)((key >> 32) & 0xffff), pu = (int)(uint32_t)key;
-            exact += item_work<N, kNT>(J, g, t, pu, smem);
+            exact += item_work<N, kNT, kDecode>(J, g, t, pu, smem);
             __threadfence();
             __syncthreads();
             complete_item(J, job, g, t, pu, queue, ctl, &s_full);
@@ -159,15 +161,20 @@ k_persist(const JobDev* __restrict__ jobs, uint64_t* queue, BatchCtl* ctl) {
 }
 
 
-template <int N>
-PersistFn persist_fn_for(int nt) {
+template <int N, bool kDecode>
+PersistFn persist_fn_nt(int nt) {
     switch (nt) {
-        case 128: return k_persist<N, 128>;
-        case 192: return k_persist<N, 192>;
-        case 256: return k_persist<N, 256>;
-        case 512: return k_persist<N, 512>;
+        case 128: return k_persist<N, 128, kDecode>;
+        case 192: return k_persist<N, 192, kDecode>;
+        case 256: return k_persist<N, 256, kDecode>;
+        case 512: return k_persist<N, 512, kDecode>;
     }
     return nullptr;
+}
+
+template <int N>
+PersistFn persist_fn_for(int nt, bool decode) {
+    return decode ? persist_fn_nt<N, true>(nt) : persist_fn_nt<N, false>(nt);
 }
 
 }  // namespace

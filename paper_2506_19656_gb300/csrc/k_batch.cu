@@ -26,10 +26,10 @@
 #include "batch.cuh"
 
 namespace xvh {
-batch::PersistFn persist_fn_ctu8(int nt);
-batch::PersistFn persist_fn_ctu16(int nt);
-batch::PersistFn persist_fn_ctu32(int nt);
-batch::PersistFn persist_fn_ctu64(int nt);
+batch::PersistFn persist_fn_ctu8(int nt, bool decode);
+batch::PersistFn persist_fn_ctu16(int nt, bool decode);
+batch::PersistFn persist_fn_ctu32(int nt, bool decode);
+batch::PersistFn persist_fn_ctu64(int nt, bool decode);
 namespace {
 
 // Batch prologue: block j < njobs handles job j (its bits and counters over
@@ -88,12 +88,12 @@ __global__ void k_bits_totals(const JobDev* __restrict__ jobs, unsigned long lon
 }
 
 using batch::PersistFn;
-PersistFn persist_fn(int ctu, int nt) {
+PersistFn persist_fn(int ctu, int nt, bool decode) {
     switch (ctu) {
-        case 8: return persist_fn_ctu8(nt);
-        case 16: return persist_fn_ctu16(nt);
-        case 32: return persist_fn_ctu32(nt);
-        case 64: return persist_fn_ctu64(nt);
+        case 8: return persist_fn_ctu8(nt, decode);
+        case 16: return persist_fn_ctu16(nt, decode);
+        case 32: return persist_fn_ctu32(nt, decode);
+        case 64: return persist_fn_ctu64(nt, decode);
     }
     return nullptr;
 }
@@ -122,8 +122,8 @@ size_t persist_smem_bytes(int ctu, int R, bool has_me) {
     return a > b ? a : b;
 }
 
-int persist_grid(int ctu, int nt, size_t smem) {
-    PersistFn fn = persist_fn(ctu, nt);
+int persist_grid(int ctu, int nt, size_t smem, bool decode) {
+    PersistFn fn = persist_fn(ctu, nt, decode);
     if (!fn) return 0;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -137,9 +137,9 @@ int persist_grid(int ctu, int nt, size_t smem) {
     return sms * per;
 }
 
-cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,
-                           int grid, cudaStream_t st) {
-    PersistFn fn = persist_fn(ctu, nt);
+cudaError_t launch_persist(int ctu, int nt, bool decode, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl,
+                           size_t smem, int grid, cudaStream_t st) {
+    PersistFn fn = persist_fn(ctu, nt, decode);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -2,5 +2,5 @@
 #include "batch.cuh"
 
 namespace xvh {
-batch::PersistFn persist_fn_ctu16(int nt) { return batch::persist_fn_for<16>(nt); }
+batch::PersistFn persist_fn_ctu16(int nt, bool decode) { return batch::persist_fn_for<16>(nt, decode); }
 }  // namespace xvh

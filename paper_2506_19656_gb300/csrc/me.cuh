@@ -111,9 +111,9 @@ __host__ __device__ constexpr size_t me_smem_bytes(int N, int R) {
 }
 
 // Samples in the window and block are stored as the float 2^23 + v (v <= 1023).
-// Its bit pattern is 0x4B000000 | v, so the integer path's __sad on the raw
-// bits gives |a - b| exactly, and the float path's |a - b| is exact too (both
-// operands lie in [2^23, 2^24), where the float spacing is 1).
+// Its bit pattern is 0x4B000000 | v, so __sad on the raw bits gives |a - b|
+// exactly (the bias cancels); read as floats the difference is exact too
+// (both operands lie in [2^23, 2^24), where the float spacing is 1).
 constexpr int kSampleBias = 0x4B000000;
 __device__ __forceinline__ int enc_sample(int v) { return kSampleBias | v; }
 __device__ __forceinline__ int dec_sample(int bits) { return bits - kSampleBias; }
@@ -163,32 +163,6 @@ __device__ __forceinline__ void row_sad8(const int* __restrict__ crow, const uin
         for (int k = 0; k < 8; ++k)
 #pragma unroll
             for (int c = 0; c < 8; ++c) sad[k] = __sad(cv[c], rv[c + k], sad[k]);
-    }
-}
-
-// The same through the FP32 pipe: the biased words read as floats, |a - b|
-// accumulated in float32, exact because every partial sum is an integer
-// below 2^24.  Running a third of the rows through this path keeps both the
-// integer ALU pipe (one __sad per abs-diff at half the issue rate) and the
-// FP32 pipe busy.
-template <int W>
-__device__ __forceinline__ void row_sad8f(const int* __restrict__ crow, const uint16_t* __restrict__ rrow,
-                                          float (&acc)[8]) {
-#pragma unroll
-    for (int c0 = 0; c0 < W; c0 += 8) {
-        float cv[8];
-        int rv[16];
-        {
-            const float4 a = *reinterpret_cast<const float4*>(crow + c0);
-            const float4 b = *reinterpret_cast<const float4*>(crow + c0 + 4);
-            cv[0] = a.x; cv[1] = a.y; cv[2] = a.z; cv[3] = a.w; cv[4] = b.x; cv[5] = b.y; cv[6] = b.z; cv[7] = b.w;
-        }
-        enc8(rrow + c0, rv);
-        enc8(rrow + c0 + 8, rv + 8);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[k] += fabsf(cv[c] - __int_as_float(rv[c + k]));
     }
 }
 
@@ -738,19 +712,11 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
                 continue;
             }
             uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            float accf[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            // rows in triples: two on the integer ALU, the third on the FP32 pipe
-            int r = q;
+            // one row at a time (a second, FP32-pipe copy of the row code for
+            // a third of the rows measured slower: it costs more in code size
+            // than it gains in pipe balance, the survivors being few)
 #pragma unroll 1
-            for (; r + 2 * P < N; r += 3 * P) {
-                row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
-                row_sad8<N>(blk + (r + P) * N, wb + woff + (r + P) * S, sad);
-                row_sad8f<N>(blk + (r + 2 * P) * N, wb + woff + (r + 2 * P) * S, accf);
-            }
-            for (; r < N; r += P) row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)  // exact integer below 2^23: read it through the 2^23 bias
-                sad[k] += __float_as_uint(accf[k] + 8388608.0f) - 0x4B000000u;
+            for (int r = q; r < N; r += P) row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
             for (int o = 1; o < P; o <<= 1)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);

@@ -66,6 +66,8 @@ xv_status cuda_fail(cudaError_t e, const char* what) {
     return XV_ECUDA;
 }
 
+const char* last_error_text() { return g_err.c_str(); }
+
 }  // namespace xvh
 
 using xvh::cuda_fail;
@@ -810,8 +812,8 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         xv_status r = XV_OK;
         for (int k = 0; k < 4; ++k) {
             if (!total[k]) continue;
-            const int grid = xvh::persist_grid(ctus[k], nt[k], smem[k]);
-            r = check_launch(xvh::launch_persist(ctus[k], nt[k], jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
+            const int grid = xvh::persist_grid(ctus[k], nt[k], smem[k], false);
+            r = check_launch(xvh::launch_persist(ctus[k], nt[k], false, jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
                                                  (xvh::BatchCtl*)c->b_ctl.ptr + k, smem[k], grid, st),
                              "persistent encode");
             if (r) return r;
@@ -1103,7 +1105,6 @@ xv_status xv_decode_batch(xv_ctx* c, const xv_djob* jobs, int njobs, uint64_t* t
         d.qfirst = (int64_t)qnext[k];
         d.tb = 0;
         d.te = j.T;
-        d.decode = 1;
         qnext[k] += (size_t)j.G * d.nx * d.ny;
     }
     e = cudaMemcpyAsync(c->b_jobs.ptr, jd.data(), sizeof(xvh::JobDev) * njobs, cudaMemcpyHostToDevice, st);
@@ -1125,11 +1126,11 @@ xv_status xv_decode_batch(xv_ctx* c, const xv_djob* jobs, int njobs, uint64_t* t
     if ((e = cudaEventRecord(c->ev0, st)) != cudaSuccess) return cuda_fail(e, "event");
     for (int k = 0; k < 4; ++k) {
         if (!total[k]) continue;
-        // measured: 256 threads for CTU 16 and 64, 128 for CTU 32 (its frames are wide)
-        const int nt = c->force_nt ? c->force_nt : (ctus[k] == 32 ? 128 : 256);
+        // measured: 128 threads for CTU 32 (its frames are wide), 512 for CTU 64, 256 otherwise
+        const int nt = c->force_nt ? c->force_nt : (ctus[k] == 32 ? 128 : ctus[k] == 64 ? 512 : 256);
         const size_t smem = xvh::decode_smem_bytes(ctus[k]);
-        const int grid = xvh::persist_grid(ctus[k], nt, smem);
-        if ((s = check_launch(xvh::launch_persist(ctus[k], nt, jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
+        const int grid = xvh::persist_grid(ctus[k], nt, smem, true);
+        if ((s = check_launch(xvh::launch_persist(ctus[k], nt, true, jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
                                                   (xvh::BatchCtl*)c->b_ctl.ptr + k, smem, grid, st),
                               "persistent decode")))
             return s;

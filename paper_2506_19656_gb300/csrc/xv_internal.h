@@ -24,6 +24,8 @@ struct DevBuf {
 };
 
 void set_error(const char* fmt, ...);
+// The calling thread's last error message.
+const char* last_error_text();
 xv_status cuda_fail(cudaError_t e, const char* what);
 
 // ---- launchers (stream = cudaStream_t)
@@ -102,7 +104,6 @@ struct JobDev {
     int nx, ny;
     int64_t qfirst;          // queue slot of this job's first window item
     int tb, te;              // frames [tb, te) are encoded by this launch (frame tb-1 is complete)
-    int decode = 0;          // 1: decode (levels, mv, tu are inputs; recon and bits outputs)
 };
 
 // One CTU class of a batch, as the prologue sees it.
@@ -143,9 +144,11 @@ cudaError_t launch_prepare_bands(const void* src, xv_dtype dt, int bands, int64_
 cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long* totals, cudaStream_t st);
 // Block sizes the persistent kernel is built for (the autotuner picks one).
 constexpr int kPersistBlockSizes[4] = {128, 192, 256, 512};
-cudaError_t launch_persist(int ctu, int nt, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl, size_t smem,
-                           int grid, cudaStream_t st);
-int persist_grid(int ctu, int nt, size_t smem);
+// decode: the decoding instantiation (the jobs' levels, vectors and TU sizes
+// are inputs, recon and bits outputs) instead of the encoder.
+cudaError_t launch_persist(int ctu, int nt, bool decode, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl,
+                           size_t smem, int grid, cudaStream_t st);
+int persist_grid(int ctu, int nt, size_t smem, bool decode);
 
 }  // namespace xvh
 

@@ -64,6 +64,7 @@ struct Request {
     int G = 0, Hp = 0, Wp = 0, nx = 0, ny = 0, nblk = 0;
     int t_next = 0;
     cudaEvent_t ready = nullptr;
+    std::string err;  // the message of a failed request (from the serving thread)
 };
 
 size_t request_bytes(const xv_request& q, int* G_, int* Hp_, int* Wp_, int* nblk_) {
@@ -129,6 +130,7 @@ void ServeState::finish(Request* q, xv_status st) {
     // caller holds the lock
     q->res.status = st;
     q->res.latency_s = now_s() - q->t_arrival;
+    if (st != XV_OK) q->err = last_error_text();
     q->state = RState::Done;
     if (q->dbuf) {
         cudaFreeAsync(q->dbuf, s_tick);
@@ -275,7 +277,10 @@ void ServeState::loop() {
             Request* q = tick[i];
             const xv_request& r = q->r;
             const int k = r.p.ctu == 8 ? 0 : r.p.ctu == 16 ? 1 : r.p.ctu == 32 ? 2 : 3;
+            // h_jobs is raw pinned memory: start every record from its
+            // defaults, then fill it
             JobDev& d = h_jobs[i];
+            d = JobDev{};
             d.planes = q->d_planes;
             d.recon = q->d_recon;
             d.mv = q->d_mv;
@@ -303,8 +308,8 @@ void ServeState::loop() {
         const int ctus[4] = {8, 16, 32, 64};
         for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
             if (!total[k]) continue;
-            const int grid = persist_grid(ctus[k], 256, smem[k]);
-            e = launch_persist(ctus[k], 256, d_jobs, d_queue + cls[k].qoff, d_ctl + k, smem[k], grid, s_tick);
+            const int grid = persist_grid(ctus[k], 256, smem[k], false);
+            e = launch_persist(ctus[k], 256, false, d_jobs, d_queue + cls[k].qoff, d_ctl + k, smem[k], grid, s_tick);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev1, s_tick);
         // results of the requests this tick finishes
@@ -346,6 +351,8 @@ void ServeState::loop() {
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 set_error("serving tick: %s", cudaGetErrorString(e));
+            } else {
+                set_error("serving tick: device status %d", err);
             }
             const xv_status st = e != cudaSuccess ? XV_ECUDA : (xv_status)err;
             for (Request* q : tick) {
@@ -471,6 +478,7 @@ xv_status serve_poll(ServeState* s, uint64_t ticket, xv_result* res, int* done) 
     *done = q->state == RState::Done;
     if (*done) {
         if (res) *res = q->res;
+        if (q->res.status != XV_OK) set_error("%s", q->err.c_str());  // for the polling thread
         s->by_ticket.erase(it);
         delete q;
     }

@@ -231,7 +231,8 @@ def xv_decode_frame(ctx: Context, levels, ref, mv, tu_log2, G: int, plane_gstrid
 def make_djob(p: xv_params, levels, mv, tu_log2, recon, bits=None, minmax=None, dst=None, bands=0, H=0,
               W=0) -> xv_djob:
     """levels [G,T,3,Hp,Wp] int16, mv [G,T,nCU,2] int16, tu_log2 [G,T,nCU] uint8, recon like levels (uint16);
-    with dst ([bands,T,H,W] float32) and minmax the reconstruction is also written in the cube's units."""
+    with dst ([bands,T,H,W] float32) and minmax the reconstruction is also written in the cube's units.
+    The job holds raw device pointers: the tensors must stay alive while it is used."""
     G, T, _, Hp, Wp = levels.shape
     return xv_djob(p=p, G=G, T=T, Hp=Hp, Wp=Wp, levels=_ptr(levels), mv=_ptr(mv), tu_log2=_ptr(tu_log2),
                    recon=_ptr(recon), bits=_ptr(bits), bands=bands, H=H, W=W, minmax=_ptr(minmax), dst=_ptr(dst))
@@ -334,6 +335,7 @@ def xv_psnr_noalloc(src, planes, recon, minmax, stream=None):
 
 def make_job(src, p: xv_params, planes, recon, minmax=None, minmax_fixed=False, mv=None, cost=None, levels=None,
              tu_log2=None, bits=None) -> xv_job:
+    """The job of one cube.  It holds raw device pointers: the tensors must stay alive while it is used."""
     bands, T, H, W = src.shape
     return xv_job(src=_ptr(src), dtype=_dtype_code(src), bands=bands, T=T, H=H, W=W, p=p, minmax=_ptr(minmax),
                   minmax_fixed=int(minmax_fixed), planes=_ptr(planes), recon=_ptr(recon), mv=_ptr(mv),
@@ -372,11 +374,16 @@ def xv_serve_submit(ctx: Context, req: xv_request) -> int:
 
 
 def xv_serve_poll(ctx: Context, ticket: int):
-    """(done, result dict or None)."""
+    """(done, result dict or None); a failed request's result carries its message as "error"."""
     r = xv_result()
     done = _i()
     check(lib().xv_serve_poll(ctx.handle, ticket, ctypes.byref(r), ctypes.byref(done)), "xv_serve_poll")
-    return (True, r.as_dict()) if done.value else (False, None)
+    if not done.value:
+        return False, None
+    res = r.as_dict()
+    if res["status"] != XV_OK:
+        res["error"] = lib().xv_last_error().decode()
+    return True, res
 
 
 def xv_serve_cancel(ctx: Context, ticket: int):

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch the benchmark times:
-every sub-cube of a workload at QP 22, 27 and 32 in one xv_encode_batch, with
-the block size the autotuner picks (the job list is bench.workload_jobs).
+every sub-cube of a workload at the benchmark's QPs (22, 27 and 32 for the
+DeepExtremeCubes shape, the workload's own otherwise) in one xv_encode_batch,
+with the block size the autotuner picks (the job list is bench.workload_jobs).
 
 DeepExtremeCubes shape (10 bands x 256 frames x 128 x 128): every output of
 the three encodes against the oracle's whole chain.
@@ -46,7 +47,8 @@ def ctx(xv):
 
 
 def test_deepextremecubes_full_cube_three_qps_one_batch(xv, ctx):
-    cfg, _, cube, _, jobs, bufs = bench.workload_jobs("deepextremecubes", device="cuda")
+    cfg, _, cube, _, jobs, bufs = bench.workload_jobs("deepextremecubes", device="cuda",
+                                                      qps=bench.default_qps("deepextremecubes"))
     assert cube.shape == (10, 256, 128, 128) and len(jobs) == 3
     res = xv.xv_encode_batch(ctx, jobs)
     mm, _ = oracle.minmax(cube)
@@ -93,7 +95,7 @@ def check_properties(xv, ctx, cfg, b, r):
 
 @pytest.mark.parametrize("workload, prefix", [("dynamicearthnet", 2), ("era5", 3)])
 def test_full_size_sampled_frames_and_properties(xv, ctx, workload, prefix):
-    cfg, lengths, cube, _, jobs, bufs = bench.workload_jobs(workload, device="cuda")
+    cfg, lengths, cube, _, jobs, bufs = bench.workload_jobs(workload, device="cuda", qps=bench.default_qps(workload))
     res = xv.xv_encode_batch(ctx, jobs)
     assert all(r["status"] == 0 for r in res)
     for T in lengths:

@@ -62,7 +62,7 @@ def wait_all(xv, ctx, tickets, timeout=120.0):
 def check(item, res):
     shape, ctu, R, mask, qp = item["spec"]
     want = oracle.encode_cube(item["cube"], ctu, R, mask, qp, want_levels=False)
-    assert res["status"] == 0
+    assert res["status"] == 0, res.get("error")
     assert np.array_equal(item["recon"].numpy().view(np.uint16), want["recon"])
     assert np.array_equal(item["mv"].numpy(), want["mv"])
     assert res["total_bits"] == want["total_bits"]
