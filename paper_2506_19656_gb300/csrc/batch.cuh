@@ -20,11 +20,14 @@ namespace {  // each including file gets its own copies
 
 
 // Resident blocks per SM the register allocation aims for, per CTU size and
-// block size (64 to 80 registers per thread where shared memory allows
-// several blocks; the CTU-64 window leaves room for one).
+// block size (64 to 128 registers per thread where shared memory allows
+// several blocks; the CTU-64 window leaves room for one).  Measured: CTU 16
+// at 128 threads is fastest with six (seven spill nothing at 72 registers
+// but run slower), CTU 32 at 128 threads with four (128 registers, no
+// spills) rather than three.
 template <int N, int NT>
 constexpr int kMinBlocks = NT == 512 ? (N == 64 ? 1 : 2)
-                                     : N == 64 ? 1 : (N == 32 ? (NT == 256 ? 2 : 3) : (NT == 256 ? 4 : (NT == 192 ? 5 : 6)));
+                                     : N == 64 ? 1 : (N == 32 ? (NT == 256 ? 2 : 4) : (NT == 256 ? 4 : (NT == 192 ? 5 : 6)));
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
     uint64_t v;

@@ -483,11 +483,11 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         if (i < 2 * R + 1) s_bitsd[i] = se_len(4 * (i - R));
         else s_costb[i - (2 * R + 1)] = (uint32_t)((lmv * (int64_t)(i - (2 * R + 1)) + 32768) >> 16);
     }
-    {  // sub-block sums, the seed unit's sums, the survivor counts start at 0;
-       // the two block-minimum slots at ~0
+    {  // sub-block sums and the survivor counts start at 0; the three
+       // block-minimum slots at ~0
         int* bs = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
         constexpr int nsb = (N / me_sb(N)) * (N / me_sb(N));
-        for (int i = tid; i < nsb + 12; i += NT) {
+        for (int i = tid; i < nsb + 13; i += NT) {
             if (i < nsb) bs[i] = 0;
             else if (i < nsb + 10) satd[i - nsb] = 0;
             else red[i - nsb - 10] = ~0ull;
@@ -626,107 +626,81 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     lbbest = block_min_u64(lbbest, red);  // its barrier also ends the bound pass
     const int useed = (int)(lbbest & 0xffffffffu);
 
-    // exact SAD of the seed unit: one block row per thread, reduced per warp
-    {
-        const int gx = useed / side, dyi = useed - gx * side;
-        const int woff = (dyi + 4) * S + gx * 8 + 4;
-        const bool single = gx == ngx;  // the last column: dx = R only
-        for (int r = tid; r < ((N + 31) & ~31); r += NT) {
-            uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (r < N) {
-                if (single) sad[0] = row_sad1<N>(blk + r * N, wb + woff + r * S, 0u);
-                else row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1)
-#pragma unroll
-                for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(0xffffffffu, sad[k], o);
-            if ((threadIdx.x & 31) == 0)
-#pragma unroll
-                for (int k = 0; k < 8; ++k) atomicAdd(satd + k, sad[k]);
-        }
-    }
-    __syncthreads();
+    // Exact search in two rounds of the same code: round 0 the seed unit alone
+    // (its best J is the pruning threshold), round 1 the surviving units; P
+    // lanes per unit interleave the block rows.
     uint64_t best = ~0ull;
-    uint32_t thr;
-    {
-        const int gx = useed / side, dyi = useed - gx * side;
-        const int by = s_bitsd[dyi];
-        const uint32_t rowbase = (uint32_t)(dyi * side);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int dx = gx * 8 - R + k;
-            if (dx <= R) {
-                const uint32_t J = satd[k] + s_costb[s_bitsd[dx + R] + by];
-                const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(dx + R));
-                best = key < best ? key : best;
-            }
-        }
-        thr = (uint32_t)(best >> 32);
-    }
-    // survivors: units (other than the seed) whose bound does not exceed
-    // the seed's J; warp-aggregated appends (satd[9] counts the single-column
-    // ones, for the executed-work statistic)
-    {
-        const int lane = threadIdx.x & 31;
-        for (int u0 = tid - lane; u0 < units; u0 += NT) {
-            const int u = u0 + lane;
-            const bool keep = u < units && u != useed && ulb[u] <= thr;
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (!bal) continue;
-            const unsigned bal1 = __ballot_sync(0xffffffffu, keep && u >= ngx * side);
-            unsigned base = 0;
-            if (lane == 0) {
-                base = atomicAdd(satd + 8, (uint32_t)__popc(bal));
-                if (bal1) atomicAdd(satd + 9, (uint32_t)__popc(bal1));
-            }
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (keep) list[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)u;
-        }
-    }
-    __syncthreads();
-    const int M = (int)satd[8];
-    const uint32_t exact_cand = 8u * (uint32_t)(M - (int)satd[9]) + satd[9] + (useed >= ngx * side ? 1u : 8u);
-    // exact search over the survivors, P lanes per unit (rows interleaved)
-    {
-        int P = 1;
-        while (P < 32 && 2 * P <= N && M * 2 * P <= NT) P *= 2;
-        const int q = tid & (P - 1);
-        const unsigned pmask = P == 1 ? 0u : (P == 32 ? 0xffffffffu : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1)));
-        for (int i = tid / P; i < M; i += NT / P) {
-            const int u = list[i];
-            const int gx = u / side, dyi = u - gx * side;
-            const int dx0 = gx * 8 - R;
-            const int woff = (dyi + 4) * S + gx * 8 + 4;
-            const uint32_t rowbase = (uint32_t)(dyi * side);
-            const int by = s_bitsd[dyi];
-            if (gx == ngx) {  // the single last column, dx = R
-                uint32_t sad1 = 0;
-                for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, wb + woff + r * S, sad1);
-                for (int o = 1; o < P; o <<= 1) sad1 += __shfl_xor_sync(pmask, sad1, o);
-                if (q == 0) {
-                    const uint32_t J = sad1 + s_costb[s_bitsd[2 * R] + by];
-                    const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(2 * R));
-                    best = key < best ? key : best;
-                }
-                continue;
-            }
-            uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            // one row at a time (a second, FP32-pipe copy of the row code for
-            // a third of the rows measured slower: it costs more in code size
-            // than it gains in pipe balance, the survivors being few)
+    int M = 1;
+    uint32_t exact_cand = 0;
 #pragma unroll 1
-            for (int r = q; r < N; r += P) row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
-            for (int o = 1; o < P; o <<= 1)
+    for (int round = 0; round < 2; ++round) {
+        if (round == 1) {
+            best = block_min_u64(best, red + 2);  // the seed unit's best key, on every thread
+            const uint32_t thr = (uint32_t)(best >> 32);
+            // survivors: units (other than the seed) whose bound does not exceed
+            // the seed's J; warp-aggregated appends (satd[9] counts the single-column
+            // ones, for the executed-work statistic)
+            {
+                const int lane = threadIdx.x & 31;
+                for (int u0 = tid - lane; u0 < units; u0 += NT) {
+                    const int u = u0 + lane;
+                    const bool keep = u < units && u != useed && ulb[u] <= thr;
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    if (!bal) continue;
+                    const unsigned bal1 = __ballot_sync(0xffffffffu, keep && u >= ngx * side);
+                    unsigned base = 0;
+                    if (lane == 0) {
+                        base = atomicAdd(satd + 8, (uint32_t)__popc(bal));
+                        if (bal1) atomicAdd(satd + 9, (uint32_t)__popc(bal1));
+                    }
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (keep) list[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)u;
+                }
+            }
+            __syncthreads();
+            M = (int)satd[8];
+            exact_cand = 8u * (uint32_t)(M - (int)satd[9]) + satd[9] + (useed >= ngx * side ? 1u : 8u);
+        }
+        {
+            int P = 1;
+            while (P < 32 && 2 * P <= N && M * 2 * P <= NT) P *= 2;
+            const int q = tid & (P - 1);
+            const unsigned pmask = P == 1 ? 0u : (P == 32 ? 0xffffffffu : ((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1)));
+            for (int i = tid / P; i < M; i += NT / P) {
+                const int u = round == 0 ? useed : (int)list[i];
+                const int gx = u / side, dyi = u - gx * side;
+                const int dx0 = gx * 8 - R;
+                const int woff = (dyi + 4) * S + gx * 8 + 4;
+                const uint32_t rowbase = (uint32_t)(dyi * side);
+                const int by = s_bitsd[dyi];
+                if (gx == ngx) {  // the single last column, dx = R
+                    uint32_t sad1 = 0;
+                    for (int r = q; r < N; r += P) sad1 = row_sad1<N>(blk + r * N, wb + woff + r * S, sad1);
+                    for (int o = 1; o < P; o <<= 1) sad1 += __shfl_xor_sync(pmask, sad1, o);
+                    if (q == 0) {
+                        const uint32_t J = sad1 + s_costb[s_bitsd[2 * R] + by];
+                        const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(2 * R));
+                        best = key < best ? key : best;
+                    }
+                    continue;
+                }
+                uint32_t sad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                // one row at a time (a second, FP32-pipe copy of the row code for
+                // a third of the rows measured slower: it costs more in code size
+                // than it gains in pipe balance, the survivors being few)
+#pragma unroll 1
+                for (int r = q; r < N; r += P) row_sad8<N>(blk + r * N, wb + woff + r * S, sad);
+                for (int o = 1; o < P; o <<= 1)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
+                    for (int k = 0; k < 8; ++k) sad[k] += __shfl_xor_sync(pmask, sad[k], o);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int dx = dx0 + k;
-                if ((k & (P - 1)) == q && dx <= R) {  // the P lanes share the candidates
-                    const uint32_t J = sad[k] + s_costb[s_bitsd[dx + R] + by];
-                    const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(dx + R));
-                    best = key < best ? key : best;
+                for (int k = 0; k < 8; ++k) {
+                    const int dx = dx0 + k;
+                    if ((k & (P - 1)) == q && dx <= R) {  // the P lanes share the candidates
+                        const uint32_t J = sad[k] + s_costb[s_bitsd[dx + R] + by];
+                        const uint64_t key = ((uint64_t)J << 32) | (rowbase + (uint32_t)(dx + R));
+                        best = key < best ? key : best;
+                    }
                 }
             }
         }
