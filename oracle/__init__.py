@@ -85,6 +85,16 @@ def lib():
             L.xvo_tqr_frame.restype = ctypes.c_uint64
             L.xvo_encode_planes.argtypes = [vp, i, i, i, i, i, i, u, i, vp, vp, vp, vp, vp, vp, vp, vp]
             L.xvo_psnr.argtypes = [vp, i, i, i, i, i, vp, vp, i, i, vp, vp, vp, vp, vp]
+            L.xvo_intra_angle.argtypes = [i]
+            L.xvo_intra_inv_angle.argtypes = [i]
+            L.xvo_intra_pred.argtypes = [vp, vp, ctypes.c_int32, i, i, vp]
+            L.xvo_intra_refs.argtypes = [vp, i, i, i, i, i, vp, vp, vp]
+            L.xvo_intra_frame.argtypes = [vp, i, i, i, u, i, i64, vp, vp, vp, vp, vp]
+            L.xvo_intra_frame.restype = ctypes.c_uint64
+            L.xvo_deblock_params.argtypes = [i, i, vp, vp]
+            L.xvo_deblock_segment.argtypes = [vp, i, i]
+            L.xvo_deblock_frame.argtypes = [vp, i, i, i, i, vp, vp, vp, i]
+            L.xvo_encode_planes_ex.argtypes = [vp, i, i, i, i, i, i, u, i, u, vp, vp, vp, vp, vp, vp, vp, vp]
             L.xvo_decode_frame.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
             L.xvo_decode_frame.restype = ctypes.c_uint64
             L.xvo_decode_planes.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
@@ -271,7 +281,8 @@ def tqr_frame(cur: np.ndarray, ref, mv, ctu: int, tu_mask: int, qp: int):
 
 
 # ----------------------------------------------------------------- C4 chain
-def encode_planes(planes: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, want_levels=True):
+def encode_planes(planes: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, want_levels=True, flags: int = 0):
+    """The chain over frames per group (flags: INTRA, DEBLOCK)."""
     planes = np.ascontiguousarray(planes, np.uint16)
     G, T, _, Hp, Wp = planes.shape
     n = (Hp // ctu) * (Wp // ctu)
@@ -285,10 +296,85 @@ def encode_planes(planes: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, w
         tu_log2=np.zeros((G, T, n), np.uint8),
         bits=np.zeros((G, T), np.uint64),
     )
-    lib().xvo_encode_planes(_p(planes), G, T, Hp, Wp, ctu, R, tu_mask, qp, _p(out["recon"]),
+    lib().xvo_encode_planes_ex(_p(planes), G, T, Hp, Wp, ctu, R, tu_mask, qp, flags, _p(out["recon"]),
                             _p(out["mv"]), _p(out["cost"]), _p(out["mv_int"]), _p(out["cost_int"]),
                             _p(out["levels"]), _p(out["tu_log2"]), _p(out["bits"]))
     return out
+
+
+# ------------------------------------- options: frame-0 intra and deblocking
+INTRA, DEBLOCK = 1, 2
+
+
+def intra_angle(mode: int) -> int:
+    return int(lib().xvo_intra_angle(mode))
+
+
+def intra_inv_angle(angle: int) -> int:
+    return int(lib().xvo_intra_inv_angle(angle))
+
+
+def intra_pred(left, top, tl: int, N: int, mode: int) -> np.ndarray:
+    """The N x N intra prediction (int32) from left[2N], top[2N] and the corner tl."""
+    left = np.ascontiguousarray(left, np.int32)
+    top = np.ascontiguousarray(top, np.int32)
+    assert left.shape == (2 * N,) and top.shape == (2 * N,)
+    out = np.zeros((N, N), np.int32)
+    lib().xvo_intra_pred(_p(left), _p(top), int(tl), N, mode, _p(out))
+    return out
+
+
+def intra_refs(plane: np.ndarray, ctu: int, x0: int, y0: int):
+    """(left[2N], top[2N], tl) of the CU at (x0, y0) from one plane [Hp,Wp]."""
+    plane = np.ascontiguousarray(plane, np.uint16)
+    Hp, Wp = plane.shape
+    left = np.zeros(2 * ctu, np.int32)
+    top = np.zeros(2 * ctu, np.int32)
+    tl = np.zeros(1, np.int32)
+    lib().xvo_intra_refs(_p(plane), Hp, Wp, ctu, x0, y0, _p(left), _p(top), _p(tl))
+    return left, top, int(tl[0])
+
+
+def intra_frame(cur: np.ndarray, ctu: int, tu_mask: int, qp: int):
+    """Frame 0 [3,Hp,Wp] with intra prediction -> dict(recon, levels, tu_log2, mode_mv, cu_bits, bits)."""
+    cur = np.ascontiguousarray(cur, np.uint16)
+    _, Hp, Wp = cur.shape
+    n = (Hp // ctu) * (Wp // ctu)
+    lf8, _ = lambdas(qp)
+    recon = np.zeros_like(cur)
+    levels = np.zeros(cur.shape, np.int16)
+    tu = np.zeros(n, np.uint8)
+    mm = np.zeros((n, 2), np.int16)
+    cub = np.zeros(n, np.uint64)
+    total = lib().xvo_intra_frame(_p(cur), Hp, Wp, ctu, tu_mask, qp, lf8, _p(recon), _p(levels), _p(tu), _p(mm),
+                                  _p(cub))
+    return dict(recon=recon, levels=levels, tu_log2=tu, mode_mv=mm, cu_bits=cub, bits=int(total))
+
+
+def deblock_params(qp: int, bs: int):
+    """(beta, tC) at 10 bits for a QP and boundary strength."""
+    b = np.zeros(1, np.int32)
+    t = np.zeros(1, np.int32)
+    lib().xvo_deblock_params(qp, bs, _p(b), _p(t))
+    return int(b[0]), int(t[0])
+
+
+def deblock_segment(s: np.ndarray, bs: int, qp: int) -> np.ndarray:
+    """One 4-line segment s[4][8] (p3 p2 p1 p0 | q0 q1 q2 q3 per line), filtered."""
+    s = np.ascontiguousarray(s, np.int32).copy()
+    assert s.shape == (4, 8)
+    lib().xvo_deblock_segment(_p(s), bs, qp)
+    return s
+
+
+def deblock_frame(rec: np.ndarray, ctu: int, qp: int, tu_log2, levels, mv, intra: bool) -> np.ndarray:
+    """A reconstructed frame [3,Hp,Wp] deblocked (a new array)."""
+    rec = np.ascontiguousarray(rec, np.uint16).copy()
+    _, Hp, Wp = rec.shape
+    lib().xvo_deblock_frame(_p(rec), Hp, Wp, ctu, qp, _p(np.ascontiguousarray(tu_log2, np.uint8)),
+                            _p(np.ascontiguousarray(levels, np.int16)), _p(np.ascontiguousarray(mv, np.int16)),
+                            int(bool(intra)))
+    return rec
 
 
 # ------------------------------------------------------------------ decoder
@@ -423,12 +509,12 @@ def psnr(src: np.ndarray, planes: np.ndarray, recon: np.ndarray, mm: np.ndarray)
                 psnr_mean=float(np.mean(ps)))
 
 
-def encode_cube(src: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, mm=None, want_levels=True):
-    """The whole path on one cube [bands,T,H,W]: A1..A11."""
+def encode_cube(src: np.ndarray, ctu: int, R: int, tu_mask: int, qp: int, mm=None, want_levels=True, flags: int = 0):
+    """The whole path on one cube [bands,T,H,W]: A1..A11 (flags: INTRA, DEBLOCK)."""
     if mm is None:
         mm, _ = minmax(src)
     planes = quantize_pack(src, ctu, mm)
-    enc = encode_planes(planes, ctu, R, tu_mask, qp, want_levels=want_levels)
+    enc = encode_planes(planes, ctu, R, tu_mask, qp, want_levels=want_levels, flags=flags)
     met = psnr(src, planes, enc["recon"], mm)
     bands, T, H, W = src.shape
     total_bits = int(enc["bits"].sum())

@@ -408,6 +408,79 @@ void xvo_me_qpel(const uint16_t* cur, const uint16_t* ref, int Hp, int Wp, int c
 
 /* ============ C4/C11/C12/C13: transform, quantise, reconstruct ============== */
 
+/* One CU at (x0, y0) from its prediction pred [3][ctu][ctu]: for each allowed
+ * TU size (ascending) the residual of every TU of every channel is
+ * transformed (C10), quantised and dequantised (C11), inverse transformed and
+ * added back; the size with the least J (C12) is kept: its reconstruction and
+ * levels are written, *bestL_out = its log2 size, and the result is its bits
+ * (per TU and channel one coded-block flag plus the levels' bits, C13). */
+static uint64_t code_cu(const uint16_t* cur, int64_t plane, int Wp, int x0, int y0, int ctu,
+                        const int32_t* pred, unsigned tu_mask, int qp, int64_t lambda_fp8,
+                        uint16_t* recon, int16_t* levels, int* bestL_out) {
+    int n2 = ctu * ctu;
+    int32_t* rec_try = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+    int32_t* lev_try = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+    int32_t* rec_best = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+    int32_t* lev_best = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+    int64_t bestJ = INT64_MAX;
+    int bestL = -1;
+    uint64_t bestBits = 0;
+    for (int L = 2; L <= 5; ++L) {
+        int N = 1 << L;
+        if (!(tu_mask & (1u << L)) || N > ctu) continue;
+        uint64_t sse = 0, bits = 0;
+        int32_t X[32 * 32], C[32 * 32], D[32 * 32], Rr[32 * 32];
+        for (int c = 0; c < 3; ++c)
+            for (int ty = 0; ty < ctu; ty += N)
+                for (int tx = 0; tx < ctu; tx += N) {
+                    for (int y = 0; y < N; ++y)
+                        for (int x = 0; x < N; ++x) {
+                            int yy = ty + y, xx = tx + x;
+                            X[y * N + x] = (int32_t)cur[c * plane + (y0 + yy) * Wp + x0 + xx] -
+                                           pred[c * n2 + yy * ctu + xx];
+                        }
+                    xvo_fwd_transform(N, X, C);
+                    uint64_t tb = 1; /* coded-block flag */
+                    for (int i = 0; i < N * N; ++i) {
+                        int32_t lv = xvo_quant(C[i], qp, L);
+                        lev_try[c * n2 + (ty + i / N) * ctu + tx + i % N] = lv;
+                        if (lv != 0) tb += (uint64_t)(2 * L + xvo_ue_len_se(lv));
+                        D[i] = xvo_dequant(lv, qp, L);
+                    }
+                    bits += tb;
+                    xvo_inv_transform(N, D, Rr);
+                    for (int y = 0; y < N; ++y)
+                        for (int x = 0; x < N; ++x) {
+                            int yy = ty + y, xx = tx + x;
+                            int r = clampi(pred[c * n2 + yy * ctu + xx] + Rr[y * N + x], 0, PIXMAX);
+                            rec_try[c * n2 + yy * ctu + xx] = r;
+                            int e = (int)cur[c * plane + (y0 + yy) * Wp + x0 + xx] - r;
+                            sse += (uint64_t)((int64_t)e * e);
+                        }
+                }
+        /* C12: J = (SSE << 8) + lambda_fp8 * bits; ascending N, ties to the
+         * larger N. */
+        int64_t J = (int64_t)(sse << 8) + lambda_fp8 * (int64_t)bits;
+        if (J <= bestJ) {
+            bestJ = J;
+            bestL = L;
+            bestBits = bits;
+            memcpy(rec_best, rec_try, sizeof(int32_t) * 3 * (size_t)n2);
+            memcpy(lev_best, lev_try, sizeof(int32_t) * 3 * (size_t)n2);
+        }
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int y = 0; y < ctu; ++y)
+            for (int x = 0; x < ctu; ++x) {
+                int64_t o = c * plane + (int64_t)(y0 + y) * Wp + x0 + x;
+                recon[o] = (uint16_t)rec_best[c * n2 + y * ctu + x];
+                if (levels) levels[o] = (int16_t)lev_best[c * n2 + y * ctu + x];
+            }
+    *bestL_out = bestL;
+    free(rec_try); free(lev_try); free(rec_best); free(lev_best);
+    return bestBits;
+}
+
 uint64_t xvo_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, int Hp, int Wp,
                        int ctu, unsigned tu_mask, int qp, int64_t lambda_fp8, uint16_t* recon,
                        int16_t* levels, uint8_t* tu_log2, uint64_t* cu_bits) {
@@ -419,10 +492,6 @@ uint64_t xvo_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* 
         int x0 = (cu % nx) * ctu, y0 = (cu / nx) * ctu;
         int n2 = ctu * ctu;
         int32_t* pred = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
-        int32_t* rec_try = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
-        int32_t* lev_try = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
-        int32_t* rec_best = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
-        int32_t* lev_best = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
         int mvx = ref ? mv[2 * cu] : 0, mvy = ref ? mv[2 * cu + 1] : 0;
         /* C4: frame 0 is predicted by the flat value 2^(B-1); later frames by
          * motion compensation from the previous reconstruction, all channels
@@ -433,65 +502,14 @@ uint64_t xvo_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* 
                     pred[c * n2 + y * ctu + x] =
                         ref ? interp_sample(ref + c * plane, Hp, Wp, x0 + x, y0 + y, mvx, mvy)
                             : (1 << (BITDEPTH - 1));
-        int64_t bestJ = INT64_MAX;
-        int bestL = -1;
-        uint64_t bestBits = 0;
-        for (int L = 2; L <= 5; ++L) {
-            int N = 1 << L;
-            if (!(tu_mask & (1u << L)) || N > ctu) continue;
-            uint64_t sse = 0, bits = 0;
-            int32_t X[32 * 32], C[32 * 32], D[32 * 32], Rr[32 * 32];
-            for (int c = 0; c < 3; ++c)
-                for (int ty = 0; ty < ctu; ty += N)
-                    for (int tx = 0; tx < ctu; tx += N) {
-                        for (int y = 0; y < N; ++y)
-                            for (int x = 0; x < N; ++x) {
-                                int yy = ty + y, xx = tx + x;
-                                X[y * N + x] = (int32_t)cur[c * plane + (y0 + yy) * Wp + x0 + xx] -
-                                               pred[c * n2 + yy * ctu + xx];
-                            }
-                        xvo_fwd_transform(N, X, C);
-                        uint64_t tb = 1; /* coded-block flag */
-                        for (int i = 0; i < N * N; ++i) {
-                            int32_t lv = xvo_quant(C[i], qp, L);
-                            lev_try[c * n2 + (ty + i / N) * ctu + tx + i % N] = lv;
-                            if (lv != 0) tb += (uint64_t)(2 * L + xvo_ue_len_se(lv));
-                            D[i] = xvo_dequant(lv, qp, L);
-                        }
-                        bits += tb;
-                        xvo_inv_transform(N, D, Rr);
-                        for (int y = 0; y < N; ++y)
-                            for (int x = 0; x < N; ++x) {
-                                int yy = ty + y, xx = tx + x;
-                                int r = clampi(pred[c * n2 + yy * ctu + xx] + Rr[y * N + x], 0, PIXMAX);
-                                rec_try[c * n2 + yy * ctu + xx] = r;
-                                int e = (int)cur[c * plane + (y0 + yy) * Wp + x0 + xx] - r;
-                                sse += (uint64_t)((int64_t)e * e);
-                            }
-                    }
-            /* C12: J = (SSE << 8) + lambda_fp8 * bits; ascending N, ties to
-             * the larger N. */
-            int64_t J = (int64_t)(sse << 8) + lambda_fp8 * (int64_t)bits;
-            if (J <= bestJ) {
-                bestJ = J;
-                bestL = L;
-                bestBits = bits;
-                memcpy(rec_best, rec_try, sizeof(int32_t) * 3 * (size_t)n2);
-                memcpy(lev_best, lev_try, sizeof(int32_t) * 3 * (size_t)n2);
-            }
-        }
-        for (int c = 0; c < 3; ++c)
-            for (int y = 0; y < ctu; ++y)
-                for (int x = 0; x < ctu; ++x) {
-                    int64_t o = c * plane + (int64_t)(y0 + y) * Wp + x0 + x;
-                    recon[o] = (uint16_t)rec_best[c * n2 + y * ctu + x];
-                    if (levels) levels[o] = (int16_t)lev_best[c * n2 + y * ctu + x];
-                }
+        int bestL;
+        uint64_t bestBits = code_cu(cur, plane, Wp, x0, y0, ctu, pred, tu_mask, qp, lambda_fp8, recon, levels,
+                                    &bestL);
         if (tu_log2) tu_log2[cu] = (uint8_t)bestL;
         /* C13: 2 bits for the TU size, the motion vector (none in frame 0),
          * then the coded TUs. */
         bits_per_cu[cu] = 2 + (ref ? (uint64_t)xvo_mv_bits(mvx, mvy) : 0) + bestBits;
-        free(pred); free(rec_try); free(lev_try); free(rec_best); free(lev_best);
+        free(pred);
     }
     uint64_t total = 0;
     for (int cu = 0; cu < ncu; ++cu) {
@@ -502,12 +520,294 @@ uint64_t xvo_tqr_frame(const uint16_t* cur, const uint16_t* ref, const int16_t* 
     return total;
 }
 
+/* ================= Intra prediction of frame 0 (option XVO_INTRA) ================ */
+
+/* The H.265 intra prediction of an N x N block (N = the CU size here, reading
+ * R4: one prediction per CU from the CU's neighbours, the TU split applying to
+ * the residual only), from its reference samples: left[y] = p[-1][y] and
+ * top[x] = p[x][-1] for 0 <= x, y < 2N, tl = p[-1][-1].  Mode 0 planar, 1 DC,
+ * 2..34 angular with the standard's angle per mode; no reference smoothing
+ * and no boundary filters (reading R4). */
+static const int intra_angle[35] = {0,   0,   32,  26,  21,  17,  13,  9,  5,  2,  0,  -2,
+                                    -5,  -9,  -13, -17, -21, -26, -32, -26, -21, -17, -13, -9,
+                                    -5,  -2,  0,   2,   5,   9,   13,  17,  21,  26,  32};
+
+int xvo_intra_angle(int mode) { return mode >= 2 && mode <= 34 ? intra_angle[mode] : 0; }
+
+/* 256 * 32 / angle rounded to the nearest integer, for the negative angles */
+int xvo_intra_inv_angle(int angle) {
+    switch (angle) {
+        case -2: return -4096;
+        case -5: return -1638;
+        case -9: return -910;
+        case -13: return -630;
+        case -17: return -482;
+        case -21: return -390;
+        case -26: return -315;
+        case -32: return -256;
+    }
+    return 0;
+}
+
+void xvo_intra_pred(const int32_t* left, const int32_t* top, int32_t tl, int N, int mode, int32_t* out) {
+    int L = ilog2(N);
+    if (mode == 0) { /* planar */
+        for (int y = 0; y < N; ++y)
+            for (int x = 0; x < N; ++x)
+                out[y * N + x] = ((N - 1 - x) * left[y] + (x + 1) * top[N] + (N - 1 - y) * top[x] +
+                                  (y + 1) * left[N] + N) >> (L + 1);
+        return;
+    }
+    if (mode == 1) { /* DC */
+        int sum = N;
+        for (int i = 0; i < N; ++i) sum += top[i] + left[i];
+        for (int i = 0; i < N * N; ++i) out[i] = sum >> (L + 1);
+        return;
+    }
+    /* angular: a main reference along the prediction direction, ref[k] for
+     * -N <= k <= 2N (stored at refbuf[k + N]); vertical modes (>= 18) read
+     * the top row, horizontal ones the left column */
+    int angle = intra_angle[mode];
+    int vertical = mode >= 18;
+    const int32_t* main_side = vertical ? top : left;
+    const int32_t* other_side = vertical ? left : top;
+    int32_t refbuf[3 * 64 + 1];
+    int32_t* ref = refbuf + N;
+    ref[0] = tl;
+    for (int k = 1; k <= N; ++k) ref[k] = main_side[k - 1];
+    if (angle < 0) {
+        int last = (N * angle) >> 5;
+        if (last < -1) {
+            int inv = xvo_intra_inv_angle(angle);
+            for (int k = last; k <= -1; ++k) ref[k] = other_side[-1 + ((k * inv + 128) >> 8)];
+        }
+    } else {
+        for (int k = N + 1; k <= 2 * N; ++k) ref[k] = main_side[k - 1];
+    }
+    for (int y = 0; y < N; ++y)
+        for (int x = 0; x < N; ++x) {
+            int pos = vertical ? y : x, along = vertical ? x : y;
+            int idx = ((pos + 1) * angle) >> 5, fact = ((pos + 1) * angle) & 31;
+            int v = fact ? ((32 - fact) * ref[along + idx + 1] + fact * ref[along + idx + 2] + 16) >> 5
+                         : ref[along + idx + 1];
+            out[y * N + x] = v;
+        }
+}
+
+/* The 4N + 1 reference samples of the CU at (x0, y0) from one reconstructed
+ * plane: a sample is available when it lies inside the plane and in a CU
+ * coded before this one in raster order (so the left, top-left, top and
+ * top-right neighbours can be, the below-left never).  Unavailable samples are
+ * substituted as H.265 does: in the scan from p[-1][2N-1] up the left column
+ * to p[-1][-1] and along the top row to p[2N-1][-1], a missing first sample
+ * takes the first available one, every other missing sample its predecessor;
+ * with none available all are 2^(B-1). */
+void xvo_intra_refs(const uint16_t* plane, int Hp, int Wp, int ctu, int x0, int y0, int32_t* left, int32_t* top,
+                    int32_t* tl) {
+    int N = ctu, M = 4 * N + 1;
+    int32_t sv[4 * 64 + 1];
+    int av[4 * 64 + 1];
+    int any = 0;
+    for (int i = 0; i < M; ++i) {
+        int x, y;
+        if (i < 2 * N) { x = x0 - 1; y = y0 + 2 * N - 1 - i; }
+        else if (i == 2 * N) { x = x0 - 1; y = y0 - 1; }
+        else { x = x0 + (i - 2 * N - 1); y = y0 - 1; }
+        int in = x >= 0 && y >= 0 && x < Wp && y < Hp;
+        int coded = in && ((y / ctu < y0 / ctu) || (y / ctu == y0 / ctu && x / ctu < x0 / ctu));
+        av[i] = coded;
+        sv[i] = coded ? plane[(int64_t)y * Wp + x] : 0;
+        any |= coded;
+    }
+    if (!any) {
+        for (int i = 0; i < M; ++i) sv[i] = 1 << (BITDEPTH - 1);
+    } else {
+        if (!av[0]) {
+            int k = 1;
+            while (!av[k]) ++k;
+            sv[0] = sv[k];
+        }
+        for (int i = 1; i < M; ++i)
+            if (!av[i]) sv[i] = sv[i - 1];
+    }
+    for (int j = 0; j < 2 * N; ++j) left[j] = sv[2 * N - 1 - j];
+    *tl = sv[2 * N];
+    for (int j = 0; j < 2 * N; ++j) top[j] = sv[2 * N + 1 + j];
+}
+
+/* Frame 0 with intra prediction, CUs in raster order: the mode with the least
+ * SATD (C9) of channel 0's residual (ties: the lower mode) predicts all three
+ * channels; then the CU is coded like an inter CU.  mode_mv[cu] = (mode, 0).
+ * Rate proxy per CU: 2 (TU size) + 6 (mode) + the coded TUs. */
+uint64_t xvo_intra_frame(const uint16_t* cur, int Hp, int Wp, int ctu, unsigned tu_mask, int qp,
+                         int64_t lambda_fp8, uint16_t* recon, int16_t* levels, uint8_t* tu_log2, int16_t* mode_mv,
+                         uint64_t* cu_bits) {
+    int nx = Wp / ctu, ny = Hp / ctu, N = ctu, n2 = N * N;
+    int64_t plane = (int64_t)Hp * Wp;
+    int32_t* pred = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+    int32_t* d = (int32_t*)malloc(sizeof(int32_t) * (size_t)n2);
+    int32_t left[3][128], top[3][128], tl[3];
+    uint64_t total = 0;
+    for (int cu = 0; cu < nx * ny; ++cu) {
+        int x0 = (cu % nx) * N, y0 = (cu / nx) * N;
+        for (int c = 0; c < 3; ++c) xvo_intra_refs(recon + c * plane, Hp, Wp, ctu, x0, y0, left[c], top[c], &tl[c]);
+        int best = 0;
+        uint32_t bestS = 0xffffffffu;
+        for (int m = 0; m < 35; ++m) {
+            xvo_intra_pred(left[0], top[0], tl[0], N, m, pred);
+            for (int y = 0; y < N; ++y)
+                for (int x = 0; x < N; ++x) d[y * N + x] = (int32_t)cur[(int64_t)(y0 + y) * Wp + x0 + x] - pred[y * N + x];
+            uint32_t sa = xvo_satd(d, N, N);
+            if (sa < bestS) { bestS = sa; best = m; }
+        }
+        for (int c = 0; c < 3; ++c) xvo_intra_pred(left[c], top[c], tl[c], N, best, pred + c * n2);
+        int bestL;
+        uint64_t b = code_cu(cur, plane, Wp, x0, y0, ctu, pred, tu_mask, qp, lambda_fp8, recon, levels, &bestL);
+        if (tu_log2) tu_log2[cu] = (uint8_t)bestL;
+        if (mode_mv) { mode_mv[2 * cu] = (int16_t)best; mode_mv[2 * cu + 1] = 0; }
+        uint64_t cb = 2 + 6 + b;
+        if (cu_bits) cu_bits[cu] = cb;
+        total += cb;
+    }
+    free(pred); free(d);
+    return total;
+}
+
+/* ==================== In-loop deblocking (option XVO_DEBLOCK) ===================== */
+
+/* The standard's beta' (QP 0..51) and tC' (QP 0..53) tables, for 8-bit
+ * samples; scaled by 2^(B-8). */
+static const int deblock_beta[52] = {0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  6,  7,
+                                     8,  9,  10, 11, 12, 13, 14, 15, 16, 17, 18, 20, 22, 24, 26, 28, 30, 32,
+                                     34, 36, 38, 40, 42, 44, 46, 48, 50, 52, 54, 56, 58, 60, 62, 64};
+static const int deblock_tc[54] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0,  1,  1,  1,  1,  1,  1,  1,  1, 1,
+                                   2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6, 6, 7, 8, 9, 10, 11, 13, 14, 16, 18, 20, 22, 24};
+
+void xvo_deblock_params(int qp, int bs, int* beta, int* tc) {
+    *beta = deblock_beta[clampi(qp, 0, 51)] << (BITDEPTH - 8);
+    *tc = bs > 0 ? deblock_tc[clampi(qp + 2 * (bs - 1), 0, 53)] << (BITDEPTH - 8) : 0;
+}
+
+/* One 4-sample edge segment: s[k][i] is sample i of line k across the edge,
+ * i = 0..3 the p side (p3, p2, p1, p0) and 4..7 the q side (q0..q3). */
+void xvo_deblock_segment(int32_t s[4][8], int bs, int qp) {
+    int beta, tc;
+    xvo_deblock_params(qp, bs, &beta, &tc);
+#define P(k, i) s[k][3 - (i)]
+#define Q(k, i) s[k][4 + (i)]
+    int dp0 = abs(P(0, 2) - 2 * P(0, 1) + P(0, 0)), dp3 = abs(P(3, 2) - 2 * P(3, 1) + P(3, 0));
+    int dq0 = abs(Q(0, 2) - 2 * Q(0, 1) + Q(0, 0)), dq3 = abs(Q(3, 2) - 2 * Q(3, 1) + Q(3, 0));
+    int d = dp0 + dq0 + dp3 + dq3;
+    if (bs == 0 || d >= beta) return;
+    int strong = 1;
+    for (int k = 0; k < 4; k += 3) {
+        int dpq = k == 0 ? dp0 + dq0 : dp3 + dq3;
+        if (!(2 * dpq < (beta >> 2) && abs(P(k, 3) - P(k, 0)) + abs(Q(k, 0) - Q(k, 3)) < (beta >> 3) &&
+              abs(P(k, 0) - Q(k, 0)) < ((5 * tc + 1) >> 1)))
+            strong = 0;
+    }
+    int dEp = (dp0 + dp3) < ((beta + (beta >> 1)) >> 3), dEq = (dq0 + dq3) < ((beta + (beta >> 1)) >> 3);
+    for (int k = 0; k < 4; ++k) {
+        int p0 = P(k, 0), p1 = P(k, 1), p2 = P(k, 2), p3 = P(k, 3);
+        int q0 = Q(k, 0), q1 = Q(k, 1), q2 = Q(k, 2), q3 = Q(k, 3);
+        if (strong) {
+            P(k, 0) = clampi((p2 + 2 * p1 + 2 * p0 + 2 * q0 + q1 + 4) >> 3, p0 - 2 * tc, p0 + 2 * tc);
+            P(k, 1) = clampi((p2 + p1 + p0 + q0 + 2) >> 2, p1 - 2 * tc, p1 + 2 * tc);
+            P(k, 2) = clampi((2 * p3 + 3 * p2 + p1 + p0 + q0 + 4) >> 3, p2 - 2 * tc, p2 + 2 * tc);
+            Q(k, 0) = clampi((p1 + 2 * p0 + 2 * q0 + 2 * q1 + q2 + 4) >> 3, q0 - 2 * tc, q0 + 2 * tc);
+            Q(k, 1) = clampi((p0 + q0 + q1 + q2 + 2) >> 2, q1 - 2 * tc, q1 + 2 * tc);
+            Q(k, 2) = clampi((p0 + q0 + q1 + 3 * q2 + 2 * q3 + 4) >> 3, q2 - 2 * tc, q2 + 2 * tc);
+        } else {
+            int delta = (9 * (q0 - p0) - 3 * (q1 - p1) + 8) >> 4;
+            if (abs(delta) >= tc * 10) continue;
+            delta = clampi(delta, -tc, tc);
+            P(k, 0) = clampi(p0 + delta, 0, PIXMAX);
+            Q(k, 0) = clampi(q0 - delta, 0, PIXMAX);
+            if (dEp) P(k, 1) = clampi(p1 + clampi((((p2 + p0 + 1) >> 1) - p1 + delta) >> 1, -(tc >> 1), tc >> 1), 0, PIXMAX);
+            if (dEq) Q(k, 1) = clampi(q1 + clampi((((q2 + q0 + 1) >> 1) - q1 - delta) >> 1, -(tc >> 1), tc >> 1), 0, PIXMAX);
+        }
+    }
+#undef P
+#undef Q
+}
+
+/* Boundary strength of the edge between the samples (xp, yp) and (xq, yq) of
+ * neighbouring CUs or TUs (reading R5): 2 when intra; 1 when either TU has a
+ * non-zero level in any channel, or the two CUs' vectors differ by 4 quarter
+ * samples or more in x or y; else 0. */
+static int deblock_bs(int xp, int yp, int xq, int yq, int Hp, int Wp, int ctu, const uint8_t* tu_log2,
+                      const int16_t* levels, const int16_t* mv, int intra) {
+    if (intra) return 2;
+    int nx = Wp / ctu;
+    int64_t plane = (int64_t)Hp * Wp;
+    int cuP = (yp / ctu) * nx + xp / ctu, cuQ = (yq / ctu) * nx + xq / ctu;
+    int pts[2][2] = {{xp, yp}, {xq, yq}};
+    int cus[2] = {cuP, cuQ};
+    for (int s2 = 0; s2 < 2; ++s2) {
+        int TS = 1 << tu_log2[cus[s2]];
+        int tx = pts[s2][0] / TS * TS, ty = pts[s2][1] / TS * TS;
+        for (int c = 0; c < 3; ++c)
+            for (int y = 0; y < TS; ++y)
+                for (int x = 0; x < TS; ++x)
+                    if (levels[c * plane + (int64_t)(ty + y) * Wp + tx + x] != 0) return 1;
+    }
+    if (cuP != cuQ && (abs(mv[2 * cuP] - mv[2 * cuQ]) >= 4 || abs(mv[2 * cuP + 1] - mv[2 * cuQ + 1]) >= 4))
+        return 1;
+    return 0;
+}
+
+/* An edge at sample position e (x for vertical edges, y for horizontal ones)
+ * is filtered when it lies on the 8 x 8 grid inside the plane and is a CU
+ * boundary or a boundary of the TUs of the CU that contains sample e. */
+static int deblock_is_edge(int e, int other, int vertical, int Wp, int ctu, const uint8_t* tu_log2) {
+    if (e % 8 != 0 || e == 0) return 0;
+    if (e % ctu == 0) return 1;
+    int nx = Wp / ctu;
+    int x = vertical ? e : other, y = vertical ? other : e;
+    int TS = 1 << tu_log2[(y / ctu) * nx + x / ctu];
+    return e % TS == 0;
+}
+
+/* Deblocks one reconstructed frame [3][Hp][Wp] in place (reading R5): the
+ * standard's luma filter on all three channels, every vertical edge of the
+ * plane first, then every horizontal edge on the result; 4-sample segments;
+ * the boundary strength decided once per segment for the three channels. */
+void xvo_deblock_frame(uint16_t* rec, int Hp, int Wp, int ctu, int qp, const uint8_t* tu_log2,
+                       const int16_t* levels, const int16_t* mv, int intra) {
+    int64_t plane = (int64_t)Hp * Wp;
+    for (int pass = 0; pass < 2; ++pass) {
+        int vertical = pass == 0;
+        int E = vertical ? Wp : Hp, O = vertical ? Hp : Wp;
+        for (int e = 8; e < E; e += 8)
+            for (int o = 0; o < O; o += 4) {
+                if (!deblock_is_edge(e, o, vertical, Wp, ctu, tu_log2)) continue;
+                int bs = vertical ? deblock_bs(e - 1, o, e, o, Hp, Wp, ctu, tu_log2, levels, mv, intra)
+                                  : deblock_bs(o, e - 1, o, e, Hp, Wp, ctu, tu_log2, levels, mv, intra);
+                if (bs == 0) continue;
+                for (int c = 0; c < 3; ++c) {
+                    int32_t s[4][8];
+                    for (int k = 0; k < 4; ++k)
+                        for (int i = 0; i < 8; ++i) {
+                            int64_t at = vertical ? (int64_t)(o + k) * Wp + (e - 4 + i) : (int64_t)(e - 4 + i) * Wp + (o + k);
+                            s[k][i] = rec[c * plane + at];
+                        }
+                    xvo_deblock_segment(s, bs, qp);
+                    for (int k = 0; k < 4; ++k)
+                        for (int i = 0; i < 8; ++i) {
+                            int64_t at = vertical ? (int64_t)(o + k) * Wp + (e - 4 + i) : (int64_t)(e - 4 + i) * Wp + (o + k);
+                            rec[c * plane + at] = (uint16_t)s[k][i];
+                        }
+                }
+            }
+    }
+}
+
 /* ===================== C4: the closed-loop chain per group ==================== */
 
-int xvo_encode_planes(const uint16_t* planes, int G, int T, int Hp, int Wp, int ctu, int R,
-                      unsigned tu_mask, int qp, uint16_t* recon, int16_t* mv, uint32_t* cost,
-                      int16_t* mv_int, uint32_t* cost_int, int16_t* levels, uint8_t* tu_log2,
-                      uint64_t* bits) {
+int xvo_encode_planes_ex(const uint16_t* planes, int G, int T, int Hp, int Wp, int ctu, int R,
+                         unsigned tu_mask, int qp, unsigned flags, uint16_t* recon, int16_t* mv, uint32_t* cost,
+                         int16_t* mv_int, uint32_t* cost_int, int16_t* levels, uint8_t* tu_log2,
+                         uint64_t* bits) {
     int64_t lf8, lmv;
     xvo_lambdas(qp, &lf8, &lmv);
     int npu = (Hp / ctu) * (Wp / ctu);
@@ -516,6 +816,10 @@ int xvo_encode_planes(const uint16_t* planes, int G, int T, int Hp, int Wp, int 
     uint32_t* ci = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)npu);
     int16_t* mvq = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)npu);
     uint32_t* cq = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)npu);
+    /* levels and TU sizes are needed by the deblocking filter even when the
+     * caller does not ask for them */
+    int16_t* lev_f = levels ? levels : (int16_t*)malloc(sizeof(int16_t) * (size_t)(G * T) * (size_t)fsz);
+    uint8_t* tu_f = tu_log2 ? tu_log2 : (uint8_t*)malloc((size_t)G * T * (size_t)npu);
     for (int g = 0; g < G; ++g)
         for (int t = 0; t < T; ++t) {
             int64_t f = (int64_t)g * T + t;
@@ -530,16 +834,33 @@ int xvo_encode_planes(const uint16_t* planes, int G, int T, int Hp, int Wp, int 
                 memset(mvq, 0, sizeof(int16_t) * 2 * (size_t)npu);
                 memset(cq, 0, sizeof(uint32_t) * (size_t)npu);
             }
+            if (!ref && (flags & XVO_INTRA)) /* frame 0 intra: its modes take the vectors' place */
+                bits[f] = xvo_intra_frame(cur, Hp, Wp, ctu, tu_mask, qp, lf8, recon + f * fsz, lev_f + f * fsz,
+                                          tu_f + f * npu, mvq, NULL);
+            else
+                bits[f] = xvo_tqr_frame(cur, ref, mvq, Hp, Wp, ctu, tu_mask, qp, lf8, recon + f * fsz,
+                                        lev_f + f * fsz, tu_f + f * npu, NULL);
             if (mv) memcpy(mv + f * 2 * npu, mvq, sizeof(int16_t) * 2 * (size_t)npu);
             if (cost) memcpy(cost + f * npu, cq, sizeof(uint32_t) * (size_t)npu);
             if (mv_int) memcpy(mv_int + f * 2 * npu, mvi, sizeof(int16_t) * 2 * (size_t)npu);
             if (cost_int) memcpy(cost_int + f * npu, ci, sizeof(uint32_t) * (size_t)npu);
-            bits[f] = xvo_tqr_frame(cur, ref, mvq, Hp, Wp, ctu, tu_mask, qp, lf8, recon + f * fsz,
-                                    levels ? levels + f * fsz : NULL,
-                                    tu_log2 ? tu_log2 + f * npu : NULL, NULL);
+            /* in-loop deblocking: the deblocked frame is the next frame's
+             * reference and the output */
+            if (flags & XVO_DEBLOCK)
+                xvo_deblock_frame(recon + f * fsz, Hp, Wp, ctu, qp, tu_f + f * npu, lev_f + f * fsz, mvq,
+                                  !ref && (flags & XVO_INTRA));
         }
     free(mvi); free(ci); free(mvq); free(cq);
+    if (!levels) free(lev_f);
+    if (!tu_log2) free(tu_f);
     return 0;
+}
+
+int xvo_encode_planes(const uint16_t* planes, int G, int T, int Hp, int Wp, int ctu, int R, unsigned tu_mask,
+                      int qp, uint16_t* recon, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
+                      int16_t* levels, uint8_t* tu_log2, uint64_t* bits) {
+    return xvo_encode_planes_ex(planes, G, T, Hp, Wp, ctu, R, tu_mask, qp, 0u, recon, mv, cost, mv_int, cost_int,
+                                levels, tu_log2, bits);
 }
 
 /* ======================= Decoder (the inverse of C4..C13) ===================== */

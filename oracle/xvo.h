@@ -80,6 +80,28 @@ int xvo_encode_planes(const uint16_t* planes /*[G][T][3][Hp][Wp]*/, int G, int T
                       uint32_t* cost_int /*or NULL*/, int16_t* levels /*or NULL*/,
                       uint8_t* tu_log2 /*[G][T][nCU] or NULL*/, uint64_t* bits /*[G][T]*/);
 
+/* ---- options: frame-0 intra prediction and in-loop deblocking ---------------- */
+#define XVO_INTRA 1u   /* frame 0 intra predicted (planar / DC / angular per CU) */
+#define XVO_DEBLOCK 2u /* every reconstructed frame deblocked before it is a reference */
+int  xvo_intra_angle(int mode);
+int  xvo_intra_inv_angle(int angle);
+void xvo_intra_pred(const int32_t* left /*[2N]*/, const int32_t* top /*[2N]*/, int32_t tl, int N, int mode,
+                    int32_t* out /*[N][N]*/);
+void xvo_intra_refs(const uint16_t* plane /*[Hp][Wp]*/, int Hp, int Wp, int ctu, int x0, int y0,
+                    int32_t* left /*[2N]*/, int32_t* top /*[2N]*/, int32_t* tl);
+uint64_t xvo_intra_frame(const uint16_t* cur /*[3][Hp][Wp]*/, int Hp, int Wp, int ctu, unsigned tu_mask, int qp,
+                         int64_t lambda_fp8, uint16_t* recon, int16_t* levels /*or NULL*/,
+                         uint8_t* tu_log2 /*or NULL*/, int16_t* mode_mv /*[nCU][2] or NULL*/,
+                         uint64_t* cu_bits /*or NULL*/);
+void xvo_deblock_params(int qp, int bs, int* beta, int* tc);
+void xvo_deblock_segment(int32_t s[4][8], int bs, int qp);
+void xvo_deblock_frame(uint16_t* rec /*[3][Hp][Wp]*/, int Hp, int Wp, int ctu, int qp,
+                       const uint8_t* tu_log2 /*[nCU]*/, const int16_t* levels /*[3][Hp][Wp]*/,
+                       const int16_t* mv /*[nCU][2]*/, int intra);
+int xvo_encode_planes_ex(const uint16_t* planes, int G, int T, int Hp, int Wp, int ctu, int R, unsigned tu_mask,
+                         int qp, unsigned flags, uint16_t* recon, int16_t* mv, uint32_t* cost, int16_t* mv_int,
+                         uint32_t* cost_int, int16_t* levels, uint8_t* tu_log2, uint64_t* bits);
+
 /* ---- decoder: coded data -> reconstruction -> cube units ---------------------- */
 uint64_t xvo_decode_frame(const int16_t* levels /*[3][Hp][Wp]*/, const uint16_t* ref /*NULL: frame 0*/,
                           const int16_t* mv /*[nCU][2]*/, const uint8_t* tu_log2 /*[nCU]*/,
