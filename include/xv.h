@@ -59,7 +59,16 @@ typedef struct {
     int qp;                 /* QP_Y in [-12, 51]; qP = qp + 6 (B - 8) */
     int64_t lambda_fp8;     /* round(256 * lambda), lambda = 0.57 * 2^((qp - 12) / 3) */
     int64_t lambda_mv_fp16; /* round(65536 * sqrt(lambda)) */
+    unsigned flags;         /* options, 0 by default: XV_INTRA | XV_DEBLOCK (xv_encode_cube only) */
 } xv_params;
+
+/* Options beyond the default conventions (flat frame-0 prediction, no loop
+ * filter): XV_INTRA codes frame 0 with intra prediction (xv_intra_frame),
+ * XV_DEBLOCK deblocks every reconstructed frame before it becomes the next
+ * frame's reference and the output (xv_deblock_frame).  xv_encode_cube runs
+ * them; the batched path, serving and the decoder reject them (XV_EINVAL). */
+#define XV_INTRA 1u
+#define XV_DEBLOCK 2u
 
 typedef struct xv_ctx xv_ctx;
 
@@ -302,6 +311,49 @@ xv_status xv_pca_project(xv_ctx* ctx, const void* src, xv_dtype dtype, int bands
  * z: device float32 [npc][T][H][W]; dst: device float32 [bands][T][H][W]. */
 xv_status xv_pca_inverse(xv_ctx* ctx, const float* z, int npc, int bands, int T, int H, int W,
                          const double* mean, const double* components, float* dst, void* stream);
+
+/* ------------------------------------- options: intra frame, deblocking */
+
+/* Frame 0 of G groups with intra prediction (the XV_INTRA option).  Per CU
+ * (size N = ctu), in raster order: the 4N + 1 reference samples of each
+ * channel -- p[-1][y] and p[x][-1] for 0 <= x, y < 2N and the corner -- from
+ * the reconstruction of the CUs coded before it (left, top-left, top,
+ * top-right; the below-left never; nothing outside the plane), unavailable
+ * samples substituted as in H.265 (in the scan from p[-1][2N-1] up to the
+ * corner and along the top row, a missing first sample takes the first
+ * available one, every other missing sample its predecessor; none available:
+ * all 2^(B-1)); the 35 predictions of H.265 (0 planar, 1 DC, 2..34 angular
+ * with the standard's angles and two-tap interpolation; no reference
+ * smoothing, no boundary filters) of channel 0, the one with the least SATD
+ * (sum over 8 x 8 blocks of (sum |Hadamard| + 2) >> 2; ties to the lower
+ * mode) predicts all three channels; then the CU is transformed, quantised
+ * and reconstructed as in xv_transform_quant_recon.  Rate proxy per CU: 2 +
+ * 6 (mode) + the coded TUs.  The GPU runs the CUs as a wavefront (CU (r, c)
+ * after (r, c - 1) and (r - 1, c + 1)), (nx - 1) + 2 (ny - 1) + 1 launches.
+ * cur/recon/levels: as in xv_transform_quant_recon (levels may be NULL).
+ * mode_mv: int16 [G][nCU][2] at + g * pu_gstride * 2: (mode, 0) per CU.
+ * tu_log2 may be NULL; bits: group g's total is ADDED to bits[g * bits_gstride]. */
+xv_status xv_intra_frame(xv_ctx* ctx, const uint16_t* cur, int G, int64_t plane_gstride, int Hp, int Wp,
+                         const xv_params* p, int64_t pu_gstride, uint16_t* recon, int16_t* levels,
+                         uint8_t* tu_log2, int16_t* mode_mv, uint64_t* bits, int64_t bits_gstride, void* stream);
+
+/* Deblocks G reconstructed frames in place (the XV_DEBLOCK option): the H.265
+ * luma deblocking filter on each of the three channels.  Edges: the lines of
+ * the 8 x 8 grid (not the plane's border) where a CU begins or a TU of the CU
+ * holding the edge's first sample after it.  Per 4-sample segment, boundary
+ * strength 2 when intra != 0, else 1 when the TU on either side has a
+ * non-zero level in any channel or the two CUs' vectors differ by >= 4
+ * quarter samples in x or y, else 0 (no filtering); beta = beta'(Clip3(0,
+ * 51, qp)) 2^(B-8), tC = tC'(Clip3(0, 53, qp + 2 (bs - 1))) 2^(B-8); the
+ * standard's decisions (d < beta; strong when both test lines pass, else
+ * weak with |Delta| < 10 tC) and filters.  Every vertical edge of the frame
+ * first, then every horizontal edge on that result.  recon: as in
+ * xv_transform_quant_recon (read and written); tu_log2: uint8 [G][nCU] and
+ * levels (plane layout) of the frame; mv: int16 [G][nCU][2] (read only when
+ * intra == 0).  All at the given group strides. */
+xv_status xv_deblock_frame(xv_ctx* ctx, uint16_t* recon, int G, int64_t plane_gstride, int Hp, int Wp,
+                           const xv_params* p, int64_t pu_gstride, const uint8_t* tu_log2, const int16_t* levels,
+                           const int16_t* mv, int intra, void* stream);
 
 /* ------------------------------------------------------ decoder */
 

@@ -327,7 +327,7 @@ __device__ __forceinline__ uint64_t conc_row_inv(int lt, const uint16_t* __restr
     return sse;
 }
 
-template <int N, int NT, bool kCoherent>
+template <int N, int NT, bool kCoherent, bool kPredGiven>
 __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
                                 int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
                                 int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
@@ -349,9 +349,11 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
         return reinterpret_cast<int*>(slots + s * tqr_conc_slot_bytes(N) + align16((size_t)3 * 3 * NN * 2));
     };
 
-    // 1. current samples, motion-compensated prediction
+    // 1. current samples, motion-compensated prediction (kPredGiven: the
+    // caller has put both in shared memory, s_cur and s_pred)
     if (tid < 3) { s_sse[tid] = 0ull; s_bits[tid] = 0u; }
-    load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
+    if constexpr (kPredGiven) __syncthreads();
+    else load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
 
     // task ranges of the allowed sizes (slot s: TU size 4 << s)
     int cum[NS + 1];
@@ -465,15 +467,19 @@ __host__ __device__ constexpr size_t tqr_smem_bytes(int N) {
 
 // Transform/quantise/reconstruct the CU at (x0, y0).  cur/ref/recon/levels:
 // the group's frame [3][Hp][Wp] (ref == nullptr: first frame).  Returns the
-// CU's rate-proxy bits; writes recon (and levels) and *tu_log2.
-template <int N, int NT, bool kCoherent = false>
+// CU's rate-proxy bits; writes recon (and levels) and *tu_log2.  kPredGiven:
+// the current samples and the prediction are already in shared memory (cur
+// u16 [3][N][N] at offset 0, the prediction right after it), written before
+// a barrier; cur, ref and the vector are then not read, and the bits count
+// no vector (ref must be nullptr).
+template <int N, int NT, bool kCoherent = false, bool kPredGiven = false>
 __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
                            int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
                            int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
                            uint8_t* tu_log2, unsigned char* smem) {
     if constexpr (N <= 16) {
-        return tqr_cu_conc<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask, lf8, recon,
-                                             levels, tu_log2, smem);
+        return tqr_cu_conc<N, NT, kCoherent, kPredGiven>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask,
+                                                         lf8, recon, levels, tu_log2, smem);
     }
     const int tid = threadIdx.x;
     uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
@@ -485,7 +491,8 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
     int16_t* s_hbuf = reinterpret_cast<int16_t*>(smem + tqr_off_hbuf(N));
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + tqr_off_red(N));
 
-    load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
+    if constexpr (!kPredGiven)
+        load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
 
     int64_t bestJ = INT64_MAX;
     int bestL = 0;

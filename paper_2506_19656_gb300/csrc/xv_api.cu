@@ -23,7 +23,7 @@ struct xv_ctx {
     size_t budget = 0;  // 0 = unlimited
     size_t held = 0;
     // scratch of the single-cube calls
-    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax, met_part, met_out, pca_part;
+    DevBuf mm_enc, bandq, psnr_part, psnr_out, tmp_mv, tmp_bits, tmp_minmax, met_part, met_out, pca_part, tmp_cbf;
     // scratch of the batched path
     DevBuf b_jobs, b_items, b_rowdone, b_depcnt, b_ctl, b_bits, b_bandq, b_minmax;
     long long wait_budget = 4000000000LL;  // cycles per dependency wait (about 2 s)
@@ -139,6 +139,7 @@ bool valid_params(const xv_params* p) {
         if ((p->tu_mask & (1u << k)) && (1 << k) <= p->ctu) any = true;
     if (!any) { set_error("tu_mask 0x%x allows no TU size <= ctu %d", p->tu_mask, p->ctu); return false; }
     if (p->qp < -12 || p->qp > 51) { set_error("qp %d: must be in [-12, 51]", p->qp); return false; }
+    if (p->flags & ~(XV_INTRA | XV_DEBLOCK)) { set_error("flags 0x%x: only XV_INTRA and XV_DEBLOCK exist", p->flags); return false; }
     if (xvd::me_smem_bytes(p->ctu, p->search_range) > 227 * 1024) {
         set_error("ctu %d with search range %d needs more shared memory than a block has", p->ctu, p->search_range);
         return false;
@@ -147,6 +148,14 @@ bool valid_params(const xv_params* p) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// The intra and deblocking options run on the per-frame path only.
+bool no_options(const xv_params* p, const char* where) {
+    if (p->flags == 0) return true;
+    set_error("%s: the XV_INTRA / XV_DEBLOCK options are supported by xv_encode_cube and the per-frame calls only",
+              where);
+    return false;
+}
 
 bool valid_planes(const void* a, const void* b, const void* c, int64_t gstride) {
     if (!aligned16(a) || !aligned16(b) || !aligned16(c) || gstride % 8 != 0) {
@@ -297,7 +306,7 @@ void xv_destroy(xv_ctx* c) {
     DeviceGuard g(c->device);
     if (c->serve) { xvh::serve_destroy(c->serve); c->serve = nullptr; }
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax,
+    DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax, &c->tmp_cbf,
                       &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
                       &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals};
     for (DevBuf* b : bufs) release(c, *b);
@@ -322,6 +331,7 @@ xv_status xv_params_init(xv_params* p, int ctu, int R, unsigned tu_mask, int qp)
     q.search_range = R;
     q.tu_mask = tu_mask;
     q.qp = qp;
+    q.flags = 0u;
     const double lambda = 0.57 * std::pow(2.0, (qp - 12) / 3.0);
     q.lambda_fp8 = std::llround(256.0 * lambda);
     q.lambda_mv_fp16 = std::llround(65536.0 * std::sqrt(lambda));
@@ -398,6 +408,51 @@ xv_status xv_transform_quant_recon(xv_ctx* c, const uint16_t* cur, const uint16_
     return check_launch(xvh::launch_tqr_frame(cur, ref, mv, G, gstride, Hp, Wp, p, pu_gstride, recon, levels, tu_log2,
                                               bits, bits_gstride, (cudaStream_t)stream),
                         "transform_quant_recon");
+}
+
+xv_status xv_intra_frame(xv_ctx* c, const uint16_t* cur, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
+                         int64_t pu_gstride, uint16_t* recon, int16_t* levels, uint8_t* tu_log2, int16_t* mode_mv,
+                         uint64_t* bits, int64_t bits_gstride, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    if (!cur || !recon || !bits || !mode_mv) { set_error("cur, recon, mode_mv and bits are required"); return XV_EINVAL; }
+    if (!valid_planes(cur, cur, recon, gstride)) return XV_EINVAL;
+    if (levels && !valid_planes(levels, levels, levels, gstride)) return XV_EINVAL;
+    DeviceGuard g(c->device);
+    uint64_t launched = 0;
+    xv_status s = check_launch(xvh::launch_intra_frame(cur, G, gstride, Hp, Wp, p, mode_mv, pu_gstride, recon, levels,
+                                                       tu_log2, bits, bits_gstride, (cudaStream_t)stream, &launched),
+                               "intra frame");
+    c->launches += launched;
+    return s;
+}
+
+// The coded-block scratch of deblocking, G (Hp / 4) (Wp / 4) bytes.
+static xv_status deblock_into(xv_ctx* c, uint16_t* recon, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
+                              int64_t pu_gstride, const uint8_t* tu_log2, const int16_t* levels, const int16_t* mv,
+                              int intra, cudaStream_t st) {
+    xv_status s = ensure(c, c->tmp_cbf, (size_t)G * (Hp / 4) * (Wp / 4));
+    if (s) return s;
+    uint64_t launched = 0;
+    s = check_launch(xvh::launch_deblock_frame(recon, G, gstride, Hp, Wp, p->ctu, p->qp, tu_log2, pu_gstride, levels, mv,
+                                               intra, (uint8_t*)c->tmp_cbf.ptr, st, &launched),
+                     "deblocking");
+    c->launches += launched;
+    return s;
+}
+
+xv_status xv_deblock_frame(xv_ctx* c, uint16_t* recon, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
+                           int64_t pu_gstride, const uint8_t* tu_log2, const int16_t* levels, const int16_t* mv,
+                           int intra, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    if (!recon || !tu_log2 || (!intra && (!levels || !mv))) {
+        set_error("recon and tu_log2 (and levels and mv unless intra) are required");
+        return XV_EINVAL;
+    }
+    if (!valid_planes(recon, recon, levels ? (const void*)levels : (const void*)recon, gstride)) return XV_EINVAL;
+    DeviceGuard g(c->device);
+    return deblock_into(c, recon, G, gstride, Hp, Wp, p, pu_gstride, tu_log2, levels, mv, intra, (cudaStream_t)stream);
 }
 
 xv_status xv_psnr(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* planes,
@@ -576,6 +631,10 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (!valid_job(j)) return XV_EINVAL;
     if (!r) { set_error("result is NULL"); return XV_EINVAL; }
+    if ((j->p.flags & XV_DEBLOCK) && (!j->levels || !j->tu_log2)) {
+        set_error("deblocking (XV_DEBLOCK) needs the job's levels and tu_log2 buffers");
+        return XV_EINVAL;
+    }
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const xv_params& p = j->p;
@@ -615,17 +674,31 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
     for (int t = 0; t < T; ++t) {
         const uint16_t* cur = j->planes + t * fsz;
         const uint16_t* ref = t > 0 ? j->recon + (t - 1) * fsz : nullptr;
-        c->launches += kLaunchTqr + (ref ? kLaunchMe : 0);
+        const bool intra = !ref && (p.flags & XV_INTRA);
+        if (intra) {  // frame 0 with intra prediction; its modes take the vectors' place
+            uint64_t launched = 0;
+            s = check_launch(xvh::launch_intra_frame(cur, G, T * fsz, Hp, Wp, &p, mv, T * npu, j->recon,
+                                                     j->levels, j->tu_log2, bits, T, st, &launched),
+                             "intra frame");
+            c->launches += launched;
+            if (s) return s;
+        }
+        if (!intra) c->launches += kLaunchTqr + (ref ? kLaunchMe : 0);
         if (ref) {
             if ((s = check_launch(xvh::launch_me_frame(cur, ref, G, T * fsz, Hp, Wp, &p, mv + t * npu * 2,
                                                        j->cost ? j->cost + t * npu : nullptr, nullptr, nullptr, T * npu, st),
                                   "motion_search")))
                 return s;
         }
-        if ((s = check_launch(xvh::launch_tqr_frame(cur, ref, mv + t * npu * 2, G, T * fsz, Hp, Wp, &p, T * npu,
+        if (!intra &&
+            (s = check_launch(xvh::launch_tqr_frame(cur, ref, mv + t * npu * 2, G, T * fsz, Hp, Wp, &p, T * npu,
                                                     j->recon + t * fsz, j->levels ? j->levels + t * fsz : nullptr,
                                                     j->tu_log2 ? j->tu_log2 + t * npu : nullptr, bits + t, T, st),
                               "transform_quant_recon")))
+            return s;
+        if ((p.flags & XV_DEBLOCK) &&
+            (s = deblock_into(c, j->recon + t * fsz, G, T * fsz, Hp, Wp, &p, T * npu, j->tu_log2 + t * npu,
+                              j->levels + t * fsz, mv + t * npu * 2, intra ? 1 : 0, st)))
             return s;
     }
     r->status = XV_OK;
@@ -680,7 +753,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (njobs < 1 || njobs > 255 || !jobs || !results) { set_error("njobs %d: must be 1..255 with jobs and results", njobs); return XV_EINVAL; }
     for (int i = 0; i < njobs; ++i)
-        if (!valid_job(&jobs[i])) return XV_EINVAL;
+        if (!valid_job(&jobs[i]) || !no_options(&jobs[i].p, "xv_encode_batch")) return XV_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t caller = (cudaStream_t)stream;
     xv_status s;
@@ -1003,7 +1076,7 @@ xv_status xv_decode_frame(xv_ctx* c, const int16_t* levels, const uint16_t* ref,
                           const uint8_t* tu_log2, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
                           int64_t pu_gstride, uint16_t* recon, uint64_t* bits, int64_t bits_gstride, void* stream) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
-    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu) || !no_options(p, "xv_decode_frame")) return XV_EINVAL;
     if (!levels || !tu_log2 || !recon || !bits || (ref && !mv)) {
         set_error("levels, tu_log2, recon, bits (and mv with ref) are required");
         return XV_EINVAL;
@@ -1033,7 +1106,7 @@ xv_status xv_decode_batch(xv_ctx* c, const xv_djob* jobs, int njobs, uint64_t* t
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (njobs < 1 || njobs > 255 || !jobs) { set_error("njobs %d: must be 1..255 with jobs", njobs); return XV_EINVAL; }
     for (int i = 0; i < njobs; ++i)
-        if (!valid_djob(&jobs[i])) return XV_EINVAL;
+        if (!valid_djob(&jobs[i]) || !no_options(&jobs[i].p, "xv_decode_batch")) return XV_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t caller = (cudaStream_t)stream;
     xv_status s;
@@ -1218,7 +1291,9 @@ xv_status xv_serve_start(xv_ctx* c, int max_slots, int frames_per_tick) {
 xv_status xv_serve_submit(xv_ctx* c, const xv_request* r, uint64_t* ticket) {
     if (!c || !c->serve) { set_error("serving not started"); return XV_EINVAL; }
     if (!r || !ticket) { set_error("request and ticket are required"); return XV_EINVAL; }
-    if (!valid_cube(r->src, r->dtype, r->bands, r->T, r->H, r->W) || !valid_params(&r->p)) return XV_EINVAL;
+    if (!valid_cube(r->src, r->dtype, r->bands, r->T, r->H, r->W) || !valid_params(&r->p) ||
+        !no_options(&r->p, "xv_serve_submit"))
+        return XV_EINVAL;
     return xvh::serve_submit(c->serve, r, ticket);
 }
 

@@ -144,6 +144,14 @@ cudaError_t launch_prepare_bands(const void* src, xv_dtype dt, int bands, int64_
 cudaError_t launch_bits_totals(const JobDev* jobs, int njobs, unsigned long long* totals, cudaStream_t st);
 // Block sizes the persistent kernel is built for (the autotuner picks one).
 constexpr int kPersistBlockSizes[4] = {128, 192, 256, 512};
+// Frame-0 intra coding of G groups: a wavefront of launches (*launches counts them).
+cudaError_t launch_intra_frame(const uint16_t* cur, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
+                               int16_t* mv, int64_t pu_gstride, uint16_t* recon, int16_t* levels, uint8_t* tu_log2,
+                               uint64_t* bits, int64_t bits_gstride, cudaStream_t st, uint64_t* launches);
+// In-place deblocking of G reconstructed frames; cbf: G (Hp / 4) (Wp / 4) bytes of scratch.
+cudaError_t launch_deblock_frame(uint16_t* recon, int G, int64_t gstride, int Hp, int Wp, int ctu, int qp,
+                                 const uint8_t* tu_log2, int64_t pu_gstride, const int16_t* levels,
+                                 const int16_t* mv, int intra, uint8_t* cbf, cudaStream_t st, uint64_t* launches);
 // decode: the decoding instantiation (the jobs' levels, vectors and TU sizes
 // are inputs, recon and bits outputs) instead of the encoder.
 cudaError_t launch_persist(int ctu, int nt, bool decode, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl,

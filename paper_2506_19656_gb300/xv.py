@@ -15,6 +15,7 @@ from .build import LIB
 XV_OK, XV_EINVAL, XV_ENOMEM, XV_EBUDGET, XV_ETIMEOUT, XV_EBUSY, XV_ECUDA, XV_ECANCELLED, XV_ENOTFOUND = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 XV_F32, XV_U16 = 0, 1
+XV_INTRA, XV_DEBLOCK = 1, 2  # xv_params.flags options (xv_encode_cube and the per-frame calls)
 XV_MAX_BANDS = 16
 
 _vp = ctypes.c_void_p
@@ -24,7 +25,7 @@ _i64 = ctypes.c_int64
 
 class xv_params(ctypes.Structure):
     _fields_ = [("bit_depth", _i), ("ctu", _i), ("search_range", _i), ("tu_mask", ctypes.c_uint),
-                ("qp", _i), ("lambda_fp8", _i64), ("lambda_mv_fp16", _i64)]
+                ("qp", _i), ("lambda_fp8", _i64), ("lambda_mv_fp16", _i64), ("flags", ctypes.c_uint)]
 
 
 class xv_job(ctypes.Structure):
@@ -79,6 +80,9 @@ _SIGS = {
     "xv_psnr": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "xv_decode_frame": [_vp, _vp, _vp, _vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp, _i64,
                         _vp],
+    "xv_intra_frame": [_vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp, _vp, _vp, _vp, _i64,
+                       _vp],
+    "xv_deblock_frame": [_vp, _vp, _i, _i64, _i, _i, ctypes.POINTER(xv_params), _i64, _vp, _vp, _vp, _i, _vp],
     "xv_decode_batch": [_vp, ctypes.POINTER(xv_djob), _i, ctypes.POINTER(ctypes.c_uint64), _vp],
     "xv_unpack": [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _vp],
     "xv_pca_fit": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp],
@@ -219,6 +223,20 @@ def xv_transform_quant_recon(ctx: Context, cur, ref, mv, G: int, plane_gstride: 
     check(lib().xv_transform_quant_recon(ctx.handle, _ptr(cur), _ptr(ref), _ptr(mv), G, plane_gstride, Hp, Wp,
                                          ctypes.byref(p), pu_gstride, _ptr(recon), _ptr(levels), _ptr(tu_log2),
                                          _ptr(bits), bits_gstride, _stream(stream)), "xv_transform_quant_recon")
+
+
+def xv_intra_frame(ctx: Context, cur, G: int, plane_gstride: int, Hp: int, Wp: int, p: xv_params, pu_gstride: int,
+                   recon, levels, tu_log2, mode_mv, bits, bits_gstride: int, stream=None):
+    check(lib().xv_intra_frame(ctx.handle, _ptr(cur), G, plane_gstride, Hp, Wp, ctypes.byref(p), pu_gstride,
+                               _ptr(recon), _ptr(levels), _ptr(tu_log2), _ptr(mode_mv), _ptr(bits), bits_gstride,
+                               _stream(stream)), "xv_intra_frame")
+
+
+def xv_deblock_frame(ctx: Context, recon, G: int, plane_gstride: int, Hp: int, Wp: int, p: xv_params,
+                     pu_gstride: int, tu_log2, levels, mv, intra: bool, stream=None):
+    check(lib().xv_deblock_frame(ctx.handle, _ptr(recon), G, plane_gstride, Hp, Wp, ctypes.byref(p), pu_gstride,
+                                 _ptr(tu_log2), _ptr(levels), _ptr(mv), int(bool(intra)), _stream(stream)),
+          "xv_deblock_frame")
 
 
 def xv_decode_frame(ctx: Context, levels, ref, mv, tu_log2, G: int, plane_gstride: int, Hp: int, Wp: int,
