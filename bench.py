@@ -409,6 +409,143 @@ def run_decode(args):
     ctx.close()
 
 
+def run_options(args):
+    """Intra / deblocking run: each step encodes the workload's cubes through
+    xv_encode_cube with XV_INTRA | XV_DEBLOCK (frame 0 intra predicted, every
+    frame deblocked before it becomes a reference); "plain" is the same
+    per-frame path without the options.  Also timed alone: the deblocking of
+    every frame (HBM roofline: per plane sample the levels read and the
+    reconstruction read and written, 6 B) and the intra frame 0."""
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2506_19656_gb300 import build, xv
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg, lengths, _, _, jobs, bufs = workload_jobs(args.workload, args.frames, dev)
+    ctx = xv.Context(0)
+    opt_jobs = []
+    for j in jobs:
+        oj = xv.xv_job.from_buffer_copy(j)
+        oj.p.flags = xv.XV_INTRA | xv.XV_DEBLOCK
+        opt_jobs.append(oj)
+    work_mpx = len(QPS) * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(step, k, before=None):
+        ms = []
+        for _ in range(k):
+            if before:
+                before()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    def with_options():
+        return [xv.xv_encode_cube(ctx, j) for j in opt_jobs]
+
+    for _ in range(args.warmup):
+        with_options()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = xv.xv_ctx_launches(ctx)
+    step_ms = timed(with_options, args.steps)
+    launches = xv.xv_ctx_launches(ctx) - launches0
+    clk = clocks.stop()
+    value = work_mpx / (sum(step_ms) / args.steps / 1e3)
+    res = with_options()
+
+    plain = None
+    if not args.no_plain:
+        for _ in range(2):
+            [xv.xv_encode_cube(ctx, j) for j in jobs]
+        pm = timed(lambda: [xv.xv_encode_cube(ctx, j) for j in jobs], max(3, min(args.steps, 5)))
+        plain = {"value": work_mpx / (statistics.mean(pm) / 1e3), "ms_per_step": statistics.mean(pm),
+                 "path": "xv_encode_cube per encode without the options (flat frame 0, no loop filter)"}
+    with_options()  # the buffers hold the options' coded data again
+
+    # deblocking alone: the frames of every encode as the "groups" of
+    # xv_deblock_frame calls, on a fresh copy of the reconstruction
+    db = []
+    for b, j in zip(bufs, opt_jobs):
+        G, Tn, _, Hp, Wp = b["recon"].shape
+        npu = b["tu_log2"].shape[2]
+        db.append(dict(src=b["recon"].reshape(G * Tn, 3, Hp, Wp), work=torch.empty_like(b["recon"]).reshape(G * Tn, 3, Hp, Wp),
+                       tu=b["tu_log2"].reshape(G * Tn, npu), lev=b["levels"].reshape(G * Tn, 3, Hp, Wp),
+                       mv=b["mv"].reshape(G * Tn, npu, 2), n=G * Tn, Hp=Hp, Wp=Wp, npu=npu, p=j.p))
+
+    def refresh():
+        for d in db:
+            d["work"].copy_(d["src"])
+
+    def deblock_all():  # in calls of at most 255 frames (the per-call group limit)
+        for d in db:
+            for a in range(0, d["n"], 255):
+                b_ = min(d["n"], a + 255)
+                xv.xv_deblock_frame(ctx, d["work"][a:b_], b_ - a, 3 * d["Hp"] * d["Wp"], d["Hp"], d["Wp"], d["p"],
+                                    d["npu"], d["tu"][a:b_], d["lev"][a:b_], d["mv"][a:b_], False)
+    refresh()
+    deblock_all()
+    dm = timed(deblock_all, max(3, min(args.steps, 10)), before=refresh)
+    samples = sum(d["work"].numel() for d in db)
+    algo = 6 * samples
+    dms = statistics.mean(dm)
+    peak = 6660.3
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    achieved = algo / (dms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_cbf + k_deblock<vertical> + k_deblock<horizontal> (deblocking)",
+                "kernel_ms": dms,
+                "work_per_launch": f"{algo:.4g} B for {sum(d['n'] for d in db)} frames (levels read, reconstruction "
+                                   f"read and written: 6 B per plane sample)",
+                "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # the intra frame 0 of every encode alone
+    def intra_all():
+        for b, j in zip(bufs, opt_jobs):
+            G, Tn, _, Hp, Wp = b["recon"].shape
+            npu = b["tu_log2"].shape[2]
+            b["bits"][:, 0].zero_()
+            xv.xv_intra_frame(ctx, b["planes"][:, 0], G, Tn * 3 * Hp * Wp, Hp, Wp, j.p, Tn * npu, b["recon"][:, 0],
+                              b["levels"][:, 0], b["tu_log2"][:, 0], b["mv"][:, 0], b["bits"][:, 0], Tn)
+    intra_all()
+    im = timed(intra_all, max(3, min(args.steps, 10)))
+    intra_mpx = len(QPS) * len(lengths) * cfg.bands * cfg.H * cfg.W / 1e6
+    line = {
+        "metric": "Mpx·band/s of ME+transform/quant/recon with frame-0 intra prediction and in-loop deblocking "
+                  "(bit-exact), per-frame path",
+        "value": value, "unit": "Mpx·band/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": cfg.name, "qps": list(QPS), "ctu": cfg.ctu, "frames": lengths if len(lengths) > 1 else cfg.T,
+                   "bands": cfg.bands, "path": "xv_encode_cube with XV_INTRA | XV_DEBLOCK",
+                   "l2": "flushed before every step (256 MB write)", "parallelism": "replicas1"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "plain": plain, "roofline": roofline,
+        "intra_frame": {"ms_per_step": statistics.mean(im), "value": intra_mpx / (statistics.mean(im) / 1e3),
+                        "unit": "Mpx·band/s", "what": "frame 0 of every encode through xv_intra_frame"},
+        "psnr_mean": [r["psnr_mean"] for r in res], "bpppb": [r["bpppb"] for r in res],
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_metrics(args):
     """Quality-metric run: the workload's encodes are made once, untimed; each
     timed step computes SSIM per band (xv_ssim) and the mean spectral angle
@@ -715,6 +852,8 @@ def main():
     ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
     ap.add_argument("--metrics", action="store_true", help="the SSIM / spectral-angle run instead")
     ap.add_argument("--pca", action="store_true", help="the PCA (fit, project, inverse) run instead")
+    ap.add_argument("--options", action="store_true",
+                    help="the per-frame path with frame-0 intra prediction and in-loop deblocking instead")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--frames-per-tick", type=int, default=8)
@@ -735,6 +874,8 @@ def main():
         return run_metrics(args)
     if args.pca:
         return run_pca(args)
+    if args.options:
+        return run_options(args)
 
     import numpy as np
     import torch
