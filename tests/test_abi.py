@@ -78,3 +78,25 @@ def test_widened_entry_points_reject_bad_arguments_without_gpu(libxv):
     assert lib.xv_pca_fit(null, null, i(0), i(3), i(1), i(8), i(8), null, null, null, null) == -1
     assert lib.xv_pca_project(null, null, i(0), i(3), i(1), i(8), i(8), null, null, i(2), null, null) == -1
     assert lib.xv_pca_inverse(null, null, i(2), i(3), i(1), i(8), i(8), null, null, null, null) == -1
+
+
+def test_option_entry_points_and_params_layout_without_gpu(libxv):
+    """xv_intra_frame and xv_deblock_frame validate before the device (NULL
+    context -> XV_EINVAL); xv_params ends with the options word, which
+    xv_params_init sets to 0, and the option bits are the header's."""
+    from paper_2506_19656_gb300 import xv
+    lib = libxv
+    vp, i, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.xv_intra_frame.restype = i
+    lib.xv_deblock_frame.restype = i
+    null = vp(0)
+    assert lib.xv_intra_frame(null, null, i(1), i64(768), i(16), i(16), null, i64(1), null, null, null, null, null,
+                              i64(1), null) == -1
+    assert lib.xv_deblock_frame(null, null, i(1), i64(768), i(16), i(16), null, i64(1), null, null, null, i(0),
+                                null) == -1
+    assert xv.xv_params.flags.offset == 40 and ctypes.sizeof(xv.xv_params) == 48
+    p = xv.xv_params_init(16, 32, 0b11100, 27)
+    assert p.flags == 0
+    header = open(os.path.join(ROOT, "include", "xv.h")).read()
+    assert re.search(r"#define XV_INTRA 1u", header) and re.search(r"#define XV_DEBLOCK 2u", header)
+    assert (xv.XV_INTRA, xv.XV_DEBLOCK) == (1, 2)
