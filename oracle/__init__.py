@@ -98,6 +98,9 @@ def lib():
             L.xvo_decode_frame.argtypes = [vp, vp, vp, vp, i, i, i, i, vp]
             L.xvo_decode_frame.restype = ctypes.c_uint64
             L.xvo_decode_planes.argtypes = [vp, vp, vp, i, i, i, i, i, i, vp, vp]
+            L.xvo_decode_intra_frame.argtypes = [vp, vp, vp, i, i, i, i, vp]
+            L.xvo_decode_intra_frame.restype = ctypes.c_uint64
+            L.xvo_decode_planes_ex.argtypes = [vp, vp, vp, i, i, i, i, i, i, u, vp, vp]
             L.xvo_unpack.argtypes = [vp, i, i, i, i, i, i, vp, vp]
             L.xvo_ssim_window.argtypes = [vp]
             L.xvo_ssim_image.argtypes = [vp, vp, i, i, ctypes.c_double, vp]
@@ -390,17 +393,27 @@ def decode_frame(levels: np.ndarray, ref, mv: np.ndarray, tu_log2: np.ndarray, c
     return recon, int(bits)
 
 
-def decode_planes(levels: np.ndarray, mv: np.ndarray, tu_log2: np.ndarray, ctu: int, qp: int):
-    """The whole chain [G,T,3,Hp,Wp]: frames in order per group.  Returns
-    dict(recon, bits[G,T])."""
+def decode_planes(levels: np.ndarray, mv: np.ndarray, tu_log2: np.ndarray, ctu: int, qp: int, flags: int = 0):
+    """The whole chain [G,T,3,Hp,Wp]: frames in order per group (flags: INTRA,
+    DEBLOCK, as the encoder used them).  Returns dict(recon, bits[G,T])."""
     levels = np.ascontiguousarray(levels, np.int16)
     G, T, _, Hp, Wp = levels.shape
     recon = np.zeros(levels.shape, np.uint16)
     bits = np.zeros((G, T), np.uint64)
-    lib().xvo_decode_planes(_p(levels), _p(np.ascontiguousarray(mv, np.int16)),
-                            _p(np.ascontiguousarray(tu_log2, np.uint8)), G, T, Hp, Wp, ctu, qp, _p(recon),
-                            _p(bits))
+    lib().xvo_decode_planes_ex(_p(levels), _p(np.ascontiguousarray(mv, np.int16)),
+                               _p(np.ascontiguousarray(tu_log2, np.uint8)), G, T, Hp, Wp, ctu, qp, flags, _p(recon),
+                               _p(bits))
     return dict(recon=recon, bits=bits)
+
+
+def decode_intra_frame(levels: np.ndarray, mode_mv: np.ndarray, tu_log2: np.ndarray, ctu: int, qp: int):
+    """Frame 0 [3,Hp,Wp] decoded with intra prediction.  Returns (recon, bits)."""
+    levels = np.ascontiguousarray(levels, np.int16)
+    _, Hp, Wp = levels.shape
+    recon = np.zeros(levels.shape, np.uint16)
+    bits = lib().xvo_decode_intra_frame(_p(levels), _p(np.ascontiguousarray(mode_mv, np.int16)),
+                                        _p(np.ascontiguousarray(tu_log2, np.uint8)), Hp, Wp, ctu, qp, _p(recon))
+    return recon, int(bits)
 
 
 def unpack(recon: np.ndarray, mm: np.ndarray, bands: int, H: int, W: int) -> np.ndarray:

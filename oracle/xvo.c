@@ -913,18 +913,78 @@ uint64_t xvo_decode_frame(const int16_t* levels, const uint16_t* ref, const int1
     return total;
 }
 
-int xvo_decode_planes(const int16_t* levels, const int16_t* mv, const uint8_t* tu_log2, int G, int T,
-                      int Hp, int Wp, int ctu, int qp, uint16_t* recon, uint64_t* bits) {
+/* Frame 0 decoded with intra prediction (the inverse of xvo_intra_frame):
+ * CUs in raster order, each predicted from its decoded neighbours with the
+ * mode mode_mv[cu][0] (clamped to 0..34), then its TUs as in
+ * xvo_decode_frame.  Returns the rate proxy, 2 + 6 + the coded TUs per CU. */
+uint64_t xvo_decode_intra_frame(const int16_t* levels, const int16_t* mode_mv, const uint8_t* tu_log2, int Hp,
+                                int Wp, int ctu, int qp, uint16_t* recon) {
+    int nx = Wp / ctu, ny = Hp / ctu, n2 = ctu * ctu;
+    int64_t plane = (int64_t)Hp * Wp;
+    int32_t* pred = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n2);
+    int32_t left[128], top[128], tl;
+    uint64_t total = 0;
+    for (int cu = 0; cu < nx * ny; ++cu) {
+        int x0 = (cu % nx) * ctu, y0 = (cu / nx) * ctu;
+        int mode = clampi(mode_mv[2 * cu], 0, 34);
+        for (int c = 0; c < 3; ++c) {
+            xvo_intra_refs(recon + c * plane, Hp, Wp, ctu, x0, y0, left, top, &tl);
+            xvo_intra_pred(left, top, tl, ctu, mode, pred + c * n2);
+        }
+        int L = tu_log2[cu], N = 1 << L;
+        uint64_t bits = 2 + 6;
+        int32_t D[32 * 32], Rr[32 * 32];
+        for (int c = 0; c < 3; ++c)
+            for (int ty = 0; ty < ctu; ty += N)
+                for (int tx = 0; tx < ctu; tx += N) {
+                    uint64_t tb = 1; /* coded-block flag */
+                    for (int y = 0; y < N; ++y)
+                        for (int x = 0; x < N; ++x) {
+                            int lv = levels[c * plane + (int64_t)(y0 + ty + y) * Wp + x0 + tx + x];
+                            if (lv != 0) tb += (uint64_t)(2 * L + xvo_ue_len_se(lv));
+                            D[y * N + x] = xvo_dequant(lv, qp, L);
+                        }
+                    bits += tb;
+                    xvo_inv_transform(N, D, Rr);
+                    for (int y = 0; y < N; ++y)
+                        for (int x = 0; x < N; ++x)
+                            recon[c * plane + (int64_t)(y0 + ty + y) * Wp + x0 + tx + x] = (uint16_t)clampi(
+                                pred[c * n2 + (ty + y) * ctu + tx + x] + Rr[y * N + x], 0, PIXMAX);
+                }
+        total += bits;
+    }
+    free(pred);
+    return total;
+}
+
+/* The whole chain per group, frames in order; with XVO_INTRA frame 0 is
+ * decoded with intra prediction, with XVO_DEBLOCK every decoded frame is
+ * deblocked before it is the next frame's reference (as the encoder does). */
+int xvo_decode_planes_ex(const int16_t* levels, const int16_t* mv, const uint8_t* tu_log2, int G, int T, int Hp,
+                         int Wp, int ctu, int qp, unsigned flags, uint16_t* recon, uint64_t* bits) {
     int npu = (Hp / ctu) * (Wp / ctu);
     int64_t fsz = 3 * (int64_t)Hp * Wp;
     for (int g = 0; g < G; ++g)
         for (int t = 0; t < T; ++t) {
             int64_t f = (int64_t)g * T + t;
-            bits[f] = xvo_decode_frame(levels + f * fsz, t > 0 ? recon + (f - 1) * fsz : NULL,
-                                       mv + f * 2 * npu, tu_log2 + f * npu, Hp, Wp, ctu, qp,
-                                       recon + f * fsz);
+            int intra = t == 0 && (flags & XVO_INTRA);
+            if (intra)
+                bits[f] = xvo_decode_intra_frame(levels + f * fsz, mv + f * 2 * npu, tu_log2 + f * npu, Hp, Wp, ctu,
+                                                 qp, recon + f * fsz);
+            else
+                bits[f] = xvo_decode_frame(levels + f * fsz, t > 0 ? recon + (f - 1) * fsz : NULL,
+                                           mv + f * 2 * npu, tu_log2 + f * npu, Hp, Wp, ctu, qp,
+                                           recon + f * fsz);
+            if (flags & XVO_DEBLOCK)
+                xvo_deblock_frame(recon + f * fsz, Hp, Wp, ctu, qp, tu_log2 + f * npu, levels + f * fsz,
+                                  mv + f * 2 * npu, intra);
         }
     return 0;
+}
+
+int xvo_decode_planes(const int16_t* levels, const int16_t* mv, const uint8_t* tu_log2, int G, int T,
+                      int Hp, int Wp, int ctu, int qp, uint16_t* recon, uint64_t* bits) {
+    return xvo_decode_planes_ex(levels, mv, tu_log2, G, T, Hp, Wp, ctu, qp, 0u, recon, bits);
 }
 
 /* The reconstruction back in the cube's units (the inverse of C1/C2): band b

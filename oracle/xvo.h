@@ -98,6 +98,11 @@ void xvo_deblock_segment(int32_t s[4][8], int bs, int qp);
 void xvo_deblock_frame(uint16_t* rec /*[3][Hp][Wp]*/, int Hp, int Wp, int ctu, int qp,
                        const uint8_t* tu_log2 /*[nCU]*/, const int16_t* levels /*[3][Hp][Wp]*/,
                        const int16_t* mv /*[nCU][2]*/, int intra);
+uint64_t xvo_decode_intra_frame(const int16_t* levels /*[3][Hp][Wp]*/, const int16_t* mode_mv /*[nCU][2]*/,
+                                const uint8_t* tu_log2 /*[nCU]*/, int Hp, int Wp, int ctu, int qp,
+                                uint16_t* recon /*[3][Hp][Wp]*/);
+int xvo_decode_planes_ex(const int16_t* levels, const int16_t* mv, const uint8_t* tu_log2, int G, int T, int Hp,
+                         int Wp, int ctu, int qp, unsigned flags, uint16_t* recon, uint64_t* bits);
 int xvo_encode_planes_ex(const uint16_t* planes, int G, int T, int Hp, int Wp, int ctu, int R, unsigned tu_mask,
                          int qp, unsigned flags, uint16_t* recon, int16_t* mv, uint32_t* cost, int16_t* mv_int,
                          uint32_t* cost_int, int16_t* levels, uint8_t* tu_log2, uint64_t* bits);

@@ -257,3 +257,22 @@ def test_chain_options_compose_from_the_frame_functions():
     plain = oracle.encode_planes(planes, 16, 8, 0b11100, 30)
     none = oracle.encode_planes(planes, 16, 8, 0b11100, 30, flags=0)
     assert all(np.array_equal(plain[k], none[k]) for k in ("recon", "mv", "levels", "bits"))
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("ctu,mask", [(8, 0b1000), (16, 0b11100), (32, 0b111100)])
+def test_decode_of_an_optioned_encode_reproduces_it(flags, ctu, mask):
+    """The decoder with the encoder's options rebuilds every reconstruction
+    and frame rate from the coded data alone (levels, vectors / modes, TU
+    sizes): the intra frame from its decoded neighbours, every frame
+    deblocked before it is a reference."""
+    from paper_2506_19656_gb300 import synth
+    cube = synth.tiny_cube(31 + ctu, T=3, H=64, W=96, bands=4)[0]
+    mm, _ = oracle.minmax(cube)
+    planes = oracle.quantize_pack(cube, ctu, mm)
+    enc = oracle.encode_planes(planes, ctu, 8, mask, 29, flags=flags)
+    dec = oracle.decode_planes(enc["levels"], enc["mv"], enc["tu_log2"], ctu, 29, flags=flags)
+    assert np.array_equal(dec["recon"], enc["recon"]) and np.array_equal(dec["bits"], enc["bits"])
+    # without the options the same data decode to something else
+    plain = oracle.decode_planes(enc["levels"], enc["mv"], enc["tu_log2"], ctu, 29)
+    assert not np.array_equal(plain["recon"], enc["recon"])
