@@ -65,8 +65,9 @@ typedef struct {
 /* Options beyond the default conventions (flat frame-0 prediction, no loop
  * filter): XV_INTRA codes frame 0 with intra prediction (xv_intra_frame),
  * XV_DEBLOCK deblocks every reconstructed frame before it becomes the next
- * frame's reference and the output (xv_deblock_frame).  xv_encode_cube runs
- * them; the batched path, serving and the decoder reject them (XV_EINVAL). */
+ * frame's reference and the output (xv_deblock_frame).  xv_encode_cube and
+ * xv_decode_frame run them; the batched path, serving and the batched
+ * decoder reject them (XV_EINVAL). */
 #define XV_INTRA 1u
 #define XV_DEBLOCK 2u
 
@@ -372,7 +373,12 @@ xv_status xv_deblock_frame(xv_ctx* ctx, uint16_t* recon, int G, int64_t plane_gs
  * (ignored when ref == NULL); tu_log2: uint8 [G][nCU] at + g * pu_gstride
  * (values outside 2..log2 ctu are clamped into it); bits: uint64, group g's
  * frame total is ADDED to bits[g * bits_gstride] (zero it first).  Only
- * p->ctu and p->qp are used. */
+ * p->ctu, p->qp and p->flags are used.  With the encoder's options: XV_INTRA
+ * decodes a frame with ref == NULL as xv_intra_frame coded it (CUs as a
+ * wavefront, each predicted from its decoded neighbours with the mode in
+ * mv[cu][0]; mv is then required), XV_DEBLOCK deblocks the decoded frame in
+ * place as xv_deblock_frame does (call the frames in order: a frame is the
+ * next one's reference only once it is deblocked). */
 xv_status xv_decode_frame(xv_ctx* ctx, const int16_t* levels, const uint16_t* ref, const int16_t* mv,
                           const uint8_t* tu_log2, int G, int64_t plane_gstride, int Hp, int Wp,
                           const xv_params* p, int64_t pu_gstride, uint16_t* recon, uint64_t* bits,

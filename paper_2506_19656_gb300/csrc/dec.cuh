@@ -73,8 +73,11 @@ __device__ uint32_t dec_tus(const int16_t* __restrict__ s_lev, uint16_t* __restr
 // Decodes the CU at (x0, y0): levels/ref/recon are the group's frame
 // [3][Hp][Wp] (ref == nullptr: frame 0); L = the CU's log2 TU size (values
 // outside 2..log2 N are clamped into it).  Writes recon; returns the CU's
-// rate-proxy bits (the same value on every thread).
-template <int N, int NT, bool kCoherent = false>
+// rate-proxy bits (the same value on every thread).  kPredGiven: the caller
+// has put the CU's levels (int16 [3][N][N] at offset 0) and its prediction
+// (right after them) in shared memory before a barrier; levels, ref and the
+// vector are then not read, and the bits count no vector.
+template <int N, int NT, bool kCoherent = false, bool kPredGiven = false>
 __device__ uint32_t dec_cu(const int16_t* __restrict__ levels, const uint16_t* __restrict__ ref, int64_t plane,
                            int Hp, int Wp, int x0, int y0, int mvx, int mvy, int L, int qp,
                            uint16_t* __restrict__ recon, unsigned char* smem) {
@@ -91,8 +94,10 @@ __device__ uint32_t dec_cu(const int16_t* __restrict__ levels, const uint16_t* _
     if (tid == 0) *s_bits = 0u;
     // the levels have the current samples' layout: one load batch with the
     // motion-compensation windows
-    load_and_predict<N, NT, kCoherent>(reinterpret_cast<const uint16_t*>(levels), ref, plane, Hp, Wp, x0, y0, mvx,
-                                       mvy, reinterpret_cast<uint16_t*>(s_lev), s_pred, s_stage, s_hbuf);
+    if constexpr (kPredGiven) __syncthreads();
+    else
+        load_and_predict<N, NT, kCoherent>(reinterpret_cast<const uint16_t*>(levels), ref, plane, Hp, Wp, x0, y0,
+                                           mvx, mvy, reinterpret_cast<uint16_t*>(s_lev), s_pred, s_stage, s_hbuf);
     L = L < 2 ? 2 : (L > LN ? LN : L);
     if (L > 5) L = 5;  // no 64-point transform
     uint32_t bits = 0;

@@ -14,6 +14,7 @@
 
 #include <cstdint>
 
+#include "dec.cuh"
 #include "me.cuh"
 #include "tqr.cuh"
 #include "xv_internal.h"
@@ -79,33 +80,15 @@ __device__ __forceinline__ int intra_sample(const int* __restrict__ sv, int N, i
     return fact ? ((32 - fact) * a + fact * refk(k0 + 1) + 16) >> 5 : a;
 }
 
+// The reference samples of the CU (r, c) of all three channels from the
+// reconstruction rg, in scan order with their availability (inside the plane
+// and in a CU coded earlier in raster order), unavailable ones substituted,
+// and each channel's DC value.  Called by all threads; ends with a barrier.
 template <int N>
-__global__ void __launch_bounds__(kNT)
-k_intra_cu(const uint16_t* __restrict__ cur, int64_t gstride, int Hp, int Wp, int wave, int r_lo, int qp,
-           unsigned tu_mask, int64_t lf8, int16_t* mv, int64_t pu_gstride, uint16_t* recon, int16_t* levels,
-           uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int NN = N * N, NR = intra_nref(N), L = N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
-    const int tid = threadIdx.x, g = blockIdx.y;
-    const int r = r_lo + blockIdx.x, c = wave - 2 * r;
-    const int x0 = c * N, y0 = r * N, nx = Wp / N;
-    const int64_t plane = (int64_t)Hp * Wp;
-    const uint16_t* cg = cur + g * gstride;
-    uint16_t* rg = recon + g * gstride;
-    uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
-    uint16_t* s_pred = s_cur + 3 * NN;
-    int* s_ref = reinterpret_cast<int*>(smem + intra_off_ref(N));
-    unsigned char* s_av = smem + intra_off_av(N);
-    int* s_dc = reinterpret_cast<int*>(smem + intra_off_misc(N));
-    unsigned* s_satd = reinterpret_cast<unsigned*>(s_dc + 3);
-    int* s_best = reinterpret_cast<int*>(s_satd + kModes);
-
-    // current samples; reference samples with their availability (inside the
-    // plane and in a CU coded earlier in raster order)
-    for (int i = tid; i < 3 * NN; i += kNT) {
-        const int ch = i / NN, y = (i / N) % N, x = i % N;
-        s_cur[i] = cg[ch * plane + (int64_t)(y0 + y) * Wp + x0 + x];
-    }
+__device__ void intra_refs(const uint16_t* __restrict__ rg, int64_t plane, int Hp, int Wp, int r, int c,
+                           int* s_ref, unsigned char* s_av, int* s_dc) {
+    constexpr int NR = intra_nref(N), L = N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
+    const int tid = threadIdx.x, x0 = c * N, y0 = r * N;
     for (int i = tid; i < 3 * NR; i += kNT) {
         const int ch = i / NR, k = i - ch * NR;
         int x, y;
@@ -117,7 +100,6 @@ k_intra_cu(const uint16_t* __restrict__ cur, int64_t gstride, int Hp, int Wp, in
         s_av[i] = coded;
         s_ref[i] = coded ? rg[ch * plane + (int64_t)y * Wp + x] : 0;
     }
-    if (tid < kModes) s_satd[tid] = 0u;
     __syncthreads();
     // substitution along the scan, one thread per channel
     if (tid < 3) {
@@ -146,6 +128,38 @@ k_intra_cu(const uint16_t* __restrict__ cur, int64_t gstride, int Hp, int Wp, in
         if (lane == 0) s_dc[ch] = (s + N) >> (L + 1);
     }
     __syncthreads();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kNT)
+k_intra_cu(const uint16_t* __restrict__ cur, int64_t gstride, int Hp, int Wp, int wave, int r_lo, int qp,
+           unsigned tu_mask, int64_t lf8, int16_t* mv, int64_t pu_gstride, uint16_t* recon, int16_t* levels,
+           uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NN = N * N, NR = intra_nref(N), L = N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
+    const int tid = threadIdx.x, g = blockIdx.y;
+    const int r = r_lo + blockIdx.x, c = wave - 2 * r;
+    const int x0 = c * N, y0 = r * N, nx = Wp / N;
+    const int64_t plane = (int64_t)Hp * Wp;
+    const uint16_t* cg = cur + g * gstride;
+    (void)NR;
+    uint16_t* rg = recon + g * gstride;
+    uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* s_pred = s_cur + 3 * NN;
+    int* s_ref = reinterpret_cast<int*>(smem + intra_off_ref(N));
+    unsigned char* s_av = smem + intra_off_av(N);
+    int* s_dc = reinterpret_cast<int*>(smem + intra_off_misc(N));
+    unsigned* s_satd = reinterpret_cast<unsigned*>(s_dc + 3);
+    int* s_best = reinterpret_cast<int*>(s_satd + kModes);
+
+    // current samples; reference samples with their availability (inside the
+    // plane and in a CU coded earlier in raster order)
+    for (int i = tid; i < 3 * NN; i += kNT) {
+        const int ch = i / NN, y = (i / N) % N, x = i % N;
+        s_cur[i] = cg[ch * plane + (int64_t)(y0 + y) * Wp + x0 + x];
+    }
+    if (tid < kModes) s_satd[tid] = 0u;  // ordered by intra_refs' barriers
+    intra_refs<N>(rg, plane, Hp, Wp, r, c, s_ref, s_av, s_dc);
     // channel-0 SATD of every mode: one 8 x 8 block of one mode per task
     {
         constexpr int NB = (N / 8) * (N / 8);
@@ -200,6 +214,82 @@ k_intra_cu(const uint16_t* __restrict__ cur, int64_t gstride, int Hp, int Wp, in
     }
 }
 
+// Decoding of frame 0 with intra prediction: the CU's levels, its references
+// from the decoded neighbours, the prediction with the stored mode
+// (mode_mv[cu][0], clamped to 0..34), then dec_cu on that prediction.
+__host__ __device__ constexpr size_t intra_dec_off_ref(int N) { return xvd::align16(xvd::dec_smem_bytes(N)); }
+__host__ __device__ constexpr size_t intra_dec_smem_bytes(int N) {
+    return intra_dec_off_ref(N) + xvd::align16((size_t)3 * intra_nref(N) * 4) + xvd::align16((size_t)3 * intra_nref(N)) +
+           4 * 4;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kNT)
+k_intra_dec_cu(const int16_t* __restrict__ levels, int64_t gstride, int Hp, int Wp, int wave, int r_lo, int qp,
+               const int16_t* __restrict__ mode_mv, int64_t pu_gstride, const uint8_t* __restrict__ tu_log2,
+               uint16_t* recon, uint64_t* bits, int64_t bits_gstride) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NN = N * N, NR = intra_nref(N), L = N == 8 ? 3 : N == 16 ? 4 : N == 32 ? 5 : 6;
+    const int tid = threadIdx.x, g = blockIdx.y;
+    const int r = r_lo + blockIdx.x, c = wave - 2 * r;
+    const int x0 = c * N, y0 = r * N, nx = Wp / N;
+    const int64_t plane = (int64_t)Hp * Wp;
+    const int16_t* lg = levels + g * gstride;
+    uint16_t* rg = recon + g * gstride;
+    int16_t* s_lev = reinterpret_cast<int16_t*>(smem);
+    uint16_t* s_pred = reinterpret_cast<uint16_t*>(s_lev + 3 * NN);
+    int* s_ref = reinterpret_cast<int*>(smem + intra_dec_off_ref(N));
+    unsigned char* s_av = reinterpret_cast<unsigned char*>(s_ref + 3 * NR);
+    int* s_dc = reinterpret_cast<int*>(smem + intra_dec_off_ref(N) + xvd::align16((size_t)3 * NR * 4) +
+                                       xvd::align16((size_t)3 * NR));
+    for (int i = tid; i < 3 * NN; i += kNT) {
+        const int ch = i / NN, y = (i / N) % N, x = i % N;
+        s_lev[i] = lg[ch * plane + (int64_t)(y0 + y) * Wp + x0 + x];
+    }
+    intra_refs<N>(rg, plane, Hp, Wp, r, c, s_ref, s_av, s_dc);
+    const int cu = r * nx + c;
+    const int64_t o = g * pu_gstride + cu;
+    const int m = mode_mv[2 * o];
+    const int mode = m < 0 ? 0 : (m > kModes - 1 ? kModes - 1 : m);
+    for (int i = tid; i < 3 * NN; i += kNT) {
+        const int ch = i / NN, y = (i / N) % N, x = i % N;
+        s_pred[i] = (uint16_t)intra_sample(s_ref + ch * NR, N, L, mode, s_dc[ch], x, y);
+    }
+    __syncthreads();
+    const uint32_t b = xvd::dec_cu<N, kNT, false, true>(nullptr, nullptr, plane, Hp, Wp, x0, y0, 0, 0, tu_log2[o], qp,
+                                                        rg, smem);
+    if (tid == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(bits + g * bits_gstride), (unsigned long long)(b + kModeBits));
+}
+
+// The wave w of a frame of nx x ny CUs: its first CU row and CU count.
+inline void wave_rows(int w, int nx, int ny, int& r_lo, int& count) {
+    const int a = w - (nx - 1);
+    r_lo = a > 0 ? (a + 1) / 2 : 0;
+    const int r_hi = w / 2 < ny - 1 ? w / 2 : ny - 1;
+    count = r_hi - r_lo + 1;
+}
+
+template <int N>
+cudaError_t intra_dec_n(const int16_t* levels, int G, int64_t gstride, int Hp, int Wp, int qp, const int16_t* mode_mv,
+                        int64_t pu_gstride, const uint8_t* tu_log2, uint16_t* recon, uint64_t* bits,
+                        int64_t bits_gstride, cudaStream_t st, uint64_t* launches) {
+    const size_t smem = intra_dec_smem_bytes(N);
+    cudaError_t e = cudaFuncSetAttribute(k_intra_dec_cu<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nx = Wp / N, ny = Hp / N;
+    for (int w = 0; w < (nx - 1) + 2 * (ny - 1) + 1; ++w) {
+        int r_lo, count;
+        wave_rows(w, nx, ny, r_lo, count);
+        if (count < 1) continue;
+        k_intra_dec_cu<N><<<dim3(count, G), kNT, smem, st>>>(levels, gstride, Hp, Wp, w, r_lo, qp, mode_mv, pu_gstride,
+                                                             tu_log2, recon, bits, bits_gstride);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) ++*launches;
+    }
+    return cudaSuccess;
+}
+
 template <int N>
 cudaError_t intra_n(const uint16_t* cur, int G, int64_t gstride, int Hp, int Wp, const xv_params* p, int16_t* mv,
                     int64_t pu_gstride, uint16_t* recon, int16_t* levels, uint8_t* tu_log2, uint64_t* bits,
@@ -232,6 +322,19 @@ cudaError_t launch_intra_frame(const uint16_t* cur, int G, int64_t gstride, int 
         case 16: return intra_n<16>(cur, G, gstride, Hp, Wp, p, mv, pu_gstride, recon, levels, tu_log2, bits, bits_gstride, st, launches);
         case 32: return intra_n<32>(cur, G, gstride, Hp, Wp, p, mv, pu_gstride, recon, levels, tu_log2, bits, bits_gstride, st, launches);
         case 64: return intra_n<64>(cur, G, gstride, Hp, Wp, p, mv, pu_gstride, recon, levels, tu_log2, bits, bits_gstride, st, launches);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_intra_decode_frame(const int16_t* levels, int G, int64_t gstride, int Hp, int Wp, int ctu, int qp,
+                                      const int16_t* mode_mv, int64_t pu_gstride, const uint8_t* tu_log2,
+                                      uint16_t* recon, uint64_t* bits, int64_t bits_gstride, cudaStream_t st,
+                                      uint64_t* launches) {
+    switch (ctu) {
+        case 8: return intra_dec_n<8>(levels, G, gstride, Hp, Wp, qp, mode_mv, pu_gstride, tu_log2, recon, bits, bits_gstride, st, launches);
+        case 16: return intra_dec_n<16>(levels, G, gstride, Hp, Wp, qp, mode_mv, pu_gstride, tu_log2, recon, bits, bits_gstride, st, launches);
+        case 32: return intra_dec_n<32>(levels, G, gstride, Hp, Wp, qp, mode_mv, pu_gstride, tu_log2, recon, bits, bits_gstride, st, launches);
+        case 64: return intra_dec_n<64>(levels, G, gstride, Hp, Wp, qp, mode_mv, pu_gstride, tu_log2, recon, bits, bits_gstride, st, launches);
     }
     return cudaErrorInvalidValue;
 }

@@ -152,7 +152,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 // The intra and deblocking options run on the per-frame path only.
 bool no_options(const xv_params* p, const char* where) {
     if (p->flags == 0) return true;
-    set_error("%s: the XV_INTRA / XV_DEBLOCK options are supported by xv_encode_cube and the per-frame calls only",
+    set_error("%s: the XV_INTRA / XV_DEBLOCK options are supported by xv_encode_cube, xv_decode_frame and the other "
+              "per-frame calls only",
               where);
     return false;
 }
@@ -1076,17 +1077,31 @@ xv_status xv_decode_frame(xv_ctx* c, const int16_t* levels, const uint16_t* ref,
                           const uint8_t* tu_log2, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
                           int64_t pu_gstride, uint16_t* recon, uint64_t* bits, int64_t bits_gstride, void* stream) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
-    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu) || !no_options(p, "xv_decode_frame")) return XV_EINVAL;
-    if (!levels || !tu_log2 || !recon || !bits || (ref && !mv)) {
-        set_error("levels, tu_log2, recon, bits (and mv with ref) are required");
+    if (!valid_params(p) || !valid_frame(G, Hp, Wp, p->ctu)) return XV_EINVAL;
+    const bool intra = !ref && (p->flags & XV_INTRA);
+    if (!levels || !tu_log2 || !recon || !bits || ((ref || intra || (p->flags & XV_DEBLOCK)) && !mv)) {
+        set_error("levels, tu_log2, recon, bits (and mv with ref or the options) are required");
         return XV_EINVAL;
     }
     if (!valid_planes(levels, ref ? ref : recon, recon, gstride)) return XV_EINVAL;
     DeviceGuard g(c->device);
-    c->launches += 1;
-    return check_launch(xvh::launch_dec_frame(levels, ref, mv, tu_log2, G, gstride, Hp, Wp, p, pu_gstride, recon, bits,
-                                              bits_gstride, (cudaStream_t)stream),
-                        "decode_frame");
+    cudaStream_t st = (cudaStream_t)stream;
+    xv_status s;
+    if (intra) {  // frame 0 with intra prediction: the modes are in mv[cu][0]
+        uint64_t launched = 0;
+        s = check_launch(xvh::launch_intra_decode_frame(levels, G, gstride, Hp, Wp, p->ctu, p->qp, mv, pu_gstride,
+                                                        tu_log2, recon, bits, bits_gstride, st, &launched),
+                         "intra decode");
+        c->launches += launched;
+    } else {
+        c->launches += 1;
+        s = check_launch(xvh::launch_dec_frame(levels, ref, mv, tu_log2, G, gstride, Hp, Wp, p, pu_gstride, recon, bits,
+                                               bits_gstride, st),
+                         "decode_frame");
+    }
+    if (!s && (p->flags & XV_DEBLOCK))
+        s = deblock_into(c, recon, G, gstride, Hp, Wp, p, pu_gstride, tu_log2, levels, mv, intra ? 1 : 0, st);
+    return s;
 }
 
 xv_status xv_unpack(xv_ctx* c, const uint16_t* recon, int bands, int T, int H, int W, int Hp, int Wp,

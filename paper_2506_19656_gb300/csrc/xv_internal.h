@@ -148,6 +148,11 @@ constexpr int kPersistBlockSizes[4] = {128, 192, 256, 512};
 cudaError_t launch_intra_frame(const uint16_t* cur, int G, int64_t gstride, int Hp, int Wp, const xv_params* p,
                                int16_t* mv, int64_t pu_gstride, uint16_t* recon, int16_t* levels, uint8_t* tu_log2,
                                uint64_t* bits, int64_t bits_gstride, cudaStream_t st, uint64_t* launches);
+// Decoding of frame 0 of G groups with intra prediction (modes in mode_mv[cu][0]).
+cudaError_t launch_intra_decode_frame(const int16_t* levels, int G, int64_t gstride, int Hp, int Wp, int ctu, int qp,
+                                      const int16_t* mode_mv, int64_t pu_gstride, const uint8_t* tu_log2,
+                                      uint16_t* recon, uint64_t* bits, int64_t bits_gstride, cudaStream_t st,
+                                      uint64_t* launches);
 // In-place deblocking of G reconstructed frames; cbf: G (Hp / 4) (Wp / 4) bytes of scratch.
 cudaError_t launch_deblock_frame(uint16_t* recon, int G, int64_t gstride, int Hp, int Wp, int ctu, int qp,
                                  const uint8_t* tu_log2, int64_t pu_gstride, const int16_t* levels,

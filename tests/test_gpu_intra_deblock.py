@@ -150,3 +150,55 @@ def test_options_are_rejected_outside_the_per_frame_path(xv, ctx):
     with pytest.raises(xv.XvError) as e2:
         xv.xv_encode_cube(ctx, job2)
     assert e2.value.status == xv.XV_EINVAL
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("case", ["tiny", "deepextremecubes", "dynamicearthnet"])
+def test_decoding_an_optioned_encode_reproduces_it(xv, ctx, case, flags):
+    """xv_decode_frame with the encoder's options, frame after frame, rebuilds
+    every reconstruction and frame rate of an xv_encode_cube run with them."""
+    c = synth.WORKLOADS[case]
+    if case == "dynamicearthnet":
+        cube = np.ascontiguousarray(synth.make_cube(case, T=3)[:, :, :192, :256])
+    else:
+        cube = synth.make_cube(case, T=None if case == "tiny" else 4)
+    job, buf = options_job(xv, cube, c.ctu, 16, c.tu_mask, 30, flags)
+    xv.xv_encode_cube(ctx, job)
+    G, T, _, Hp, Wp = buf["levels"].shape
+    n = buf["tu_log2"].shape[2]
+    fsz = 3 * Hp * Wp
+    rec = torch.zeros_like(buf["recon"])
+    bits = torch.zeros((G, T), dtype=torch.int64, device="cuda")
+    for t in range(T):
+        xv.xv_decode_frame(ctx, buf["levels"][:, t], rec[:, t - 1] if t else None, buf["mv"][:, t],
+                           buf["tu_log2"][:, t], G, T * fsz, Hp, Wp, job.p, T * n, rec[:, t], bits[:, t], T)
+    assert torch.equal(rec.view(torch.int16), buf["recon"].view(torch.int16))
+    assert torch.equal(bits, buf["bits"])
+    want = oracle.decode_planes(to_np(buf["levels"]), to_np(buf["mv"]), to_np(buf["tu_log2"]), c.ctu, 30, flags=flags)
+    assert np.array_equal(to_np(rec), want["recon"]) and np.array_equal(to_np(bits).astype(np.uint64), want["bits"])
+
+
+@pytest.mark.parametrize("deblock", [False, True])
+@pytest.mark.parametrize("ctu,mask", [(8, 0b1100), (16, 0b11100), (32, 0b111100), (64, 0b111100)])
+def test_intra_decode_of_arbitrary_coded_data_matches_the_oracle(xv, ctx, ctu, mask, deblock):
+    """Frame 0 decoded with XV_INTRA from arbitrary coded data -- every mode,
+    random TU sizes, levels up to +-400 -- against the oracle (then
+    deblocked as an intra frame with XV_DEBLOCK)."""
+    rng = np.random.default_rng(ctu + 7 * deblock)
+    G, Hp, Wp = 2, 2 * ctu + (64 if ctu < 64 else 0), 3 * ctu
+    n = (Hp // ctu) * (Wp // ctu)
+    sizes = [k for k in range(2, 6) if (mask >> k) & 1 and (1 << k) <= ctu]
+    tu = rng.choice(sizes, (G, n)).astype(np.uint8)
+    lev = np.where(rng.random((G, 3, Hp, Wp)) < 0.05, rng.integers(-400, 401, (G, 3, Hp, Wp)), 0).astype(np.int16)
+    modes = np.stack([rng.integers(0, 35, (G, n)), np.zeros((G, n), int)], -1).astype(np.int16)
+    p = xv.xv_params_init(ctu, 8, mask, 27)
+    p.flags = xv.XV_INTRA | (xv.XV_DEBLOCK if deblock else 0)
+    rec = torch.zeros((G, 3, Hp, Wp), dtype=torch.uint16, device="cuda")
+    bits = torch.zeros(G, dtype=torch.int64, device="cuda")
+    xv.xv_decode_frame(ctx, to_dev(lev), None, to_dev(modes), to_dev(tu), G, 3 * Hp * Wp, Hp, Wp, p, n, rec, bits, 1)
+    for g in range(G):
+        want, wbits = oracle.decode_intra_frame(lev[g], modes[g], tu[g], ctu, 27)
+        if deblock:
+            want = oracle.deblock_frame(want, ctu, 27, tu[g], lev[g], modes[g], intra=True)
+        assert np.array_equal(to_np(rec[g]), want), g
+        assert int(bits[g]) == wbits, g
