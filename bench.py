@@ -152,11 +152,19 @@ def algorithmic_ad(cfg, T):
     return G * (T - 1) * npu * cfg.ctu ** 2 * (2 * cfg.R + 1) ** 2
 
 
+# The sources the persistent encode kernel is compiled from (its translation
+# unit for 16 x 16 CTUs and everything it includes): the recorded DRAM
+# traffic holds only while these are unchanged.
+PERSIST_SOURCES = ("paper_2506_19656_gb300/csrc/k_batch_ctu16.cu", "paper_2506_19656_gb300/csrc/batch.cuh",
+                   "paper_2506_19656_gb300/csrc/dec.cuh", "paper_2506_19656_gb300/csrc/me.cuh",
+                   "paper_2506_19656_gb300/csrc/tqr.cuh", "paper_2506_19656_gb300/csrc/xv_dev.cuh",
+                   "paper_2506_19656_gb300/csrc/xv_internal.h", "include/xv.h")
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2506_19656_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    for f in PERSIST_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

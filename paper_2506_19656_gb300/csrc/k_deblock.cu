@@ -116,7 +116,11 @@ __global__ void k_deblock(uint16_t* rec, int64_t gstride, int G, int Hp, int Wp,
          it += (int64_t)gridDim.x * blockDim.x) {
         const int g = (int)(it / ((int64_t)nedge * nseg));
         const int rem = (int)(it - (int64_t)g * nedge * nseg);
-        const int e = 8 * (rem / nseg + 1), o = 4 * (rem % nseg);
+        // consecutive threads take neighbouring segments along the rows: the
+        // edges of one row band for vertical edges, the 4-column segments of
+        // one edge for horizontal ones (their sample windows are contiguous)
+        const int e = kVertical ? 8 * (rem % nedge + 1) : 8 * (rem / nseg + 1);
+        const int o = kVertical ? 4 * (rem / nedge) : 4 * (rem % nseg);
         // the q-side sample and the p-side sample of the segment's first line
         const int xq = kVertical ? e : o, yq = kVertical ? o : e;
         const int xp = kVertical ? e - 1 : o, yp = kVertical ? o : e - 1;
