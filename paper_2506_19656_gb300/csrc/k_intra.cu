@@ -142,7 +142,6 @@ k_intra_cu(const uint16_t* __restrict__ cur, int64_t gstride, int Hp, int Wp, in
     const int x0 = c * N, y0 = r * N, nx = Wp / N;
     const int64_t plane = (int64_t)Hp * Wp;
     const uint16_t* cg = cur + g * gstride;
-    (void)NR;
     uint16_t* rg = recon + g * gstride;
     uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
     uint16_t* s_pred = s_cur + 3 * NN;
