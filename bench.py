@@ -1024,12 +1024,16 @@ def main():
            "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hosts)),
            "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant kernel (the persistent encode)
+    # roofline of the dominant kernel(s): the persistent encode, or in the
+    # per-frame mode (block size 1) the motion-search and transform launches
+    # of the concurrent chains (the recorded traffic is the persistent
+    # kernel's, so none then)
+    frames_mode = block_size == 1
     ad = len(QPS) * sum(algorithmic_ad(cfg, T) for T in lengths)
     kms = statistics.mean(kern_ms)
     achieved = ad / (kms / 1e3)
     executed = executed_ad(cfg, exact_cand, full_cand)
-    traffic = recorded_traffic()
+    traffic = None if frames_mode else recorded_traffic()
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_AD_PER_S / 1e9, "unit": "GAD/s",
                 "frac": achieved / ALU_PEAK_AD_PER_S, "traffic": traffic,
                 "effective": "achieved/frac count the full search's abs-diffs (the method's definition); the kernel "
@@ -1037,7 +1041,9 @@ def main():
                 "executed": executed["ad"] / (kms / 1e3) / 1e9,
                 "executed_frac": executed["ad"] / (kms / 1e3) / ALU_PEAK_AD_PER_S,
                 "executed_work": executed,
-                "kernel": f"k_persist<{cfg.ctu}> (motion search + refinement + transform/quant/recon, fused)",
+                "kernel": (f"k_me_frame<{cfg.ctu}> + k_tqr_frame<{cfg.ctu}> (the jobs as per-frame chains on "
+                           f"concurrent streams)" if frames_mode else
+                           f"k_persist<{cfg.ctu}> (motion search + refinement + transform/quant/recon, fused)"),
                 "work_per_launch": f"{ad:.4g} integer-search abs-diffs ({cfg.ctu}^2 x {2 * cfg.R + 1}^2 per PU "
                                    f"and P-frame)",
                 "kernel_ms": kms,
@@ -1052,7 +1058,8 @@ def main():
         "config": {"workload": cfg.name, "qps": list(QPS), "ctu": cfg.ctu, "search_range": cfg.R,
                    "tu_sizes": list(cfg.tu_sizes), "frames": lengths if len(lengths) > 1 else cfg.T,
                    "bands": cfg.bands,
-                   "path": "xv_encode_batch (persistent kernel)",
+                   "path": "xv_encode_batch (" + ("per-frame chains on concurrent streams, the autotuner's choice"
+                                                  if frames_mode else "persistent kernel") + ")",
                    "block_size": block_size, "l2": "flushed before every step (256 MB write); "
                    "the float32 cube (168 MB) is also larger than L2", "parallelism": f"replicas{ws}"},
         "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),

@@ -250,11 +250,14 @@ xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void
 /* Batched path: all jobs' frames run in ONE persistent launch per CTU size,
  * scheduled by data flow over a device ready queue of (job, group, frame, PU)
  * items: an item is queued once the previous frame's reconstruction rows it
- * reads are complete, and blocks take queued items in order.  The block size
- * is chosen by an autotuner: the first batch of a given shape on a context
- * runs once per candidate size and the fastest is kept for later batches of
- * that shape.  Output is bit-identical to xv_encode_cube for each job, for
- * every block size.  results: HOST [njobs].  Synchronous.  XV_ETIMEOUT if a
+ * reads are complete, and blocks take queued items in order.  The autotuner
+ * also weighs a second execution mode, the per-frame mode: every job's frames
+ * as the per-frame motion-search and transform launches of xv_encode_cube,
+ * the jobs on up to 16 concurrent streams forked from and joined back to the
+ * batch's stream.  The first batch of a given shape on a context runs once
+ * per candidate (the four block sizes and the per-frame mode) and the fastest
+ * is kept for later batches of that shape.  Output is bit-identical to
+ * xv_encode_cube for each job, in every mode.  results: HOST [njobs].  Synchronous.  XV_ETIMEOUT if a
  * bounded device wait ran out of time (results then invalid; the context
  * stays usable). */
 xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
@@ -478,7 +481,8 @@ xv_status xv_set_batch_graphs(xv_ctx* ctx, int enable);
 /* Graphs captured and graph launches so far on this context.  Host only. */
 xv_status xv_batch_graph_stats(const xv_ctx* ctx, uint64_t* captures, uint64_t* launches);
 /* Threads per block of the last xv_encode_batch persistent launch (the
- * autotuner's choice for that batch shape).  Host only. */
+ * autotuner's choice for that batch shape), or 1 when the autotuner chose the
+ * per-frame mode (see xv_encode_batch).  Host only. */
 xv_status xv_last_batch_block_size(const xv_ctx* ctx, int* block_size);
 /* Integer-search work of the last xv_encode_batch on this context.
  * `full_candidates`: the candidates of the integer full search defined at
@@ -496,8 +500,9 @@ uint64_t xv_ctx_launches(const xv_ctx* ctx);
 /* Spin budget (SM clock cycles, default 4e9, about 2 s) of each dependency
  * wait in xv_encode_batch.  Host only. */
 xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
-/* Run xv_encode_batch with this block size (128, 192, 256 or 512) instead of the
- * autotuner's choice; 0 restores the autotuner.  Host only. */
+/* Run xv_encode_batch with this block size (128, 192, 256 or 512), or 1 for
+ * its per-frame mode, instead of the autotuner's choice; 0 restores the
+ * autotuner.  Host only. */
 xv_status xv_debug_force_block_size(xv_ctx* ctx, int block_size);
 /* Make one dependency counter of xv_encode_batch impossible to complete: the
  * CTU row `row` of the first job, indexed over its [G][T][rows] counters, is

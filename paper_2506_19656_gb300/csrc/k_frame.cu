@@ -19,7 +19,7 @@ template <int N>
 __global__ void __launch_bounds__(kNT, kMinBlocks<N>)
 k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t gstride, int Hp, int Wp,
            int R, int64_t lmv, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
-           int64_t pu_gstride) {
+           int64_t pu_gstride, unsigned long long* exact) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int pu = blockIdx.x, g = blockIdx.y, nx = Wp / N;
     xvd::MeResult r = xvd::me_pu<N, kNT>(cur + g * gstride, ref + g * gstride, Hp, Wp, (pu % nx) * N,
@@ -31,6 +31,7 @@ k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, i
         if (cost) cost[o] = r.cost;
         if (mv_int) { mv_int[2 * o] = (int16_t)r.mvx_int; mv_int[2 * o + 1] = (int16_t)r.mvy_int; }
         if (cost_int) cost_int[o] = r.cost_int;
+        if (exact) atomicAdd(exact, (unsigned long long)r.exact_cand);
     }
 }
 
@@ -55,13 +56,13 @@ k_tqr_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, 
 template <int N>
 cudaError_t me_n(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                  const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
-                 int64_t pu_gstride, cudaStream_t st) {
+                 int64_t pu_gstride, cudaStream_t st, unsigned long long* exact) {
     size_t smem = xvd::me_smem_bytes(N, p->search_range);
     cudaError_t e = cudaFuncSetAttribute(k_me_frame<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Hp / N) * (Wp / N), G);
     k_me_frame<N><<<grid, kNT, smem, st>>>(cur, ref, gstride, Hp, Wp, p->search_range, p->lambda_mv_fp16, mv,
-                                           cost, mv_int, cost_int, pu_gstride);
+                                           cost, mv_int, cost_int, pu_gstride, exact);
     return cudaGetLastError();
 }
 
@@ -82,12 +83,12 @@ cudaError_t tqr_n(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, i
 
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
-                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st) {
+                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st, unsigned long long* exact) {
     switch (p->ctu) {
-        case 8: return me_n<8>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st);
-        case 16: return me_n<16>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st);
-        case 32: return me_n<32>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st);
-        case 64: return me_n<64>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st);
+        case 8: return me_n<8>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
+        case 16: return me_n<16>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
+        case 32: return me_n<32>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
+        case 64: return me_n<64>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
     }
     return cudaErrorInvalidValue;
 }

@@ -45,8 +45,18 @@ struct xv_ctx {
     std::string graph_key;
     int use_graph = 1;
     uint64_t graph_launches = 0, graph_captures = 0;
+    // the batched path's second execution mode: the jobs as per-frame chains
+    // on side streams (vectors of jobs without an mv buffer, exact-candidate count)
+    cudaStream_t side[16] = {};
+    cudaEvent_t side_ev[16] = {};
+    cudaEvent_t fork_ev = nullptr;
+    DevBuf b_mv, b_exact;
     xvh::ServeState* serve = nullptr;
 };
+
+// Block size value that selects the batched path's per-frame mode.
+constexpr int kFramesMode = 1;
+constexpr int kSideStreams = 16;
 
 namespace xvh {
 
@@ -309,11 +319,16 @@ void xv_destroy(xv_ctx* c) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax, &c->tmp_cbf,
                       &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
-                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals};
+                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals, &c->b_mv, &c->b_exact};
     for (DevBuf* b : bufs) release(c, *b);
     for (cudaGraphExec_t& gx : c->graph)
         if (gx) cudaGraphExecDestroy(gx);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (int k = 0; k < kSideStreams; ++k) {
+        if (c->side[k]) cudaStreamDestroy(c->side[k]);
+        if (c->side_ev[k]) cudaEventDestroy(c->side_ev[k]);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     if (c->work) cudaStreamDestroy(c->work);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -726,6 +741,17 @@ xv_status ensure_work_stream(xv_ctx* c) {
     return XV_OK;
 }
 
+xv_status ensure_side_streams(xv_ctx* c) {
+    cudaError_t e = cudaSuccess;
+    if (!c->fork_ev) e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
+        if (!c->side[k]) e = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !c->side_ev[k]) e = cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "side streams");
+    return XV_OK;
+}
+
 bool valid_djob(const xv_djob* j) {
     if (!j) { set_error("job is NULL"); return false; }
     if (!valid_params(&j->p) || !valid_frame(j->G, j->Hp, j->Wp, j->p.ctu)) return false;
@@ -765,9 +791,9 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     // ---- geometry, descriptors, queue layout (host)
     const int ctus[4] = {8, 16, 32, 64};
     std::vector<xvh::JobDev> jd(njobs);
-    std::vector<int64_t> bits_off(njobs), row_off(njobs), part_off(njobs);
+    std::vector<int64_t> bits_off(njobs), row_off(njobs), part_off(njobs), mv_off(njobs);
     std::vector<int> nblk(njobs);
-    int64_t nbits = 0, nrows = 0, nparts = 0;
+    int64_t nbits = 0, nrows = 0, nparts = 0, nmv = 0;
     size_t total[4] = {0, 0, 0, 0}, nfirst[4] = {0, 0, 0, 0}, smem[4] = {0, 0, 0, 0};
     std::string shape[4];
     for (int i = 0; i < njobs; ++i) {
@@ -780,6 +806,8 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         nblk[i] = xvh::psnr_blocks_per_band((int64_t)j.T * j.H * j.W);
         part_off[i] = nparts;
         nparts += (int64_t)nblk[i] * j.bands;
+        mv_off[i] = nmv;
+        if (!j.mv) nmv += (int64_t)G * j.T * (Hp / j.p.ctu) * (Wp / j.p.ctu) * 2;
         const int k = j.p.ctu == 8 ? 0 : j.p.ctu == 16 ? 1 : j.p.ctu == 32 ? 2 : 3;
         const int64_t npu = (int64_t)(Hp / j.p.ctu) * (Wp / j.p.ctu);
         total[k] += (size_t)G * j.T * npu;
@@ -809,8 +837,11 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if ((s = ensure(c, c->b_out, sizeof(xvh::PsnrPart) * XV_MAX_BANDS * njobs))) return s;
     if ((s = ensure(c, c->b_totals, sizeof(unsigned long long) * njobs))) return s;
     if ((s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * XV_MAX_BANDS))) return s;
+    if ((s = ensure(c, c->b_mv, sizeof(int16_t) * (nmv > 0 ? nmv : 1)))) return s;
+    if ((s = ensure(c, c->b_exact, sizeof(unsigned long long)))) return s;
+    if ((s = ensure_side_streams(c))) return s;
     const size_t stage_bytes = sizeof(xvh::BatchCtl) * 4 + sizeof(unsigned long long) * njobs +
-                               (sizeof(xvh::PsnrPart) + sizeof(BandQ)) * XV_MAX_BANDS * njobs;
+                               (sizeof(xvh::PsnrPart) + sizeof(BandQ)) * XV_MAX_BANDS * njobs + sizeof(unsigned long long);
     if (c->h_stage_bytes < stage_bytes) {
         if (c->h_stage) cudaFreeHost(c->h_stage);
         c->h_stage = nullptr;
@@ -859,6 +890,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     unsigned long long* h_tot = (unsigned long long*)(hs + sizeof(xvh::BatchCtl) * 4);
     xvh::PsnrPart* h_out = (xvh::PsnrPart*)(h_tot + njobs);
     BandQ* h_bq = (BandQ*)(h_out + XV_MAX_BANDS * njobs);
+    unsigned long long* h_exact = (unsigned long long*)(h_bq + XV_MAX_BANDS * njobs);
 
     // ---- the batch as three stream-ordered, capturable parts: setup,
     // persistent kernels, results; the timing events go between them
@@ -882,7 +914,66 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                                    "batch prologue");
         return r;
     };
+    // the per-frame mode runs the whole batch when any CTU class with work is
+    // tuned (or forced) to it
+    auto frames_mode = [&](const int nt[4]) {
+        for (int k = 0; k < 4; ++k)
+            if (total[k] && nt[k] == kFramesMode) return true;
+        return false;
+    };
+    // the per-frame mode: job i's frames on side stream i mod 16 (motion
+    // search, then transform per frame, as xv_encode_cube runs them), forked
+    // from and joined back into the work stream by events (capturable)
+    auto part_frames = [&]() -> xv_status {
+        cudaError_t err = cudaMemsetAsync(c->b_exact.ptr, 0, sizeof(unsigned long long), st);
+        if (err == cudaSuccess) err = cudaEventRecord(c->fork_ev, st);
+        const int nside = njobs < kSideStreams ? njobs : kSideStreams;
+        for (int k = 0; k < nside && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(c->side[k], c->fork_ev, 0);
+        if (err != cudaSuccess) return cuda_fail(err, "fork");
+        unsigned long long* exact = (unsigned long long*)c->b_exact.ptr;
+        for (int i = 0; i < njobs; ++i) {
+            const xv_job& j = jobs[i];
+            cudaStream_t ss = c->side[i % kSideStreams];
+            const int G = jd[i].G, T = j.T, Hp = jd[i].Hp, Wp = jd[i].Wp;
+            const int64_t npu = (int64_t)jd[i].nx * jd[i].ny, fsz = 3LL * Hp * Wp;
+            int16_t* mv = j.mv ? j.mv : (int16_t*)c->b_mv.ptr + mv_off[i];
+            for (int g = 0; g < G && err == cudaSuccess; ++g) {  // frame 0 has no motion
+                err = cudaMemsetAsync(mv + (int64_t)g * T * npu * 2, 0, sizeof(int16_t) * 2 * npu, ss);
+                if (err == cudaSuccess && j.cost)
+                    err = cudaMemsetAsync(j.cost + (int64_t)g * T * npu, 0, sizeof(uint32_t) * npu, ss);
+            }
+            if (err != cudaSuccess) return cuda_fail(err, "frame 0 vectors");
+            for (int t = 0; t < T; ++t) {
+                const uint16_t* cur = j.planes + t * fsz;
+                const uint16_t* ref = t > 0 ? j.recon + (t - 1) * fsz : nullptr;
+                xv_status r;
+                if (ref) {
+                    c->launches += kLaunchMe;
+                    if ((r = check_launch(xvh::launch_me_frame(cur, ref, G, T * fsz, Hp, Wp, &j.p, mv + t * npu * 2,
+                                                               j.cost ? j.cost + t * npu : nullptr, nullptr, nullptr,
+                                                               T * npu, ss, exact),
+                                          "motion_search")))
+                        return r;
+                }
+                c->launches += kLaunchTqr;
+                if ((r = check_launch(xvh::launch_tqr_frame(cur, ref, mv + t * npu * 2, G, T * fsz, Hp, Wp, &j.p, T * npu,
+                                                            j.recon + t * fsz, j.levels ? j.levels + t * fsz : nullptr,
+                                                            j.tu_log2 ? j.tu_log2 + t * npu : nullptr,
+                                                            jd[i].bits + t, T, ss),
+                                      "transform_quant_recon")))
+                    return r;
+            }
+        }
+        for (int k = 0; k < nside && err == cudaSuccess; ++k) {
+            err = cudaEventRecord(c->side_ev[k], c->side[k]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(st, c->side_ev[k], 0);
+        }
+        if (err != cudaSuccess) return cuda_fail(err, "join");
+        c->batch_nt = kFramesMode;
+        return XV_OK;
+    };
     auto part_kernels = [&](const int nt[4]) -> xv_status {
+        if (frames_mode(nt)) return part_frames();
         xv_status r = XV_OK;
         for (int k = 0; k < 4; ++k) {
             if (!total[k]) continue;
@@ -921,6 +1012,8 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                                   cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess)
             err = cudaMemcpyAsync(h_bq, bq_all, sizeof(BandQ) * XV_MAX_BANDS * njobs, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(h_exact, c->b_exact.ptr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
         if (err != cudaSuccess) return cuda_fail(err, "batch results");
         return XV_OK;
     };
@@ -955,7 +1048,9 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if (tune && !debug) {
         float best_ms = 1e30f;
         int best_nt = 256;
-        for (int cand : xvh::kPersistBlockSizes) {
+        const int cands[5] = {xvh::kPersistBlockSizes[0], xvh::kPersistBlockSizes[1], xvh::kPersistBlockSizes[2],
+                              xvh::kPersistBlockSizes[3], kFramesMode};
+        for (int cand : cands) {
             int trial[4] = {cand, cand, cand, cand};
             if ((s = body(trial))) return s;
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune");
@@ -982,10 +1077,10 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                      (void*)j.tu_log2, (void*)j.bits);
             key += buf;
         }
-        snprintf(buf, sizeof buf, "|%d,%d,%d,%d|%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p|%lld", nt[0], nt[1], nt[2], nt[3],
-                 c->b_jobs.ptr, c->b_bits.ptr, c->b_rowdone.ptr, c->b_depcnt.ptr, c->b_bandq.ptr, c->b_minmax.ptr,
+        snprintf(buf, sizeof buf, "|%d,%d,%d,%d|%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p,%p|%lld", nt[0], nt[1], nt[2],
+                 nt[3], c->b_jobs.ptr, c->b_bits.ptr, c->b_rowdone.ptr, c->b_depcnt.ptr, c->b_bandq.ptr, c->b_minmax.ptr,
                  c->b_ctl.ptr, c->b_cls.ptr, c->b_items.ptr, c->b_part.ptr, c->b_out.ptr, c->b_totals.ptr,
-                 c->h_stage, c->wait_budget);
+                 c->h_stage, c->b_mv.ptr, c->b_exact.ptr, c->wait_budget);
         key += buf;
         if (!c->graph[0] || key != c->graph_key) {
             for (cudaGraphExec_t& gx : c->graph)
@@ -1013,7 +1108,12 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
             return cuda_fail(e, "graph launch");
         c->graph_launches++;
         c->launches += (uint64_t)njobs * (kLaunchMinmax + kLaunchQuant + kLaunchPsnr) + 2;
-        for (int k = 0; k < 4; ++k) if (total[k]) c->launches += kLaunchPersist;
+        if (frames_mode(nt)) {
+            for (int i = 0; i < njobs; ++i) c->launches += (uint64_t)jobs[i].T * kLaunchTqr + (uint64_t)(jobs[i].T - 1) * kLaunchMe;
+            c->batch_nt = kFramesMode;
+        } else {
+            for (int k = 0; k < 4; ++k) if (total[k]) { c->launches += kLaunchPersist; c->batch_nt = nt[k]; }
+        }
         for (int i = 0; i < njobs; ++i)
             if (jobs[i].minmax_fixed) c->launches -= kLaunchMinmax - kLaunchBandq;
     } else {
@@ -1034,14 +1134,18 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     // ---- results (host)
     c->batch_exact = 0;
     c->batch_full = 0;
-    for (int k = 0; k < 4; ++k)
-        if (total[k]) c->batch_exact += h_ctl[k].exact_cand;
+    if (frames_mode(nt)) {
+        c->batch_exact = *h_exact;
+    } else {
+        for (int k = 0; k < 4; ++k)
+            if (total[k]) c->batch_exact += h_ctl[k].exact_cand;
+    }
     for (int i = 0; i < njobs; ++i) {
         const uint64_t side = 2 * (uint64_t)jobs[i].p.search_range + 1;
         c->batch_full += (uint64_t)jd[i].G * (uint64_t)(jobs[i].T - 1) * jd[i].nx * jd[i].ny * side * side;
     }
     for (int k = 0; k < 4; ++k)
-        if (total[k] && h_ctl[k].err) {
+        if (!frames_mode(nt) && total[k] && h_ctl[k].err) {
             set_error("a dependency wait of the persistent encode (CTU %d) ran out of time", ctus[k]);
             for (int i = 0; i < njobs; ++i) results[i].status = XV_ETIMEOUT;
             return (xv_status)h_ctl[k].err;
@@ -1352,9 +1456,13 @@ xv_status xv_set_batch_graphs(xv_ctx* c, int enable) {
 
 xv_status xv_debug_force_block_size(xv_ctx* c, int nt) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
-    bool ok = nt == 0;
+    bool ok = nt == 0 || nt == kFramesMode;
     for (int v : xvh::kPersistBlockSizes) ok = ok || nt == v;
-    if (!ok) { set_error("block size %d is not one the persistent kernel is built for", nt); return XV_EINVAL; }
+    if (!ok) {
+        set_error("block size %d is neither one the persistent kernel is built for nor %d (per-frame mode)", nt,
+                  kFramesMode);
+        return XV_EINVAL;
+    }
     c->force_nt = nt;
     return XV_OK;
 }

@@ -35,9 +35,11 @@ cudaError_t launch_bandq(const double* minmax, int bands, BandQ* bq, cudaStream_
 cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T, int H, int W, int Hp, int Wp,
                                  const BandQ* bq, uint16_t* planes, cudaStream_t st);
 
+// exact: when not null, the integer-search candidates evaluated exactly are added to *exact.
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
-                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st);
+                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st,
+                            unsigned long long* exact = nullptr);
 // PCA over bands (k_pca.cu).
 int pca_fit_blocks(int64_t npix);
 cudaError_t launch_pca_sums(const void* src, xv_dtype dt, int bands, int64_t npix, double* part, int nblk,

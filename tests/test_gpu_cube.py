@@ -93,8 +93,9 @@ def test_ragged_shapes_and_mixed_batch(xv, ctx):
     assert_matches(b, xv.xv_encode_cube(ctx, j), wants[0])
 
 
-@pytest.mark.parametrize("block_size", [128, 192, 256, 512])
+@pytest.mark.parametrize("block_size", [128, 192, 256, 512, 1])
 def test_every_block_size_is_bit_exact(xv, ctx, block_size):
+    """Every persistent-kernel block size, and the per-frame mode (1)."""
     """The autotuner's candidates all give the oracle's bytes (mixed CTU sizes)."""
     specs = [((4, 4, 40, 56), 8, 6, 0b1100, 30), ((5, 3, 37, 53), 16, 9, 0b11100, 22),
              ((2, 3, 70, 33), 32, 5, 0b111100, 27)]
