@@ -6,15 +6,18 @@ Workload: the DeepExtremeCubes-shaped cube (10 float32 bands, 256 frames of
 27 and 32 (CTU 16, search range 32, TU 4/8/16).  One step is the whole path
 for the three encodes -- min/max, quantise/pack, motion search, transform /
 quantise / reconstruct, PSNR and rate -- through the batched C-ABI call
-xv_encode_batch (one persistent launch).  The metric counts pixels x bands x
-frames of the three encodes per second.
+xv_encode_batch (one captured graph: the persistent kernel, or the jobs as
+per-frame chains on concurrent streams, whichever the autotuner timed faster).
+The metric counts pixels x bands x frames of the three encodes per second.
 
   value   inputs resident in HBM, device time of K steps (CUDA events)
   e2e     the same call with the cube copied from pinned host memory and the
           results read back inside every timed step
-  plain   the per-frame launch path (xv_encode_cube per encode), same work
-  roofline  the persistent kernel (dominant): integer-search abs-diffs per
-          launch / its event-timed duration, against the ALU peak
+  plain   the per-frame launch path (xv_encode_cube per encode), same work,
+          one encode after another and on concurrent streams
+  roofline  the dominant kernel (the persistent kernel, or the per-frame
+          chains in that mode): integer-search abs-diffs per launch / its
+          event-timed duration, against the ALU peak
   cpu_baseline  the CPU oracle on a bounded causal prefix of the same cube
 
 --impl reference times the CPU oracle (the reference arm of this tier) on
