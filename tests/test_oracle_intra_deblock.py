@@ -3,9 +3,11 @@ DC and angular predictions per CU) and in-loop deblocking (reading R5: the
 H.265 luma filter on every channel), checked against what the definitions
 fix: exact copies and diagonals, rounded means, the transpose symmetry of the
 angular modes, linear references, the availability and substitution rules,
-the filter's mirror symmetry, its step response and where it may act.  The
-beta / tC tables themselves are the standard's printed values and are not
-pinned here."""
+the filter's mirror symmetry, its step response and where it may act.  Of
+the beta / tC tables (the standard's printed values), the structure is pinned:
+beta's piecewise-linear growth with QP, tC's growth with the quantiser step,
+the 10-bit scaling and the boundary-strength offset; tC's individual values at
+low QP are not."""
 import numpy as np
 import pytest
 
@@ -152,6 +154,35 @@ def side_info(H, W, ctu, tu_log2=4, coded=False, mv=None):
         lev[:, ::4, ::4] = 1
     mvv = np.zeros((n, 2), np.int16) if mv is None else mv
     return tu, lev, mvv
+
+
+def test_threshold_tables_follow_their_design_laws():
+    """beta' (8-bit) is 0 up to QP 15, then grows by 1 per QP from 6 at QP 16
+    to 18 at QP 28 and by 2 per QP from 20 at QP 29 to 64 at QP 51 (clamped
+    outside 0..51).  tC' is non-decreasing, 0 up to QP 17 and 1 from 18, ends
+    at 24 (QP 53), and above QP 35 roughly doubles every 6 QP like the
+    quantiser step 2^((QP-4)/6).  Both are scaled by 2^(10-8) = 4 for 10-bit
+    samples; tC is read at QP + 2 (bS - 1) and is 0 at bS 0; beta does not
+    depend on bS."""
+    beta8 = {}
+    tc8 = {}
+    for q in range(0, 54):
+        b, t = oracle.deblock_params(q, 1)
+        assert b % 4 == 0 and t % 4 == 0
+        beta8[q], tc8[q] = b // 4, t // 4
+        b2, t2 = oracle.deblock_params(q, 2)
+        assert b2 == b and oracle.deblock_params(q, 0) == (b, 0)
+        assert t2 == oracle.deblock_params(min(q + 2, 53), 1)[1]
+    for q in range(0, 52):
+        want = 0 if q <= 15 else (q - 10 if q <= 28 else 2 * q - 38)
+        assert beta8[q] == want, q
+    assert beta8[52] == beta8[53] == 64
+    assert all(tc8[q + 1] >= tc8[q] for q in range(53))
+    assert all(tc8[q] == 0 for q in range(18)) and tc8[18] == 1 and tc8[53] == 24
+    for q in range(36, 48):
+        assert 1.7 <= tc8[q + 6] / tc8[q] <= 2.2, q
+    assert oracle.deblock_params(-5, 1) == oracle.deblock_params(0, 1)
+    assert oracle.deblock_params(60, 1) == oracle.deblock_params(53, 1)
 
 
 def test_no_filtering_at_boundary_strength_zero():
