@@ -1037,8 +1037,14 @@ def main():
     achieved = ad / (kms / 1e3)
     executed = executed_ad(cfg, exact_cand, full_cand)
     traffic = None if frames_mode else recorded_traffic()
+    if traffic is not None:
+        traffic_note = "dram bytes read + written per launch, ncu capture of the same kernel sources"
+    elif frames_mode:
+        traffic_note = "none: no ncu DRAM capture of the per-frame chains is recorded"
+    else:
+        traffic_note = "none: the recorded ncu capture was taken on other kernel sources"
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_AD_PER_S / 1e9, "unit": "GAD/s",
-                "frac": achieved / ALU_PEAK_AD_PER_S, "traffic": traffic,
+                "frac": achieved / ALU_PEAK_AD_PER_S, "traffic": traffic, "traffic_note": traffic_note,
                 "effective": "achieved/frac count the full search's abs-diffs (the method's definition); the kernel "
                              "skips candidates that the exact sub-block bound excludes, so frac can exceed 1",
                 "executed": executed["ad"] / (kms / 1e3) / 1e9,
