@@ -145,6 +145,29 @@ def test_intra_frame_outputs_are_consistent_and_beat_the_flat_prediction():
     assert sse(got["recon"]) <= 1.5 * sse(flat["recon"])
 
 
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_mode_decision_finds_the_copy_modes_and_breaks_ties_low(N):
+    """Vertical stripes (every column constant, random levels) are predicted
+    best by the vertical mode 26 in every CU below the first row (their top
+    neighbours are the reconstructed stripes; any slanted mode shifts them);
+    horizontal stripes by mode 10 right of the first column.  A constant
+    frame at the substitution value 512 is predicted exactly by every mode,
+    so the tie goes to the lowest, planar (0), and nothing is coded."""
+    H = W = 4 * N
+    mask = 0b11100 if N <= 16 else 0b111100
+    s = rng.integers(100, 900, W)
+    cur = np.broadcast_to(s[None, None, :], (3, H, W)).astype(np.uint16).copy()
+    modes = oracle.intra_frame(cur, N, mask, 4)["mode_mv"][:, 0].reshape(H // N, W // N)
+    assert np.all(modes[1:] == 26)
+    s = rng.integers(100, 900, H)
+    cur = np.broadcast_to(s[None, :, None], (3, H, W)).astype(np.uint16).copy()
+    modes = oracle.intra_frame(cur, N, mask, 4)["mode_mv"][:, 0].reshape(H // N, W // N)
+    assert np.all(modes[:, 1:] == 10)
+    cur = np.full((3, H, W), 512, np.uint16)
+    got = oracle.intra_frame(cur, N, mask, 27)
+    assert np.all(got["mode_mv"][:, 0] == 0) and np.array_equal(got["recon"], cur) and not got["levels"].any()
+
+
 # ------------------------------------------------------------- deblocking
 def side_info(H, W, ctu, tu_log2=4, coded=False, mv=None):
     n = (H // ctu) * (W // ctu)
