@@ -214,6 +214,41 @@ def test_no_filtering_at_boundary_strength_zero():
     assert np.array_equal(oracle.deblock_frame(rec, 16, 37, tu, lev, mv, intra=False), rec)
 
 
+def test_boundary_strength_rules_on_a_step_at_a_cu_edge():
+    """A small step between two 16 x 16 CUs (x = 16), filtered where the
+    boundary strength is > 0: vectors differing by 4 quarter samples in x or
+    y (BS 1; by 3: BS 0, untouched), a coded coefficient in the p-side TU
+    that touches the edge, in any channel (BS 1 for all three channels, on
+    that TU's segments only; in a TU away from the edge: untouched), an intra
+    frame (BS 2 everywhere).  The filter moves at most three samples on each
+    side.  (Rows below a filtered segment can change too: the horizontal
+    pass runs after the vertical one and sees the new differences.)"""
+    H, W, ctu, qp = 32, 32, 16, 37
+    rec = np.full((3, H, W), 500, np.uint16)
+    rec[:, :, 16:] = 508
+    zero = np.zeros((3, H, W), np.int16)
+
+    def changed(mv=((0, 0),) * 4, lev=zero, tu=4, intra=False):
+        out = oracle.deblock_frame(rec, ctu, qp, np.full(4, tu, np.uint8), lev, np.array(mv, np.int16), intra)
+        return out != rec
+
+    for mv in ([[0, 0], [4, 0], [0, 0], [0, 0]], [[0, 0], [0, -4], [0, 0], [0, 0]]):
+        c = changed(mv)
+        assert c[:, :16, 15:17].all() and not c[:, 20:].any()
+        assert not c[:, :, :13].any() and not c[:, :, 19:].any()
+    assert not changed([[0, 0], [3, 0], [0, 0], [0, 0]]).any()
+    assert not changed([[0, 0], [0, 3], [0, 0], [0, 0]]).any()
+    lev = zero.copy()
+    lev[2, 3, 12] = 1                       # channel 2, TU x 8..15 / y 0..7
+    c = changed(lev=lev, tu=3)
+    assert c[:, :8, 15:17].all() and not c[:, 12:].any()
+    lev = zero.copy()
+    lev[2, 3, 4] = 1                        # channel 2, TU x 0..7: not at the step
+    assert not changed(lev=lev, tu=3).any()
+    c = changed(intra=True)
+    assert c[:, :, 15:17].all() and not c[:, :, :13].any() and not c[:, :, 19:].any()
+
+
 def test_flat_frame_is_unchanged_at_any_strength():
     rec = np.full((3, 32, 32), 613, np.uint16)
     tu, lev, mv = side_info(32, 32, 16, tu_log2=3)
