@@ -155,6 +155,29 @@ def algorithmic_ad(cfg, T):
     return G * (T - 1) * npu * cfg.ctu ** 2 * (2 * cfg.R + 1) ** 2
 
 
+def butterfly_mults(n):
+    """Multiply-adds of one n-point 1-D transform by partial butterflies (the
+    kernels' form, forward or inverse): the even half recursively, the odd
+    half as an (n/2) x (n/2) product; 2 at n = 2.  The matrix form takes n^2."""
+    return 2 if n == 2 else butterfly_mults(n // 2) + (n // 2) ** 2
+
+
+def transform_macs(cfg, T):
+    """Transform multiply-adds of one encode: every TU size of the mask tiles
+    every CU of every channel, group and frame, and each is transformed
+    forward and back (the RD choice compares the reconstructions), i.e.
+    4 M(n) / n per sample and size.  Returns (butterfly count, matrix-form
+    count, 4 n per sample and size)."""
+    G = (cfg.bands + 2) // 3
+    Hp = -(-cfg.H // cfg.ctu) * cfg.ctu
+    Wp = -(-cfg.W // cfg.ctu) * cfg.ctu
+    samples = G * T * 3 * Hp * Wp
+    sizes = [n for n in cfg.tu_sizes if n <= cfg.ctu]
+    bfly = sum(samples * 4 * butterfly_mults(n) // n for n in sizes)
+    matrix = sum(samples * 4 * n for n in sizes)
+    return bfly, matrix
+
+
 # The sources the persistent encode kernel is compiled from (its translation
 # unit for 16 x 16 CTUs and everything it includes): the recorded DRAM
 # traffic holds only while these are unchanged.
@@ -1036,6 +1059,7 @@ def main():
     kms = statistics.mean(kern_ms)
     achieved = ad / (kms / 1e3)
     executed = executed_ad(cfg, exact_cand, full_cand)
+    tmac = [len(QPS) * sum(transform_macs(cfg, T)[i] for T in lengths) for i in (0, 1)]
     traffic = None if frames_mode else recorded_traffic()
     if traffic is not None:
         traffic_note = "dram bytes read + written per launch, ncu capture of the same kernel sources"
@@ -1056,6 +1080,10 @@ def main():
                 "work_per_launch": f"{ad:.4g} integer-search abs-diffs ({cfg.ctu}^2 x {2 * cfg.R + 1}^2 per PU "
                                    f"and P-frame)",
                 "kernel_ms": kms,
+                "transform": {"butterfly_mac": tmac[0], "matrix_form_mac": tmac[1],
+                              "butterfly_gmac_s_lower_bound": tmac[0] / (kms / 1e3) / 1e9,
+                              "note": "forward + inverse of every allowed TU size over every sample (the RD "
+                                      "choice); the rate divides by the whole encode section, search included"},
                 "peak_basis": "derived: 152 SMs x 96 abs-diffs/clock x 2.07 GHz (issue-limited mix of one-instruction "
                               "__sad on the half-rate ALU pipe and two-instruction FP32 |a-b|; a microbenchmark of "
                               "the mix measured 30.3 T/s)"}

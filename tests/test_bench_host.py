@@ -91,3 +91,56 @@ def test_recorded_traffic_only_for_the_same_sources(tmp_path, monkeypatch):
 def test_recorded_traffic_absent(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.recorded_traffic() is None
+
+
+def _butterfly(x, N, T, count, inverse=False):
+    """An N-point partial butterfly written out in Python (forward y = T x,
+    inverse x = T^T c), counting its multiplications by matrix entries."""
+    if N == 2:
+        count[0] += 2
+        return [64 * (x[0] + x[1]), 64 * (x[0] - x[1])]
+    h = N // 2
+    if not inverse:
+        e = [x[k] + x[N - 1 - k] for k in range(h)]
+        o = [x[k] - x[N - 1 - k] for k in range(h)]
+        ye = _butterfly(e, h, T[::2, :h], count)
+        y = [0] * N
+        y[::2] = ye
+        for k in range(1, N, 2):
+            y[k] = sum(int(T[k, n]) * o[n] for n in range(h))
+            count[0] += h
+        return y
+    ee = _butterfly(x[::2], h, T[::2, :h], count, True)
+    out = [0] * N
+    for n in range(h):
+        o = sum(int(T[2 * i + 1, n]) * x[2 * i + 1] for i in range(h))
+        count[0] += h
+        out[n], out[N - 1 - n] = ee[n] + o, ee[n] - o
+    return out
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 32])
+def test_butterfly_multiply_count(N):
+    """The partial butterfly reproduces the oracle's matrix product exactly
+    (forward and inverse) with bench.butterfly_mults(N) multiplications,
+    against N^2 for the matrix form."""
+    import oracle
+    oracle.build()
+    T = oracle.transform_matrix(N).astype(np.int64)
+    x = np.random.default_rng(N).integers(-512, 512, N)
+    for inverse in (False, True):
+        count = [0]
+        y = _butterfly([int(v) for v in x], N, T, count, inverse)
+        want = (T.T @ x) if inverse else (T @ x)
+        assert np.array_equal(np.array(y), want)
+        assert count[0] == bench.butterfly_mults(N) < N * N
+
+
+def test_transform_work_per_step():
+    """DeepExtremeCubes-shaped step: 3 encodes x 4 groups x 256 frames x 3
+    channels x 128^2 samples, TU 4 / 8 / 16 forward and back: 38.5
+    multiply-adds per sample by butterflies, 112 by the matrix form."""
+    cfg = synth.WORKLOADS["deepextremecubes"]
+    samples = 3 * 4 * 256 * 3 * 128 * 128
+    b, m = (3 * v for v in bench.transform_macs(cfg, cfg.T))
+    assert b * 2 == samples * 77 and m == samples * 112
