@@ -18,7 +18,8 @@ The metric counts pixels x bands x frames of the three encodes per second.
   roofline  the dominant kernel (the persistent kernel, or the per-frame
           chains in that mode): integer-search abs-diffs per launch / its
           event-timed duration, against the ALU peak
-  cpu_baseline  the CPU oracle on a bounded causal prefix of the same cube
+  cpu_baseline  the CPU oracle on a bounded causal prefix of the same cube,
+          on every host core (and, in `single_thread`, on one)
 
 --impl reference times the CPU oracle (the reference arm of this tier) on
 bounded prefixes of the same workload.  Under torchrun each rank runs its own
@@ -215,20 +216,36 @@ def recorded_traffic():
         return None
 
 
-def cpu_baseline(cube, cfg, frames=16):
-    """The oracle, as it stands, on the first `frames` frames at each QP."""
+def cpu_baseline(cube, cfg, frames=16, single_frames=0):
+    """The oracle, as it stands, on the first `frames` frames at each QP, with
+    its OpenMP threads on every host core; with single_frames > 0 also on one
+    thread over the first `single_frames` frames."""
     import oracle
     oracle.build()
-    frames = min(frames, cube.shape[1])
-    sample = cube[:, :frames].copy()
-    t0 = time.perf_counter()
-    for qp in QPS:
-        oracle.encode_cube(sample, cfg.ctu, cfg.R, cfg.tu_mask, qp, want_levels=True)
-    dt = time.perf_counter() - t0
-    work = len(QPS) * cfg.bands * frames * cfg.H * cfg.W / 1e6
-    return {"value": work / dt, "unit": "Mpx·band/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"first {frames} of {cfg.T} frames (causal prefix) of the same cube at QP {QPS}, "
-                      f"{dt:.1f} s"}
+
+    def run(n):
+        n = min(n, cube.shape[1])
+        sample = cube[:, :n].copy()
+        t0 = time.perf_counter()
+        for qp in QPS:
+            oracle.encode_cube(sample, cfg.ctu, cfg.R, cfg.tu_mask, qp, want_levels=True)
+        dt = time.perf_counter() - t0
+        work = len(QPS) * cfg.bands * n * cfg.H * cfg.W / 1e6
+        return work / dt, (f"first {n} of {cfg.T} frames (causal prefix) of the same cube at QP {QPS}, "
+                           f"{dt:.1f} s")
+
+    value, sample = run(frames)
+    out = {"value": value, "unit": "Mpx·band/s", "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": sample}
+    if single_frames:
+        threads = oracle.max_threads()
+        oracle.set_threads(1)
+        try:
+            v1, s1 = run(single_frames)
+        finally:
+            oracle.set_threads(threads)
+        out["single_thread"] = {"value": v1, "unit": "Mpx·band/s", "cores": 1, "sample": s1}
+    return out
 
 
 def plain_concurrent(jobs, stream, flush, k):
@@ -1104,7 +1121,8 @@ def main():
         "gpu_launches": int(launches),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=192 if args.workload == WORKLOAD else 4)
+        dec = args.workload == WORKLOAD
+        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=192 if dec else 4, single_frames=8 if dec else 2)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

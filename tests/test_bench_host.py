@@ -144,3 +144,16 @@ def test_transform_work_per_step():
     samples = 3 * 4 * 256 * 3 * 128 * 128
     b, m = (3 * v for v in bench.transform_macs(cfg, cfg.T))
     assert b * 2 == samples * 77 and m == samples * 112
+
+
+def test_cpu_baseline_all_cores_and_one_thread():
+    import oracle
+    oracle.build()
+    cfg = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny")
+    before = oracle.max_threads()
+    got = bench.cpu_baseline(cube, cfg, frames=4, single_frames=2)
+    assert got["kind"] == "oracle" and got["cores"] == before and got["value"] > 0
+    assert got["single_thread"]["cores"] == 1 and got["single_thread"]["value"] > 0
+    assert "first 2 of 8 frames" in got["single_thread"]["sample"]
+    assert oracle.max_threads() == before          # the thread count is restored
