@@ -5,8 +5,14 @@ per-band min-max quantisation to 10-bit planes with three-band packing
 (paper Sec. 2.1), integer full-search + quarter-pel motion estimation, the
 HEVC-style integer core transform, quantise / dequantise / inverse /
 reconstruct, and the PSNR and bits-per-pixel-per-band reductions (paper
-Sec. 2.3).  The arithmetic lives in ``xvo.c`` (plain C loops, compiled with
-gcc); this module only marshals numpy arrays.
+Sec. 2.3); beyond the encoder, the decoder (the video2xarray step), SSIM and
+spectral angle (Sec. 2.3), frame-0 intra prediction and in-loop deblocking
+(options), and PCA over bands (Sec. 2.1).  The arithmetic lives in ``xvo.c``
+(plain C loops, compiled with gcc); this module only marshals numpy arrays,
+except for PCA, which is numpy in float64 with ``eigh`` as the library step.
+
+Parity unpinned (see ``xvo.h``): the deblocking tC table's individual values
+below QP 36, and the end-to-end outputs of whole synthetic encodes.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA library.
