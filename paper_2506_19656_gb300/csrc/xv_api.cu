@@ -921,15 +921,8 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
             if (total[k] && nt[k] == kFramesMode) return true;
         return false;
     };
-    // the per-frame mode: job i's frames on side stream i mod 16 (motion
-    // search, then transform per frame, as xv_encode_cube runs them), forked
-    // from and joined back into the work stream by events (capturable)
-    auto part_frames = [&]() -> xv_status {
-        cudaError_t err = cudaMemsetAsync(c->b_exact.ptr, 0, sizeof(unsigned long long), st);
-        if (err == cudaSuccess) err = cudaEventRecord(c->fork_ev, st);
-        const int nside = njobs < kSideStreams ? njobs : kSideStreams;
-        for (int k = 0; k < nside && err == cudaSuccess; ++k) err = cudaStreamWaitEvent(c->side[k], c->fork_ev, 0);
-        if (err != cudaSuccess) return cuda_fail(err, "fork");
+    auto run_frames = [&]() -> xv_status {
+        cudaError_t err = cudaSuccess;
         unsigned long long* exact = (unsigned long long*)c->b_exact.ptr;
         for (int i = 0; i < njobs; ++i) {
             const xv_job& j = jobs[i];
@@ -964,11 +957,30 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                     return r;
             }
         }
-        for (int k = 0; k < nside && err == cudaSuccess; ++k) {
-            err = cudaEventRecord(c->side_ev[k], c->side[k]);
-            if (err == cudaSuccess) err = cudaStreamWaitEvent(st, c->side_ev[k], 0);
+        return XV_OK;
+    };
+    // the per-frame mode: job i's frames on side stream i mod 16 (motion
+    // search, then transform per frame, as xv_encode_cube runs them), forked
+    // from and joined back into the work stream by events (capturable).  The
+    // side streams are joined even when a launch fails, so that no work of
+    // the batch is left running after the call returns (and a capture stays
+    // well formed).
+    auto part_frames = [&]() -> xv_status {
+        cudaError_t err = cudaMemsetAsync(c->b_exact.ptr, 0, sizeof(unsigned long long), st);
+        if (err == cudaSuccess) err = cudaEventRecord(c->fork_ev, st);
+        const int nside = njobs < kSideStreams ? njobs : kSideStreams;
+        int forked = 0;  // side streams that joined the fork
+        for (int k = 0; k < nside && err == cudaSuccess; ++k)
+            if ((err = cudaStreamWaitEvent(c->side[k], c->fork_ev, 0)) == cudaSuccess) forked = k + 1;
+        xv_status r = err != cudaSuccess ? cuda_fail(err, "fork") : run_frames();
+        cudaError_t je = cudaSuccess;
+        for (int k = 0; k < forked; ++k) {
+            cudaError_t a = cudaEventRecord(c->side_ev[k], c->side[k]);
+            if (a == cudaSuccess) a = cudaStreamWaitEvent(st, c->side_ev[k], 0);
+            if (je == cudaSuccess) je = a;
         }
-        if (err != cudaSuccess) return cuda_fail(err, "join");
+        if (r) return r;
+        if (je != cudaSuccess) return cuda_fail(je, "join");
         c->batch_nt = kFramesMode;
         return XV_OK;
     };
