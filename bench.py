@@ -168,7 +168,7 @@ def transform_macs(cfg, T):
     every CU of every channel, group and frame, and each is transformed
     forward and back (the RD choice compares the reconstructions), i.e.
     4 M(n) / n per sample and size.  Returns (butterfly count, matrix-form
-    count, 4 n per sample and size)."""
+    count); the matrix form takes 4 n per sample and size."""
     G = (cfg.bands + 2) // 3
     Hp = -(-cfg.H // cfg.ctu) * cfg.ctu
     Wp = -(-cfg.W // cfg.ctu) * cfg.ctu
