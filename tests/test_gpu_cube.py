@@ -95,8 +95,8 @@ def test_ragged_shapes_and_mixed_batch(xv, ctx):
 
 @pytest.mark.parametrize("block_size", [128, 192, 256, 512, 1])
 def test_every_block_size_is_bit_exact(xv, ctx, block_size):
-    """Every persistent-kernel block size, and the per-frame mode (1)."""
-    """The autotuner's candidates all give the oracle's bytes (mixed CTU sizes)."""
+    """The autotuner's candidates, every persistent-kernel block size and the
+    per-frame mode (1), all give the oracle's bytes (mixed CTU sizes)."""
     specs = [((4, 4, 40, 56), 8, 6, 0b1100, 30), ((5, 3, 37, 53), 16, 9, 0b11100, 22),
              ((2, 3, 70, 33), 32, 5, 0b111100, 27)]
     jobs, bufs, wants = [], [], []
