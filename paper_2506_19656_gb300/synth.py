@@ -8,9 +8,11 @@ and the CPU oracle are fed from it.  Every draw comes from
 ``numpy.random.default_rng(seed)`` with ``seed = seed_base + cube`` (a seed
 base per workload).
 
-Each generator is frame-addressable: ``T`` may be smaller than the workload's
-length to draw a causal prefix (the first ``T`` frames are the same numbers a
-full draw would give).
+The DeepExtremeCubes-, DynamicEarthNet- and ERA5-shaped generators are
+frame-addressable: ``T`` may be smaller than the workload's length to draw a
+causal prefix (the first ``T`` frames are the same numbers a full draw would
+give).  The tiny generator is not: its motion steps and noise come from one
+stream whose use depends on ``T``.
 """
 from __future__ import annotations
 
