@@ -1123,6 +1123,9 @@ def main():
                    "the float32 cube (168 MB) is also larger than L2", "parallelism": f"replicas{ws}"},
         "p50_ms": statistics.median(lat_ms), "p99_ms": float(np.percentile(lat_ms, 99)),
         "latency_samples": len(lat_ms),
+        "stage_ms": {"search_and_transform": kms, "rest": statistics.mean(step_ms) - kms,
+                     "rest_is": "min/max, quantise/pack, PSNR, rate totals and the results read-back (the step's "
+                                "time outside the encode section)"},
         "plain": plain, "e2e": e2e, "roofline": roofline, "clocks": clk,
         "gpu_launches": int(launches),
     }
