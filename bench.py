@@ -954,8 +954,9 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--frames-per-tick", type=int, default=8)
     ap.add_argument("--block-size", type=int, default=0,
-                    help="persistent-kernel block size (128/192/256/512) instead of the autotuner's choice, e.g. to "
-                         "profile the variant an uninstrumented run picks")
+                    help="the batched path's execution mode instead of the autotuner's choice: a persistent-kernel "
+                         "block size (128/192/256/512) or 1 for the per-frame mode, e.g. to profile the variant an "
+                         "uninstrumented run picks")
     args = ap.parse_args()
     globals()["QPS"] = tuple(int(q) for q in args.qps.split(",")) if args.qps else default_qps(args.workload)
     if args.warmup < 3:
