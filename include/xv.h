@@ -469,13 +469,15 @@ xv_status xv_serve_stop(xv_ctx* ctx);
 
 /* ------------------------------------------------------ measurement */
 
-/* Device time of the persistent kernel launches of the last xv_encode_batch
- * on this context (CUDA events recorded on the call's stream around the
- * launches), in milliseconds.  Host only. */
+/* Device time of the encode section of the last xv_encode_batch on this
+ * context: the persistent kernel launches, or in the per-frame mode the jobs'
+ * per-frame chains from their fork to their join (CUDA events recorded on the
+ * call's stream around them), in milliseconds.  Host only. */
 xv_status xv_last_batch_kernel_ms(const xv_ctx* ctx, double* ms);
 /* xv_encode_batch runs a batch as one CUDA graph: captured on the first call
  * with a given set of jobs (shapes, parameters and buffer pointers) and the
- * autotuned block size, replayed while the same batch is submitted again.
+ * autotuned block size or mode, replayed while the same batch is submitted
+ * again.
  * `enable` = 0 launches the same kernels directly instead.  Host only. */
 xv_status xv_set_batch_graphs(xv_ctx* ctx, int enable);
 /* Graphs captured and graph launches so far on this context.  Host only. */
