@@ -11,8 +11,8 @@ spectral angle (Sec. 2.3), frame-0 intra prediction and in-loop deblocking
 (plain C loops, compiled with gcc); this module only marshals numpy arrays,
 except for PCA, which is numpy in float64 with ``eigh`` as the library step.
 
-Parity unpinned (see ``xvo.h``): the deblocking tC table's individual values
-below QP 36, and the end-to-end outputs of whole synthetic encodes.
+Parity unpinned (see ``xvo.h``): only the end-to-end outputs of whole
+synthetic encodes, which no published value fixes.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA library.

@@ -18,11 +18,12 @@
  * in-loop deblocking as options (readings R4/R5); PCA over bands (Sec. 2.1,
  * reading R3) is in the Python module, numpy over eigh.
  *
- * Parity unpinned: the deblocking tC table's individual values below QP 36
- * (the standard's printed values, restated; the tests pin only the table's
- * monotone growth, its endpoints and the beta table's piecewise-linear law),
- * and the end-to-end outputs of whole synthetic encodes, which no published
- * value fixes (they are pinned through the invariants of every step).
+ * Parity unpinned: only the end-to-end outputs of whole synthetic encodes,
+ * which no published value fixes (they are pinned through the invariants of
+ * every step).  The deblocking beta'/tC' tables are pinned value by value to
+ * the standard's table (a golden fixture), and the refinement's visiting
+ * order and strict-improvement rule to an independent restatement on frames
+ * built to tie.
  *
  * All signed right shifts are arithmetic (floor).  Bit depth B = 10.
  */

@@ -208,6 +208,23 @@ def test_threshold_tables_follow_their_design_laws():
     assert oracle.deblock_params(60, 1) == oracle.deblock_params(53, 1)
 
 
+def test_threshold_tables_equal_the_published_values():
+    """Every beta' (Q = 0..51) and tC' (Q = 0..53) value equals the standard's
+    table (tests/golden/hevc_deblock_thresholds.txt), scaled by 2^(10-8):
+    beta at bS 1 and tC at Q = qp with bS 1, i.e. no offset."""
+    from conftest import read_golden
+    g = read_golden("hevc_deblock_thresholds.txt")
+    beta, tc = g["BETA"][0], g["TC"][0]
+    assert len(beta) == 52 and len(tc) == 54
+    for q in range(54):
+        b, t = oracle.deblock_params(q, 1)
+        assert b == 4 * beta[min(q, 51)], q
+        assert t == 4 * tc[q], q
+    # intra edges (bS 2) read tC' two steps up, clamped at 53
+    for q in range(54):
+        assert oracle.deblock_params(q, 2)[1] == 4 * tc[min(q + 2, 53)], q
+
+
 def test_no_filtering_at_boundary_strength_zero():
     rec = rng.integers(0, 1024, (3, 32, 32)).astype(np.uint16)
     tu, lev, mv = side_info(32, 32, 16)

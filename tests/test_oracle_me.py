@@ -4,6 +4,8 @@ and an independent numpy brute force on tiny frames."""
 import numpy as np
 import pytest
 
+from conftest import read_golden
+
 
 def test_ue_lengths(xvo):
     # se(v) -> ue(k): 0->0, 1->1, -1->2, 2->3, -2->4 ...; Exp-Golomb code
@@ -139,3 +141,149 @@ def test_planted_subpel_shift_is_recovered(xvo, mvq):
                 assert J[pu] == xvo.mv_cost(mvq[0], mvq[1], lmv)
                 hits += 1
     assert hits >= 2
+
+
+# ---------------------------------------------------------------------------
+# Independent restatement of the quarter-sample refinement (C8): its own
+# interpolation from the published taps, its own SATD from scipy's Hadamard
+# matrix, and the stated search order.  The oracle's refinement must agree
+# with it on frames built to tie, where a wrong visiting order, a
+# non-strict replacement or a wrong centre for the second stage change the
+# answer.
+
+RING = [(-1, -1), (0, -1), (1, -1), (-1, 0), (1, 0), (-1, 1), (0, 1), (1, 1)]
+
+
+def _se_bits(v):
+    k = 2 * v - 1 if v > 0 else -2 * v
+    return 2 * int(np.floor(np.log2(k + 1))) + 1
+
+
+def _interp(ref, x0, y0, n, mvx, mvy, taps):
+    """The n x n prediction at quarter-sample vector (mvx, mvy): edge-padded
+    reference, full samples << 4, one fractional axis >> 2, both: horizontal
+    >> 2 then vertical >> 6, weighted-default rounding (v + 8) >> 4, 10 bits."""
+    pad = 80
+    p = np.pad(ref.astype(np.int64), pad, mode="edge")
+    ix, fx, iy, fy = mvx >> 2, mvx & 3, mvy >> 2, mvy & 3
+    ys = y0 + iy + pad + np.arange(-3, n + 5)
+    xs = x0 + ix + pad + np.arange(-3, n + 5)
+    win = p[np.ix_(ys, xs)]  # rows/cols -3 .. n+4 around the block
+    if fx:
+        f = np.asarray(taps[fx], np.int64)
+        h = sum(f[i] * win[:, i:i + n] for i in range(8)) >> 2   # rows -3..n+4, cols 0..n-1
+    else:
+        h = win[:, 3:3 + n]
+    if fy:
+        f = np.asarray(taps[fy], np.int64)
+        v = sum(f[i] * h[i:i + n, :] for i in range(8))
+        v = v >> (6 if fx else 2)
+    else:
+        v = h[3:3 + n, :] if fx else h[3:3 + n, :] << 4
+    return np.clip((v + 8) >> 4, 0, 1023)
+
+
+def _satd(d):
+    import scipy.linalg
+    H8 = scipy.linalg.hadamard(8)
+    s = 0
+    for by in range(0, d.shape[0], 8):
+        for bx in range(0, d.shape[1], 8):
+            s += (int(np.abs(H8 @ d[by:by + 8, bx:bx + 8] @ H8.T).sum()) + 2) >> 2
+    return s
+
+
+def restated_refinement(cur, ref, ctu, lmv, mv_int, taps, order=RING, strict=True, second_centre="best"):
+    """Per PU: J at 4 mv_int, then the 8 half-sample neighbours in `order`
+    (replace when J is strictly lower), then the 8 quarter-sample neighbours
+    of the best.  The keyword arguments plant known mistakes for the
+    sensitivity check below."""
+    H, W = cur.shape
+    nx = W // ctu
+    out, cost = [], []
+    for pu in range(len(mv_int)):
+        x0, y0 = (pu % nx) * ctu, (pu // nx) * ctu
+        blk = cur[y0:y0 + ctu, x0:x0 + ctu].astype(np.int64)
+
+        def J(mx, my):
+            sat = _satd(blk - _interp(ref, x0, y0, ctu, mx, my, taps))
+            return sat + ((lmv * (_se_bits(mx) + _se_bits(my)) + 32768) >> 16)
+
+        start = (4 * int(mv_int[pu][0]), 4 * int(mv_int[pu][1]))
+        best, bJ = start, J(*start)
+        for step in (2, 1):
+            c = best if (step == 2 or second_centre == "best") else start
+            for ox, oy in order:
+                m = (c[0] + step * ox, c[1] + step * oy)
+                j = J(*m)
+                if j < bJ or (not strict and j == bJ):
+                    best, bJ = m, j
+        out.append(best)
+        cost.append(bJ)
+    return out, cost
+
+
+def _tie_frames():
+    """(cur, ref) pairs whose candidates tie often: constant, period-2
+    stripes in x and y, a checkerboard, a ramp, and a random texture."""
+    rng = np.random.default_rng(31)
+    H = W = 24
+    yy, xx = np.mgrid[0:H, 0:W]
+    planes = [
+        np.full((H, W), 600),
+        np.where(xx % 2 == 0, 200, 800),
+        np.where(yy % 2 == 0, 300, 700),
+        np.where((xx + yy) % 2 == 0, 100, 900),
+        4 * xx + 8 * yy + 50,
+        rng.integers(0, 1024, (H, W)),
+    ]
+    out = []
+    for i, r in enumerate(planes):
+        r = r.astype(np.uint16)
+        out.append((r, r))                                       # cur = ref
+        out.append((np.roll(r, (1, -1), axis=(0, 1)), r))        # shifted copy
+        c = np.clip(r.astype(np.int64) + rng.integers(-3, 4, r.shape), 0, 1023).astype(np.uint16)
+        out.append((c, r))                                       # noisy copy
+    return out
+
+
+def _starts(n, rng):
+    return np.array([[int(rng.integers(-3, 4)), int(rng.integers(-3, 4))] for _ in range(n)], np.int16)
+
+
+def test_refinement_matches_independent_restatement(xvo):
+    taps_g = read_golden("hevc_luma_filter.txt")
+    taps = {1: taps_g["QUARTER"][0], 2: taps_g["HALF"][0], 3: taps_g["THREEQUARTER"][0]}
+    rng = np.random.default_rng(7)
+    ctu = 8
+    for cur, ref in _tie_frames():
+        for lmv in (4096, 65536, 300000):  # small lambdas round many bit counts to one cost
+            starts = _starts((cur.shape[0] // ctu) * (cur.shape[1] // ctu), rng)
+            mv, J = xvo.me_qpel(cur, ref, ctu, lmv, starts)
+            want, wJ = restated_refinement(cur, ref, ctu, lmv, starts, taps)
+            assert [tuple(int(v) for v in m) for m in mv] == want
+            assert [int(j) for j in J] == wJ
+
+
+def test_refinement_fixture_detects_planted_mistakes(xvo):
+    """The frames above separate the stated order from plausible misreadings:
+    for each planted mistake at least one PU's answer changes."""
+    taps_g = read_golden("hevc_luma_filter.txt")
+    taps = {1: taps_g["QUARTER"][0], 2: taps_g["HALF"][0], 3: taps_g["THREEQUARTER"][0]}
+    mistakes = {
+        "non-strict replacement": dict(strict=False),
+        "reversed ring order": dict(order=RING[::-1]),
+        "column-major ring order": dict(order=sorted(RING)),
+        "second stage around the start": dict(second_centre="start"),
+    }
+    ctu = 8
+    found = {k: False for k in mistakes}
+    rng = np.random.default_rng(7)
+    for cur, ref in _tie_frames():
+        for lmv in (4096, 65536, 300000):
+            starts = _starts((cur.shape[0] // ctu) * (cur.shape[1] // ctu), rng)
+            right = restated_refinement(cur, ref, ctu, lmv, starts, taps)
+            for k, kw in mistakes.items():
+                if not found[k] and restated_refinement(cur, ref, ctu, lmv, starts, taps, **kw) != right:
+                    found[k] = True
+    assert all(found.values()), found
