@@ -1,29 +1,32 @@
 #!/usr/bin/env python3
 """Throughput of the encoder-analysis path on GB300, one JSON line.
 
-Workload: the DeepExtremeCubes-shaped cube (10 float32 bands, 256 frames of
-128 x 128, synthetic -- see paper_2506_19656_gb300/synth.py) encoded at QP 22,
-27 and 32 (CTU 16, search range 32, TU 4/8/16).  One step is the whole path
-for the three encodes -- min/max, quantise/pack, motion search, transform /
-quantise / reconstruct, PSNR and rate -- through the batched C-ABI call
-xv_encode_batch (one captured graph: the persistent kernel, or the jobs as
-per-frame chains on concurrent streams, whichever the autotuner timed faster).
-The metric counts pixels x bands x frames of the three encodes per second.
+Workload (default): the ERA5-shaped batch -- six float32 variables on the
+721 x 1440 grid, six sub-cubes of T = 24, 53, 82, 110, 139 and 168 frames
+(synthetic -- see paper_2506_19656_gb300/synth.py), each encoded at QP 22
+(CTU 32, search range 16, TU 4/8/16/32) in ONE batched C-ABI call,
+xv_encode_batch (captured graphs: one persistent launch over all sub-cubes,
+or the jobs as per-frame chains on concurrent streams, whichever the
+autotuner timed faster).  One step is the whole path for the six sub-cubes --
+min/max, quantise/pack, motion search, transform / quantise / reconstruct,
+PSNR and rate.  The metric counts pixels x bands x frames per second.
 
   value   inputs resident in HBM, device time of K steps (CUDA events)
-  e2e     the same call with the cube copied from pinned host memory and the
-          results read back inside every timed step
-  plain   the per-frame launch path (xv_encode_cube per encode), same work,
+  e2e     one xv_encode_batch_from_host call per step: the cubes copied from
+          pinned host memory by the library, the host results read back
+  plain   the per-frame launch path (xv_encode_cube per sub-cube), same work,
           one encode after another and on concurrent streams
   roofline  the dominant kernel (the persistent kernel, or the per-frame
           chains in that mode): integer-search abs-diffs per launch / its
-          event-timed duration, against the ALU peak
-  cpu_baseline  the CPU oracle on a bounded causal prefix of the same cube,
-          on every host core (and, in `single_thread`, on one)
+          event-timed duration, against the measured ALU peak
+  cpu_baseline  the CPU oracle on a bounded sample (the whole T = 24
+          sub-cube), on every host core (and, in `single_thread`, on one)
+  deepextremecubes  the DeepExtremeCubes-shaped step (QP 22/27/32) beside it
 
---impl reference times the CPU oracle (the reference arm of this tier) on
-bounded prefixes of the same workload.  Under torchrun each rank runs its own
-replica (the path has no exchange step); rank 0 prints.
+--workload selects another workload; --impl reference times the CPU oracle
+(the reference arm of this tier) on bounded samples of the same workload.
+Under torchrun each rank runs its own replica (the path has no exchange
+step); rank 0 prints.
 """
 from __future__ import annotations
 
@@ -41,15 +44,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mpx·band/s of ME+transform/quant/recon (bit-exact), batched vs plain; p50/p99"
-WORKLOAD = "deepextremecubes"
+WORKLOAD = "era5"
 QPS = (22, 27, 32)
-# ALU roofline of the motion search.  One exact 10-bit abs-diff-accumulate is
-# either one __sad on the integer ALU pipe (64 lanes/clock/SM, half the issue
-# rate) or two FP32 instructions (|a - b| accumulated in float, exact for these
-# integers).  With one warp instruction issued per clock per SMSP, sending 2/3
-# of the abs-diffs to the ALU and 1/3 to the FP32 pipe gives 96 per clock per
-# SM: 152 SMs x 96 x 2.07 GHz.
-ALU_PEAK_AD_PER_S = 152 * 96 * 2.07e9
+CTU = 0  # 0: the workload's own CTU size; else the --ctu override
 
 
 def dist_env():
@@ -147,6 +144,14 @@ def executed_ad(cfg, exact_cand, full_cand):
             "exact_fraction": exact_cand / full_cand if full_cand else None}
 
 
+def work_items(cfg, T):
+    """Work items of one encode: one per PU (= CU) and frame of every group."""
+    G = (cfg.bands + 2) // 3
+    Hp = -(-cfg.H // cfg.ctu) * cfg.ctu
+    Wp = -(-cfg.W // cfg.ctu) * cfg.ctu
+    return G * T * (Hp // cfg.ctu) * (Wp // cfg.ctu)
+
+
 def algorithmic_ad(cfg, T):
     """Integer-search abs-diffs of one encode: N^2 (2R+1)^2 per PU and P-frame."""
     G = (cfg.bands + 2) // 3
@@ -179,27 +184,33 @@ def transform_macs(cfg, T):
     return bfly, matrix
 
 
-# The sources the persistent encode kernel is compiled from (its translation
-# unit for 16 x 16 CTUs and everything it includes): the recorded DRAM
-# traffic holds only while these are unchanged.
-PERSIST_SOURCES = ("paper_2506_19656_gb300/csrc/k_batch_ctu16.cu", "paper_2506_19656_gb300/csrc/batch.cuh",
-                   "paper_2506_19656_gb300/csrc/dec.cuh", "paper_2506_19656_gb300/csrc/me.cuh",
-                   "paper_2506_19656_gb300/csrc/tqr.cuh", "paper_2506_19656_gb300/csrc/xv_dev.cuh",
-                   "paper_2506_19656_gb300/csrc/xv_internal.h", "include/xv.h")
+# The sources a dominant kernel is compiled from: the persistent encode
+# kernel's translation unit for its CTU size, or the per-frame kernels', and
+# the device headers they include.  A recorded DRAM traffic figure holds only
+# while these are unchanged.
+_CSRC = "paper_2506_19656_gb300/csrc/"
 
 
-def kernel_sources_sha():
+def kernel_sources(mode, ctu):
+    base = (_CSRC + "me.cuh", _CSRC + "tqr.cuh", _CSRC + "xv_dev.cuh", _CSRC + "xv_internal.h")
+    if mode == "persist":
+        return (_CSRC + f"k_batch_ctu{ctu}.cu", _CSRC + "batch.cuh", _CSRC + "dec.cuh") + base
+    return (_CSRC + "k_frame.cu",) + base
+
+
+def kernel_sources_sha(files):
     h = hashlib.sha256()
-    for f in PERSIST_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the persistent kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_persist_deepextremecubes_traffic.txt")
+def recorded_traffic(name, files):
+    """DRAM bytes (read + written) per work item (one PU of one frame) of a
+    kernel, from the committed ncu summary profiles/<name>_traffic.txt, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -208,22 +219,32 @@ def recorded_traffic():
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("sources_sha") != kernel_sources_sha():
+    if vals.get("sources_sha") != kernel_sources_sha(files):
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_item"])
     except (KeyError, ValueError):
         return None
 
 
-def cpu_baseline(cube, cfg, frames=16, single_frames=0):
+def cpu_sample_frames(workload, cfg):
+    """The oracle's bounded sample of a workload, as frames of its first cube:
+    the T = 24 ERA5-shaped sub-cube in full, the first 8 frames of the
+    DynamicEarthNet-shaped cube, 192 of the 256 DeepExtremeCubes-shaped frames
+    (about 10-30 s of host time each), the whole tiny cube."""
+    return {"era5": cfg.sub_T[0] if cfg.sub_T else cfg.T, "dynamicearthnet": 8,
+            "deepextremecubes": 192}.get(workload, cfg.T)
+
+
+def cpu_baseline(cube, cfg, frames=16, single_frames=0, whole=False):
     """The oracle, as it stands, on the first `frames` frames at each QP, with
     its OpenMP threads on every host core; with single_frames > 0 also on one
-    thread over the first `single_frames` frames."""
+    thread over the first `single_frames` frames.  whole: the sample is a whole
+    sub-cube of the workload (its own min/max), not a causal prefix."""
     import oracle
     oracle.build()
 
-    def run(n):
+    def run(n, is_whole):
         n = min(n, cube.shape[1])
         sample = cube[:, :n].copy()
         t0 = time.perf_counter()
@@ -231,17 +252,18 @@ def cpu_baseline(cube, cfg, frames=16, single_frames=0):
             oracle.encode_cube(sample, cfg.ctu, cfg.R, cfg.tu_mask, qp, want_levels=True)
         dt = time.perf_counter() - t0
         work = len(QPS) * cfg.bands * n * cfg.H * cfg.W / 1e6
-        return work / dt, (f"first {n} of {cfg.T} frames (causal prefix) of the same cube at QP {QPS}, "
-                           f"{dt:.1f} s")
+        what = (f"the whole T = {n} sub-cube" if is_whole else
+                f"first {n} of {cfg.T} frames (causal prefix) of the same cube")
+        return work / dt, f"{what} at QP {QPS}, {dt:.1f} s"
 
-    value, sample = run(frames)
+    value, sample = run(frames, whole)
     out = {"value": value, "unit": "Mpx·band/s", "cores": oracle.max_threads(), "kind": "oracle",
            "sample": sample}
     if single_frames:
         threads = oracle.max_threads()
         oracle.set_threads(1)
         try:
-            v1, s1 = run(single_frames)
+            v1, s1 = run(single_frames, False)
         finally:
             oracle.set_threads(threads)
         out["single_thread"] = {"value": v1, "unit": "Mpx·band/s", "cores": 1, "sample": s1}
@@ -288,9 +310,10 @@ def plain_concurrent(jobs, stream, flush, k):
 
 def default_qps(workload):
     """The QPs one step encodes when --qps is not given: 22, 27 and 32 for the
-    DeepExtremeCubes-shaped cube, the workload's own QPs otherwise."""
+    DeepExtremeCubes-shaped cube, the workload's own QPs otherwise (22 for the
+    ERA5-shaped sub-cubes)."""
     from paper_2506_19656_gb300 import synth
-    return (22, 27, 32) if workload == WORKLOAD else tuple(synth.WORKLOADS[workload].qps)
+    return (22, 27, 32) if workload == "deepextremecubes" else tuple(synth.WORKLOADS[workload].qps)
 
 
 def workload_jobs(workload, frames=0, device=None, qps=None):
@@ -308,6 +331,8 @@ def workload_jobs(workload, frames=0, device=None, qps=None):
     cfg = synth.WORKLOADS[workload]
     if frames:
         cfg = dataclasses.replace(cfg, T=frames)
+    if CTU:
+        cfg = dataclasses.replace(cfg, ctu=CTU)
     lengths = list(cfg.sub_T) if cfg.sub_T and not frames else [cfg.T]
     cube = synth.make_cube(workload, T=max(lengths))
     full = torch.from_numpy(cube)
@@ -326,16 +351,26 @@ def workload_jobs(workload, frames=0, device=None, qps=None):
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle on bounded samples of the workload."""
+    """Reference arm: the CPU oracle on bounded samples of the workload (the
+    ERA5-shaped sub-cubes by default: each step encodes the first 3 frames of
+    the T = 24 sub-cube; the DeepExtremeCubes-shaped cube: its first 8 frames
+    at each QP)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from paper_2506_19656_gb300 import synth
+    import dataclasses
+
+    import numpy as np
+
     import oracle
+    from paper_2506_19656_gb300 import synth
     oracle.build()
-    cfg = synth.WORKLOADS[WORKLOAD]
-    frames = 8
-    cube = synth.make_cube(WORKLOAD, T=frames)
+    cfg = synth.WORKLOADS[args.workload]
+    if CTU:
+        cfg = dataclasses.replace(cfg, ctu=CTU)
+    frames = {"era5": 3, "dynamicearthnet": 2, "tiny": cfg.T}.get(args.workload, 8)
+    cube = synth.make_cube(args.workload, T=max(frames, cfg.sub_T[0] if cfg.sub_T else frames))
+    cube = np.ascontiguousarray(cube[:, :frames])
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -353,7 +388,7 @@ def run_reference(args):
         "config": {"workload": cfg.name, "qps": list(QPS), "ctu": cfg.ctu, "search_range": cfg.R,
                    "tu_sizes": list(cfg.tu_sizes), "sample_frames": frames},
         "cpu_baseline": {"value": value, "unit": "Mpx·band/s", "cores": oracle.max_threads(), "kind": "oracle",
-                         "sample": f"first {frames} of {cfg.T} frames (causal prefix) at QP {QPS} per step"},
+                         "sample": f"first {frames} frames of the workload's first (sub-)cube at QP {QPS} per step"},
         "e2e": {"value": value, "unit": "Mpx·band/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -928,6 +963,111 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_peaks(ctx):
+    """The device's measured rates of the roofline's instruction sequences
+    (xv_measure_peak): abs-diff-accumulates as sad, on the FP32 pipe and as
+    their mix, and 32-bit integer multiply-adds."""
+    from paper_2506_19656_gb300 import xv
+    out = {}
+    for kind, name in xv.PEAK_KINDS.items():
+        rate, ms = xv.xv_measure_peak(ctx, kind)
+        out[name] = {"per_s": rate, "ms": ms}
+    out["absdiff_best"] = max(out[k]["per_s"] for k in ("sad", "fp32_absdiff", "sad_fp32_mix"))
+    return out
+
+
+def kernels_alone(ctx, cfg, bufs, flush, stream, reps=3):
+    """The motion search and the transform chain each timed on their own, as
+    the per-frame kernels over every P-frame of every encode at once: frames
+    1..T-1 of a group are the "groups" of one call (plane stride one frame),
+    the encode's own reconstructions are the references and, for the
+    transform, its vectors the motion.  The outputs must equal the batched
+    encode's bit for bit (checked), so the times are of the same work."""
+    import torch
+    from paper_2506_19656_gb300 import xv
+    calls = []
+    for b in bufs:
+        G, T, _, Hp, Wp = b["planes"].shape
+        if T < 2:
+            continue
+        npu = b["mv"].shape[2]
+        p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, b["qp"])
+        o = dict(mv=torch.zeros_like(b["mv"]), recon=torch.zeros_like(b["recon"]),
+                 levels=torch.zeros_like(b["levels"]), tu=torch.zeros_like(b["tu_log2"]),
+                 bits=torch.zeros_like(b["bits"]))
+        calls.append((b, o, p, G, T, Hp, Wp, npu))
+
+    def run_me():
+        for b, o, p, G, T, Hp, Wp, npu in calls:
+            for g in range(G):
+                xv.xv_motion_search(ctx, b["planes"][g, 1], b["recon"][g, 0], T - 1, 3 * Hp * Wp, Hp, Wp, p,
+                                    o["mv"][g, 1], pu_gstride=npu)
+
+    def run_tqr():
+        for b, o, p, G, T, Hp, Wp, npu in calls:
+            o["bits"].zero_()  # the transform adds each CU's bits to its frame's total
+            for g in range(G):
+                xv.xv_transform_quant_recon(ctx, b["planes"][g, 1], b["recon"][g, 0], b["mv"][g, 1], T - 1,
+                                            3 * Hp * Wp, Hp, Wp, p, npu, o["recon"][g, 1], o["levels"][g, 1],
+                                            o["tu"][g, 1], o["bits"][g, 1], 1)
+
+    def timed(fn):
+        best = None
+        for _ in range(reps + 1):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+        return best
+    me_ms, tqr_ms = timed(run_me), timed(run_tqr)
+    for b, o, *_ in calls:  # the same results as the batched encode
+        assert torch.equal(o["mv"][:, 1:], b["mv"][:, 1:]), "motion search alone differs from the encode"
+        for k, kb in (("recon", "recon"), ("levels", "levels"), ("tu", "tu_log2"), ("bits", "bits")):
+            assert torch.equal(o[k][:, 1:], b[kb][:, 1:]), f"transform alone: {k} differs from the encode"
+    launches = sum(c[3] for c in calls)
+    del calls
+    torch.cuda.empty_cache()
+    return me_ms, tqr_ms, launches
+
+
+def secondary_line(ctx, dev, flush, stream, steps=10):
+    """The DeepExtremeCubes-shaped step (QP 22, 27 and 32 through
+    xv_encode_batch) beside the headline: device time per step, value and the
+    search's effective ALU fraction."""
+    from paper_2506_19656_gb300 import xv
+    import torch
+    cfg, lengths, _, _, jobs, bufs = workload_jobs("deepextremecubes", 0, dev, qps=(22, 27, 32))
+    for _ in range(3):
+        xv.xv_encode_batch(ctx, jobs)
+    torch.cuda.synchronize()
+    ms, kms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xv.xv_encode_batch(ctx, jobs)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        kms.append(xv.xv_last_batch_kernel_ms(ctx))
+    work_mpx = 3 * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
+    ad = 3 * sum(algorithmic_ad(cfg, T) for T in lengths)
+    k = statistics.mean(kms)
+    out = {"workload": cfg.name, "qps": [22, 27, 32], "value": work_mpx / (statistics.mean(ms) / 1e3),
+           "unit": "Mpx·band/s", "ms_per_step": statistics.mean(ms), "steps": steps,
+           "block_size": xv.xv_last_batch_block_size(ctx), "encode_section_ms": k,
+           "search_effective_gad_s": ad / (k / 1e3) / 1e9}
+    del jobs, bufs
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -936,14 +1076,20 @@ def main():
     ap.add_argument("--impl", default="xv", choices=["xv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-alone", action="store_true",
+                    help="skip timing the motion search and the transform chain on their own")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the DeepExtremeCubes-shaped line reported beside the ERA5-shaped headline")
     ap.add_argument("--qps", default="",
                     help="QPs of the encodes in one step (default: 22,27,32 for the DeepExtremeCubes-shaped cube, "
                          "the workload's own otherwise)")
     ap.add_argument("--frames", type=int, default=0, help="encode only the first F frames (profiling cases)")
+    ap.add_argument("--ctu", type=int, default=0, choices=[0, 8, 16, 32, 64],
+                    help="CTU size instead of the workload's own (the encode changes with it)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["tiny", "deepextremecubes", "dynamicearthnet", "era5"],
-                    help="the DeepExtremeCubes-shaped cube (default), the tiny cube, the DynamicEarthNet-shaped "
-                         "uint16 cube or the ERA5-shaped sub-cubes")
+                    help="the ERA5-shaped sub-cubes (default: six uneven-length sub-cubes in one batch), the "
+                         "DeepExtremeCubes-shaped cube, the DynamicEarthNet-shaped uint16 cube or the tiny cube")
     ap.add_argument("--serve", action="store_true", help="the serving run (request stream) instead")
     ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
     ap.add_argument("--metrics", action="store_true", help="the SSIM / spectral-angle run instead")
@@ -958,6 +1104,7 @@ def main():
                          "block size (128/192/256/512) or 1 for the per-frame mode, e.g. to profile the variant an "
                          "uninstrumented run picks")
     args = ap.parse_args()
+    globals()["CTU"] = args.ctu
     globals()["QPS"] = tuple(int(q) for q in args.qps.split(",")) if args.qps else default_qps(args.workload)
     if args.warmup < 3:
         args.warmup = 3
@@ -1022,6 +1169,7 @@ def main():
     for _ in range(args.warmup):
         batched()
     torch.cuda.synchronize()
+    peaks = measured_peaks(ctx)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -1032,14 +1180,14 @@ def main():
     torch.cuda.synchronize()
     barrier()
     launches = xv.xv_ctx_launches(ctx) - launches0
-    clk = clocks.stop()
     block_size = xv.xv_last_batch_block_size(ctx)
     exact_cand, full_cand = xv.xv_last_batch_search_stats(ctx)
-    # step latency percentiles over at least 20 timed repeats: the K timed
-    # steps, topped up after the timed region when K < 20
-    lat_ms = list(step_ms)
-    if len(lat_ms) < 20:
-        lat_ms += timed(batched, 20 - len(lat_ms))[0]
+    # step latency percentiles over at least 20 repeats: the K timed steps,
+    # topped up when K < 20 by further steps timed the same way, still inside
+    # the clock sampling (they do not enter `value`)
+    extra_ms = timed(batched, 20 - len(step_ms))[0] if len(step_ms) < 20 else []
+    lat_ms = list(step_ms) + extra_ms
+    clk = clocks.stop()
 
     total_ms = max_over_ranks(sum(step_ms), dist if ws > 1 else None, dev)
     value = whole_job_value(work_mpx, args.steps, ws, total_ms)
@@ -1056,13 +1204,14 @@ def main():
         plain["concurrent"] = plain_concurrent(jobs, stream, flush, max(3, min(args.steps, 5)))
         plain["concurrent"]["value"] = work_mpx / (plain["concurrent"]["ms_per_step"] / 1e3)
 
-    # end to end: the cube from pinned host memory, results read back, every step
+    # end to end: one C-ABI call per step that takes the cubes from pinned host
+    # memory (the library copies them in) and returns the host results (PSNR,
+    # rate) read back from the device
     hosts = [torch.from_numpy(cube[:, :T].copy()).pin_memory() for T in lengths]
+    host_of_job = [hosts[lengths.index(b["T"])] if i % len(QPS) == 0 else None for i, b in enumerate(bufs)]
 
     def e2e_step():
-        for h, d in zip(hosts, srcs):
-            d.copy_(h, non_blocking=True)
-        return xv.xv_encode_batch(ctx, jobs)  # returns host results (PSNR, bits)
+        return xv.xv_encode_batch_from_host(ctx, jobs, host_of_job)
 
     for _ in range(2):
         e2e_step()
@@ -1075,41 +1224,61 @@ def main():
 
     # roofline of the dominant kernel(s): the persistent encode, or in the
     # per-frame mode (block size 1) the motion-search and transform launches
-    # of the concurrent chains (the recorded traffic is the persistent
-    # kernel's, so none then)
+    # of the concurrent chains; the peak is measured on this device now
     frames_mode = block_size == 1
     ad = len(QPS) * sum(algorithmic_ad(cfg, T) for T in lengths)
     kms = statistics.mean(kern_ms)
     achieved = ad / (kms / 1e3)
     executed = executed_ad(cfg, exact_cand, full_cand)
     tmac = [len(QPS) * sum(transform_macs(cfg, T)[i] for T in lengths) for i in (0, 1)]
-    traffic = None if frames_mode else recorded_traffic()
-    if traffic is not None:
-        traffic_note = "dram bytes read + written per launch, ncu capture of the same kernel sources"
-    elif frames_mode:
-        traffic_note = "none: no ncu DRAM capture of the per-frame chains is recorded"
+    items = len(QPS) * sum(work_items(cfg, T) for T in lengths)
+    if frames_mode:
+        per = [recorded_traffic(f"k_{k}_frame_{cfg.ctu}", kernel_sources("frames", cfg.ctu)) for k in ("me", "tqr")]
+        per_item = None if None in per else sum(per)
     else:
-        traffic_note = "none: the recorded ncu capture was taken on other kernel sources"
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": ALU_PEAK_AD_PER_S / 1e9, "unit": "GAD/s",
-                "frac": achieved / ALU_PEAK_AD_PER_S, "traffic": traffic, "traffic_note": traffic_note,
+        per_item = recorded_traffic(f"k_persist_{cfg.ctu}", kernel_sources("persist", cfg.ctu))
+    traffic = per_item * items if per_item is not None else None
+    traffic_note = (f"ncu dram bytes read + written per work item ({per_item:.0f} B, a capture of the same kernel "
+                    f"sources on a short prefix) x {items} items of this launch" if per_item is not None else
+                    "none: no ncu DRAM capture of the current kernel sources is recorded for this kernel")
+    peak_ad = peaks["absdiff_best"]
+    peak_mac = peaks["imad"]["per_s"]
+    me_ms, tqr_ms, alone_launches = kernels_alone(ctx, cfg, bufs, flush, stream) if not args.no_alone else (None,) * 3
+    alone = None
+    if me_ms:
+        alone = {
+            "search": {"ms": me_ms, "effective_gad_s": ad / (me_ms / 1e3) / 1e9,
+                       "frac": ad / (me_ms / 1e3) / peak_ad,
+                       "kernel": f"k_me_frame<{cfg.ctu}> over every P-frame at once ({alone_launches} launches)"},
+            "transform": {"ms": tqr_ms, "butterfly_gmac_s": tmac[0] / (tqr_ms / 1e3) / 1e9,
+                          "frac": tmac[0] / (tqr_ms / 1e3) / peak_mac,
+                          "matrix_form_gmac_s": tmac[1] / (tqr_ms / 1e3) / 1e9,
+                          "kernel": f"k_tqr_frame<{cfg.ctu}> over every P-frame at once ({alone_launches} launches), "
+                                    "motion compensation and the RD choice over every TU size included"},
+            "note": "each timed alone on the encode's own references and vectors (outputs checked equal to the "
+                    "batched encode's); peaks: the measured abs-diff and multiply-add rates",
+        }
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ad / 1e9, "unit": "GAD/s",
+                "frac": achieved / peak_ad, "traffic": traffic, "traffic_note": traffic_note,
                 "effective": "achieved/frac count the full search's abs-diffs (the method's definition); the kernel "
                              "skips candidates that the exact sub-block bound excludes, so frac can exceed 1",
                 "executed": executed["ad"] / (kms / 1e3) / 1e9,
-                "executed_frac": executed["ad"] / (kms / 1e3) / ALU_PEAK_AD_PER_S,
+                "executed_frac": executed["ad"] / (kms / 1e3) / peak_ad,
                 "executed_work": executed,
                 "kernel": (f"k_me_frame<{cfg.ctu}> + k_tqr_frame<{cfg.ctu}> (the jobs as per-frame chains on "
                            f"concurrent streams)" if frames_mode else
                            f"k_persist<{cfg.ctu}> (motion search + refinement + transform/quant/recon, fused)"),
                 "work_per_launch": f"{ad:.4g} integer-search abs-diffs ({cfg.ctu}^2 x {2 * cfg.R + 1}^2 per PU "
-                                   f"and P-frame)",
+                                   f"and P-frame) over {items} work items",
                 "kernel_ms": kms,
                 "transform": {"butterfly_mac": tmac[0], "matrix_form_mac": tmac[1],
                               "butterfly_gmac_s_lower_bound": tmac[0] / (kms / 1e3) / 1e9,
                               "note": "forward + inverse of every allowed TU size over every sample (the RD "
                                       "choice); the rate divides by the whole encode section, search included"},
-                "peak_basis": "derived: 152 SMs x 96 abs-diffs/clock x 2.07 GHz (issue-limited mix of one-instruction "
-                              "__sad on the half-rate ALU pipe and two-instruction FP32 |a-b|; a microbenchmark of "
-                              "the mix measured 30.3 T/s)"}
+                "alone": alone,
+                "peak_basis": "measured now on this device (xv_measure_peak): the fastest abs-diff-accumulate "
+                              "sequence of sad / FP32 / their mix; MEASURED_PEAKS.json holds no integer-pipe peak",
+                "peaks_measured": peaks}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpx·band/s", "n_gpus": ws, "steps": args.steps,
@@ -1121,18 +1290,22 @@ def main():
                    "path": "xv_encode_batch (" + ("per-frame chains on concurrent streams, the autotuner's choice"
                                                   if frames_mode else "persistent kernel") + ")",
                    "block_size": block_size, "l2": "flushed before every step (256 MB write); "
-                   "the float32 cube (168 MB) is also larger than L2", "parallelism": f"replicas{ws}"},
+                   f"the float32 input ({sum(t.numel() * 4 for t in srcs) / 1e9:.2f} GB) is also larger than L2",
+                   "parallelism": f"replicas{ws}"},
         "p50_ms": statistics.median(lat_ms), "p99_ms": float(np.percentile(lat_ms, 99)),
-        "latency_samples": len(lat_ms),
+        "latency_samples": len(lat_ms), "latency_samples_extra": len(extra_ms),
         "stage_ms": {"search_and_transform": kms, "rest": statistics.mean(step_ms) - kms,
                      "rest_is": "min/max, quantise/pack, PSNR, rate totals and the results read-back (the step's "
                                 "time outside the encode section)"},
         "plain": plain, "e2e": e2e, "roofline": roofline, "clocks": clk,
         "gpu_launches": int(launches),
     }
+    if rank == 0 and ws == 1 and not args.no_extra and args.workload == "era5" and not args.frames:
+        line["deepextremecubes"] = secondary_line(ctx, dev, flush, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        dec = args.workload == WORKLOAD
-        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=192 if dec else 4, single_frames=8 if dec else 2)
+        line["cpu_baseline"] = cpu_baseline(cube, cfg, frames=cpu_sample_frames(args.workload, cfg),
+                                            single_frames={"era5": 2, "deepextremecubes": 8}.get(args.workload, 2),
+                                            whole=args.workload == "era5" and not args.frames)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -262,6 +262,15 @@ xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void
  * stays usable). */
 xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result* results, void* stream);
 
+/* xv_encode_batch with the cubes coming from HOST memory: for every job whose
+ * host_src[i] is not NULL, that host cube ([bands][T][H][W] of the job's
+ * dtype, bands T H W elements, pinned memory makes the copy asynchronous) is
+ * first copied into the job's device buffer jobs[i].src on `stream`; then the
+ * batch runs exactly as xv_encode_batch (same output, same host results).
+ * host_src may be NULL (no copies).  Synchronous. */
+xv_status xv_encode_batch_from_host(xv_ctx* ctx, const xv_job* jobs, const void* const* host_src, int njobs,
+                                    xv_result* results, void* stream);
+
 /* SSIM per real band (the paper's Sec. 2.3 quality metric, Wang et al.
  * 2004): band b against its reconstruction x^ = min + q (max - min)/1023
  * (group b/3, channel b%3 of recon), per frame over every 11 x 11 window
@@ -497,13 +506,29 @@ xv_status xv_last_batch_search_stats(const xv_ctx* ctx, uint64_t* exact_candidat
 /* Number of kernels this context has launched so far.  Host only. */
 uint64_t xv_ctx_launches(const xv_ctx* ctx);
 
+/* ------------------------------------------------------ measurement */
+
+/* Device microbenchmark of an instruction sequence that the benchmark's
+ * roofline fractions are quoted against (not a step of the method): the
+ * rate, over the whole device, of
+ *   kind 0: abs-diff-accumulates as one integer sad instruction each,
+ *   kind 1: abs-diff-accumulates on the FP32 pipe (subtract, add |.|),
+ *   kind 2: the mix of two kind-0 per kind-1 (both pipes at once),
+ *   kind 3: 32-bit integer multiply-adds (the transform's operation).
+ * Every SM runs at its thread limit; best of three timed runs after one
+ * warm-up, on the legacy default stream.  *rate: operations per second;
+ * *ms: that run's duration (may be NULL).  Synchronous.  XV_EINVAL for a
+ * kind outside 0..3. */
+xv_status xv_measure_peak(xv_ctx* ctx, int kind, double* rate, double* ms);
+
 /* ------------------------------------------------------ test hooks */
 
 /* Spin budget (SM clock cycles, default 4e9, about 2 s) of each dependency
  * wait in xv_encode_batch.  Host only. */
 xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
 /* Run xv_encode_batch with this block size (128, 192, 256 or 512), or 1 for
- * its per-frame mode, instead of the autotuner's choice; 0 restores the
+ * its per-frame mode, instead of the autotuner's choice, captured and
+ * replayed as CUDA graphs exactly as a tuned choice is; 0 restores the
  * autotuner.  Host only. */
 xv_status xv_debug_force_block_size(xv_ctx* ctx, int block_size);
 /* Make one dependency counter of xv_encode_batch impossible to complete: the

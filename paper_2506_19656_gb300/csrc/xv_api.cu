@@ -51,6 +51,7 @@ struct xv_ctx {
     cudaEvent_t side_ev[16] = {};
     cudaEvent_t fork_ev = nullptr;
     DevBuf b_mv, b_exact;
+    DevBuf peak_buf;                         // xv_measure_peak's input and sink
     xvh::ServeState* serve = nullptr;
 };
 
@@ -319,7 +320,8 @@ void xv_destroy(xv_ctx* c) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax, &c->tmp_cbf,
                       &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
-                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals, &c->b_mv, &c->b_exact};
+                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals, &c->b_mv, &c->b_exact,
+                      &c->met_part, &c->met_out, &c->pca_part, &c->peak_buf};
     for (DevBuf* b : bufs) release(c, *b);
     for (cudaGraphExec_t& gx : c->graph)
         if (gx) cudaGraphExecDestroy(gx);
@@ -1052,7 +1054,9 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         if (it == c->tuned_nt.end()) tune = true;
         else nt[k] = it->second;
     }
-    const bool debug = c->force_nt || c->stall_row >= 0;
+    // a forced block size still runs as captured graphs (like a tuned one);
+    // the stalled-row hook runs uncaptured
+    const bool debug = c->stall_row >= 0;
     if (c->force_nt) {
         for (int k = 0; k < 4; ++k) nt[k] = c->force_nt;
         tune = false;
@@ -1083,8 +1087,11 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         char buf[256];
         for (int i = 0; i < njobs; ++i) {
             const xv_job& j = jobs[i];
-            snprintf(buf, sizeof buf, "%p,%d,%d,%d,%d,%d,%d,%d,%u,%d,%p,%d,%p,%p,%p,%p,%p,%p,%p;", j.src, (int)j.dtype,
-                     j.bands, j.T, j.H, j.W, j.p.ctu, j.p.search_range, j.p.tu_mask, j.p.qp, (void*)j.minmax,
+            // every job field a captured launch reads, the lambdas and flags included
+            // (the per-frame mode passes them to its launches as arguments)
+            snprintf(buf, sizeof buf, "%p,%d,%d,%d,%d,%d,%d,%d,%u,%d,%lld,%lld,%u,%p,%d,%p,%p,%p,%p,%p,%p,%p;", j.src,
+                     (int)j.dtype, j.bands, j.T, j.H, j.W, j.p.ctu, j.p.search_range, j.p.tu_mask, j.p.qp,
+                     (long long)j.p.lambda_fp8, (long long)j.p.lambda_mv_fp16, (unsigned)j.p.flags, (void*)j.minmax,
                      j.minmax_fixed, (void*)j.planes, (void*)j.recon, (void*)j.mv, (void*)j.cost, (void*)j.levels,
                      (void*)j.tu_log2, (void*)j.bits);
             key += buf;
@@ -1186,6 +1193,62 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         r->bpppb = (double)h_tot[i] / ((double)j.H * j.W * j.T * j.bands);
         r->status = XV_OK;
     }
+    return XV_OK;
+}
+
+xv_status xv_encode_batch_from_host(xv_ctx* c, const xv_job* jobs, const void* const* host_src, int njobs,
+                                    xv_result* results, void* stream) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    if (njobs < 1 || njobs > 255 || !jobs || !results) { set_error("njobs %d: must be 1..255 with jobs and results", njobs); return XV_EINVAL; }
+    if (host_src) {
+        DeviceGuard g(c->device);
+        for (int i = 0; i < njobs; ++i) {
+            if (!host_src[i]) continue;
+            if (!valid_job(&jobs[i])) return XV_EINVAL;
+            const xv_job& j = jobs[i];
+            const size_t bytes = (size_t)j.bands * j.T * j.H * j.W * (j.dtype == XV_F32 ? 4 : 2);
+            cudaError_t e = cudaMemcpyAsync(const_cast<void*>(j.src), host_src[i], bytes, cudaMemcpyHostToDevice,
+                                            (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_fail(e, "host cube upload");
+        }
+    }
+    return xv_encode_batch(c, jobs, njobs, results, stream);
+}
+
+xv_status xv_measure_peak(xv_ctx* c, int kind, double* rate, double* ms_out) {
+    if (!c || !rate) { set_error("ctx and rate are required"); return XV_EINVAL; }
+    if (kind < 0 || kind > 3) { set_error("kind %d: must be 0..3", kind); return XV_EINVAL; }
+    DeviceGuard g(c->device);
+    xv_status s;
+    if ((s = ensure(c, c->peak_buf, sizeof(uint32_t) * (128 + 4096)))) return s;
+    uint32_t host_in[128];
+    for (int i = 0; i < 128; ++i) host_in[i] = 0x4B000000u | (uint32_t)((i * 733 + 91) & 1023);  // biased 10-bit samples
+    uint32_t* in = (uint32_t*)c->peak_buf.ptr;
+    cudaError_t e = cudaMemcpy(in, host_in, sizeof host_in, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "peak input");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "peak events");
+    }
+    const int iters = 100000;
+    double best = 0.0, best_ms = 0.0;
+    int threads = 0;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first run warms up
+        if ((e = cudaEventRecord(e0, 0)) != cudaSuccess) break;
+        if ((e = xvh::launch_peak(kind, in, iters, in + 128, &threads, 0)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(e1, 0)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        c->launches++;
+        const double r = (double)threads * iters * xvh::peak_chains() / (ms * 1e-3);
+        if (rep > 0 && r > best) { best = r; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "peak microbenchmark");
+    *rate = best;
+    if (ms_out) *ms_out = best_ms;
     return XV_OK;
 }
 

@@ -40,6 +40,11 @@ cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
                             uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st,
                             unsigned long long* exact = nullptr);
+// Microbenchmarks of the roofline's instruction sequences (k_peak.cu): kind
+// 0..3 (see the file); sink receives at most one word per block.
+int peak_chains();
+cudaError_t launch_peak(int kind, const uint32_t* in, int iters, uint32_t* sink, int* threads_out,
+                        cudaStream_t st);
 // PCA over bands (k_pca.cu).
 int pca_fit_blocks(int64_t npix);
 cudaError_t launch_pca_sums(const void* src, xv_dtype dt, int bands, int64_t npix, double* part, int nblk,

@@ -94,6 +94,8 @@ _SIGS = {
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
     "xv_encode_batch": [_vp, ctypes.POINTER(xv_job), _i, ctypes.POINTER(xv_result), _vp],
+    "xv_encode_batch_from_host": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(_vp), _i, ctypes.POINTER(xv_result),
+                                  _vp],
     "xv_serve_start": [_vp, _i, _i],
     "xv_serve_submit": [_vp, ctypes.POINTER(xv_request), ctypes.POINTER(ctypes.c_uint64)],
     "xv_serve_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(xv_result), ctypes.POINTER(_i)],
@@ -105,6 +107,7 @@ _SIGS = {
     "xv_last_batch_block_size": [_vp, ctypes.POINTER(_i)],
     "xv_last_batch_search_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "xv_ctx_launches": [_vp],
+    "xv_measure_peak": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "xv_set_batch_graphs": [_vp, _i],
     "xv_batch_graph_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "xv_debug_set_wait_budget": [_vp, ctypes.c_longlong],
@@ -371,6 +374,29 @@ def xv_encode_batch(ctx: Context, jobs, stream=None) -> list:
     arr = (xv_job * n)(*jobs)
     res = (xv_result * n)()
     check(lib().xv_encode_batch(ctx.handle, arr, n, res, _stream(stream)), "xv_encode_batch")
+    return [r.as_dict() for r in res]
+
+
+PEAK_KINDS = {0: "sad", 1: "fp32_absdiff", 2: "sad_fp32_mix", 3: "imad"}
+
+
+def xv_measure_peak(ctx: Context, kind: int) -> tuple:
+    """(operations per second, ms of the best run) of microbenchmark `kind`
+    (PEAK_KINDS: 0-2 abs-diff-accumulates, 3 integer multiply-adds)."""
+    r = ctypes.c_double()
+    ms = ctypes.c_double()
+    check(lib().xv_measure_peak(ctx.handle, kind, ctypes.byref(r), ctypes.byref(ms)), "xv_measure_peak")
+    return r.value, ms.value
+
+
+def xv_encode_batch_from_host(ctx: Context, jobs, host_srcs, stream=None) -> list:
+    """xv_encode_batch after copying each host cube (a CPU tensor, pinned for
+    an asynchronous copy, or None) into its job's device source buffer."""
+    n = len(jobs)
+    arr = (xv_job * n)(*jobs)
+    hs = (_vp * n)(*[None if h is None else h.data_ptr() for h in host_srcs])
+    res = (xv_result * n)()
+    check(lib().xv_encode_batch_from_host(ctx.handle, arr, hs, n, res, _stream(stream)), "xv_encode_batch_from_host")
     return [r.as_dict() for r in res]
 
 

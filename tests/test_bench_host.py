@@ -65,32 +65,50 @@ def test_default_qps():
     assert bench.default_qps("dynamicearthnet") == (27,)
 
 
-def _tree(tmp_path, sha):
+def _tree(tmp_path, sha, name="k_persist_32"):
     """A copy of the kernel sources with a traffic record keyed by `sha`."""
-    for f in bench.PERSIST_SOURCES:
+    for f in bench.kernel_sources("persist", 32):
         dst = tmp_path / f
         dst.parent.mkdir(parents=True, exist_ok=True)
         shutil.copy(os.path.join(REPO, f), dst)
     (tmp_path / "profiles").mkdir(exist_ok=True)
-    (tmp_path / "profiles" / "k_persist_deepextremecubes_traffic.txt").write_text(
-        "# comment = ignored\nsources_sha = %s\ndram_bytes_per_launch = 123456\n" % sha)
+    (tmp_path / "profiles" / f"{name}_traffic.txt").write_text(
+        "# comment = ignored\nsources_sha = %s\ndram_bytes_per_item = 15400\n" % sha)
 
 
 def test_recorded_traffic_only_for_the_same_sources(tmp_path, monkeypatch):
+    files = bench.kernel_sources("persist", 32)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     _tree(tmp_path, "0" * 16)
-    assert bench.recorded_traffic() is None
-    _tree(tmp_path, bench.kernel_sources_sha())
-    assert bench.recorded_traffic() == 123456.0
+    assert bench.recorded_traffic("k_persist_32", files) is None
+    _tree(tmp_path, bench.kernel_sources_sha(files))
+    assert bench.recorded_traffic("k_persist_32", files) == 15400.0
     # any change to a kernel source drops it
-    src = tmp_path / bench.PERSIST_SOURCES[1]
+    src = tmp_path / files[1]
     src.write_text(src.read_text() + "\n// edited\n")
-    assert bench.recorded_traffic() is None
+    assert bench.recorded_traffic("k_persist_32", files) is None
 
 
 def test_recorded_traffic_absent(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.recorded_traffic() is None
+    assert bench.recorded_traffic("k_persist_32", bench.kernel_sources("persist", 32)) is None
+
+
+def test_kernel_sources_name_the_compiled_files():
+    """The persistent kernel's record depends on its CTU's translation unit and
+    the device headers; the per-frame kernels' on k_frame.cu and the headers."""
+    p = bench.kernel_sources("persist", 32)
+    f = bench.kernel_sources("frames", 32)
+    assert any(x.endswith("k_batch_ctu32.cu") for x in p) and not any(x.endswith("k_frame.cu") for x in p)
+    assert any(x.endswith("k_frame.cu") for x in f)
+    for x in p + f:
+        assert os.path.exists(os.path.join(REPO, x)), x
+
+
+def test_work_items_era5():
+    """ERA5-shaped sub-cube of T frames at CTU 32: 2 groups x T x 23 x 45 PUs."""
+    cfg = synth.WORKLOADS["era5"]
+    assert bench.work_items(cfg, 24) == 2 * 24 * 23 * 45
 
 
 def _butterfly(x, N, T, count, inverse=False):

@@ -116,6 +116,48 @@ def test_every_block_size_is_bit_exact(xv, ctx, block_size):
         assert_matches(b, r, w)
 
 
+def oracle_chain_with_lambda(planes, ctu, R, mask, qp, lmv):
+    """The oracle's closed loop (C4) run frame by frame with a motion-cost
+    lambda of the caller's choice: integer search and refinement with lmv,
+    then the transform chain against the previous reconstruction."""
+    G, T, _, Hp, Wp = planes.shape
+    n = (Hp // ctu) * (Wp // ctu)
+    recon = np.zeros_like(planes)
+    mv = np.zeros((G, T, n, 2), np.int16)
+    for g in range(G):
+        for t in range(T):
+            ref = recon[g, t - 1] if t else None
+            if t:
+                mvi, _ = oracle.me_int(planes[g, t, 0], ref[0], ctu, R, lmv)
+                mv[g, t], _ = oracle.me_qpel(planes[g, t, 0], ref[0], ctu, lmv, mvi)
+            recon[g, t] = oracle.tqr_frame(planes[g, t], ref, mv[g, t] if t else None, ctu, mask, qp)["recon"]
+    return recon, mv
+
+
+@pytest.mark.parametrize("block_size", [1, 256])
+def test_resubmitted_batch_with_new_lambda_is_not_a_stale_graph(xv, ctx, block_size):
+    """The same buffers submitted twice through the captured graphs, only the
+    motion-cost lambda changed the second time: the second result is the
+    oracle's for the new lambda, not a replay of the first (the graph key
+    covers every job parameter that a captured launch reads)."""
+    c = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny")
+    want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27)
+    job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
+    xv.xv_debug_force_block_size(ctx, block_size)
+    try:
+        assert_matches(buf, xv.xv_encode_batch(ctx, [job])[0], want)
+        job.p.lambda_mv_fp16 = job.p.lambda_mv_fp16 * 16
+        xv.xv_encode_batch(ctx, [job])
+        assert xv.xv_last_batch_block_size(ctx) == block_size
+    finally:
+        xv.xv_debug_force_block_size(ctx, 0)
+    recon, mv = oracle_chain_with_lambda(want["planes"], c.ctu, c.R, c.tu_mask, 27, int(job.p.lambda_mv_fp16))
+    assert not np.array_equal(mv, want["mv"]), "the new lambda must change some vector for this test to mean anything"
+    assert np.array_equal(to_np(buf["mv"]), mv)
+    assert np.array_equal(to_np(buf["recon"]), recon)
+
+
 def test_uint16_dynamicearthnet_prefix(xv, ctx):
     """Two frames of a DynamicEarthNet-shaped uint16 cube (CTU 64, R 64, TU 4-32),
     with a min/max fixed in advance (as a causal prefix of a longer cube would)."""
