@@ -856,6 +856,104 @@ def run_pca(args):
     ctx.close()
 
 
+def run_pca_all(args):
+    """The paper's "PCA - all bands" test (Sec. 3, Tab. 5) on the workload's
+    cube: each timed step fits the PCA over all bands, projects the cube onto
+    every component, packs the components three to a group and encodes every
+    group at its own QP (xv_split_groups + one xv_encode_batch; the i-th group
+    at base QP + 5 i, later components at lower quality), then rebuilds the
+    cube: the groups' reconstructions back to component units (xv_unpack)
+    and the inverse projection.  The line reports the step's throughput and
+    the rebuilt cube's PSNR per band against the original (peak = the band's
+    maximum, as the codec's PSNR), beside one QP for all groups."""
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2506_19656_gb300 import build, synth, xv
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg = synth.WORKLOADS[args.workload]
+    T = args.frames or cfg.T
+    cube = synth.make_cube(args.workload, T=T)
+    src = torch.from_numpy(np.ascontiguousarray(cube)).to(dev)
+    bands = cube.shape[0]
+    G = (bands + 2) // 3
+    base = QPS[0]
+    qps_all = [base + 5 * g for g in range(G)]
+    ctx = xv.Context(0)
+    z = torch.empty(cube.shape, dtype=torch.float32, device=dev)
+    zr = torch.empty(cube.shape, dtype=torch.float32, device=dev)
+    back = torch.empty(cube.shape, dtype=torch.float32, device=dev)
+    p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, base)
+    buf = xv.alloc_cube_buffers(bands, T, cfg.H, cfg.W, p, device=dev)
+    whole = xv.make_job(z, p, buf["planes"], buf["recon"], minmax=buf["minmax"], mv=buf["mv"], cost=buf["cost"],
+                        levels=buf["levels"], tu_log2=buf["tu_log2"], bits=buf["bits"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(qps):
+        mean, comps, var = xv.xv_pca_fit(ctx, src)
+        xv.xv_pca_project(ctx, src, mean, comps, bands, z)
+        res = xv.xv_encode_batch(ctx, xv.xv_split_groups(whole, qps))
+        xv.xv_unpack(ctx, buf["recon"], bands, cfg.H, cfg.W, buf["minmax"], zr)
+        xv.xv_pca_inverse(ctx, zr, mean, comps, back)
+        return res
+
+    def timed(qps, k):
+        ms = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(qps)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, res
+
+    def quality(res):
+        x = src.double()
+        e = (back.double() - x).pow(2).mean(dim=(1, 2, 3))
+        peak = x.amax(dim=(1, 2, 3))
+        psnr = (10 * torch.log10(peak * peak / e)).tolist()
+        bits = sum(r["total_bits"] for r in res)
+        return {"psnr_band": psnr, "psnr_mean": float(np.mean(psnr)), "bpppb": bits / (bands * T * cfg.H * cfg.W)}
+
+    for _ in range(args.warmup):
+        step(qps_all)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = xv.xv_ctx_launches(ctx)
+    step_ms, res = timed(qps_all, args.steps)
+    launches = xv.xv_ctx_launches(ctx) - launches0
+    clk = clocks.stop()
+    q_all = quality(res)
+    for _ in range(2):
+        step([base] * G)
+    one_ms, res1 = timed([base] * G, max(3, min(args.steps, 5)))
+    q_one = quality(res1)
+    work_mpx = bands * T * cfg.H * cfg.W / 1e6
+    line = {
+        "metric": "Mpx·band/s of PCA over all bands + per-group-QP encode of the components + rebuild (\"PCA - all bands\")",
+        "value": work_mpx / (statistics.mean(step_ms) / 1e3), "unit": "Mpx·band/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 encode, f64 fit, f32 projections", "data": "synthetic",
+        "config": {"workload": cfg.name, "frames": T, "bands": bands, "group_qps": qps_all, "ctu": cfg.ctu,
+                   "path": "xv_pca_fit + xv_pca_project + xv_split_groups + xv_encode_batch + xv_unpack + "
+                           "xv_pca_inverse", "l2": "flushed before every step (256 MB write)", "parallelism": "replicas1"},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "per_group_qp": q_all,
+        "one_qp": dict(q_one, qp=base, ms_per_step=statistics.mean(one_ms)),
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Serving run: a stream of requests with Poisson arrivals, kinds drawn
     uniformly from the four workloads, through xv_serve_*; against the plain
@@ -961,6 +1059,19 @@ def run_serve(args):
                   "path": "xv_encode_cube per request in arrival order (measured service times, FIFO timeline)"},
     }
     print(json.dumps(line), flush=True)
+
+
+def parse_tune_log(log):
+    """The autotuner's candidate timings as {candidate: ms} ("ctu32 nt128 per4"
+    = a CTU-32 persistent launch of 128-thread blocks, 4 resident per SM;
+    "frames" = the per-frame mode)."""
+    out = {}
+    for item in log.split(";"):
+        item = item.strip()
+        if item:
+            name, ms = item.rsplit(" ", 1)
+            out[name] = float(ms)
+    return out
 
 
 def measured_peaks(ctx):
@@ -1094,6 +1205,8 @@ def main():
     ap.add_argument("--decode", action="store_true", help="the decode run (the workload's coded data) instead")
     ap.add_argument("--metrics", action="store_true", help="the SSIM / spectral-angle run instead")
     ap.add_argument("--pca", action="store_true", help="the PCA (fit, project, inverse) run instead")
+    ap.add_argument("--pca-all", action="store_true",
+                    help="the PCA over all bands with one QP per component group (encode and rebuild) instead")
     ap.add_argument("--options", action="store_true",
                     help="the per-frame path with frame-0 intra prediction and in-loop deblocking instead")
     ap.add_argument("--requests", type=int, default=200)
@@ -1118,6 +1231,8 @@ def main():
         return run_metrics(args)
     if args.pca:
         return run_pca(args)
+    if args.pca_all:
+        return run_pca_all(args)
     if args.options:
         return run_options(args)
 
@@ -1169,6 +1284,7 @@ def main():
     for _ in range(args.warmup):
         batched()
     torch.cuda.synchronize()
+    tune_log = xv.xv_last_tune_log(ctx)  # the first batch of this shape tuned it
     peaks = measured_peaks(ctx)
 
     clocks = ClockSampler(local)
@@ -1181,6 +1297,7 @@ def main():
     barrier()
     launches = xv.xv_ctx_launches(ctx) - launches0
     block_size = xv.xv_last_batch_block_size(ctx)
+    _, blocks_per_sm = xv.xv_last_batch_config(ctx, cfg.ctu)
     exact_cand, full_cand = xv.xv_last_batch_search_stats(ctx)
     # step latency percentiles over at least 20 repeats: the K timed steps,
     # topped up when K < 20 by further steps timed the same way, still inside
@@ -1289,7 +1406,9 @@ def main():
                    "bands": cfg.bands,
                    "path": "xv_encode_batch (" + ("per-frame chains on concurrent streams, the autotuner's choice"
                                                   if frames_mode else "persistent kernel") + ")",
-                   "block_size": block_size, "l2": "flushed before every step (256 MB write); "
+                   "block_size": block_size, "blocks_per_sm": blocks_per_sm or "as many as fit",
+                   "autotune_ms": parse_tune_log(tune_log) if tune_log else "forced (--block-size)",
+                   "l2": "flushed before every step (256 MB write); "
                    f"the float32 input ({sum(t.numel() * 4 for t in srcs) / 1e9:.2f} GB) is also larger than L2",
                    "parallelism": f"replicas{ws}"},
         "p50_ms": statistics.median(lat_ms), "p99_ms": float(np.percentile(lat_ms, 99)),

@@ -237,7 +237,24 @@ typedef struct {
     double mse_band[XV_MAX_BANDS];
     uint64_t sse10_band[XV_MAX_BANDS];
     double latency_s;    /* serving: arrival to completion */
+    int ctu;             /* the CTU size the cube was encoded with (its job's p.ctu) */
+    int block_size;      /* execution mode of its encode: persistent block size, 1 = per-frame launches */
 } xv_result;
+
+/* Splits a cube's job into one job per 3-band group, each with its own QP
+ * (the paper's "PCA - all bands" test, Sec. 3 and Tab. 5: the principal
+ * components are packed three to a video and the less important videos are
+ * coded at a lower quality).  Group g of `whole` (bands 3g .. 3g + 2, the
+ * last group repeating its last band) becomes out[g]: src, minmax, planes,
+ * recon, mv, cost, levels, tu_log2 and bits point at group g's part of the
+ * whole job's buffers (which keep the whole cube's layout), bands = the
+ * group's real bands, and its parameters are xv_params_init(ctu, R, tu_mask,
+ * qp[g]) with whole->p's flags.  Encoding the out[] jobs (xv_encode_batch)
+ * gives, for every group, exactly the whole job's outputs at that group's
+ * QP: groups are independent chains and a band's min/max is its own.
+ * qp: HOST [G], G = ceil(bands / 3); out: HOST [G], *njobs = G.  Host only;
+ * XV_EINVAL for a malformed job or a QP outside [-12, 51]. */
+xv_status xv_split_groups(const xv_job* whole, const int* qp, xv_job* out, int* njobs);
 
 /* Bytes of device scratch a job needs beyond its own buffers. */
 size_t xv_job_scratch_bytes(const xv_job* job);
@@ -254,9 +271,13 @@ xv_status xv_encode_cube(xv_ctx* ctx, const xv_job* job, xv_result* result, void
  * also weighs a second execution mode, the per-frame mode: every job's frames
  * as the per-frame motion-search and transform launches of xv_encode_cube,
  * the jobs on up to 16 concurrent streams forked from and joined back to the
- * batch's stream.  The first batch of a given shape on a context runs once
- * per candidate (the four block sizes and the per-frame mode) and the fastest
- * is kept for later batches of that shape.  Output is bit-identical to
+ * batch's stream.  The first batch of a given shape on a context tunes: per
+ * CTU class every block size (128, 192, 256, 512) with as many resident
+ * blocks per SM as fit and with one fewer, and the per-frame mode for the
+ * whole batch, each timed as the CUDA graph it would replay (median of three
+ * replays after one warm-up); each class keeps its fastest configuration
+ * unless the per-frame mode beats their sum (xv_last_batch_config,
+ * xv_last_tune_log).  Output is bit-identical to
  * xv_encode_cube for each job, in every mode.  results: HOST [njobs].  Synchronous.  XV_ETIMEOUT if a
  * bounded device wait ran out of time (results then invalid; the context
  * stays usable). */
@@ -503,6 +524,18 @@ xv_status xv_last_batch_block_size(const xv_ctx* ctx, int* block_size);
  * excluded by the sub-block sum bound and cannot be the minimum.  Either
  * pointer may be NULL.  Host only. */
 xv_status xv_last_batch_search_stats(const xv_ctx* ctx, uint64_t* exact_candidates, uint64_t* full_candidates);
+/* The configuration the last xv_encode_batch ran for its CTU class `ctu`
+ * (8, 16, 32, 64): *block_size = the persistent kernel's block size, or 1
+ * for the per-frame mode (0: the class had no work); *blocks_per_sm = the
+ * cap on resident blocks per SM (0: as many as fit), may be NULL.  Host
+ * only. */
+xv_status xv_last_batch_config(const xv_ctx* ctx, int ctu, int* block_size, int* blocks_per_sm);
+/* The autotuner's timings of its last run on this context: one entry per
+ * candidate, "ctu<C> nt<B> per<P> <ms>;" for a class's persistent
+ * configuration and "frames <ms>;" for the per-frame mode (median of three
+ * replays of the captured candidate); "" before any tuning.  The string is
+ * owned by the context.  Host only. */
+const char* xv_last_tune_log(const xv_ctx* ctx);
 /* Number of kernels this context has launched so far.  Host only. */
 uint64_t xv_ctx_launches(const xv_ctx* ctx);
 
@@ -526,10 +559,11 @@ xv_status xv_measure_peak(xv_ctx* ctx, int kind, double* rate, double* ms);
 /* Spin budget (SM clock cycles, default 4e9, about 2 s) of each dependency
  * wait in xv_encode_batch.  Host only. */
 xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
-/* Run xv_encode_batch with this block size (128, 192, 256 or 512), or 1 for
- * its per-frame mode, instead of the autotuner's choice, captured and
- * replayed as CUDA graphs exactly as a tuned choice is; 0 restores the
- * autotuner.  Host only. */
+/* Run xv_encode_batch with this block size (128, 192, 256 or 512, plus
+ * 1024 x a cap on resident blocks per SM, 1..32, if wanted), or 1 for its
+ * per-frame mode, instead of the autotuner's choice, captured and replayed
+ * as CUDA graphs exactly as a tuned choice is; 0 restores the autotuner.
+ * Host only. */
 xv_status xv_debug_force_block_size(xv_ctx* ctx, int block_size);
 /* Make one dependency counter of xv_encode_batch impossible to complete: the
  * CTU row `row` of the first job, indexed over its [G][T][rows] counters, is

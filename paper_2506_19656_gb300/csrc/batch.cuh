@@ -27,7 +27,7 @@ namespace {  // each including file gets its own copies
 // spills) rather than three.
 template <int N, int NT>
 constexpr int kMinBlocks = NT == 512 ? (N == 64 ? 1 : 2)
-                                     : N == 64 ? 1 : (N == 32 ? (NT == 256 ? 2 : 4) : (NT == 256 ? 4 : (NT == 192 ? 5 : 6)));
+                                     : N == 64 ? 1 : (N == 32 ? (NT == 256 ? 2 : 3) : (NT == 256 ? 4 : (NT == 192 ? 5 : 6)));
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
     uint64_t v;

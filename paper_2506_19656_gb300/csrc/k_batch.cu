@@ -122,7 +122,7 @@ size_t persist_smem_bytes(int ctu, int R, bool has_me) {
     return a > b ? a : b;
 }
 
-int persist_grid(int ctu, int nt, size_t smem, bool decode) {
+int persist_grid(int ctu, int nt, size_t smem, bool decode, int per_cap) {
     PersistFn fn = persist_fn(ctu, nt, decode);
     if (!fn) return 0;
     int dev = 0, sms = 0, per = 0;
@@ -133,6 +133,7 @@ int persist_grid(int ctu, int nt, size_t smem, bool decode) {
         cudaGetLastError();  // reported by the launch that follows, not left behind
         per = 1;
     }
+    if (per_cap > 0 && per > per_cap) per = per_cap;
     if (per < 1) per = 1;
     return sms * per;
 }

@@ -2,13 +2,15 @@
 // roofline fractions are quoted against (measurement only, not a step of the
 // method).
 //
-// Each thread runs kChains independent accumulation chains for `iters`
-// rounds.  The operations are inline PTX marked volatile, so the compiler
-// can neither hoist them out of the loop nor fold a chain of identical
-// additions into one multiplication (both happened to plain C loops); the
-// operands are per-thread values loaded from memory.  A full grid (every
-// SM at its thread limit) keeps enough warps in flight for issue, not
-// latency, to bound the rate.
+// Each thread runs kChains accumulation chains for `iters` rounds.  An
+// operation's first operand is the accumulator of the next chain, a value
+// carried around the loop, so no compiler stage can hoist a loop-invariant
+// part out of the loop (ptxas did, for a subtraction of two invariant
+// floats) or fold a chain of identical additions into a multiplication; the
+// operations are inline PTX marked volatile.  The values themselves are
+// meaningless (the floats may overflow; the timing does not depend on it).
+// A full grid (every SM at its thread limit) keeps enough warps in flight
+// for issue, not latency, to bound the rate.
 //   kind 0: abs-diff-accumulate as one integer sad.s32 (the ALU pipe)
 //   kind 1: abs-diff-accumulate on the FP32 pipe: sub.f32, then add.f32 of
 //           its absolute value (exact for 10-bit samples stored as floats)
@@ -42,26 +44,26 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(const uint32_t* __restric
                                                         uint32_t* __restrict__ sink) {
     const int t = threadIdx.x & 63;
     uint32_t a[kChains], b[kChains], acc[kChains];
-    float fa[kChains], fb[kChains], facc[kChains];
+    float fb[kChains], facc[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) {
         a[k] = in[(t + k) & 63];
         b[k] = in[64 + ((t + 3 * k) & 63)];
-        acc[k] = 0u;
-        fa[k] = __uint_as_float(a[k]);
+        acc[k] = a[k];
         fb[k] = __uint_as_float(b[k]);
-        facc[k] = 0.f;
+        facc[k] = __uint_as_float(a[k]);
     }
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) {
-            if (KIND == 0) sad_op(acc[k], a[k], b[k]);
-            if (KIND == 1) fad_op(facc[k], fa[k], fb[k]);
-            if (KIND == 2) {
-                if (k % 3 == 2) fad_op(facc[k], fa[k], fb[k]);
-                else sad_op(acc[k], a[k], b[k]);
+            const int n = (k + 1) % kChains;  // the next chain's accumulator is the first operand
+            if (KIND == 0) sad_op(acc[k], acc[n], b[k]);
+            if (KIND == 1) fad_op(facc[k], facc[n], fb[k]);
+            if (KIND == 2) {  // the next chain of the same kind: chains 3j + 2 are FP32, the rest integer
+                if (k % 3 == 2) fad_op(facc[k], facc[(k + 3) % kChains], fb[k]);
+                else sad_op(acc[k], acc[(k + 1) % 3 == 2 ? (k + 2) % kChains : n], b[k]);
             }
-            if (KIND == 3) mad_op(acc[k], a[k], b[k]);
+            if (KIND == 3) mad_op(acc[k], acc[n], b[k]);
         }
     }
     uint32_t s = 0;

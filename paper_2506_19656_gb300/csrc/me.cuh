@@ -90,12 +90,10 @@ __host__ __device__ constexpr size_t me_off_satd(int N, int R) { return me_off_r
 // rounded cost of b bits, b < 64
 __host__ __device__ constexpr size_t me_off_cost(int N, int R) { return me_off_satd(N, R) + 16 * 4; }
 __host__ __device__ constexpr size_t me_off_scr(int N, int R) { return me_off_cost(N, R) + me_align16((129 + 64) * 4); }
-// refinement view of the scratch region
-__host__ __device__ constexpr size_t me_hp_bytes(int N) { return me_align16((size_t)3 * (N + 8) * N * (N <= 32 ? 4 : 2)); }
-__host__ __device__ constexpr size_t me_off_hp(int N, int R) { return me_off_scr(N, R); }
-__host__ __device__ constexpr size_t me_off_had(int N, int R) { return me_off_scr(N, R) + me_hp_bytes(N); }
-// Candidates' horizontally transformed differences (PUs up to 32 only).
-__host__ __device__ constexpr size_t me_had_bytes(int N) { return N <= 32 ? me_align16((size_t)9 * N * N * 2) : 0; }
+// refinement view of the scratch region: three horizontally filtered planes
+// (int16 [N + 8][N] each: block rows -4 .. N + 3 around the integer vector)
+__host__ __device__ constexpr size_t me_plane_elems(int N) { return (size_t)(N + 8) * N; }
+__host__ __device__ constexpr size_t me_planes_bytes(int N) { return me_align16(3 * me_plane_elems(N) * 2); }
 // pruning view: box table (later the survivor list), sub-block sums of the
 // PU, per-unit bounds
 __host__ __device__ constexpr size_t me_max(size_t a, size_t b) { return a > b ? a : b; }
@@ -107,7 +105,7 @@ __host__ __device__ constexpr size_t me_off_ulb(int N, int R) {
     return me_off_bsub(N, R) + me_align16((size_t)(N / me_sb(N)) * (N / me_sb(N)) * 4);
 }
 __host__ __device__ constexpr size_t me_smem_bytes(int N, int R) {
-    return me_max(me_off_had(N, R) + me_had_bytes(N), me_off_ulb(N, R) + me_align16((size_t)me_units(R) * 4));
+    return me_max(me_off_scr(N, R) + me_planes_bytes(N), me_off_ulb(N, R) + me_align16((size_t)me_units(R) * 4));
 }
 
 // Samples in the window and block are stored as the float 2^23 + v (v <= 1023).
@@ -209,194 +207,186 @@ __device__ __forceinline__ void hadamard8_row(int (&v)[8]) {
             }
 }
 
-// Refinement stage: evaluate `ncand` quarter-sample candidates around
-// (cx, cy) with step s (candidate k as stage_cand gives it, all within one
-// column-set of three x-vectors cx - s, cx, cx + s), SATD summed into satd[].
+// Horizontal pass of the refinement for up to three x-vectors m[i] (quarter
+// samples) into planes dst[i] (int16 [N + 8][N]): row r holds block row
+// q = r - 4 + my, column x the sample at x + m/4: the full sample itself
+// when m is a multiple of 4, else the 8-tap filter of its phase over the
+// window, >> shift1.  One task per plane row and 8 columns: 15 window
+// samples in registers give the 8 outputs, stored as one 16-byte word.
 template <int N, int NT>
-__device__ void satd_stage(const uint16_t* __restrict__ wb, int S, int R, const int* __restrict__ blk,
-                           int16_t* __restrict__ hp, int cx, int cy, int s, bool centre, int ncand,
-                           uint32_t* satd) {
-    const int tid = threadIdx.x;
-    const int iy_min = (cy - s) >> 2, iy_max = (cy + s) >> 2;
-    const int rbase = iy_min - 3;          // block-relative row of hp row 0
-    const int nr = N + 7 + (iy_max - iy_min);
-    // 1. horizontal pass for the three x-vectors (raw samples for phase 0)
-    for (int idx = tid; idx < 3 * nr * N; idx += NT) {
-        int j = idx / (nr * N), rem = idx - j * nr * N;
-        int r = rem / N, x = rem - r * N;
-        int m = cx + (j - 1) * s;
-        int hx = m & 3, ix = m >> 2;
-        const uint16_t* wr = wb + (rbase + r + R + 4) * S + (x + ix + R + 4);
-        int v;
+__device__ __forceinline__ void refine_planes(const uint16_t* __restrict__ wb, int S, int R, int my, int np,
+                                              int m0, int m1, int m2, int16_t* d0, int16_t* d1, int16_t* d2) {
+    constexpr int SPR = N / 8;
+    constexpr int TPP = (N + 8) * SPR;
+    for (int task = threadIdx.x; task < np * TPP; task += NT) {
+        const int pi = task / TPP, rem = task - pi * TPP;
+        const int r = rem / SPR, x0 = (rem - r * SPR) * 8;
+        const int m = pi == 0 ? m0 : (pi == 1 ? m1 : m2);
+        int16_t* dst = pi == 0 ? d0 : (pi == 1 ? d1 : d2);
+        const int hx = m & 3, ix = m >> 2;
+        const uint16_t* w = wb + (r + my + R) * S + x0 + ix + R + 4;  // block row q, column x0 + ix
+        int o[8];
         if (hx == 0) {
-            v = wr[0];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) o[c] = w[c];
         } else {
+            int v[15];
+#pragma unroll
+            for (int i = 0; i < 15; ++i) v[i] = w[i - 3];
             int tap[8];
             luma_taps(hx, tap);
-            int acc = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc += tap[i] * (int)wr[i - 3];
-            v = acc >> kShift1;
-        }
-        hp[(j * (N + 8) + r) * N + x] = (int16_t)v;
-    }
-    for (int k = tid; k < ncand; k += NT) satd[k] = 0;
-    __syncthreads();
-    // 2. one 8x8 sub-block of one candidate per 8 lanes (lane = row)
-    constexpr int NB = (N / 8) * (N / 8);
-    const int lane8 = tid & 7;
-    const unsigned gmask = 0xffu << (threadIdx.x & 24);
-    for (int task = tid >> 3; task < ncand * NB; task += NT / 8) {
-        int k = task / NB, b = task - k * NB;
-        int by = (b / (N / 8)) * 8, bx = (b % (N / 8)) * 8;
-        int mvx, mvy;
-        stage_cand(k, cx, cy, s, centre, mvx, mvy);
-        int j = (mvx - cx) / s + 1;
-        int hx = mvx & 3, fy = mvy & 3, iy = mvy >> 2;
-        int y = by + lane8;
-        const int16_t* col = hp + (size_t)j * (N + 8) * N + bx;
-        int r0 = y + iy - 3 - rbase;  // hp row of tap 0
-        int d[8];
-        int tap[8];
-        luma_taps(fy == 0 ? 2 : fy, tap);
-#pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            int v;
-            if (fy == 0) {
-                int a = col[(r0 + 3) * N + x];
-                v = hx == 0 ? a << kShift3 : a;
-            } else {
+            for (int c = 0; c < 8; ++c) {
                 int acc = 0;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc += tap[t] * (int)col[(r0 + t) * N + x];
-                v = hx == 0 ? acc >> kShift1 : acc >> kShift2;
-            }
-            d[x] = dec_sample(blk[y * N + bx + x]) - wp_round(v);
-        }
-        hadamard8_row(d);
-        // vertical transform across the 8 lanes of the group
-#pragma unroll
-        for (int h = 1; h < 8; h <<= 1) {
-#pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                int o = __shfl_xor_sync(gmask, d[x], h);
-                d[x] = (lane8 & h) ? o - d[x] : d[x] + o;
+                for (int i = 0; i < 8; ++i) acc += tap[i] * v[c + i];
+                o[c] = acc >> kShift1;
             }
         }
-        int sum = 0;
-#pragma unroll
-        for (int x = 0; x < 8; ++x) sum += d[x] < 0 ? -d[x] : d[x];
-        sum += __shfl_xor_sync(gmask, sum, 1);
-        sum += __shfl_xor_sync(gmask, sum, 2);
-        sum += __shfl_xor_sync(gmask, sum, 4);
-        if (lane8 == 0) atomicAdd(&satd[k], (uint32_t)((sum + 2) >> 2));
+        uint4 pk;
+        pk.x = (uint32_t)(uint16_t)o[0] | ((uint32_t)(uint16_t)o[1] << 16);
+        pk.y = (uint32_t)(uint16_t)o[2] | ((uint32_t)(uint16_t)o[3] << 16);
+        pk.z = (uint32_t)(uint16_t)o[4] | ((uint32_t)(uint16_t)o[5] << 16);
+        pk.w = (uint32_t)(uint16_t)o[6] | ((uint32_t)(uint16_t)o[7] << 16);
+        *reinterpret_cast<uint4*>(dst + r * N + x0) = pk;
     }
-    __syncthreads();
 }
 
-// Refinement stage through shared memory (PUs up to 32): horizontally
-// filtered columns, then one task per (candidate, row, 8-column block) that
-// forms the 8 predicted samples, their differences and the row Hadamard,
-// then one task per (candidate, 8x8 block, column) that finishes the column
-// Hadamard; the 8 column tasks of a block are adjacent lanes and add their
-// absolute sums before the block's (S + 2) >> 2.
-template <int N, int NT>
-__device__ void satd_stage_smem(const uint16_t* __restrict__ wb, int S, int R, const int* __restrict__ blk,
-                                int* __restrict__ hp, int16_t* __restrict__ had, int cx, int cy, int s,
-                                bool centre, int ncand, uint32_t* satd) {
-    const int tid = threadIdx.x;
-    const int iy_min = (cy - s) >> 2, iy_max = (cy + s) >> 2;
-    const int rbase = iy_min - 3;
-    const int nr = N + 7 + (iy_max - iy_min);
-    for (int idx = tid; idx < 3 * nr * N; idx += NT) {
-        int j = idx / (nr * N), rem = idx - j * nr * N;
-        int r = rem / N, x = rem - r * N;
-        int m = cx + (j - 1) * s;
-        int hx = m & 3, ix = m >> 2;
-        const uint16_t* wr = wb + (rbase + r + R + 4) * S + (x + ix + R + 4);
-        int v;
-        if (hx == 0) {
-            v = wr[0];
-        } else {
-            int tap[8];
-            luma_taps(hx, tap);
-            int acc = 0;
+// 8 int16 of a plane row (16-byte aligned) as ints.
+__device__ __forceinline__ void load_row8(const int16_t* p, int (&v)[8]) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc += tap[i] * (int)wr[i - 3];
-            v = acc >> kShift1;
-        }
-        hp[(j * (N + 8) + r) * N + x] = v;
+    for (int i = 0; i < 4; ++i) {
+        v[2 * i] = (int)(int16_t)(w[i] & 0xffffu);
+        v[2 * i + 1] = (int)w[i] >> 16;
     }
-    for (int k = tid; k < ncand; k += NT) satd[k] = 0;
-    __syncthreads();
-    constexpr int NBX = N / 8;
-    for (int task = tid; task < ncand * N * NBX; task += NT) {
-        const int k = task / (N * NBX), rem = task - k * N * NBX;
-        const int y = rem / NBX, bx = (rem - y * NBX) * 8;
-        int mvx, mvy;
-        stage_cand(k, cx, cy, s, centre, mvx, mvy);
-        const int j = (mvx - cx) / s + 1;
-        const int hx = mvx & 3, fy = mvy & 3, iy = mvy >> 2;
-        const int* col = hp + (size_t)j * (N + 8) * N + bx;
-        const int r0 = y + iy - 3 - rbase;
-        int cb[8];
-        {
-            const int4 a = *reinterpret_cast<const int4*>(blk + y * N + bx);
-            const int4 b = *reinterpret_cast<const int4*>(blk + y * N + bx + 4);
-            cb[0] = a.x; cb[1] = a.y; cb[2] = a.z; cb[3] = a.w; cb[4] = b.x; cb[5] = b.y; cb[6] = b.z; cb[7] = b.w;
-        }
-        int d[8];
-        if (fy == 0) {
-            const int4 a = *reinterpret_cast<const int4*>(col + (r0 + 3) * N);
-            const int4 b = *reinterpret_cast<const int4*>(col + (r0 + 3) * N + 4);
-            const int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int x = 0; x < 8; ++x) d[x] = dec_sample(cb[x]) - wp_round(hx == 0 ? v[x] << kShift3 : v[x]);
-        } else {
-            int tap[8];
-            luma_taps(fy, tap);
-            const int sh = hx == 0 ? kShift1 : kShift2;
-            int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int4 a = *reinterpret_cast<const int4*>(col + (r0 + t) * N);
-                const int4 b = *reinterpret_cast<const int4*>(col + (r0 + t) * N + 4);
-                acc[0] += tap[t] * a.x; acc[1] += tap[t] * a.y; acc[2] += tap[t] * a.z; acc[3] += tap[t] * a.w;
-                acc[4] += tap[t] * b.x; acc[5] += tap[t] * b.y; acc[6] += tap[t] * b.z; acc[7] += tap[t] * b.w;
-            }
-#pragma unroll
-            for (int x = 0; x < 8; ++x) d[x] = dec_sample(cb[x]) - wp_round(acc[x] >> sh);
-        }
-        hadamard8_row(d);
-        uint4 pk;
-        pk.x = (uint32_t)(uint16_t)d[0] | ((uint32_t)(uint16_t)d[1] << 16);
-        pk.y = (uint32_t)(uint16_t)d[2] | ((uint32_t)(uint16_t)d[3] << 16);
-        pk.z = (uint32_t)(uint16_t)d[4] | ((uint32_t)(uint16_t)d[5] << 16);
-        pk.w = (uint32_t)(uint16_t)d[6] | ((uint32_t)(uint16_t)d[7] << 16);
-        *reinterpret_cast<uint4*>(had + ((size_t)k * N + y) * N + bx) = pk;
-    }
-    __syncthreads();
-    constexpr int NB = NBX * NBX;
-    const unsigned gmask = 0xffu << (threadIdx.x & 24);
-    for (int task = tid; task < ncand * NB * 8; task += NT) {
-        const int x = task & 7, kb = task >> 3;
-        const int k = kb / NB, b = kb - k * NB;
-        const int by = (b / NBX) * 8, bx = (b % NBX) * 8;
-        const int16_t* h = had + ((size_t)k * N + by) * N + bx + x;
-        int v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = h[i * N];
-        hadamard8_row(v);
-        int sum = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) sum += v[i] < 0 ? -v[i] : v[i];
-        sum += __shfl_xor_sync(gmask, sum, 1);
-        sum += __shfl_xor_sync(gmask, sum, 2);
-        sum += __shfl_xor_sync(gmask, sum, 4);
-        if (x == 0) atomicAdd(&satd[k], (uint32_t)((sum + 2) >> 2));
-    }
-    __syncthreads();
 }
+
+// W (1, 2 or 4) int16 of a plane row (2W-byte aligned) as ints.
+template <int W>
+__device__ __forceinline__ void load_row_n(const int16_t* p, int (&v)[W]) {
+    if constexpr (W == 4) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        v[0] = (int)(int16_t)(q.x & 0xffffu); v[1] = (int)q.x >> 16;
+        v[2] = (int)(int16_t)(q.y & 0xffffu); v[3] = (int)q.y >> 16;
+    } else if constexpr (W == 2) {
+        const uint32_t q = *reinterpret_cast<const uint32_t*>(p);
+        v[0] = (int)(int16_t)(q & 0xffffu); v[1] = (int)q >> 16;
+    } else {
+        v[0] = p[0];
+    }
+}
+
+// Part of the SATD of the 8x8 block at (bx0, by0) of the PU, against its
+// prediction at a quarter-sample vector whose horizontal pass is plane P
+// (vertical phase fy, iyr = the vector's integer row - my, hx0 = its column
+// is a full sample): LPB lanes (2, 4 or 8, adjacent, all calling this for the
+// same block) take 8 / LPB columns each, lane part p the columns from
+// bx0 + (8 / LPB) p.  The prediction (vertical 8-tap filter over 15 plane
+// rows, or the plane row itself; default weighted rounding), the difference
+// with the current block and the Hadamard transform along the columns stay
+// in the lane's registers; the transform along the rows takes its stages
+// across the lanes by shuffle and the rest within the lane (the Hadamard's
+// stages commute, and the absolute sum does not depend on the order of the
+// coefficients).  Every lane of the group returns the block's (S + 2) >> 2.
+template <int N, int LPB>
+__device__ __forceinline__ uint32_t satd_part(const int16_t* __restrict__ P, const int* __restrict__ blk, int bx0,
+                                              int by0, int part, int iyr, int fy, bool hx0) {
+    constexpr int CW = 8 / LPB;
+    constexpr int LCW = CW == 4 ? 2 : (CW == 2 ? 1 : 0);
+    const int xc = bx0 + CW * part;
+    int a[8][CW];
+    if (fy == 0) {
+        const int16_t* p = P + (by0 + iyr + 4) * N + xc;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            int v[CW];
+            load_row_n<CW>(p + y * N, v);
+#pragma unroll
+            for (int c = 0; c < CW; ++c) a[y][c] = hx0 ? v[c] : wp_round(v[c]);
+        }
+    } else {
+        int tap[8];
+        luma_taps(fy, tap);
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) a[y][c] = 0;
+        const int16_t* p = P + (by0 + iyr + 1) * N + xc;  // block row by0 + iy - 3
+#pragma unroll
+        for (int rho = 0; rho < 15; ++rho) {
+            int v[CW];
+            load_row_n<CW>(p + rho * N, v);
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                const int t = rho - y;
+                if (t >= 0 && t < 8)
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) a[y][c] += tap[t] * v[c];
+            }
+        }
+        const int sh = hx0 ? kShift1 : kShift2;
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) a[y][c] = wp_round(a[y][c] >> sh);
+    }
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+        const int* cp = blk + (by0 + y) * N + xc;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) a[y][c] = dec_sample(cp[c]) - a[y][c];
+    }
+    // Hadamard along each column (over y)
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+        int col[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) col[y] = a[y][c];
+        hadamard8_row(col);
+#pragma unroll
+        for (int y = 0; y < 8; ++y) a[y][c] = col[y];
+    }
+    // along each row: the stages over the column-index bits held by the
+    // lane part (across lanes), then those within the lane
+    const unsigned gmask = ((1u << LPB) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(LPB - 1));
+#pragma unroll
+    for (int hl = 1; hl < LPB; hl <<= 1) {
+        const bool upper = (part & hl) != 0;
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                const int o = __shfl_xor_sync(gmask, a[y][c], hl);
+                a[y][c] = upper ? o - a[y][c] : a[y][c] + o;
+            }
+    }
+    uint32_t sum = 0;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+#pragma unroll
+        for (int h = 1; h < CW; h <<= 1)
+#pragma unroll
+            for (int c = 0; c < CW; ++c)
+                if (!(c & h)) {
+                    const int u = a[y][c], w = a[y][c + h];
+                    a[y][c] = u + w;
+                    a[y][c + h] = u - w;
+                }
+#pragma unroll
+        for (int c = 0; c < CW; ++c) sum += (uint32_t)abs(a[y][c]);
+    }
+#pragma unroll
+    for (int hl = 1; hl < LPB; hl <<= 1) sum += __shfl_xor_sync(gmask, sum, hl);
+    (void)LCW;
+    return (sum + 2) >> 2;
+}
+
+// Lanes per 8x8 block of the refinement's SATD: more for small PUs, which
+// have few blocks per candidate.
+template <int N>
+__host__ __device__ constexpr int me_lpb() { return N >= 32 ? 2 : 8; }
 
 // Motion estimation of the PU at (x0, y0).  cur0/ref0: channel-0 planes.
 // Must be called by all NT threads of the block; smem holds me_smem_bytes.
@@ -409,10 +399,9 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     uint16_t* win = reinterpret_cast<uint16_t*>(smem);
     const uint16_t* wb = win + 4;  // window column 0 of row 0
     int* blk = reinterpret_cast<int*>(smem + me_off_blk(N, R));
-    int16_t* hp = reinterpret_cast<int16_t*>(smem + me_off_hp(N, R));
+    int16_t* planes = reinterpret_cast<int16_t*>(smem + me_off_scr(N, R));
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + me_off_red(N, R));
     uint32_t* satd = reinterpret_cast<uint32_t*>(smem + me_off_satd(N, R));
-    int16_t* had = reinterpret_cast<int16_t*>(smem + me_off_had(N, R));
     int* s_bitsd = reinterpret_cast<int*>(smem + me_off_cost(N, R));  // |se(4d)|, index d + R
     uint32_t* s_costb = reinterpret_cast<uint32_t*>(s_bitsd + 129);    // cost of b bits
 
@@ -526,39 +515,66 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         atomicAdd(bsub + sbk, (int)(acc - (uint32_t)SB * (uint32_t)kSampleBias));
     }
     // Box table of row class m: entry (t, tx) = sum of the SB x SB window
-    // samples with top-left corner (4 + m + K t, 4 + tx).  One task per 8
-    // consecutive entries: horizontal running sums over SB window rows (the
-    // 16-byte loads start at window column 8 c + 4, a word boundary).
+    // samples with top-left corner (4 + m + K t, 4 + tx).  One task per MR
+    // consecutive table rows and 8 consecutive entries (16-byte loads start
+    // at window column 8 c + 4, a word boundary): the column sums over SB
+    // window rows are kept as packed 16-bit pairs (SB x 1023 < 2^16, so a
+    // lane never carries into the next, and a row leaves a sum only after it
+    // entered it) and slid down K rows from one table row to the next; the
+    // 8 entries are sliding sums of SB column sums.
     auto build_tab = [&](int m) {
+        constexpr int MR = 4;
+        constexpr int NQ = (8 + SB + 7) / 8;  // 16-byte loads per row segment
         const int nr = (2 * R + N - SB - m) / K + 1;
         const int nch = TS / 8;
-        for (int task = tid; task < nr * nch; task += NT) {
-            const int t = task / nch, c = task - t * nch;
-            const uint16_t* w0 = wb + (4 + m + K * t) * S + 8 * c + 4;
-            uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll 1
-            for (int r = 0; r < SB; ++r) {
-                uint32_t v[(8 + SB + 7) / 8 * 8];
+        const int ngrp = (nr + MR - 1) / MR;
+        for (int task = tid; task < ngrp * nch; task += NT) {
+            const int g = task / nch, c = task - g * nch;
+            const int t0 = g * MR;
+            const uint16_t* w0 = wb + (4 + m + K * t0) * S + 8 * c + 4;
+            uint32_t vs[4 * NQ];
 #pragma unroll
-                for (int i = 0; i < 8 + SB; i += 8) {
-                    const uint4 q4 = *reinterpret_cast<const uint4*>(w0 + r * S + i);
-                    v[i] = q4.x & 0xffffu; v[i + 1] = q4.x >> 16; v[i + 2] = q4.y & 0xffffu; v[i + 3] = q4.y >> 16;
-                    v[i + 4] = q4.z & 0xffffu; v[i + 5] = q4.z >> 16; v[i + 6] = q4.w & 0xffffu; v[i + 7] = q4.w >> 16;
+            for (int i = 0; i < 4 * NQ; ++i) vs[i] = 0u;
+#pragma unroll 4
+            for (int r = 0; r < SB; ++r) {
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) {
+                    const uint4 q4 = *reinterpret_cast<const uint4*>(w0 + r * S + 8 * j);
+                    vs[4 * j] += q4.x; vs[4 * j + 1] += q4.y; vs[4 * j + 2] += q4.z; vs[4 * j + 3] += q4.w;
                 }
+            }
+#pragma unroll 1
+            for (int tt = 0; tt < MR; ++tt) {
+                const int t = t0 + tt;
+                if (t >= nr) break;
+                if (tt > 0) {
+#pragma unroll 1
+                    for (int r = K * (tt - 1); r < K * tt; ++r) {
+#pragma unroll
+                        for (int j = 0; j < NQ; ++j) {
+                            const uint4 a4 = *reinterpret_cast<const uint4*>(w0 + (r + SB) * S + 8 * j);
+                            const uint4 d4 = *reinterpret_cast<const uint4*>(w0 + r * S + 8 * j);
+                            vs[4 * j] += a4.x - d4.x; vs[4 * j + 1] += a4.y - d4.y;
+                            vs[4 * j + 2] += a4.z - d4.z; vs[4 * j + 3] += a4.w - d4.w;
+                        }
+                    }
+                }
+                uint32_t v[8 * NQ];
+#pragma unroll
+                for (int i = 0; i < 4 * NQ; ++i) { v[2 * i] = vs[i] & 0xffffu; v[2 * i + 1] = vs[i] >> 16; }
+                uint32_t acc[8];
                 uint32_t h = 0;
 #pragma unroll
                 for (int i = 0; i < SB; ++i) h += v[i];
-                acc[0] += h;
+                acc[0] = h;
 #pragma unroll
                 for (int k = 1; k < 8; ++k) {
                     h += v[k + SB - 1] - v[k - 1];
-                    acc[k] += h;
+                    acc[k] = h;
                 }
+                *reinterpret_cast<uint4*>(tab + t * TP + 8 * c) = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+                *reinterpret_cast<uint4*>(tab + t * TP + 8 * c + 4) = make_uint4(acc[4], acc[5], acc[6], acc[7]);
             }
-            const uint4 o0 = make_uint4(acc[0], acc[1], acc[2], acc[3]);
-            const uint4 o1 = make_uint4(acc[4], acc[5], acc[6], acc[7]);
-            *reinterpret_cast<uint4*>(tab + t * TP + 8 * c) = o0;
-            *reinterpret_cast<uint4*>(tab + t * TP + 8 * c + 4) = o1;
         }
     };
     build_tab(0);
@@ -716,32 +732,70 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     }
 
     // ---- quarter-sample refinement: centre + 8 half-sample, then 8 quarter
-    int cx = 4 * res.mvx_int, cy = 4 * res.mvy_int;
-    if constexpr (N <= 32)
-        satd_stage_smem<N, NT>(wb, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 2, true, 9, satd);
-    else satd_stage<N, NT>(wb, S, R, blk, hp, cx, cy, 2, true, 9, satd);
-    uint32_t bJ = satd[0] + mv_cost(cx, cy, lmv);
+    // Stage 1 evaluates the centre (the integer vector) and its 8 half-sample
+    // neighbours, stage 2 the 8 quarter-sample neighbours of the best; each
+    // candidate's J = SATD + motion cost replaces the best only when strictly
+    // lower, in the ring order.  A stage builds the horizontal passes of its
+    // three x-vectors (stage 2 keeps the one of the best's column from stage
+    // 1), then one task per (candidate, 8x8 block) forms the prediction and
+    // the SATD.
+    constexpr int NB = (N / 8) * (N / 8);
+    const int my = res.mvy_int;
+    int16_t* const pl0 = planes;
+    int16_t* const pl1 = planes + me_plane_elems(N);
+    int16_t* const pl2 = planes + 2 * me_plane_elems(N);
+    int cx = 4 * res.mvx_int, cy = 4 * my;
     int bx = cx, by = cy;
-#pragma unroll
-    for (int k = 1; k < 9; ++k) {
-        int mx, my;
-        stage_cand(k, cx, cy, 2, true, mx, my);
-        const uint32_t J = satd[k] + mv_cost(mx, my, lmv);
-        if (J < bJ) { bJ = J; bx = mx; by = my; }
+    uint32_t bJ = 0;
+    int pm0 = cx - 2, pm1 = cx, pm2 = cx + 2;  // x-vector of each plane
+#pragma unroll 1
+    for (int stage = 0; stage < 2; ++stage) {
+        const int s = stage == 0 ? 2 : 1;
+        const int ncand = stage == 0 ? 9 : 8;
+        if (stage == 0) {
+            refine_planes<N, NT>(wb, S, R, my, 3, pm0, pm1, pm2, pl0, pl1, pl2);
+        } else {
+            // keep the plane of the best's column; the other two take bx - 1 and bx + 1
+            if (pm0 == bx) {
+                pm1 = bx - 1; pm2 = bx + 1;
+                refine_planes<N, NT>(wb, S, R, my, 2, pm1, pm2, 0, pl1, pl2, nullptr);
+            } else if (pm1 == bx) {
+                pm0 = bx - 1; pm2 = bx + 1;
+                refine_planes<N, NT>(wb, S, R, my, 2, pm0, pm2, 0, pl0, pl2, nullptr);
+            } else {
+                pm0 = bx - 1; pm1 = bx + 1;
+                refine_planes<N, NT>(wb, S, R, my, 2, pm0, pm1, 0, pl0, pl1, nullptr);
+            }
+        }
+        for (int k = tid; k < ncand; k += NT) satd[k] = 0;
+        __syncthreads();
+        // LPB adjacent lanes per (candidate, 8x8 block); NT is a multiple of
+        // 32, so all lanes of a block are taken in the same round
+        constexpr int LPB = me_lpb<N>();
+        for (int task = tid; task < LPB * ncand * NB; task += NT) {
+            const int kb = task / LPB;
+            const int k = kb / NB, b = kb - k * NB;
+            int mvx, mvy;
+            stage_cand(k, cx, cy, s, stage == 0, mvx, mvy);
+            const int16_t* P = pm0 == mvx ? pl0 : (pm1 == mvx ? pl1 : pl2);
+            const uint32_t v = satd_part<N, LPB>(P, blk, (b % (N / 8)) * 8, (b / (N / 8)) * 8, task & (LPB - 1),
+                                                 (mvy >> 2) - my, mvy & 3, (mvx & 3) == 0);
+            if ((task & (LPB - 1)) == 0) atomicAdd(&satd[k], v);
+        }
+        __syncthreads();
+        int k0 = 0;
+        if (stage == 0) { bJ = satd[0] + mv_cost(cx, cy, lmv); k0 = 1; }
+#pragma unroll 1
+        for (int k = k0; k < ncand; ++k) {
+            int mx, my2;
+            stage_cand(k, cx, cy, s, stage == 0, mx, my2);
+            const uint32_t J = satd[k] + mv_cost(mx, my2, lmv);
+            if (J < bJ) { bJ = J; bx = mx; by = my2; }
+        }
+        __syncthreads();
+        cx = bx;
+        cy = by;
     }
-    __syncthreads();
-    cx = bx; cy = by;
-    if constexpr (N <= 32)
-        satd_stage_smem<N, NT>(wb, S, R, blk, reinterpret_cast<int*>(hp), had, cx, cy, 1, false, 8, satd);
-    else satd_stage<N, NT>(wb, S, R, blk, hp, cx, cy, 1, false, 8, satd);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        int mx, my;
-        stage_cand(k, cx, cy, 1, false, mx, my);
-        const uint32_t J = satd[k] + mv_cost(mx, my, lmv);
-        if (J < bJ) { bJ = J; bx = mx; by = my; }
-    }
-    __syncthreads();
     res.mvx = bx;
     res.mvy = by;
     res.cost = bJ;

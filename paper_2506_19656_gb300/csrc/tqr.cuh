@@ -21,11 +21,22 @@
 namespace xvd {
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+// The motion-compensation window of a channel (N + 7 rows and columns) is
+// staged as whole 16-byte chunks of the reference rows: its first column
+// lies anywhere in an 8-sample chunk, so a staged row holds up to
+// (N + 7 + 7) / 8 + 1 chunks.
+__host__ __device__ constexpr int tqr_stage_stride(int N) { return ((N + 7 + 7) / 8 + 1) * 8; }
+__host__ __device__ constexpr size_t tqr_stage_bytes(int N) { return align16((size_t)3 * (N + 7) * tqr_stage_stride(N) * 2); }
+__host__ __device__ constexpr size_t tqr_hbuf_bytes(int N) { return align16((size_t)3 * (N + 7) * N * 2); }
 // Byte offsets of the shared-memory regions (every region 16-byte aligned).
 __host__ __device__ constexpr size_t tqr_off_stage(int N) { return align16((size_t)5 * 3 * N * N * 2); }
-__host__ __device__ constexpr size_t tqr_off_hbuf(int N) { return tqr_off_stage(N) + align16((size_t)3 * (N + 7) * (N + 7) * 2); }
-__host__ __device__ constexpr size_t tqr_off_red(int N) { return tqr_off_hbuf(N) + align16((size_t)3 * (N + 7) * N * 2); }
-__host__ __device__ constexpr size_t tqr_seq_smem_bytes(int N) { return tqr_off_red(N) + 64 * 8; }
+__host__ __device__ constexpr size_t tqr_off_hbuf(int N) { return tqr_off_stage(N) + tqr_stage_bytes(N); }
+__host__ __device__ constexpr size_t tqr_off_red(int N) { return tqr_off_hbuf(N) + tqr_hbuf_bytes(N); }
+// the 32-point halves' coefficient table (CUs of 32 and more)
+__host__ __device__ constexpr size_t tqr_off_t32(int N) { return tqr_off_red(N) + 64 * 8; }
+__host__ __device__ constexpr size_t tqr_seq_smem_bytes(int N) {
+    return tqr_off_t32(N) + (N >= 32 ? (size_t)kT32HalvesInts * 4 : 0);
+}
 
 template <int NT>
 __device__ __forceinline__ void block_sum2(uint64_t& a, uint32_t& b, uint64_t* red) {
@@ -44,28 +55,35 @@ __device__ __forceinline__ void block_sum2(uint64_t& a, uint32_t& b, uint64_t* r
 }
 
 // Loads the CU's current samples (s_cur) and, with a reference, the motion-
-// compensation windows of all three channels (s_stage [3][N+7][N+7]: rows
-// y0+iy-3 .. y0+iy+N+3, columns likewise, coordinates clamped to the plane),
-// as 16-byte chunks with every load of a thread in flight before its
-// stores.  Then predicts the CU (s_pred; flat 512 without a reference):
-// HEVC 8-tap luma filter, horizontal pass into s_hbuf [3][N+7][N], vertical
-// pass, default weighted rounding.  Ends with a block barrier.
+// compensation windows of all three channels (rows y0+iy-3 .. y0+iy+N+3,
+// columns likewise, coordinates clamped to the plane) as whole 16-byte
+// chunks of the reference rows into s_stage [3][N+7][tqr_stage_stride(N)]
+// (window column q at staged column q + off, off = the window's offset in
+// its first chunk), every load of a thread in flight before its stores.
+// Then predicts the CU (s_pred; flat 512 without a reference): HEVC 8-tap
+// luma filter, horizontal pass into s_hbuf [3][N+7][N] (one task per 8
+// outputs of a row, its 15 inputs in registers), vertical pass over 4 x 4
+// output blocks (11 input rows each), default weighted rounding.  Ends with
+// a block barrier.
 template <int N, int NT, bool kCoherent>
 __device__ void load_and_predict(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
                                  int Hp, int Wp, int x0, int y0, int mvx, int mvy, uint16_t* __restrict__ s_cur,
                                  uint16_t* __restrict__ s_pred, int16_t* __restrict__ s_stage,
                                  int16_t* __restrict__ s_hbuf) {
     constexpr int SW = N + 7;
+    constexpr int SP = tqr_stage_stride(N);
     constexpr int NN = N * N;
     constexpr int CCH = N / 8;  // 16-byte chunks per current row
     const int tid = threadIdx.x;
     const int ix = mvx >> 2, iy = mvy >> 2, fx = mvx & 3, fy = mvy & 3;
     const int wx = x0 + ix - 3, wy = y0 + iy - 3;   // window origin
     const int xa = wx - (((wx % 8) + 8) % 8);       // 8-aligned start at or left of wx
-    const int mch = (wx + SW - xa + 7) / 8;         // chunks per window row
+    const int off = wx - xa;                        // staged column of window column 0
+    const int mch = (off + SW + 7) / 8;             // chunks per window row
     const int ncur = 3 * N * CCH;
     const int ntask = ncur + (ref ? 3 * SW * mch : 0);
     constexpr int kILP = 2;
+#pragma unroll 1
     for (int base = tid; base < ntask; base += NT * kILP) {
         uint4 v[kILP];
 #pragma unroll
@@ -100,61 +118,147 @@ __device__ void load_and_predict(const uint16_t* __restrict__ cur, const uint16_
             } else if (task < ntask) {
                 const int t2 = task - ncur;
                 const int c = t2 / (SW * mch), rem = t2 - c * SW * mch, r = rem / mch, ch = rem - r * mch;
-                const int q0 = xa + 8 * ch - wx;
-                const uint32_t w[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-                int16_t* srow = s_stage + c * SW * SW + r * SW;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int q = q0 + i;
-                    if (q >= 0 && q < SW) srow[q] = (int16_t)((w[i >> 1] >> (16 * (i & 1))) & 0xffffu);
-                }
+                *reinterpret_cast<uint4*>(s_stage + (c * SW + r) * SP + 8 * ch) = v[j];
             }
         }
     }
     if (!ref) {
+#pragma unroll 1
         for (int idx = tid; idx < 3 * NN; idx += NT) s_pred[idx] = (uint16_t)kFlat;
         __syncthreads();
         return;
     }
     __syncthreads();
+    const uint16_t* st = reinterpret_cast<const uint16_t*>(s_stage);
     if (fx != 0) {
         int tap[8];
         luma_taps(fx, tap);
-        for (int idx = tid; idx < 3 * SW * N; idx += NT) {
-            const int c = idx / (SW * N), rem = idx - c * SW * N, r = rem / N, x = rem - r * N;
-            const int16_t* st = s_stage + c * SW * SW + r * SW + x;
-            int acc = 0;
+        constexpr int SPR = N / 8;
+#pragma unroll 1
+        for (int task = tid; task < 3 * SW * SPR; task += NT) {
+            const int cr = task / SPR, xs = (task - cr * SPR) * 8;  // cr = c * SW + r
+            const uint16_t* srow = st + cr * SP + xs + off;
+            int v[15];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc += tap[i] * st[i];
-            s_hbuf[idx] = (int16_t)(acc >> kShift1);
+            for (int i = 0; i < 15; ++i) v[i] = srow[i];
+            int o[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int acc = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc += tap[i] * v[k + i];
+                o[k] = acc >> kShift1;
+            }
+            uint4 pk;
+            pk.x = (uint32_t)(uint16_t)o[0] | ((uint32_t)(uint16_t)o[1] << 16);
+            pk.y = (uint32_t)(uint16_t)o[2] | ((uint32_t)(uint16_t)o[3] << 16);
+            pk.z = (uint32_t)(uint16_t)o[4] | ((uint32_t)(uint16_t)o[5] << 16);
+            pk.w = (uint32_t)(uint16_t)o[6] | ((uint32_t)(uint16_t)o[7] << 16);
+            *reinterpret_cast<uint4*>(s_hbuf + cr * N + xs) = pk;
         }
         __syncthreads();
     }
     int vtap[8];
     luma_taps(fy == 0 ? 2 : fy, vtap);
-    for (int idx = tid; idx < 3 * NN; idx += NT) {
-        const int c = idx / NN, rem = idx - c * NN, y = rem / N, x = rem - y * N;
-        const int16_t* st = s_stage + c * SW * SW;
-        const int16_t* hb = s_hbuf + c * SW * N;
-        int v;
-        if (fx == 0 && fy == 0) {
-            v = st[(y + 3) * SW + x + 3] << kShift3;
-        } else if (fy == 0) {
-            v = hb[(y + 3) * N + x];
-        } else if (fx == 0) {
-            int acc = 0;
+    constexpr int B4 = N / 4;
+#pragma unroll 1
+    for (int task = tid; task < 3 * B4 * B4; task += NT) {
+        const int c = task / (B4 * B4), rem = task - c * B4 * B4;
+        const int yb = (rem / B4) * 4, xb = (rem - (rem / B4) * B4) * 4;
+        int o[4][4];
+        if (fy == 0) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) acc += vtap[t] * st[(y + t) * SW + x + 3];
-            v = acc >> kShift1;
+            for (int y = 0; y < 4; ++y) {
+                const int r = yb + y + 3;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    o[y][k] = wp_round(fx ? (int)s_hbuf[(c * SW + r) * N + xb + k]
+                                          : (int)st[(c * SW + r) * SP + xb + k + 3 + off] << kShift3);
+            }
         } else {
-            int acc = 0;
 #pragma unroll
-            for (int t = 0; t < 8; ++t) acc += vtap[t] * hb[(y + t) * N + x];
-            v = acc >> kShift2;
+            for (int y = 0; y < 4; ++y)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[y][k] = 0;
+#pragma unroll
+            for (int rho = 0; rho < 11; ++rho) {
+                const int r = yb + rho;
+                int v[4];
+                if (fx) {
+                    const uint2 q = *reinterpret_cast<const uint2*>(s_hbuf + (c * SW + r) * N + xb);
+                    v[0] = (int)(int16_t)(q.x & 0xffffu); v[1] = (int)q.x >> 16;
+                    v[2] = (int)(int16_t)(q.y & 0xffffu); v[3] = (int)q.y >> 16;
+                } else {
+                    const uint16_t* sr = st + (c * SW + r) * SP + xb + 3 + off;
+                    v[0] = sr[0]; v[1] = sr[1]; v[2] = sr[2]; v[3] = sr[3];
+                }
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int t = rho - y;
+                    if (t >= 0 && t < 8)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) o[y][k] += vtap[t] * v[k];
+                }
+            }
+            const int sh = fx ? kShift2 : kShift1;
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[y][k] = wp_round(o[y][k] >> sh);
         }
-        s_pred[idx] = (uint16_t)wp_round(v);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            uint2 pk;
+            pk.x = (uint32_t)o[y][0] | ((uint32_t)o[y][1] << 16);
+            pk.y = (uint32_t)o[y][2] | ((uint32_t)o[y][3] << 16);
+            *reinterpret_cast<uint2*>(s_pred + c * NN + (yb + y) * N + xb) = pk;
+        }
     }
     __syncthreads();
+}
+
+// TS consecutive samples of a row (16-byte aligned for TS >= 8, 8-byte for 4).
+template <int TS, bool kSigned>
+__device__ __forceinline__ void load_seg(const void* p, int (&v)[TS]) {
+    if constexpr (TS == 4) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        const uint32_t w[2] = {q.x, q.y};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            v[2 * i] = kSigned ? (int)(int16_t)(w[i] & 0xffffu) : (int)(w[i] & 0xffffu);
+            v[2 * i + 1] = kSigned ? (int)w[i] >> 16 : (int)(w[i] >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < TS / 8; ++k) {
+            const uint4 q = reinterpret_cast<const uint4*>(p)[k];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[8 * k + 2 * i] = kSigned ? (int)(int16_t)(w[i] & 0xffffu) : (int)(w[i] & 0xffffu);
+                v[8 * k + 2 * i + 1] = kSigned ? (int)w[i] >> 16 : (int)(w[i] >> 16);
+            }
+        }
+    }
+}
+template <int TS>
+__device__ __forceinline__ void store_seg(void* p, const int (&v)[TS]) {
+    if constexpr (TS == 4) {
+        uint2 q;
+        q.x = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+        q.y = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+        *reinterpret_cast<uint2*>(p) = q;
+    } else {
+#pragma unroll
+        for (int k = 0; k < TS / 8; ++k) {
+            uint4 q;
+            q.x = (uint32_t)(uint16_t)v[8 * k] | ((uint32_t)(uint16_t)v[8 * k + 1] << 16);
+            q.y = (uint32_t)(uint16_t)v[8 * k + 2] | ((uint32_t)(uint16_t)v[8 * k + 3] << 16);
+            q.z = (uint32_t)(uint16_t)v[8 * k + 4] | ((uint32_t)(uint16_t)v[8 * k + 5] << 16);
+            q.w = (uint32_t)(uint16_t)v[8 * k + 6] | ((uint32_t)(uint16_t)v[8 * k + 7] << 16);
+            reinterpret_cast<uint4*>(p)[k] = q;
+        }
+    }
 }
 
 // One TU size over the whole CU; returns (SSE, bits) through the reduction.
@@ -168,20 +272,25 @@ __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __rest
     const int tid = threadIdx.x;
     const QuantParams q = quant_params(qp, L);
     // forward rows
+#pragma unroll 1
     for (int t = tid; t < TASKS; t += NT) {
         int c = t / (N * NTU), rem = t - c * N * NTU;
         int y = rem / NTU, tx = rem - y * NTU;
         const int base = c * N * N + y * N + tx * TS;
         int x[TS], yv[TS];
+        load_seg<TS, false>(cur + base, x);
+        load_seg<TS, false>(pred + base, yv);
 #pragma unroll
-        for (int i = 0; i < TS; ++i) x[i] = (int)cur[base + i] - (int)pred[base + i];
+        for (int i = 0; i < TS; ++i) x[i] -= yv[i];
         fwd1d<TS>(x, yv);
 #pragma unroll
-        for (int i = 0; i < TS; ++i) work[base + i] = (int16_t)rshift_round(yv[i], L + kBitDepth - 9);
+        for (int i = 0; i < TS; ++i) yv[i] = rshift_round(yv[i], L + kBitDepth - 9);
+        store_seg<TS>(work + base, yv);
     }
     __syncthreads();
     // columns: forward, quantise, dequantise, inverse
     uint32_t bits = 0;
+#pragma unroll 1
     for (int t = tid; t < TASKS; t += NT) {
         int c = t / (N * NTU), rem = t - c * N * NTU;
         int ty = rem / N, x = rem - ty * N;
@@ -204,20 +313,134 @@ __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __rest
     __syncthreads();
     // inverse rows and reconstruction
     uint64_t sse = 0;
+#pragma unroll 1
     for (int t = tid; t < TASKS; t += NT) {
         int c = t / (N * NTU), rem = t - c * N * NTU;
         int y = rem / NTU, tx = rem - y * NTU;
         const int base = c * N * N + y * N + tx * TS;
         int e[TS], r[TS];
-#pragma unroll
-        for (int i = 0; i < TS; ++i) e[i] = work[base + i];
+        load_seg<TS, true>(work + base, e);
         inv1d<TS>(e, r);
+        load_seg<TS, false>(pred + base, e);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) r[i] = clip_pix(e[i] + rshift_round(r[i], 20 - kBitDepth));
+        store_seg<TS>(rec + base, r);
+        load_seg<TS, false>(cur + base, e);
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
-            int v = clip_pix((int)pred[base + i] + rshift_round(r[i], 20 - kBitDepth));
-            rec[base + i] = (uint16_t)v;
-            int d = (int)cur[base + i] - v;
+            const int d = e[i] - r[i];
             sse += (uint64_t)(d * d);
+        }
+    }
+    block_sum2<NT>(sse, bits, red);
+    sse_out = sse;
+    bits_out = bits + 3u * NTU * NTU;  // one coded-block flag per TU and channel
+}
+
+// tu_pass for 32 x 32 TUs with two lanes per TU row or column (lane part p
+// = the lane's parity, partners in adjacent lanes): each row or column task
+// would otherwise leave most of the block idle (3 N tasks per pass), and its
+// 32-point transforms are long dependent chains.  The lanes split every
+// 32-point transform in halves (fwd32_half / inv32_half, coefficient table
+// `tab`); in the column pass each lane quantises its 16 coefficients and the
+// two exchange their dequantised halves by shuffle before the inverse.
+template <int N, int NT>
+__device__ void tu_pass32(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
+                          int16_t* __restrict__ work, int16_t* __restrict__ lev, uint16_t* __restrict__ rec, int qp,
+                          const int* __restrict__ tab, uint64_t& sse_out, uint32_t& bits_out, uint64_t* red) {
+    constexpr int L = 5;
+    constexpr int NTU = N / 32;
+    constexpr int TASKS = 2 * 3 * N * NTU;  // two lanes per TU row (or column) of every channel
+    static_assert(NT % 2 == 0, "lane pairs");
+    const int tid = threadIdx.x;
+    const QuantParams q = quant_params(qp, L);
+    const unsigned pmask = 3u << ((threadIdx.x & 31) & ~1u);
+    // forward rows: lane part p writes y[16p .. 16p + 15]
+#pragma unroll 1
+    for (int t = tid; t < TASKS; t += NT) {
+        const int p = t & 1, task = t >> 1;
+        const int c = task / (N * NTU), rem = task - c * N * NTU;
+        const int y = rem / NTU, tx = rem - y * NTU;
+        const int base = c * N * N + y * N + tx * 32;
+        int x[32];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int cv[8], pv[8];
+            load_seg<8, false>(cur + base + 8 * k, cv);
+            load_seg<8, false>(pred + base + 8 * k, pv);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[8 * k + i] = cv[i] - pv[i];
+        }
+        int yh[16];
+        fwd32_half(x, p, tab, yh);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) yh[i] = rshift_round(yh[i], L + kBitDepth - 9);
+        store_seg<16>(work + base + 16 * p, yh);
+    }
+    __syncthreads();
+    // columns: forward, quantise and dequantise (16 coefficients per lane),
+    // exchange, inverse
+    uint32_t bits = 0;
+#pragma unroll 1
+    for (int t = tid; t < TASKS; t += NT) {
+        const int p = t & 1, task = t >> 1;
+        const int c = task / (N * NTU), rem = task - c * N * NTU;
+        const int ty = rem / N, x = rem - ty * N;
+        const int base = c * N * N + ty * 32 * N + x;
+        int col[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) col[i] = work[base + i * N];
+        int cf[16];
+        fwd32_half(col, p, tab, cf);
+        int d[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int lv = quantize(rshift_round(cf[i], L + 6), q);
+            lev[base + (16 * p + i) * N] = (int16_t)lv;
+            if (lv != 0) bits += (uint32_t)(2 * L + se_len(lv));
+            d[i] = dequantize(lv, q);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int o = __shfl_xor_sync(pmask, d[i], 1);
+            col[i] = p ? o : d[i];
+            col[16 + i] = p ? d[i] : o;
+        }
+        int lo[8], hi[8];
+        inv32_half(col, p, tab, lo, hi);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            work[base + (8 * p + i) * N] = (int16_t)clip16(rshift_round(lo[i], 7));
+            work[base + (24 - 8 * p + i) * N] = (int16_t)clip16(rshift_round(hi[i], 7));
+        }
+    }
+    __syncthreads();
+    // inverse rows and reconstruction: lane part p rebuilds x[8p .. 8p + 7]
+    // and x[24 - 8p .. 31 - 8p]
+    uint64_t sse = 0;
+#pragma unroll 1
+    for (int t = tid; t < TASKS; t += NT) {
+        const int p = t & 1, task = t >> 1;
+        const int c = task / (N * NTU), rem = task - c * N * NTU;
+        const int y = rem / NTU, tx = rem - y * NTU;
+        const int base = c * N * N + y * N + tx * 32;
+        int e[32];
+        load_seg<32, true>(work + base, e);
+        int lo[8], hi[8];
+        inv32_half(e, p, tab, lo, hi);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int off = h == 0 ? 8 * p : 24 - 8 * p;
+            int v[8], pr[8], cu[8];
+            load_seg<8, false>(pred + base + off, pr);
+            load_seg<8, false>(cur + base + off, cu);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                v[i] = clip_pix(pr[i] + rshift_round(h == 0 ? lo[i] : hi[i], 20 - kBitDepth));
+                const int dd = cu[i] - v[i];
+                sse += (uint64_t)(dd * dd);
+            }
+            store_seg<8>(rec + base + off, v);
         }
     }
     block_sum2<NT>(sse, bits, red);
@@ -248,8 +471,8 @@ __device__ __forceinline__ void copy_out(const uint16_t* __restrict__ rec, const
 template <int N>
 __host__ __device__ constexpr int tqr_nslots() { return N >= 16 ? 3 : (N >= 8 ? 2 : 1); }
 __host__ __device__ constexpr size_t tqr_conc_off_stage(int N) { return align16((size_t)2 * 3 * N * N * 2); }
-__host__ __device__ constexpr size_t tqr_conc_off_hbuf(int N) { return tqr_conc_off_stage(N) + align16((size_t)3 * (N + 7) * (N + 7) * 2); }
-__host__ __device__ constexpr size_t tqr_conc_off_slots(int N) { return tqr_conc_off_hbuf(N) + align16((size_t)3 * (N + 7) * N * 2); }
+__host__ __device__ constexpr size_t tqr_conc_off_hbuf(int N) { return tqr_conc_off_stage(N) + tqr_stage_bytes(N); }
+__host__ __device__ constexpr size_t tqr_conc_off_slots(int N) { return tqr_conc_off_hbuf(N) + tqr_hbuf_bytes(N); }
 __host__ __device__ constexpr size_t tqr_conc_slot_bytes(int N) {
     return align16((size_t)3 * 3 * N * N * 2) + align16((size_t)3 * N * N * 4);
 }
@@ -363,6 +586,7 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
     const int TOT = cum[NS];
 
     // 2. forward rows, all sizes
+#pragma unroll 1
     for (int t = tid; t < TOT; t += NT) {
         int s = 0;
         while (s < NS - 1 && t >= cum[s + 1]) ++s;
@@ -379,6 +603,7 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
     uint64_t sseS[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) { bitsS[s] = 0; sseS[s] = 0; }
+#pragma unroll 1
     for (int t = tid; t < TOT; t += NT) {
         int s = 0;
         while (s < NS - 1 && t >= cum[s + 1]) ++s;
@@ -410,6 +635,7 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
         }
     }
     __syncthreads();
+#pragma unroll 1
     for (int t = tid; t < TOT; t += NT) {
         int s = 0;
         while (s < NS - 1 && t >= cum[s + 1]) ++s;
@@ -420,6 +646,7 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
     }
     __syncthreads();
     // 4. inverse rows, reconstruction, SSE
+#pragma unroll 1
     for (int t = tid; t < TOT; t += NT) {
         int s = 0;
         while (s < NS - 1 && t >= cum[s + 1]) ++s;
@@ -472,6 +699,12 @@ __host__ __device__ constexpr size_t tqr_smem_bytes(int N) {
 // u16 [3][N][N] at offset 0, the prediction right after it), written before
 // a barrier; cur, ref and the vector are then not read, and the bits count
 // no vector (ref must be nullptr).
+template <int N, int NT, bool kCoherent, bool kPredGiven>
+__device__ uint32_t tqr_cu_seq(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
+                               int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
+                               int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
+                               uint8_t* tu_log2, unsigned char* smem);
+
 template <int N, int NT, bool kCoherent = false, bool kPredGiven = false>
 __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
                            int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
@@ -480,7 +713,20 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
     if constexpr (N <= 16) {
         return tqr_cu_conc<N, NT, kCoherent, kPredGiven>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask,
                                                          lf8, recon, levels, tu_log2, smem);
+    } else {
+        return tqr_cu_seq<N, NT, kCoherent, kPredGiven>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask, lf8,
+                                                        recon, levels, tu_log2, smem);
     }
+}
+
+// The size-by-size form: one TU size after another over the whole CU, the
+// reconstruction and levels of the best so far copied out as soon as a size
+// improves on it.
+template <int N, int NT, bool kCoherent, bool kPredGiven>
+__device__ uint32_t tqr_cu_seq(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
+                               int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
+                               int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
+                               uint8_t* tu_log2, unsigned char* smem) {
     const int tid = threadIdx.x;
     uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
     uint16_t* s_pred = s_cur + 3 * N * N;
@@ -491,8 +737,14 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
     int16_t* s_hbuf = reinterpret_cast<int16_t*>(smem + tqr_off_hbuf(N));
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + tqr_off_red(N));
 
+    int* t32tab = reinterpret_cast<int*>(smem + tqr_off_t32(N));
+    if constexpr (N >= 32) t32_halves_init(t32tab);  // in flight during the prediction
     if constexpr (!kPredGiven)
         load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
+    if constexpr (N >= 32) {
+        t32_halves_wait();
+        __syncthreads();
+    }
 
     int64_t bestJ = INT64_MAX;
     int bestL = 0;
@@ -515,7 +767,7 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
     if constexpr (N >= 16)
         if (tu_mask & (1u << 4)) { tu_pass<N, 16, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(4, sse, bits); }
     if constexpr (N >= 32)
-        if (tu_mask & (1u << 5)) { tu_pass<N, 32, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(5, sse, bits); }
+        if (tu_mask & (1u << 5)) { tu_pass32<N, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, t32tab, sse, bits, red); consider(5, sse, bits); }
     if (tid == 0 && tu_log2) *tu_log2 = (uint8_t)bestL;
     uint32_t mvbits = ref ? (uint32_t)(se_len(mvx) + se_len(mvy)) : 0u;
     return 2u + mvbits + bestBits;

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -52,11 +53,19 @@ struct xv_ctx {
     cudaEvent_t fork_ev = nullptr;
     DevBuf b_mv, b_exact;
     DevBuf peak_buf;                         // xv_measure_peak's input and sink
+    int batch_cfg[4] = {0, 0, 0, 0};         // configuration code of each CTU class in the last batch
+    int class_tuned[4] = {0, 0, 0, 0};       // the autotuner's latest persistent choice per CTU class
+    std::string tune_log;                    // the autotuner's last timings
     xvh::ServeState* serve = nullptr;
 };
 
 // Block size value that selects the batched path's per-frame mode.
 constexpr int kFramesMode = 1;
+// A persistent-kernel configuration of one CTU class: block size + 1024 x
+// the cap on resident blocks per SM (0: as many as fit).
+constexpr int cfg_code(int nt, int per_cap) { return nt + 1024 * per_cap; }
+constexpr int cfg_nt(int code) { return code == kFramesMode ? kFramesMode : code % 1024; }
+constexpr int cfg_per(int code) { return code == kFramesMode ? 0 : code / 1024; }
 constexpr int kSideStreams = 16;
 
 namespace xvh {
@@ -266,6 +275,8 @@ xv_status fill_result(const xv_job* j, const uint64_t* bits_dev, int G, xv_resul
     r->total_bits = tot;
     r->bands = j->bands;
     r->bpppb = (double)tot / ((double)j->H * j->W * j->T * j->bands);
+    r->ctu = j->p.ctu;
+    r->block_size = 1;  // the per-frame launches
     return XV_OK;
 }
 
@@ -645,6 +656,35 @@ size_t xv_job_scratch_bytes(const xv_job* j) {
     return (size_t)G * j->T * (npu * 4 + npu * 4 + 8) + 4096;
 }
 
+xv_status xv_split_groups(const xv_job* whole, const int* qp, xv_job* out, int* njobs) {
+    if (!valid_job(whole)) return XV_EINVAL;
+    if (!qp || !out || !njobs) { set_error("qp, out and njobs are required"); return XV_EINVAL; }
+    const xv_job& j = *whole;
+    const int G = (j.bands + 2) / 3, Hp = plane_dim(j.H, j.p.ctu), Wp = plane_dim(j.W, j.p.ctu);
+    const int64_t npu = (int64_t)(Hp / j.p.ctu) * (Wp / j.p.ctu);
+    const int64_t fsz = 3LL * Hp * Wp, band = (int64_t)j.T * j.H * j.W;
+    const size_t esz = j.dtype == XV_F32 ? 4 : 2;
+    for (int g = 0; g < G; ++g) {
+        xv_job o = j;
+        xv_status s = xv_params_init(&o.p, j.p.ctu, j.p.search_range, j.p.tu_mask, qp[g]);
+        if (s) return s;
+        o.p.flags = j.p.flags;
+        o.bands = std::min(3, j.bands - 3 * g);
+        o.src = (const char*)j.src + (size_t)(3 * g) * band * esz;
+        if (j.minmax) o.minmax = j.minmax + 2 * 3 * g;
+        o.planes = j.planes + (size_t)g * j.T * fsz;
+        o.recon = j.recon + (size_t)g * j.T * fsz;
+        if (j.mv) o.mv = j.mv + (size_t)g * j.T * npu * 2;
+        if (j.cost) o.cost = j.cost + (size_t)g * j.T * npu;
+        if (j.levels) o.levels = j.levels + (size_t)g * j.T * fsz;
+        if (j.tu_log2) o.tu_log2 = j.tu_log2 + (size_t)g * j.T * npu;
+        if (j.bits) o.bits = j.bits + (size_t)g * j.T;
+        out[g] = o;
+    }
+    *njobs = G;
+    return XV_OK;
+}
+
 xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (!valid_job(j)) return XV_EINVAL;
@@ -984,6 +1024,21 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         if (r) return r;
         if (je != cudaSuccess) return cuda_fail(je, "join");
         c->batch_nt = kFramesMode;
+        for (int k = 0; k < 4; ++k) c->batch_cfg[k] = total[k] ? kFramesMode : 0;
+        return XV_OK;
+    };
+    // the persistent launch of CTU class k in configuration `code`
+    auto launch_class = [&](int k, int code) -> xv_status {
+        const int bnt = cfg_nt(code);
+        const int grid = xvh::persist_grid(ctus[k], bnt, smem[k], false, cfg_per(code));
+        xv_status r = check_launch(xvh::launch_persist(ctus[k], bnt, false, jobs_dev,
+                                                       (uint64_t*)c->b_items.ptr + cls[k].qoff,
+                                                       (xvh::BatchCtl*)c->b_ctl.ptr + k, smem[k], grid, st),
+                                   "persistent encode");
+        if (r) return r;
+        c->launches += kLaunchPersist;
+        c->batch_nt = bnt;
+        c->batch_cfg[k] = code;
         return XV_OK;
     };
     auto part_kernels = [&](const int nt[4]) -> xv_status {
@@ -991,13 +1046,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         xv_status r = XV_OK;
         for (int k = 0; k < 4; ++k) {
             if (!total[k]) continue;
-            const int grid = xvh::persist_grid(ctus[k], nt[k], smem[k], false);
-            r = check_launch(xvh::launch_persist(ctus[k], nt[k], false, jobs_dev, (uint64_t*)c->b_items.ptr + cls[k].qoff,
-                                                 (xvh::BatchCtl*)c->b_ctl.ptr + k, smem[k], grid, st),
-                             "persistent encode");
-            if (r) return r;
-            c->launches += kLaunchPersist;
-            c->batch_nt = nt[k];
+            if ((r = launch_class(k, nt[k]))) return r;
         }
         return r;
     };
@@ -1045,7 +1094,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if ((e = cudaEventRecord(c->ev_in, caller)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c->ev_in, 0)) != cudaSuccess)
         return cuda_fail(e, "stream order");
 
-    // ---- block size: forced, cached, or tuned now (uncaptured runs)
+    // ---- configuration per CTU class: forced, cached, or tuned now
     int nt[4] = {256, 256, 256, 256};
     bool tune = false;
     for (int k = 0; k < 4; ++k) {
@@ -1062,24 +1111,87 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         tune = false;
     }
     if (tune && !debug) {
-        float best_ms = 1e30f;
-        int best_nt = 256;
-        const int cands[5] = {xvh::kPersistBlockSizes[0], xvh::kPersistBlockSizes[1], xvh::kPersistBlockSizes[2],
-                              xvh::kPersistBlockSizes[3], kFramesMode};
-        for (int cand : cands) {
-            int trial[4] = {cand, cand, cand, cand};
-            if ((s = body(trial))) return s;
-            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune");
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) != cudaSuccess) { cudaGetLastError(); ms = 1e30f; }
-            if (ms < best_ms) { best_ms = ms; best_nt = cand; }
-        }
+        // The autotuner.  Candidates: per CTU class, every block size the
+        // persistent kernel is built for, with as many resident blocks per
+        // SM as fit and with one fewer; for the whole batch, the per-frame
+        // mode.  Each is timed as the CUDA graph it would replay (the batch
+        // prologue, which resets the counters, then the candidate's
+        // launches): one warm-up replay, then the median of three.  A
+        // class's persistent launches are independent of the other classes',
+        // so each class keeps its fastest configuration; the per-frame mode
+        // wins when it beats the sum of those.
+        if ((s = part_setup())) return s;  // the planes and counters every candidate reads
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune setup");
+        const uint64_t launches_before = c->launches;
+        auto time_graph = [&](const std::function<xv_status()>& record, float* med) -> xv_status {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t te = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (te != cudaSuccess) return cuda_fail(te, "autotune capture");
+            xv_status r = check_launch(xvh::launch_batch_prologue(jobs_dev, njobs, (const xvh::ClassDev*)c->b_cls.ptr,
+                                                                  (uint64_t*)c->b_items.ptr, (xvh::BatchCtl*)c->b_ctl.ptr,
+                                                                  c->wait_budget, c->stall_row, st),
+                                       "batch prologue");
+            if (!r) r = record();
+            te = cudaStreamEndCapture(st, &graph);
+            if (r) { if (graph) cudaGraphDestroy(graph); return r; }
+            if (te != cudaSuccess) return cuda_fail(te, "autotune capture");
+            te = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (te != cudaSuccess) return cuda_fail(te, "autotune instantiate");
+            float ms[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int rep = 0; rep < 4 && te == cudaSuccess; ++rep) {
+                if ((te = cudaEventRecord(c->ev0, st)) != cudaSuccess || (te = cudaGraphLaunch(exec, st)) != cudaSuccess ||
+                    (te = cudaEventRecord(c->ev1, st)) != cudaSuccess || (te = cudaStreamSynchronize(st)) != cudaSuccess)
+                    break;
+                te = cudaEventElapsedTime(&ms[rep], c->ev0, c->ev1);
+            }
+            cudaGraphExecDestroy(exec);
+            if (te != cudaSuccess) return cuda_fail(te, "autotune replay");
+            std::sort(ms + 1, ms + 4);  // ms[0] is the warm-up
+            *med = ms[2];
+            return XV_OK;
+        };
+        float persist_total = 0.f;
+        int best_code[4] = {0, 0, 0, 0};
+        c->tune_log.clear();
         for (int k = 0; k < 4; ++k) {
             if (!total[k]) continue;
-            c->tuned_nt[shape[k]] = best_nt;
-            nt[k] = best_nt;
+            float best = 1e30f;
+            for (int bnt : xvh::kPersistBlockSizes) {
+                const int maxper = xvh::persist_blocks_per_sm(ctus[k], bnt, smem[k], false);
+                const int npers = maxper >= 2 ? 2 : 1;  // as many as fit, and one fewer
+                for (int pi = 0; pi < npers; ++pi) {
+                    const int per = pi == 0 ? 0 : maxper - 1;
+                    const int code = cfg_code(bnt, per);
+                    float ms = 0.f;
+                    if ((s = time_graph([&]() { return launch_class(k, code); }, &ms))) return s;
+                    char line[96];
+                    snprintf(line, sizeof line, "ctu%d nt%d per%d %.3f;", ctus[k], bnt, per ? per : maxper, ms);
+                    c->tune_log += line;
+                    if (ms < best) { best = ms; best_code[k] = code; }
+                }
+            }
+            persist_total += best;
         }
+        float frames_ms = 0.f;
+        if ((s = time_graph([&]() { return part_frames(); }, &frames_ms))) return s;
+        {
+            char line[64];
+            snprintf(line, sizeof line, "frames %.3f;", frames_ms);
+            c->tune_log += line;
+        }
+        const bool frames = frames_ms < persist_total;
+        for (int k = 0; k < 4; ++k) {
+            if (!total[k]) continue;
+            nt[k] = frames ? kFramesMode : best_code[k];
+            c->tuned_nt[shape[k]] = nt[k];
+            c->class_tuned[k] = best_code[k];  // the persistent kernel's best, also when the batch runs per frame
+        }
+        c->launches = launches_before;  // the candidates' launches are not the batch's
     }
+
+    for (int k = 0; k < 4; ++k) c->batch_cfg[k] = total[k] ? (frames_mode(nt) ? kFramesMode : nt[k]) : 0;
 
     // ---- run: replay the captured graph of this exact batch, or capture it
     if (c->use_graph && !debug) {
@@ -1191,6 +1303,9 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         r->total_bits = h_tot[i];
         r->bands = j.bands;
         r->bpppb = (double)h_tot[i] / ((double)j.H * j.W * j.T * j.bands);
+        r->ctu = j.p.ctu;
+        const int k = j.p.ctu == 8 ? 0 : j.p.ctu == 16 ? 1 : j.p.ctu == 32 ? 2 : 3;
+        r->block_size = cfg_nt(c->batch_cfg[k]);
         r->status = XV_OK;
     }
     return XV_OK;
@@ -1445,6 +1560,17 @@ xv_status xv_last_batch_block_size(const xv_ctx* c, int* nt) {
     return XV_OK;
 }
 
+xv_status xv_last_batch_config(const xv_ctx* c, int ctu, int* block_size, int* blocks_per_sm) {
+    if (!c || !block_size) { set_error("ctx and block_size are required"); return XV_EINVAL; }
+    const int k = ctu == 8 ? 0 : ctu == 16 ? 1 : ctu == 32 ? 2 : ctu == 64 ? 3 : -1;
+    if (k < 0) { set_error("ctu %d: must be 8, 16, 32 or 64", ctu); return XV_EINVAL; }
+    *block_size = cfg_nt(c->batch_cfg[k]);
+    if (blocks_per_sm) *blocks_per_sm = cfg_per(c->batch_cfg[k]);
+    return XV_OK;
+}
+
+const char* xv_last_tune_log(const xv_ctx* c) { return c ? c->tune_log.c_str() : ""; }
+
 xv_status xv_last_batch_search_stats(const xv_ctx* c, uint64_t* exact_candidates, uint64_t* full_candidates) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (exact_candidates) *exact_candidates = c->batch_exact;
@@ -1476,7 +1602,17 @@ xv_status xv_serve_start(xv_ctx* c, int max_slots, int frames_per_tick) {
     }
     DeviceGuard g(c->device);
     xv_status st = XV_OK;
-    xvh::ServeState* s = xvh::serve_create(c->device, max_slots, frames_per_tick, c->budget, c->wait_budget, &st);
+    // the persistent configuration per CTU class: the autotuner's latest
+    // choice for that class on this context, else 256-thread blocks
+    int block[4], per_cap[4];
+    for (int k = 0; k < 4; ++k) {
+        const int code = c->class_tuned[k];
+        const bool persistent = code != 0 && code != kFramesMode;
+        block[k] = persistent ? cfg_nt(code) : 256;
+        per_cap[k] = persistent ? cfg_per(code) : 0;
+    }
+    xvh::ServeState* s = xvh::serve_create(c->device, max_slots, frames_per_tick, c->budget, c->wait_budget, block,
+                                           per_cap, &st);
     if (st) { xvh::serve_destroy(s); return st; }
     c->serve = s;
     return XV_OK;
@@ -1532,7 +1668,7 @@ xv_status xv_set_batch_graphs(xv_ctx* c, int enable) {
 xv_status xv_debug_force_block_size(xv_ctx* c, int nt) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     bool ok = nt == 0 || nt == kFramesMode;
-    for (int v : xvh::kPersistBlockSizes) ok = ok || nt == v;
+    for (int v : xvh::kPersistBlockSizes) ok = ok || (nt >= 0 && cfg_nt(nt) == v && cfg_per(nt) <= 32);
     if (!ok) {
         set_error("block size %d is neither one the persistent kernel is built for nor %d (per-frame mode)", nt,
                   kFramesMode);

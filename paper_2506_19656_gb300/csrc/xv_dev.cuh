@@ -87,6 +87,105 @@ __device__ __forceinline__ void inv1d(const int (&c)[N], int (&x)[N]) {
 }
 
 __device__ __forceinline__ int rshift_round(int v, int s) { return (v + (1 << (s - 1))) >> s; }
+
+// The 32-point transform shared by two lanes (l and l ^ 1, lane part p = 0
+// or 1), both executing the same instructions on different coefficients:
+// the even half (a 16-point transform) is computed by both, the 16 x 16 odd
+// part is split in two 8 x 16 halves whose coefficients come from a table in
+// shared memory (t32_halves_init) instead of instruction immediates.
+//   table[0 .. 255]:   forward, [p][j][n] = T32[2 (8p + j) + 1][n]
+//   table[256 .. 511]: inverse, [p][i][j] = T32[2j + 1][8p + i]
+constexpr int kT32HalvesInts = 512;
+// A 16-byte shared-memory load the compiler keeps where it is written: the
+// coefficient loads do not depend on the task, and hoisted out of a task
+// loop 256 of them would stay in registers.
+__device__ __forceinline__ int4 lds_coef4(const int* p) {
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
+struct T32Halves {
+    int v[kT32HalvesInts];
+};
+__host__ __device__ constexpr T32Halves make_t32_halves() {
+    T32Halves t{};
+    for (int idx = 0; idx < kT32HalvesInts; ++idx) {
+        const int inv = idx >> 8, p = (idx >> 7) & 1, a = (idx >> 4) & 7, b = idx & 15;
+        t.v[idx] = inv ? t32(2 * b + 1, 8 * p + a) : t32(2 * (8 * p + a) + 1, b);
+    }
+    return t;
+}
+// the table, computed at compile time (global memory, read once per CU)
+__device__ const T32Halves kT32HalvesTab = make_t32_halves();
+// Starts copying the table into shared memory `tab` (16-byte aligned) with
+// asynchronous copies, so that no thread waits on the loads here; the
+// copying threads must call t32_halves_wait() before a barrier that
+// precedes the first use.
+__device__ __forceinline__ void t32_halves_init(int* tab) {
+    for (int i = threadIdx.x; i < kT32HalvesInts / 4; i += blockDim.x) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(tab + 4 * i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(kT32HalvesTab.v + 4 * i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void t32_halves_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// y[16p .. 16p + 15] of y = T32 x (x: all 32 samples, on both lanes).  The
+// odd part first, so that its inputs are dead before the even part starts.
+__device__ __forceinline__ void fwd32_half(const int (&x)[32], int p, const int* __restrict__ tab, int (&y)[16]) {
+    int e[16], o[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        e[k] = x[k] + x[31 - k];
+        o[k] = x[k] - x[31 - k];
+    }
+    const int* f = tab + p * 128;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {  // y[2 (8p + j) + 1] = y[16p + 2j + 1]
+        int acc = 0;
+#pragma unroll
+        for (int n = 0; n < 16; n += 4) {
+            const int4 c = lds_coef4(f + j * 16 + n);
+            acc += c.x * o[n] + c.y * o[n + 1] + c.z * o[n + 2] + c.w * o[n + 3];
+        }
+        y[2 * j + 1] = acc;
+    }
+    int ye[16];
+    fwd1d<16>(e, ye);  // y[2i] = ye[i]
+#pragma unroll
+    for (int j = 0; j < 8; ++j) y[2 * j] = p ? ye[8 + j] : ye[j];
+}
+
+// Part of x = T32^T c (c: all 32 coefficients, on both lanes): lo[i] =
+// x[8p + i] and hi[i] = x[24 - 8p + i], i < 8.  The odd part first.
+__device__ __forceinline__ void inv32_half(const int (&c)[32], int p, const int* __restrict__ tab, int (&lo)[8],
+                                           int (&hi)[8]) {
+    const int* f = tab + 256 + p * 128;
+    int o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {  // n = 8p + i
+        int acc = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+            const int4 t = lds_coef4(f + i * 16 + j);
+            acc += t.x * c[2 * j + 1] + t.y * c[2 * j + 3] + t.z * c[2 * j + 5] + t.w * c[2 * j + 7];
+        }
+        o[i] = acc;
+    }
+    int ce[16], ee[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ce[i] = c[2 * i];
+    inv1d<16>(ce, ee);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int en = p ? ee[8 + i] : ee[i];
+        lo[i] = en + o[i];
+        hi[7 - i] = en - o[i];
+    }
+}
+
 __device__ __forceinline__ int clip16(int v) { return v < -32768 ? -32768 : (v > 32767 ? 32767 : v); }
 __device__ __forceinline__ int clip_pix(int v) { return v < 0 ? 0 : (v > kPixMax ? kPixMax : v); }
 
@@ -104,6 +203,7 @@ struct QuantParams {
     int64_t qscale;   // forward scale for qP % 6
     int64_t dqscale;  // 16 * levelScale[qP % 6] << (qP / 6)
     int bd;           // B + log2N - 5
+    int lmax32;       // |level| <= lmax32: level * dqscale + 2^(bd-1) fits int32
 };
 
 __device__ __forceinline__ QuantParams quant_params(int qp, int log2n) {
@@ -114,6 +214,7 @@ __device__ __forceinline__ QuantParams quant_params(int qp, int log2n) {
     q.qscale = quant_scale(qP % 6);
     q.dqscale = ((int64_t)16 * level_scale(qP % 6)) << (qP / 6);
     q.bd = kBitDepth + log2n - 5;
+    q.lmax32 = (int)((((int64_t)1 << 31) - 1 - ((int64_t)1 << (q.bd - 1))) / q.dqscale);
     return q;
 }
 
@@ -132,6 +233,11 @@ __device__ __forceinline__ int quantize(int c, const QuantParams& q) {
 
 __device__ __forceinline__ int dequantize(int level, const QuantParams& q) {
     if (level == 0) return 0;  // (0 + 2^(bd-1)) >> bd
+    if ((unsigned)(level + q.lmax32) <= 2u * (unsigned)q.lmax32) {
+        // the product and the rounding offset fit 32 bits: the same floor
+        const int v = (level * (int)q.dqscale + (1 << (q.bd - 1))) >> q.bd;
+        return v < -32768 ? -32768 : (v > 32767 ? 32767 : v);
+    }
     int64_t v = ((int64_t)level * q.dqscale + ((int64_t)1 << (q.bd - 1))) >> q.bd;
     return v < -32768 ? -32768 : (v > 32767 ? 32767 : (int)v);
 }

@@ -168,7 +168,16 @@ cudaError_t launch_deblock_frame(uint16_t* recon, int G, int64_t gstride, int Hp
 // are inputs, recon and bits outputs) instead of the encoder.
 cudaError_t launch_persist(int ctu, int nt, bool decode, const JobDev* jobs, uint64_t* queue, BatchCtl* ctl,
                            size_t smem, int grid, cudaStream_t st);
-int persist_grid(int ctu, int nt, size_t smem, bool decode);
+// Grid of a persistent launch: every SM times the resident blocks per SM
+// (at most per_cap of them when per_cap > 0).
+int persist_grid(int ctu, int nt, size_t smem, bool decode, int per_cap = 0);
+// Resident blocks per SM of a persistent kernel configuration.
+inline int persist_blocks_per_sm(int ctu, int nt, size_t smem, bool decode) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return persist_grid(ctu, nt, smem, decode) / (sms > 0 ? sms : 1);
+}
 
 }  // namespace xvh
 
@@ -176,8 +185,10 @@ namespace xvh {
 
 // Serving (csrc/xv_serve.cu).
 struct ServeState;
+// block / per_cap: the persistent kernel's block size and resident-block cap
+// per SM for each CTU class (8, 16, 32, 64).
 ServeState* serve_create(int device, int max_slots, int frames_per_tick, size_t budget, long long wait_budget,
-                         xv_status* st);
+                         const int block[4], const int per_cap[4], xv_status* st);
 void serve_destroy(ServeState* s);
 xv_status serve_submit(ServeState* s, const xv_request* r, uint64_t* ticket);
 xv_status serve_poll(ServeState* s, uint64_t ticket, xv_result* res, int* done);

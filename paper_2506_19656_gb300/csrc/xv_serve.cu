@@ -95,6 +95,8 @@ struct ServeState {
     int max_slots = 0, frames_per_tick = 0;
     size_t budget = 0, in_use = 0;
     long long wait_budget = 0;
+    int block[4] = {256, 256, 256, 256};  // persistent block size per CTU class (8, 16, 32, 64)
+    int per_cap[4] = {0, 0, 0, 0};        // resident-block cap per SM (0: as many as fit)
     std::thread th;
     std::mutex mu;
     std::condition_variable cv;
@@ -308,8 +310,9 @@ void ServeState::loop() {
         const int ctus[4] = {8, 16, 32, 64};
         for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
             if (!total[k]) continue;
-            const int grid = persist_grid(ctus[k], 256, smem[k], false);
-            e = launch_persist(ctus[k], 256, false, d_jobs, d_queue + cls[k].qoff, d_ctl + k, smem[k], grid, s_tick);
+            const int grid = persist_grid(ctus[k], block[k], smem[k], false, per_cap[k]);
+            e = launch_persist(ctus[k], block[k], false, d_jobs, d_queue + cls[k].qoff, d_ctl + k, smem[k], grid,
+                               s_tick);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev1, s_tick);
         // results of the requests this tick finishes
@@ -386,6 +389,8 @@ void ServeState::loop() {
             q->res.total_bits = h_tot[i];
             q->res.bands = r.bands;
             q->res.bpppb = (double)h_tot[i] / ((double)r.H * r.W * r.T * r.bands);
+            q->res.ctu = r.p.ctu;
+            q->res.block_size = block[r.p.ctu == 8 ? 0 : r.p.ctu == 16 ? 1 : r.p.ctu == 32 ? 2 : 3];
             finish(q, XV_OK);
             active.erase(std::find(active.begin(), active.end(), q));
         }
@@ -394,8 +399,12 @@ void ServeState::loop() {
 }
 
 ServeState* serve_create(int device, int max_slots, int frames_per_tick, size_t budget, long long wait_budget,
-                         xv_status* st) {
+                         const int block[4], const int per_cap[4], xv_status* st) {
     ServeState* s = new ServeState;
+    for (int k = 0; k < 4; ++k) {
+        s->block[k] = block[k];
+        s->per_cap[k] = per_cap[k];
+    }
     s->device = device;
     s->max_slots = max_slots;
     s->frames_per_tick = frames_per_tick;

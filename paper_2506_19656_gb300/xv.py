@@ -49,13 +49,14 @@ class xv_result(ctypes.Structure):
     _fields_ = [("status", _i), ("bands", _i), ("psnr_mean", ctypes.c_double), ("bpppb", ctypes.c_double),
                 ("total_bits", ctypes.c_uint64), ("psnr_band", ctypes.c_double * XV_MAX_BANDS),
                 ("mse_band", ctypes.c_double * XV_MAX_BANDS), ("sse10_band", ctypes.c_uint64 * XV_MAX_BANDS),
-                ("latency_s", ctypes.c_double)]
+                ("latency_s", ctypes.c_double), ("ctu", _i), ("block_size", _i)]
 
     def as_dict(self):
         n = self.bands
         return dict(status=self.status, psnr_mean=self.psnr_mean, bpppb=self.bpppb, total_bits=self.total_bits,
                     psnr_band=list(self.psnr_band[:n]), mse_band=list(self.mse_band[:n]),
-                    sse10_band=list(self.sse10_band[:n]), latency_s=self.latency_s)
+                    sse10_band=list(self.sse10_band[:n]), latency_s=self.latency_s, ctu=self.ctu,
+                    block_size=self.block_size)
 
 
 class XvError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "xv_psnr_noalloc": [_vp, _i, _i, _i, _i, _i, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "xv_job_scratch_bytes": [ctypes.POINTER(xv_job)],
     "xv_encode_cube": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(xv_result), _vp],
+    "xv_split_groups": [ctypes.POINTER(xv_job), ctypes.POINTER(_i), ctypes.POINTER(xv_job), ctypes.POINTER(_i)],
     "xv_encode_batch": [_vp, ctypes.POINTER(xv_job), _i, ctypes.POINTER(xv_result), _vp],
     "xv_encode_batch_from_host": [_vp, ctypes.POINTER(xv_job), ctypes.POINTER(_vp), _i, ctypes.POINTER(xv_result),
                                   _vp],
@@ -107,6 +109,8 @@ _SIGS = {
     "xv_last_batch_block_size": [_vp, ctypes.POINTER(_i)],
     "xv_last_batch_search_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
     "xv_ctx_launches": [_vp],
+    "xv_last_batch_config": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)],
+    "xv_last_tune_log": [_vp],
     "xv_measure_peak": [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "xv_set_batch_graphs": [_vp, _i],
     "xv_batch_graph_stats": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)],
@@ -131,6 +135,7 @@ def lib():
         L.xv_ctx_bytes.restype = ctypes.c_size_t
         L.xv_job_scratch_bytes.restype = ctypes.c_size_t
         L.xv_ctx_launches.restype = ctypes.c_uint64
+        L.xv_last_tune_log.restype = ctypes.c_char_p
         L.xv_last_error.restype = ctypes.c_char_p
         L.xv_status_string.restype = ctypes.c_char_p
         L.xv_status_string.argtypes = [_i]
@@ -363,6 +368,17 @@ def make_job(src, p: xv_params, planes, recon, minmax=None, minmax_fixed=False, 
                   cost=_ptr(cost), levels=_ptr(levels), tu_log2=_ptr(tu_log2), bits=_ptr(bits))
 
 
+def xv_split_groups(job: xv_job, qps) -> list:
+    """One job per 3-band group of `job`, group g at QP qps[g] (views of the
+    whole job's buffers)."""
+    G = (job.bands + 2) // 3
+    q = (_i * G)(*[int(v) for v in qps])
+    out = (xv_job * G)()
+    n = _i()
+    check(lib().xv_split_groups(ctypes.byref(job), q, out, ctypes.byref(n)), "xv_split_groups")
+    return [out[i] for i in range(n.value)]
+
+
 def xv_encode_cube(ctx: Context, job: xv_job, stream=None) -> dict:
     r = xv_result()
     check(lib().xv_encode_cube(ctx.handle, ctypes.byref(job), ctypes.byref(r), _stream(stream)), "xv_encode_cube")
@@ -387,6 +403,19 @@ def xv_measure_peak(ctx: Context, kind: int) -> tuple:
     ms = ctypes.c_double()
     check(lib().xv_measure_peak(ctx.handle, kind, ctypes.byref(r), ctypes.byref(ms)), "xv_measure_peak")
     return r.value, ms.value
+
+
+def xv_last_batch_config(ctx: Context, ctu: int) -> tuple:
+    """(block size or 1 for the per-frame mode, resident-block cap per SM or 0)
+    of CTU class `ctu` in the last xv_encode_batch."""
+    nt, per = _i(), _i()
+    check(lib().xv_last_batch_config(ctx.handle, ctu, ctypes.byref(nt), ctypes.byref(per)), "xv_last_batch_config")
+    return nt.value, per.value
+
+
+def xv_last_tune_log(ctx: Context) -> str:
+    """The autotuner's last candidate timings ("ctu32 nt128 per4 12.345;...")."""
+    return lib().xv_last_tune_log(ctx.handle).decode()
 
 
 def xv_encode_batch_from_host(ctx: Context, jobs, host_srcs, stream=None) -> list:

@@ -175,3 +175,8 @@ def test_cpu_baseline_all_cores_and_one_thread():
     assert got["single_thread"]["cores"] == 1 and got["single_thread"]["value"] > 0
     assert "first 2 of 8 frames" in got["single_thread"]["sample"]
     assert oracle.max_threads() == before          # the thread count is restored
+
+
+def test_parse_tune_log():
+    got = bench.parse_tune_log("ctu32 nt128 per4 161.250;ctu32 nt128 per3 170.000;frames 180.500;")
+    assert got == {"ctu32 nt128 per4": 161.25, "ctu32 nt128 per3": 170.0, "frames": 180.5}

@@ -116,6 +116,44 @@ def test_every_block_size_is_bit_exact(xv, ctx, block_size):
         assert_matches(b, r, w)
 
 
+def test_tuner_picks_per_class_configurations_and_every_candidate_is_bit_exact(xv):
+    """A fresh context tunes a mixed batch (CTU 8, 16, 32): its log holds every
+    class's persistent candidates and the per-frame mode, each class reports
+    the configuration it ran, and the tuned batch -- and every candidate with
+    a capped number of resident blocks per SM -- gives the oracle's bytes."""
+    specs = [((4, 4, 40, 56), 8, 6, 0b1100, 30), ((5, 3, 37, 53), 16, 9, 0b11100, 22),
+             ((2, 3, 70, 33), 32, 5, 0b111100, 27)]
+    jobs, bufs, wants = [], [], []
+    for i, (shape, ctu, R, mask, qp) in enumerate(specs):
+        cube, _ = synth.tiny_cube(400 + i, T=shape[1], H=shape[2], W=shape[3], bands=shape[0])
+        wants.append(oracle.encode_cube(cube, ctu, R, mask, qp))
+        j, b = gpu_job(xv, cube, ctu, R, mask, qp)
+        jobs.append(j)
+        bufs.append(b)
+    c = xv.Context(0)
+    try:
+        results = xv.xv_encode_batch(c, jobs)
+        log = xv.xv_last_tune_log(c)
+        entries = [e for e in log.split(";") if e]
+        for ctu in (8, 16, 32):
+            assert sum(e.startswith(f"ctu{ctu} ") for e in entries) >= 4, log
+            nt, per = xv.xv_last_batch_config(c, ctu)
+            assert nt in (1, 128, 192, 256, 512)
+        assert any(e.startswith("frames ") for e in entries), log
+        assert xv.xv_last_batch_config(c, 64) == (0, 0)  # no CTU-64 work
+        for b, r, w in zip(bufs, results, wants):
+            assert_matches(b, r, w)
+        for code in (128 + 1024 * 1, 256 + 1024 * 2):
+            xv.xv_debug_force_block_size(c, code)
+            results = xv.xv_encode_batch(c, jobs)
+            for ctu in (8, 16, 32):
+                assert xv.xv_last_batch_config(c, ctu) == (code % 1024, code // 1024)
+            for b, r, w in zip(bufs, results, wants):
+                assert_matches(b, r, w)
+    finally:
+        c.close()
+
+
 def oracle_chain_with_lambda(planes, ctu, R, mask, qp, lmv):
     """The oracle's closed loop (C4) run frame by frame with a motion-cost
     lambda of the caller's choice: integer search and refinement with lmv,

@@ -14,7 +14,11 @@ computes, from the synthetic cube alone,
   - the quantised planes of frames sampled across the whole cube,
   - every output of the first frames of every encode (the causal prefix,
     quantised with the whole sub-cube's min/max);
-and the other frames are checked by properties that hold at any size: the
+and, deep in every chain (frames T/3, T/2 and T-1 of every encode), the
+oracle's motion search, refinement and transform chain run on the GPU's own
+reconstruction of the previous frame as the reference: every vector, cost,
+level, reconstruction, TU size and frame rate there must be the oracle's;
+the other frames are checked by properties that hold at any size: the
 decoder (bit-exact against the oracle in its own tests) reproduces every
 reconstruction and frame rate from the coded data, samples stay 10-bit,
 vectors stay within the search range (+-(4R + 3) quarter samples), frame 0
@@ -93,6 +97,27 @@ def check_properties(xv, ctx, cfg, b, r):
     assert torch.equal(dbits, b["bits"]) and tot == r["total_bits"]
 
 
+def check_deep_frames(cfg, b, frames):
+    """Frames t > 0 of one encode against the oracle run on that frame alone,
+    with the GPU's reconstruction of frame t - 1 as the reference (the closed
+    loop's input at t): vectors, costs, levels, reconstruction, TU sizes and
+    the frame's rate."""
+    lf8, lmv = oracle.lambdas(b["qp"])
+    G = b["planes"].shape[0]
+    for g in range(G):
+        for t in frames:  # only these frames leave the device
+            cur, ref = to_np(b["planes"][g, t]), to_np(b["recon"][g, t - 1])
+            mvi, _ = oracle.me_int(cur[0], ref[0], cfg.ctu, cfg.R, lmv)
+            wmv, wcost = oracle.me_qpel(cur[0], ref[0], cfg.ctu, lmv, mvi)
+            assert np.array_equal(to_np(b["mv"][g, t]), wmv), (g, t)
+            assert np.array_equal(to_np(b["cost"][g, t]).astype(np.uint32), wcost), (g, t)
+            w = oracle.tqr_frame(cur, ref, wmv, cfg.ctu, cfg.tu_mask, b["qp"])
+            assert np.array_equal(to_np(b["recon"][g, t]), w["recon"]), (g, t)
+            assert np.array_equal(to_np(b["levels"][g, t]), w["levels"]), (g, t)
+            assert np.array_equal(to_np(b["tu_log2"][g, t]), w["tu_log2"]), (g, t)
+            assert int(b["bits"][g, t]) == w["bits"], (g, t)
+
+
 @pytest.mark.parametrize("workload, prefix", [("dynamicearthnet", 2), ("era5", 3)])
 def test_full_size_sampled_frames_and_properties(xv, ctx, workload, prefix):
     cfg, lengths, cube, _, jobs, bufs = bench.workload_jobs(workload, device="cuda", qps=bench.default_qps(workload))
@@ -111,6 +136,7 @@ def test_full_size_sampled_frames_and_properties(xv, ctx, workload, prefix):
             assert np.array_equal(to_np(b["planes"].view(torch.int16)[:, ts]).view(np.uint16), want_planes)
             want = oracle.encode_cube(head, cfg.ctu, cfg.R, cfg.tu_mask, b["qp"], mm=mm)
             assert_matches(b, r, want, frames=prefix)
+            check_deep_frames(cfg, b, sorted({max(1, T // 3), max(1, T // 2), T - 1}))
             check_properties(xv, ctx, cfg, b, r)
     del jobs, bufs
     torch.cuda.empty_cache()

@@ -98,3 +98,43 @@ def test_pca_then_encode_decode_inverse(xv, ctx):
     xv.xv_pca_inverse(ctx, out, gm, gc, back)
     wb = oracle.pca_inverse(to_np(out), gm, gc)
     assert np.allclose(to_np(back), wb, rtol=0, atol=1e-5 * float(np.abs(wb).max()))
+
+
+def test_pca_all_bands_one_qp_per_group(xv, ctx):
+    """The paper's "PCA - all bands" test (Sec. 3, Tab. 5): all ten components
+    of a DeepExtremeCubes-shaped prefix, packed three to a group, every group
+    at its own QP (later components at lower quality) through
+    xv_split_groups + one xv_encode_batch.  Each group equals the oracle's
+    encode of its three components at that group's QP, and a group equals
+    the whole-cube encode's group at the same QP (the split changes nothing
+    but the QP)."""
+    from paper_2506_19656_gb300 import synth
+    cfg = synth.WORKLOADS["deepextremecubes"]
+    cube = synth.make_cube("deepextremecubes", T=4)
+    src = to_dev(cube)
+    mean, comps, _ = xv.xv_pca_fit(ctx, src)
+    z = torch.empty(cube.shape, dtype=torch.float32, device="cuda")
+    xv.xv_pca_project(ctx, src, mean, comps, cube.shape[0], z)
+    zh = to_np(z)
+    qps = [22, 27, 32, 37]
+    p = xv.xv_params_init(cfg.ctu, cfg.R, cfg.tu_mask, qps[0])
+    buf = xv.alloc_cube_buffers(cube.shape[0], 4, cfg.H, cfg.W, p)
+    whole = xv.make_job(z, p, buf["planes"], buf["recon"], minmax=buf["minmax"], mv=buf["mv"], cost=buf["cost"],
+                        levels=buf["levels"], tu_log2=buf["tu_log2"], bits=buf["bits"])
+    jobs = xv.xv_split_groups(whole, qps)
+    assert len(jobs) == 4 and [j.bands for j in jobs] == [3, 3, 3, 1] and [j.p.qp for j in jobs] == qps
+    res = xv.xv_encode_batch(ctx, jobs)
+    for g, (qp, r) in enumerate(zip(qps, res)):
+        b0, b1 = 3 * g, min(3 * g + 3, cube.shape[0])
+        want = oracle.encode_cube(np.ascontiguousarray(zh[b0:b1]), cfg.ctu, cfg.R, cfg.tu_mask, qp)
+        assert np.array_equal(to_np(buf["planes"][g]), want["planes"][0])
+        assert np.array_equal(to_np(buf["recon"][g]), want["recon"][0])
+        assert np.array_equal(to_np(buf["mv"][g]), want["mv"][0])
+        assert np.array_equal(to_np(buf["levels"][g]), want["levels"][0])
+        assert np.array_equal(to_np(buf["bits"][g]).astype(np.uint64), want["bits"][0])
+        assert r["total_bits"] == want["total_bits"]
+        for a, w in zip(r["psnr_band"], want["psnr_band"]):
+            assert (np.isinf(a) and np.isinf(w)) or abs(a - w) <= 1e-9 * abs(w)
+    recon_g0 = to_np(buf["recon"][0]).copy()
+    xv.xv_encode_batch(ctx, [whole])  # every group at qps[0]
+    assert np.array_equal(to_np(buf["recon"][0]), recon_g0)
