@@ -1146,6 +1146,40 @@ def kernels_alone(ctx, cfg, bufs, flush, stream, reps=3):
     return me_ms, tqr_ms, launches
 
 
+def tune_ctu(dev, candidates=(16, 32, 64), reps=3):
+    """The CTU size for a workload whose configuration leaves it open (the
+    ERA5-shaped sub-cubes): the T = 24 sub-cube encoded through
+    xv_encode_batch at each candidate size (each after its own autotuning
+    call), the fastest encode section (median of `reps`) wins.  The choice
+    changes the output (the CTU is part of the encode's definition), so the
+    encode is then run, and checked, at the chosen size."""
+    import torch
+    from paper_2506_19656_gb300 import synth, xv
+    global CTU
+    cfg = synth.WORKLOADS["era5"]
+    times = {}
+    saved = CTU
+    try:
+        for ctu in candidates:
+            CTU = ctu
+            c, lengths, _, _, jobs, bufs = workload_jobs("era5", frames=cfg.sub_T[0], device=dev)
+            ctx = xv.Context(dev.index or 0)
+            xv.xv_encode_batch(ctx, jobs)  # tunes this shape
+            ms = []
+            for _ in range(reps):
+                xv.xv_encode_batch(ctx, jobs)
+                ms.append(xv.xv_last_batch_kernel_ms(ctx))
+            times[ctu] = statistics.median(ms)
+            ctx.close()
+            del jobs, bufs
+            torch.cuda.empty_cache()
+    finally:
+        CTU = saved
+    best = min(times, key=times.get)
+    return best, {"encode_section_ms": {str(k): v for k, v in times.items()}, "chosen": best,
+                  "sample": f"the T = {cfg.sub_T[0]} sub-cube, median of {reps} batched encodes per CTU size"}
+
+
 def secondary_line(ctx, dev, flush, stream, steps=10):
     """The DeepExtremeCubes-shaped step (QP 22, 27 and 32 through
     xv_encode_batch) beside the headline: device time per step, value and the
@@ -1252,6 +1286,11 @@ def main():
     from paper_2506_19656_gb300 import build, xv
     build.build()
     dev = torch.device("cuda", local)
+    ctu_tuning = None
+    if args.workload == "era5" and not args.ctu and not args.frames:
+        # the configuration leaves the ERA5-shaped batch's CTU open: tune it
+        chosen, ctu_tuning = tune_ctu(dev)
+        globals()["CTU"] = chosen
     ctx = xv.Context(local)
     if args.block_size:
         xv.xv_debug_force_block_size(ctx, args.block_size)
@@ -1361,6 +1400,25 @@ def main():
     peak_ad = peaks["absdiff_best"]
     peak_mac = peaks["imad"]["per_s"]
     me_ms, tqr_ms, alone_launches = kernels_alone(ctx, cfg, bufs, flush, stream) if not args.no_alone else (None,) * 3
+    window_tma = None
+    if frames_mode and not args.no_alone:
+        # the per-frame mode's search windows by TMA (the default) against the
+        # threads' own 16-byte loads: the encode section both ways
+        def section_ms(k=3):
+            out = []
+            for _ in range(k):
+                flush.zero_()
+                xv.xv_encode_batch(ctx, jobs)
+                out.append(xv.xv_last_batch_kernel_ms(ctx))
+            return statistics.median(out)
+        xv.xv_debug_set_window_wait(ctx, -1)
+        xv.xv_encode_batch(ctx, jobs)  # captures the variant's graphs
+        off_ms = section_ms()
+        xv.xv_debug_set_window_wait(ctx, 0)
+        xv.xv_encode_batch(ctx, jobs)
+        on_ms = section_ms()
+        window_tma = {"tma_ms": on_ms, "loads_ms": off_ms,
+                      "what": "encode section (median of 3) with the search windows by TMA vs by 16-byte loads"}
     alone = None
     if me_ms:
         alone = {
@@ -1393,6 +1451,7 @@ def main():
                               "note": "forward + inverse of every allowed TU size over every sample (the RD "
                                       "choice); the rate divides by the whole encode section, search included"},
                 "alone": alone,
+                "window_tma": window_tma,
                 "peak_basis": "measured now on this device (xv_measure_peak): the fastest abs-diff-accumulate "
                               "sequence of sad / FP32 / their mix; MEASURED_PEAKS.json holds no integer-pipe peak",
                 "peaks_measured": peaks}
@@ -1408,6 +1467,7 @@ def main():
                                                   if frames_mode else "persistent kernel") + ")",
                    "block_size": block_size, "blocks_per_sm": blocks_per_sm or "as many as fit",
                    "autotune_ms": parse_tune_log(tune_log) if tune_log else "forced (--block-size)",
+                   "ctu_autotune": ctu_tuning,
                    "l2": "flushed before every step (256 MB write); "
                    f"the float32 input ({sum(t.numel() * 4 for t in srcs) / 1e9:.2f} GB) is also larger than L2",
                    "parallelism": f"replicas{ws}"},

@@ -565,6 +565,14 @@ xv_status xv_debug_set_wait_budget(xv_ctx* ctx, long long cycles);
  * as CUDA graphs exactly as a tuned choice is; 0 restores the autotuner.
  * Host only. */
 xv_status xv_debug_force_block_size(xv_ctx* ctx, int block_size);
+/* Bound (mbarrier polls, default 2^24; 0 restores it) of the per-frame
+ * search's wait for its window copy (the window comes by TMA where it lies
+ * inside the plane); a negative value turns the TMA copies off (every window
+ * by the threads' own 16-byte loads, for comparison).  A copy that does not
+ * complete within the bound makes xv_encode_cube / xv_encode_batch
+ * (per-frame mode) return XV_ETIMEOUT without any fault; the context stays
+ * usable.  Host only. */
+xv_status xv_debug_set_window_wait(xv_ctx* ctx, long long polls);
 /* Make one dependency counter of xv_encode_batch impossible to complete: the
  * CTU row `row` of the first job, indexed over its [G][T][rows] counters, is
  * then never queued, a block waiting for it runs out of its budget, and the

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libxv.so")
-SOURCES = ["xv_api.cu", "xv_serve.cu", "k_quant.cu", "k_psnr.cu", "k_psnr_static.cu", "k_peak.cu", "k_frame.cu", "k_dec.cu", "k_metrics.cu", "k_pca.cu", "k_intra.cu", "k_deblock.cu", "k_batch.cu",
+SOURCES = ["xv_api.cu", "xv_serve.cu", "k_quant.cu", "k_psnr.cu", "k_psnr_static.cu", "k_peak.cu", "tma.cu", "k_frame.cu", "k_dec.cu", "k_metrics.cu", "k_pca.cu", "k_intra.cu", "k_deblock.cu", "k_batch.cu",
            "k_batch_ctu8.cu", "k_batch_ctu16.cu", "k_batch_ctu32.cu", "k_batch_ctu64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

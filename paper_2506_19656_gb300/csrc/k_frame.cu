@@ -13,17 +13,20 @@ namespace xvh {
 namespace {
 
 constexpr int kNT = 256;
-template <int N> constexpr int kMinBlocks = N == 64 ? 1 : (N == 32 ? 2 : 4);
+// resident blocks per SM the register allocation aims for
+template <int N> constexpr int kMinBlocksMe = N == 64 ? 1 : (N == 32 ? 3 : 4);
+template <int N> constexpr int kMinBlocksTqr = N == 64 ? 1 : (N == 32 ? 3 : 4);
 
 template <int N>
-__global__ void __launch_bounds__(kNT, kMinBlocks<N>)
+__global__ void __launch_bounds__(kNT, kMinBlocksMe<N>)
 k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t gstride, int Hp, int Wp,
            int R, int64_t lmv, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
-           int64_t pu_gstride, unsigned long long* exact) {
-    extern __shared__ __align__(16) unsigned char smem[];
+           int64_t pu_gstride, unsigned long long* exact, const __grid_constant__ WindowMap wmap, int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
     const int pu = blockIdx.x, g = blockIdx.y, nx = Wp / N;
     xvd::MeResult r = xvd::me_pu<N, kNT>(cur + g * gstride, ref + g * gstride, Hp, Wp, (pu % nx) * N,
-                                         (pu / nx) * N, R, lmv, smem);
+                                         (pu / nx) * N, R, lmv, smem, wmap.valid ? wmap.bytes : nullptr, g, err,
+                                         wmap.polls);
     if (threadIdx.x == 0) {
         const int64_t o = g * pu_gstride + pu;
         mv[2 * o] = (int16_t)r.mvx;
@@ -36,11 +39,11 @@ k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, i
 }
 
 template <int N>
-__global__ void __launch_bounds__(kNT, kMinBlocks<N>)
+__global__ void __launch_bounds__(kNT, kMinBlocksTqr<N>)
 k_tqr_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, const int16_t* __restrict__ mv,
             int64_t gstride, int Hp, int Wp, int qp, unsigned tu_mask, int64_t lf8, int64_t pu_gstride,
             uint16_t* recon, int16_t* levels, uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int cu = blockIdx.x, g = blockIdx.y, nx = Wp / N;
     const int64_t o = g * pu_gstride + cu;
     int mvx = 0, mvy = 0;
@@ -56,13 +59,15 @@ k_tqr_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, 
 template <int N>
 cudaError_t me_n(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                  const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
-                 int64_t pu_gstride, cudaStream_t st, unsigned long long* exact) {
+                 int64_t pu_gstride, cudaStream_t st, unsigned long long* exact, const WindowMap* wmap, int* err) {
+    WindowMap m{};
+    if (wmap && wmap->valid && err) m = *wmap;
     size_t smem = xvd::me_smem_bytes(N, p->search_range);
     cudaError_t e = cudaFuncSetAttribute(k_me_frame<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Hp / N) * (Wp / N), G);
     k_me_frame<N><<<grid, kNT, smem, st>>>(cur, ref, gstride, Hp, Wp, p->search_range, p->lambda_mv_fp16, mv,
-                                           cost, mv_int, cost_int, pu_gstride, exact);
+                                           cost, mv_int, cost_int, pu_gstride, exact, m, err);
     return cudaGetLastError();
 }
 
@@ -83,12 +88,13 @@ cudaError_t tqr_n(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, i
 
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
-                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st, unsigned long long* exact) {
+                            uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st, unsigned long long* exact,
+                            const WindowMap* wmap, int* err) {
     switch (p->ctu) {
-        case 8: return me_n<8>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
-        case 16: return me_n<16>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
-        case 32: return me_n<32>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
-        case 64: return me_n<64>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact);
+        case 8: return me_n<8>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact, wmap, err);
+        case 16: return me_n<16>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact, wmap, err);
+        case 32: return me_n<32>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact, wmap, err);
+        case 64: return me_n<64>(cur, ref, G, gstride, Hp, Wp, p, mv, cost, mv_int, cost_int, pu_gstride, st, exact, wmap, err);
     }
     return cudaErrorInvalidValue;
 }

@@ -29,6 +29,7 @@
 // tie-break of the definition.
 #pragma once
 #include <cstdint>
+#include "../../include/xv.h"
 #include "xv_dev.cuh"
 
 namespace xvd {
@@ -388,11 +389,52 @@ __device__ __forceinline__ uint32_t satd_part(const int16_t* __restrict__ P, con
 template <int N>
 __host__ __device__ constexpr int me_lpb() { return N >= 32 ? 2 : 8; }
 
+// The search window by one tiled bulk copy (TMA): thread 0 initialises the
+// item's mbarrier, announces the copy's bytes and issues it; the copy lands
+// while the block loads the PU's samples and the cost tables.  `tmap` is a
+// 3-D tensor map (x, y, group) over the reference frame's channel-0 planes
+// (a kernel parameter), box (S, WW, 1), read from chunk column xa and row
+// wy0 of group tz.
+__device__ __forceinline__ void window_tma_issue(uint16_t* win, const void* tmap, int xa, int wy0, int tz,
+                                                 uint32_t mbar, uint32_t bytes) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(win);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // earlier reads of the window (the previous item) before the copy engine's writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(tmap), "r"(xa), "r"(wy0), "r"(tz), "r"(mbar)
+        : "memory");
+}
+
+// Waits (bounded) for the mbarrier's phase `parity` to complete; false when
+// the bound ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long polls) {
+    for (long long i = 0; i < polls; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Motion estimation of the PU at (x0, y0).  cur0/ref0: channel-0 planes.
 // Must be called by all NT threads of the block; smem holds me_smem_bytes.
+// With `tmap` (a tensor map over the reference planes, see window_tma_issue;
+// tz = the group's coordinate in it) the window comes by TMA where it lies
+// inside the plane; a copy that does not complete within the wait bound sets
+// *err to XV_ETIMEOUT (the result is then not valid).
 template <int N, int NT, bool kCoherent = false>
 __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __restrict__ ref0,
-                          int Hp, int Wp, int x0, int y0, int R, int64_t lmv, unsigned char* smem) {
+                          int Hp, int Wp, int x0, int y0, int R, int64_t lmv, unsigned char* smem,
+                          const void* tmap = nullptr, int tz = 0, int* err = nullptr,
+                          long long tma_polls = 1ll << 24) {
     static_assert(N % 8 == 0, "PU size must be a multiple of 8");
     const int tid = threadIdx.x;
     const int WW = me_win(N, R), S = me_stride(N, R);
@@ -410,7 +452,12 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     const int wx0 = x0 - R - 4, wy0 = y0 - R - 4;
     const int xa = wx0 - (((wx0 % 8) + 8) % 8);  // 8-aligned start at or left of wx0
     const int nch = (wx0 + WW - xa + 7) / 8;
-    const int nwin = WW * nch;
+    // the TMA path: the window (from chunk column xa, S columns) inside the
+    // plane, starting 4 samples into its chunk as the layout wants
+    const bool tma = tmap != nullptr && wx0 - xa == 4 && xa >= 0 && xa + S <= Wp && wy0 >= 0 && wy0 + WW <= Hp;
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(red + 16);
+    if (tma && tid == 0) window_tma_issue(win, tmap, xa, wy0, tz, mbar, (uint32_t)(S * WW * 2));
+    const int nwin = tma ? 0 : WW * nch;
     constexpr int BCH = N / 8;                 // 16-byte chunks per block row
     const int ntask = nwin + N * BCH;          // window chunks, then the PU's
     constexpr int kILP = 5;  // loads in flight per thread before the first store
@@ -483,6 +530,10 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         }
     }
     __syncthreads();
+    if (tma && !mbar_wait_bounded(mbar, 0, tma_polls)) {
+        if (err) atomicExch(err, (int)XV_ETIMEOUT);
+        mbar_wait_bounded(mbar, 0, 1ll << 24);  // give the copy in flight a second bound before the smem is reused
+    }
 
     // ---- integer search, exact pruning (see me_sb above)
     // Units: (dy, 8 consecutive dx) for the first 8m columns of candidates;
@@ -774,7 +825,11 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
         constexpr int LPB = me_lpb<N>();
         for (int task = tid; task < LPB * ncand * NB; task += NT) {
             const int kb = task / LPB;
-            const int k = kb / NB, b = kb - k * NB;
+            // stage 1 takes the centre last: without a vertical filter it is
+            // the cheapest candidate, so the tasks past the first round are
+            // short ones
+            const int kk = kb / NB, b = kb - kk * NB;
+            const int k = stage == 0 ? (kk + 1) % 9 : kk;
             int mvx, mvy;
             stage_cand(k, cx, cy, s, stage == 0, mvx, mvy);
             const int16_t* P = pm0 == mvx ? pl0 : (pm1 == mvx ? pl1 : pl2);

@@ -53,6 +53,9 @@ struct xv_ctx {
     cudaEvent_t fork_ev = nullptr;
     DevBuf b_mv, b_exact;
     DevBuf peak_buf;                         // xv_measure_peak's input and sink
+    DevBuf dev_err;                          // status word the per-frame search sets on a copy timeout
+    long long tma_polls = 1ll << 24;         // bound of the search window copy's wait (test hook)
+    bool tma_off = false;                    // the search loads every window itself (test hook)
     int batch_cfg[4] = {0, 0, 0, 0};         // configuration code of each CTU class in the last batch
     int class_tuned[4] = {0, 0, 0, 0};       // the autotuner's latest persistent choice per CTU class
     std::string tune_log;                    // the autotuner's last timings
@@ -206,6 +209,37 @@ bool valid_cube(const void* src, xv_dtype dt, int bands, int T, int H, int W) {
 
 int plane_dim(int n, int ctu) { return (n + ctu - 1) / ctu * ctu; }
 
+// The device status word of the per-frame search (zeroed when created).
+xv_status ensure_err_word(xv_ctx* c) {
+    if (c->dev_err.ptr) return XV_OK;
+    xv_status s = ensure(c, c->dev_err, sizeof(int));
+    if (s) return s;
+    cudaError_t e = cudaMemset(c->dev_err.ptr, 0, sizeof(int));
+    return e == cudaSuccess ? XV_OK : cuda_fail(e, "status word");
+}
+
+// The window map of frame t's reference (channel 0 of reconstruction t - 1 of
+// every group); invalid (the search loads the window itself) when not usable.
+xvh::WindowMap window_map(const xv_ctx* c, const uint16_t* ref_frame, int Wp, int Hp, int64_t gstride, int G,
+                          const xv_params& p) {
+    xvh::WindowMap m{};
+    if (!c->tma_off && xvh::encode_window_map(&m, ref_frame, Wp, Hp, gstride, G, p.ctu, p.search_range))
+        m.polls = c->tma_polls;
+    return m;
+}
+
+// Reads and clears the per-frame search's status word (synchronous).
+xv_status take_err_word(xv_ctx* c) {
+    if (!c->dev_err.ptr) return XV_OK;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, c->dev_err.ptr, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status word");
+    if (v == 0) return XV_OK;
+    cudaMemset(c->dev_err.ptr, 0, sizeof(int));
+    set_error("a search window copy did not complete within its wait bound");
+    return (xv_status)v;
+}
+
 xv_status check_launch(cudaError_t e, const char* what) {
     if (e != cudaSuccess) return cuda_fail(e, what);
     return XV_OK;
@@ -332,7 +366,7 @@ void xv_destroy(xv_ctx* c) {
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax, &c->tmp_cbf,
                       &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
                       &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals, &c->b_mv, &c->b_exact,
-                      &c->met_part, &c->met_out, &c->pca_part, &c->peak_buf};
+                      &c->met_part, &c->met_out, &c->pca_part, &c->peak_buf, &c->dev_err};
     for (DevBuf* b : bufs) release(c, *b);
     for (cudaGraphExec_t& gx : c->graph)
         if (gx) cudaGraphExecDestroy(gx);
@@ -723,6 +757,7 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
         if ((s = ensure(c, c->tmp_bits, sizeof(uint64_t) * G * T))) return s;
         bits = (uint64_t*)c->tmp_bits.ptr;
     }
+    if ((s = ensure_err_word(c))) return s;
     cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(uint64_t) * G * T, st);
     for (int gi = 0; gi < G && e == cudaSuccess; ++gi) {  // frame 0 has no motion
         e = cudaMemsetAsync(mv + (int64_t)gi * T * npu * 2, 0, sizeof(int16_t) * 2 * npu, st);
@@ -743,8 +778,10 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
         }
         if (!intra) c->launches += kLaunchTqr + (ref ? kLaunchMe : 0);
         if (ref) {
+            const xvh::WindowMap wm = window_map(c, ref, Wp, Hp, T * fsz, G, p);
             if ((s = check_launch(xvh::launch_me_frame(cur, ref, G, T * fsz, Hp, Wp, &p, mv + t * npu * 2,
-                                                       j->cost ? j->cost + t * npu : nullptr, nullptr, nullptr, T * npu, st),
+                                                       j->cost ? j->cost + t * npu : nullptr, nullptr, nullptr, T * npu, st,
+                                                       nullptr, &wm, (int*)c->dev_err.ptr),
                                   "motion_search")))
                 return s;
         }
@@ -763,7 +800,9 @@ xv_status xv_encode_cube(xv_ctx* c, const xv_job* j, xv_result* r, void* stream)
     if ((s = psnr_into(c, j->src, j->dtype, j->bands, T, j->H, j->W, j->planes, j->recon, Hp, Wp, bq, r->psnr_band,
                        r->mse_band, r->sse10_band, &r->psnr_mean, st)))
         return s;
-    return fill_result(j, bits, G, r, st);
+    if ((s = fill_result(j, bits, G, r, st))) return s;
+    if ((s = take_err_word(c))) r->status = s;
+    return s;
 }
 
 }  // extern "C"
@@ -882,6 +921,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if ((s = ensure(c, c->b_mv, sizeof(int16_t) * (nmv > 0 ? nmv : 1)))) return s;
     if ((s = ensure(c, c->b_exact, sizeof(unsigned long long)))) return s;
     if ((s = ensure_side_streams(c))) return s;
+    if ((s = ensure_err_word(c))) return s;
     const size_t stage_bytes = sizeof(xvh::BatchCtl) * 4 + sizeof(unsigned long long) * njobs +
                                (sizeof(xvh::PsnrPart) + sizeof(BandQ)) * XV_MAX_BANDS * njobs + sizeof(unsigned long long);
     if (c->h_stage_bytes < stage_bytes) {
@@ -984,9 +1024,10 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                 xv_status r;
                 if (ref) {
                     c->launches += kLaunchMe;
+                    const xvh::WindowMap wm = window_map(c, ref, Wp, Hp, T * fsz, G, j.p);
                     if ((r = check_launch(xvh::launch_me_frame(cur, ref, G, T * fsz, Hp, Wp, &j.p, mv + t * npu * 2,
                                                                j.cost ? j.cost + t * npu : nullptr, nullptr, nullptr,
-                                                               T * npu, ss, exact),
+                                                               T * npu, ss, exact, &wm, (int*)c->dev_err.ptr),
                                           "motion_search")))
                         return r;
                 }
@@ -1212,6 +1253,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                  nt[3], c->b_jobs.ptr, c->b_bits.ptr, c->b_rowdone.ptr, c->b_depcnt.ptr, c->b_bandq.ptr, c->b_minmax.ptr,
                  c->b_ctl.ptr, c->b_cls.ptr, c->b_items.ptr, c->b_part.ptr, c->b_out.ptr, c->b_totals.ptr,
                  c->h_stage, c->b_mv.ptr, c->b_exact.ptr, c->wait_budget);
+        key += "|" + std::to_string(c->tma_polls) + (c->tma_off ? "n" : "t");
         key += buf;
         if (!c->graph[0] || key != c->graph_key) {
             for (cudaGraphExec_t& gx : c->graph)
@@ -1274,6 +1316,10 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     for (int i = 0; i < njobs; ++i) {
         const uint64_t side = 2 * (uint64_t)jobs[i].p.search_range + 1;
         c->batch_full += (uint64_t)jd[i].G * (uint64_t)(jobs[i].T - 1) * jd[i].nx * jd[i].ny * side * side;
+    }
+    if (frames_mode(nt) && (s = take_err_word(c))) {
+        for (int i = 0; i < njobs; ++i) results[i].status = s;
+        return s;
     }
     for (int k = 0; k < 4; ++k)
         if (!frames_mode(nt) && total[k] && h_ctl[k].err) {
@@ -1675,6 +1721,13 @@ xv_status xv_debug_force_block_size(xv_ctx* c, int nt) {
         return XV_EINVAL;
     }
     c->force_nt = nt;
+    return XV_OK;
+}
+
+xv_status xv_debug_set_window_wait(xv_ctx* c, long long polls) {
+    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
+    c->tma_polls = polls > 0 ? polls : (1ll << 24);
+    c->tma_off = polls < 0;
     return XV_OK;
 }
 

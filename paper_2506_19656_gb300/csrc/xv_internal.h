@@ -35,11 +35,24 @@ cudaError_t launch_bandq(const double* minmax, int bands, BandQ* bq, cudaStream_
 cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T, int H, int W, int Hp, int Wp,
                                  const BandQ* bq, uint16_t* planes, cudaStream_t st);
 
+// A tensor map (CUtensorMap, 128 bytes) for the TMA loads of the search
+// window over the G groups' channel-0 planes of one frame (tma.cu);
+// valid = 0: not usable here (the search loads the window itself).
+struct alignas(64) WindowMap {
+    unsigned char bytes[128];
+    int valid;
+    long long polls;  // the bound of the wait for the copy (mbarrier polls)
+};
+bool window_map_usable(int ctu, int R);
+bool encode_window_map(WindowMap* m, const uint16_t* plane0, int Wp, int Hp, int64_t gstride, int G, int ctu, int R);
+
 // exact: when not null, the integer-search candidates evaluated exactly are added to *exact.
+// wmap (valid) and err: the window by TMA, a copy that does not complete
+// within the wait bound setting *err to XV_ETIMEOUT.
 cudaError_t launch_me_frame(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstride, int Hp, int Wp,
                             const xv_params* p, int16_t* mv, uint32_t* cost, int16_t* mv_int,
                             uint32_t* cost_int, int64_t pu_gstride, cudaStream_t st,
-                            unsigned long long* exact = nullptr);
+                            unsigned long long* exact = nullptr, const WindowMap* wmap = nullptr, int* err = nullptr);
 // Microbenchmarks of the roofline's instruction sequences (k_peak.cu): kind
 // 0..3 (see the file); sink receives at most one word per block.
 int peak_chains();

@@ -117,6 +117,7 @@ _SIGS = {
     "xv_debug_set_wait_budget": [_vp, ctypes.c_longlong],
     "xv_debug_force_block_size": [_vp, _i],
     "xv_debug_stall_row": [_vp, ctypes.c_longlong],
+    "xv_debug_set_window_wait": [_vp, ctypes.c_longlong],
 }
 
 
@@ -515,6 +516,10 @@ def xv_debug_set_wait_budget(ctx: Context, cycles: int):
 
 def xv_debug_force_block_size(ctx: Context, block_size: int):
     check(lib().xv_debug_force_block_size(ctx.handle, block_size), "xv_debug_force_block_size")
+
+
+def xv_debug_set_window_wait(ctx: Context, polls: int):
+    check(lib().xv_debug_set_window_wait(ctx.handle, polls), "xv_debug_set_window_wait")
 
 
 def xv_debug_stall_row(ctx: Context, row: int):

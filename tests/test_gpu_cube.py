@@ -273,3 +273,26 @@ def test_full_resolution_dynamicearthnet_and_era5_prefixes(xv, ctx):
     r2, r3 = xv.xv_encode_batch(ctx, [j2, j3])
     assert_matches(b2, r2, w2)
     assert_matches(b3, r3, w3)
+
+
+def test_window_copy_wait_bound_reports_and_context_survives(xv):
+    """The per-frame search's wait for its TMA window copy is bounded: with a
+    bound of one poll the encode either completes (the copy was already in)
+    or returns XV_ETIMEOUT without any fault; with the default bound the same
+    context then encodes the oracle's bytes."""
+    c = synth.WORKLOADS["tiny"]
+    cube = synth.make_cube("tiny", T=3)
+    want = oracle.encode_cube(cube, c.ctu, c.R, c.tu_mask, 27)
+    ctx = xv.Context(0)
+    try:
+        xv.xv_debug_set_window_wait(ctx, 1)
+        job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
+        try:
+            assert_matches(buf, xv.xv_encode_cube(ctx, job), want)
+        except xv.XvError as e:
+            assert e.status == xv.XV_ETIMEOUT
+        xv.xv_debug_set_window_wait(ctx, 0)
+        job, buf = gpu_job(xv, cube, c.ctu, c.R, c.tu_mask, 27)
+        assert_matches(buf, xv.xv_encode_cube(ctx, job), want)
+    finally:
+        ctx.close()
