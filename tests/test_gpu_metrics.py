@@ -110,3 +110,46 @@ def test_metrics_on_an_encoded_cube(xv, ctx):
         assert math.isclose(ga, wa, rel_tol=SA_RTOL)
         res.append((got["ssim_mean"], ga))
     assert res[0][0] > res[1][0] and res[0][1] < res[1][1]
+
+
+SSIM_WINDOW_TOL = 5e-5  # one window's index: a few 1e-5 (see the module docstring)
+
+
+def test_ssim_per_window(xv, ctx):
+    """One 11 x 11 window per band (T = 1, H = W = 11): the band value is that
+    single window's SSIM, so errors cannot average out across windows.  40
+    windows over random cubes of several amplitudes, offsets and ranges."""
+    rng = np.random.default_rng(77)
+    n = 0
+    for trial in range(10):
+        bands = int(rng.integers(1, 6))
+        lo = rng.uniform(-50, 50, (bands, 1, 1, 1))
+        scale = rng.uniform(0.01, 100, (bands, 1, 1, 1))
+        cube = (lo + scale * rng.uniform(0, 1, (bands, 1, 11, 11))).astype(np.float32)
+        mm, _ = oracle.minmax(cube)
+        planes = oracle.quantize_pack(cube, 8, mm)
+        recon = noisy_recon(rng, planes, int(rng.integers(1, 60)))
+        want = oracle.ssim(cube, recon, mm)
+        got = xv.xv_ssim(ctx, to_dev(cube), to_dev(recon), to_dev(mm))
+        for b in range(bands):
+            assert abs(got["ssim_band"][b] - want[b]) <= SSIM_WINDOW_TOL, (trial, b, got["ssim_band"][b], want[b])
+            n += 1
+    assert n >= 20
+
+
+def test_spectral_angle_per_pixel(xv, ctx):
+    """One pixel per call (T = H = W = 1): the mean angle is that pixel's angle,
+    checked at the per-pixel relative error of a few 1e-6 (1e-5 here), for
+    spectra of 2 to 16 bands and angles from small to large."""
+    rng = np.random.default_rng(78)
+    for trial in range(24):
+        bands = int(rng.integers(2, 17))
+        cube = rng.uniform(0.1, 1, (bands, 1, 1, 1)).astype(np.float32)
+        mm = np.stack([cube.reshape(bands) - rng.uniform(0.05, 0.5, bands),
+                       cube.reshape(bands) + rng.uniform(0.05, 0.5, bands)], axis=1)
+        planes = oracle.quantize_pack(cube, 8, mm)
+        recon = noisy_recon(rng, planes, int(rng.integers(1, 200)))
+        wa, wn = oracle.sa(cube, recon, mm)
+        ga, gn = xv.xv_sa(ctx, to_dev(cube), to_dev(recon), to_dev(mm))
+        assert gn == wn == 1
+        assert math.isclose(ga, wa, rel_tol=SA_RTOL, abs_tol=1e-9), (trial, ga, wa)

@@ -23,7 +23,8 @@ def _case(seed, bands, T, H, W, ctu, dtype):
     mm, _ = oracle.minmax(cube)
     planes = oracle.quantize_pack(cube, ctu, mm)
     recon = np.clip(planes.astype(int) + rng.integers(-4, 5, planes.shape), 0, 1023).astype(np.uint16)
-    return to_dev(cube), to_dev(planes), to_dev(recon), to_dev(mm)
+    want = oracle.psnr(cube, planes, recon, mm)
+    return (to_dev(cube), to_dev(planes), to_dev(recon), to_dev(mm)), want
 
 
 def _same(a, b):
@@ -43,11 +44,18 @@ def test_noalloc_psnr_matches_xv_psnr_twice():
     try:
         first = _case(1, 10, 4, 70, 90, 16, "f32")    # 10 bands
         second = _case(2, 4, 3, 33, 41, 8, "u16")     # fewer bands, other sizes
-        for args in (first, second):
+        # 786,432 samples per band: the partial sums per band reach their
+        # maximum of 256 blocks (each block then takes more samples)
+        third = _case(3, 6, 3, 512, 512, 32, "f32")
+        for args, oracle_want in (first, second, third):
             want = xv.xv_psnr(ctx, *args)
             got = xv.xv_psnr_noalloc(*args)
             torch.cuda.synchronize()
             _same(got, want)
+            # and against the oracle's definition itself
+            for x, y in zip(got["psnr_band"], oracle_want["psnr_band"]):
+                assert (np.isinf(x) and np.isinf(y)) or abs(x - y) <= 1e-9 * abs(y)
+            assert got["sse10_band"] == [int(v) for v in oracle_want["sse10_band"]]
     finally:
         ctx.close()
 
