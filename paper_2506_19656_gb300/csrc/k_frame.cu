@@ -12,19 +12,26 @@
 namespace xvh {
 namespace {
 
-constexpr int kNT = 256;
-// resident blocks per SM the register allocation aims for
-template <int N> constexpr int kMinBlocksMe = N == 64 ? 1 : (N == 32 ? 3 : 4);
-template <int N> constexpr int kMinBlocksTqr = N == 64 ? 1 : (N == 32 ? 3 : 4);
+// Threads per block and the resident blocks per SM the register allocation
+// aims for.  CTU 32: the search at 128 threads x 6 blocks (six 34 KB
+// windows fit the SM's shared memory) and the transform at 192 threads x 4
+// blocks, whose row and column passes then have exactly one task per thread
+// for the 16- and 32-point sizes (3 channels x 32 rows, halved rows for the
+// 32-point transform) and whole rounds for the 4- and 8-point ones; both
+// measured faster than 256 threads x 3 blocks, results unchanged.
+template <int N> constexpr int kNTMe = N == 32 ? 128 : 256;
+template <int N> constexpr int kNTTqr = N == 32 ? 192 : 256;
+template <int N> constexpr int kMinBlocksMe = N == 64 ? 1 : (N == 32 ? 6 : 4);
+template <int N> constexpr int kMinBlocksTqr = N == 64 ? 1 : 4;
 
 template <int N>
-__global__ void __launch_bounds__(kNT, kMinBlocksMe<N>)
+__global__ void __launch_bounds__(kNTMe<N>, kMinBlocksMe<N>)
 k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t gstride, int Hp, int Wp,
            int R, int64_t lmv, int16_t* mv, uint32_t* cost, int16_t* mv_int, uint32_t* cost_int,
            int64_t pu_gstride, unsigned long long* exact, const __grid_constant__ WindowMap wmap, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int pu = blockIdx.x, g = blockIdx.y, nx = Wp / N;
-    xvd::MeResult r = xvd::me_pu<N, kNT>(cur + g * gstride, ref + g * gstride, Hp, Wp, (pu % nx) * N,
+    xvd::MeResult r = xvd::me_pu<N, kNTMe<N>>(cur + g * gstride, ref + g * gstride, Hp, Wp, (pu % nx) * N,
                                          (pu / nx) * N, R, lmv, smem, wmap.valid ? wmap.bytes : nullptr, g, err,
                                          wmap.polls);
     if (threadIdx.x == 0) {
@@ -39,7 +46,7 @@ k_me_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, i
 }
 
 template <int N>
-__global__ void __launch_bounds__(kNT, kMinBlocksTqr<N>)
+__global__ void __launch_bounds__(kNTTqr<N>, kMinBlocksTqr<N>)
 k_tqr_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, const int16_t* __restrict__ mv,
             int64_t gstride, int Hp, int Wp, int qp, unsigned tu_mask, int64_t lf8, int64_t pu_gstride,
             uint16_t* recon, int16_t* levels, uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride) {
@@ -48,7 +55,7 @@ k_tqr_frame(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, 
     const int64_t o = g * pu_gstride + cu;
     int mvx = 0, mvy = 0;
     if (ref) { mvx = mv[2 * o]; mvy = mv[2 * o + 1]; }
-    uint32_t b = xvd::tqr_cu<N, kNT>(cur + g * gstride, ref ? ref + g * gstride : nullptr, (int64_t)Hp * Wp, Hp,
+    uint32_t b = xvd::tqr_cu<N, kNTTqr<N>>(cur + g * gstride, ref ? ref + g * gstride : nullptr, (int64_t)Hp * Wp, Hp,
                                      Wp, (cu % nx) * N, (cu / nx) * N, mvx, mvy, qp, tu_mask, lf8,
                                      recon + g * gstride, levels ? levels + g * gstride : nullptr,
                                      tu_log2 ? tu_log2 + o : nullptr, smem);
@@ -66,7 +73,7 @@ cudaError_t me_n(const uint16_t* cur, const uint16_t* ref, int G, int64_t gstrid
     cudaError_t e = cudaFuncSetAttribute(k_me_frame<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Hp / N) * (Wp / N), G);
-    k_me_frame<N><<<grid, kNT, smem, st>>>(cur, ref, gstride, Hp, Wp, p->search_range, p->lambda_mv_fp16, mv,
+    k_me_frame<N><<<grid, kNTMe<N>, smem, st>>>(cur, ref, gstride, Hp, Wp, p->search_range, p->lambda_mv_fp16, mv,
                                            cost, mv_int, cost_int, pu_gstride, exact, m, err);
     return cudaGetLastError();
 }
@@ -79,7 +86,7 @@ cudaError_t tqr_n(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, i
     cudaError_t e = cudaFuncSetAttribute(k_tqr_frame<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Hp / N) * (Wp / N), G);
-    k_tqr_frame<N><<<grid, kNT, smem, st>>>(cur, ref, mv, gstride, Hp, Wp, p->qp, p->tu_mask, p->lambda_fp8,
+    k_tqr_frame<N><<<grid, kNTTqr<N>, smem, st>>>(cur, ref, mv, gstride, Hp, Wp, p->qp, p->tu_mask, p->lambda_fp8,
                                             pu_gstride, recon, levels, tu_log2, bits, bits_gstride);
     return cudaGetLastError();
 }

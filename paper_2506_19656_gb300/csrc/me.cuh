@@ -818,7 +818,10 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
                 refine_planes<N, NT>(wb, S, R, my, 2, pm0, pm1, 0, pl0, pl1, nullptr);
             }
         }
-        for (int k = tid; k < ncand; k += NT) satd[k] = 0;
+        // stage 2 sums into its own array, so that stage 1's selection
+        // needs no barrier before stage 2 starts
+        uint32_t* acc = stage == 0 ? satd : reinterpret_cast<uint32_t*>(red + 4);
+        for (int k = tid; k < ncand; k += NT) acc[k] = 0;
         __syncthreads();
         // LPB adjacent lanes per (candidate, 8x8 block); NT is a multiple of
         // 32, so all lanes of a block are taken in the same round
@@ -835,19 +838,19 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
             const int16_t* P = pm0 == mvx ? pl0 : (pm1 == mvx ? pl1 : pl2);
             const uint32_t v = satd_part<N, LPB>(P, blk, (b % (N / 8)) * 8, (b / (N / 8)) * 8, task & (LPB - 1),
                                                  (mvy >> 2) - my, mvy & 3, (mvx & 3) == 0);
-            if ((task & (LPB - 1)) == 0) atomicAdd(&satd[k], v);
+            if ((task & (LPB - 1)) == 0) atomicAdd(&acc[k], v);
         }
         __syncthreads();
         int k0 = 0;
-        if (stage == 0) { bJ = satd[0] + mv_cost(cx, cy, lmv); k0 = 1; }
+        if (stage == 0) { bJ = acc[0] + mv_cost(cx, cy, lmv); k0 = 1; }
 #pragma unroll 1
         for (int k = k0; k < ncand; ++k) {
             int mx, my2;
             stage_cand(k, cx, cy, s, stage == 0, mx, my2);
-            const uint32_t J = satd[k] + mv_cost(mx, my2, lmv);
+            const uint32_t J = acc[k] + mv_cost(mx, my2, lmv);
             if (J < bJ) { bJ = J; bx = mx; by = my2; }
         }
-        __syncthreads();
+        if (stage == 1) __syncthreads();  // the caller may reuse the shared memory
         cx = bx;
         cy = by;
     }

@@ -38,6 +38,27 @@ __host__ __device__ constexpr size_t tqr_seq_smem_bytes(int N) {
     return tqr_off_t32(N) + (N >= 32 ? (size_t)kT32HalvesInts * 4 : 0);
 }
 
+// Block-wide sums of (a, b) with one barrier: a warp-level sum, then one
+// shared-memory atomic per warp into slot `slot` of red (red[slot] for a,
+// the 32-bit word 8 + slot of red for b), which must hold 0 (cleared before
+// an earlier barrier) and is not reused within the CU.
+template <int NT>
+__device__ __forceinline__ void block_sum2_slot(uint64_t& a, uint32_t& b, uint64_t* red, int slot) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    uint32_t* rb = reinterpret_cast<uint32_t*>(red) + 8;
+    if ((threadIdx.x & 31) == 0 && (a | b)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(red + slot), (unsigned long long)a);
+        atomicAdd(rb + slot, b);
+    }
+    __syncthreads();
+    a = red[slot];
+    b = rb[slot];
+}
+
 template <int NT>
 __device__ __forceinline__ void block_sum2(uint64_t& a, uint32_t& b, uint64_t* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -265,7 +286,7 @@ __device__ __forceinline__ void store_seg(void* p, const int (&v)[TS]) {
 template <int N, int TS, int NT>
 __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
                         int16_t* __restrict__ work, int16_t* __restrict__ lev, uint16_t* __restrict__ rec,
-                        int qp, uint64_t& sse_out, uint32_t& bits_out, uint64_t* red) {
+                        int qp, uint64_t& sse_out, uint32_t& bits_out, uint64_t* red, int slot = -1) {
     constexpr int L = TS == 4 ? 2 : TS == 8 ? 3 : TS == 16 ? 4 : 5;
     constexpr int NTU = N / TS;            // TUs per CU side
     constexpr int TASKS = 3 * N * NTU;     // rows (or columns) of all TUs of all channels
@@ -301,18 +322,17 @@ __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __rest
         fwd1d<TS>(col, cf);
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
-            int lv = quantize(rshift_round(cf[i], L + 6), q);
+            const int lv = quant_rate_deq(rshift_round(cf[i], L + 6), q, L, bits, col[i]);
             lev[base + i * N] = (int16_t)lv;
-            if (lv != 0) bits += (uint32_t)(2 * L + se_len(lv));
-            col[i] = dequantize(lv, q);
         }
         inv1d<TS>(col, cf);
 #pragma unroll
         for (int i = 0; i < TS; ++i) work[base + i * N] = (int16_t)clip16(rshift_round(cf[i], 7));
     }
     __syncthreads();
-    // inverse rows and reconstruction
-    uint64_t sse = 0;
+    // inverse rows and reconstruction; the SSE of a thread fits 32 bits (at
+    // most 3 N^2 / NT <= 384 samples of error <= 1023)
+    uint32_t sse32 = 0;
 #pragma unroll 1
     for (int t = tid; t < TASKS; t += NT) {
         int c = t / (N * NTU), rem = t - c * N * NTU;
@@ -329,10 +349,12 @@ __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __rest
 #pragma unroll
         for (int i = 0; i < TS; ++i) {
             const int d = e[i] - r[i];
-            sse += (uint64_t)(d * d);
+            sse32 += (uint32_t)(d * d);
         }
     }
-    block_sum2<NT>(sse, bits, red);
+    uint64_t sse = sse32;
+    if (slot >= 0) block_sum2_slot<NT>(sse, bits, red, slot);
+    else block_sum2<NT>(sse, bits, red);
     sse_out = sse;
     bits_out = bits + 3u * NTU * NTU;  // one coded-block flag per TU and channel
 }
@@ -347,7 +369,8 @@ __device__ void tu_pass(const uint16_t* __restrict__ cur, const uint16_t* __rest
 template <int N, int NT>
 __device__ void tu_pass32(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
                           int16_t* __restrict__ work, int16_t* __restrict__ lev, uint16_t* __restrict__ rec, int qp,
-                          const int* __restrict__ tab, uint64_t& sse_out, uint32_t& bits_out, uint64_t* red) {
+                          const int* __restrict__ tab, uint64_t& sse_out, uint32_t& bits_out, uint64_t* red,
+                          int slot = -1) {
     constexpr int L = 5;
     constexpr int NTU = N / 32;
     constexpr int TASKS = 2 * 3 * N * NTU;  // two lanes per TU row (or column) of every channel
@@ -395,10 +418,8 @@ __device__ void tu_pass32(const uint16_t* __restrict__ cur, const uint16_t* __re
         int d[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const int lv = quantize(rshift_round(cf[i], L + 6), q);
+            const int lv = quant_rate_deq(rshift_round(cf[i], L + 6), q, L, bits, d[i]);
             lev[base + (16 * p + i) * N] = (int16_t)lv;
-            if (lv != 0) bits += (uint32_t)(2 * L + se_len(lv));
-            d[i] = dequantize(lv, q);
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -416,8 +437,8 @@ __device__ void tu_pass32(const uint16_t* __restrict__ cur, const uint16_t* __re
     }
     __syncthreads();
     // inverse rows and reconstruction: lane part p rebuilds x[8p .. 8p + 7]
-    // and x[24 - 8p .. 31 - 8p]
-    uint64_t sse = 0;
+    // and x[24 - 8p .. 31 - 8p]; the SSE of a thread fits 32 bits
+    uint32_t sse32 = 0;
 #pragma unroll 1
     for (int t = tid; t < TASKS; t += NT) {
         const int p = t & 1, task = t >> 1;
@@ -438,12 +459,14 @@ __device__ void tu_pass32(const uint16_t* __restrict__ cur, const uint16_t* __re
             for (int i = 0; i < 8; ++i) {
                 v[i] = clip_pix(pr[i] + rshift_round(h == 0 ? lo[i] : hi[i], 20 - kBitDepth));
                 const int dd = cu[i] - v[i];
-                sse += (uint64_t)(dd * dd);
+                sse32 += (uint32_t)(dd * dd);
             }
             store_seg<8>(rec + base + off, v);
         }
     }
-    block_sum2<NT>(sse, bits, red);
+    uint64_t sse = sse32;
+    if (slot >= 0) block_sum2_slot<NT>(sse, bits, red, slot);
+    else block_sum2<NT>(sse, bits, red);
     sse_out = sse;
     bits_out = bits + 3u * NTU * NTU;  // one coded-block flag per TU and channel
 }
@@ -623,14 +646,9 @@ __device__ uint32_t tqr_cu_conc(const uint16_t* __restrict__ cur, const uint16_t
             int* cf = coef_of(s);
             int16_t* lv = lev_of(s);
             for (int i = tid; i < 3 * NN; i += NT) {
-                const int l = quantize(cf[i], qs[s]);
-                lv[i] = (int16_t)l;
-                if (l != 0) {
-                    bitsS[s] += (uint32_t)(2 * (s + 2) + se_len(l));
-                    cf[i] = dequantize(l, qs[s]);
-                } else {
-                    cf[i] = 0;
-                }
+                int d;
+                lv[i] = (int16_t)quant_rate_deq(cf[i], qs[s], s + 2, bitsS[s], d);
+                cf[i] = d;
             }
         }
     }
@@ -739,6 +757,7 @@ __device__ uint32_t tqr_cu_seq(const uint16_t* __restrict__ cur, const uint16_t*
 
     int* t32tab = reinterpret_cast<int*>(smem + tqr_off_t32(N));
     if constexpr (N >= 32) t32_halves_init(t32tab);  // in flight during the prediction
+    if (tid < 8) red[tid] = 0ull;  // the per-size sum slots (visible after the next barrier)
     if constexpr (!kPredGiven)
         load_and_predict<N, NT, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred, s_stage, s_hbuf);
     if constexpr (N >= 32) {
@@ -757,17 +776,18 @@ __device__ uint32_t tqr_cu_seq(const uint16_t* __restrict__ cur, const uint16_t*
             bestBits = bits;
             copy_out<N, NT>(s_rec, s_lev, recon, levels, plane, Wp, x0, y0);
         }
-        __syncthreads();
+        // no barrier: the next size's first pass writes only the work planes,
+        // and its levels and reconstruction only after its own barriers
     };
     uint64_t sse;
     uint32_t bits;
-    if (tu_mask & (1u << 2)) { tu_pass<N, 4, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(2, sse, bits); }
+    if (tu_mask & (1u << 2)) { tu_pass<N, 4, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red, 0); consider(2, sse, bits); }
     if constexpr (N >= 8)
-        if (tu_mask & (1u << 3)) { tu_pass<N, 8, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(3, sse, bits); }
+        if (tu_mask & (1u << 3)) { tu_pass<N, 8, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red, 1); consider(3, sse, bits); }
     if constexpr (N >= 16)
-        if (tu_mask & (1u << 4)) { tu_pass<N, 16, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red); consider(4, sse, bits); }
+        if (tu_mask & (1u << 4)) { tu_pass<N, 16, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, sse, bits, red, 2); consider(4, sse, bits); }
     if constexpr (N >= 32)
-        if (tu_mask & (1u << 5)) { tu_pass32<N, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, t32tab, sse, bits, red); consider(5, sse, bits); }
+        if (tu_mask & (1u << 5)) { tu_pass32<N, NT>(s_cur, s_pred, s_work, s_lev, s_rec, qp, t32tab, sse, bits, red, 3); consider(5, sse, bits); }
     if (tid == 0 && tu_log2) *tu_log2 = (uint8_t)bestL;
     uint32_t mvbits = ref ? (uint32_t)(se_len(mvx) + se_len(mvy)) : 0u;
     return 2u + mvbits + bestBits;
