@@ -15,12 +15,11 @@ namespace {
 // Threads per block and the resident blocks per SM the register allocation
 // aims for.  CTU 32: the search at 128 threads x 6 blocks (six 34 KB
 // windows fit the SM's shared memory) and the transform at 192 threads x 4
-// blocks, whose row and column passes then have exactly one task per thread
-// for the 16- and 32-point sizes (3 channels x 32 rows, halved rows for the
-// 32-point transform) and whole rounds for the 4- and 8-point ones; both
-// measured faster than 256 threads x 3 blocks, results unchanged.
+// blocks, one warp per channel half-CU (tqr_cu_w32); both measured faster
+// than 256 threads x 3 blocks, results unchanged.  CTU 64: the transform at
+// 512 threads (one block per SM either way).
 template <int N> constexpr int kNTMe = N == 32 ? 128 : 256;
-template <int N> constexpr int kNTTqr = N == 32 ? 192 : 256;
+template <int N> constexpr int kNTTqr = N == 32 ? 192 : (N == 64 ? 512 : 256);
 template <int N> constexpr int kMinBlocksMe = N == 64 ? 1 : (N == 32 ? 6 : 4);
 template <int N> constexpr int kMinBlocksTqr = N == 64 ? 1 : 4;
 
@@ -82,7 +81,7 @@ template <int N>
 cudaError_t tqr_n(const uint16_t* cur, const uint16_t* ref, const int16_t* mv, int G, int64_t gstride, int Hp,
                   int Wp, const xv_params* p, int64_t pu_gstride, uint16_t* recon, int16_t* levels,
                   uint8_t* tu_log2, uint64_t* bits, int64_t bits_gstride, cudaStream_t st) {
-    size_t smem = xvd::tqr_smem_bytes(N);
+    const size_t smem = N == 32 && kNTTqr<N> == xvd::kW32Threads ? xvd::tqr_w32_smem_bytes() : xvd::tqr_smem_bytes(N);
     cudaError_t e = cudaFuncSetAttribute(k_tqr_frame<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((Hp / N) * (Wp / N), G);

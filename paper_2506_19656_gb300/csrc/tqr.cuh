@@ -710,6 +710,313 @@ __host__ __device__ constexpr size_t tqr_smem_bytes(int N) {
     return N <= 16 ? tqr_conc_smem_bytes(N) : tqr_seq_smem_bytes(N);
 }
 
+// ---------------------------------------------------------------------------
+// CTU 32 with 192 threads (six warps).  Warp w = 2c + h owns rows 16h ..
+// 16h + 15 of channel c for every TU size up to 16, so those passes exchange
+// data through shared memory within the warp only (__syncwarp): 4 x 4 TUs
+// one per lane, entirely in registers; 8 x 8 TUs four lanes each; 16 x 16
+// TUs sixteen lanes each.  The 32 x 32 TU of a channel pairs the channel's
+// two warps (a 64-thread named barrier between its passes).  Each size
+// writes its levels and reconstruction into whichever of two buffers does
+// not hold the best size so far; one block barrier per size makes its
+// totals known, and the best buffer is copied out once at the end.  Same
+// definitions and results as tqr_cu_seq.
+//
+// Shared memory: cur, pred, work ([3][32][32] each), buffers 0 and 1 (levels
+// int16 then reconstruction u16, [3][32][32] each), the per-size sums, the
+// 32-point table.  The motion-compensation staging and its horizontal pass
+// live in the two buffers until the prediction is done.
+constexpr int kW32Threads = 192;
+__host__ __device__ constexpr size_t w32_plane_bytes() { return (size_t)3 * 32 * 32 * 2; }
+__host__ __device__ constexpr size_t w32_off_buf(int i) { return (3 + 2 * (size_t)i) * w32_plane_bytes(); }
+__host__ __device__ constexpr size_t w32_off_red() { return w32_off_buf(2); }
+__host__ __device__ constexpr size_t w32_off_t32() { return w32_off_red() + 8 * 8; }
+__host__ __device__ constexpr size_t tqr_w32_smem_bytes() { return w32_off_t32() + (size_t)kT32HalvesInts * 4; }
+static_assert(tqr_stage_bytes(32) + tqr_hbuf_bytes(32) <= 4 * w32_plane_bytes(), "staging fits the two buffers");
+static_assert(tqr_w32_smem_bytes() <= tqr_seq_smem_bytes(32), "fits every caller's CTU-32 allocation");
+
+// Warp sums of (sse, bits) added to slot `slot` (sse at red[slot], bits at
+// red[4 + slot]).  A warp's SSE fits 32 bits: 512 samples of error <= 1023.
+__device__ __forceinline__ void w32_warp_sums(uint32_t sse, uint32_t bits, unsigned long long* red, int slot) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        sse += __shfl_xor_sync(0xffffffffu, sse, o);
+        bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(red + slot, (unsigned long long)sse);
+        atomicAdd(red + 4 + slot, (unsigned long long)bits);
+    }
+}
+
+// 4 x 4 TUs: lane = (TU row 0..3, TU column 0..7) of the warp's region.
+__device__ __forceinline__ void w32_tu4(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
+                                        int16_t* __restrict__ lev, uint16_t* __restrict__ rec, const QuantParams& q,
+                                        int rbase, int lane, uint32_t& sse, uint32_t& bits) {
+    constexpr int L = 2;
+    const int base = rbase + (lane >> 3) * 4 * 32 + (lane & 7) * 4;
+    int x[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int cv[4], pv[4];
+        load_seg<4, false>(cur + base + 32 * i, cv);
+        load_seg<4, false>(pred + base + 32 * i, pv);
+        int y[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cv[k] -= pv[k];
+        fwd1d<4>(cv, y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[i][k] = rshift_round(y[k], L + kBitDepth - 9);
+    }
+    int lv[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int col[4], cf[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) col[i] = x[i][k];
+        fwd1d<4>(col, cf);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lv[i][k] = quant_rate_deq(rshift_round(cf[i], L + 6), q, L, bits, col[i]);
+        inv1d<4>(col, cf);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i][k] = clip16(rshift_round(cf[i], 7));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        store_seg<4>(lev + base + 32 * i, lv[i]);
+        int r[4], cv[4], pv[4];
+        inv1d<4>(x[i], r);
+        load_seg<4, false>(pred + base + 32 * i, pv);
+        load_seg<4, false>(cur + base + 32 * i, cv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            r[k] = clip_pix(pv[k] + rshift_round(r[k], 20 - kBitDepth));
+            const int d = cv[k] - r[k];
+            sse += (uint32_t)(d * d);
+        }
+        store_seg<4>(rec + base + 32 * i, r);
+    }
+}
+
+// 8 x 8 and 16 x 16 TUs over the warp's region (16 rows x 32 columns, row
+// stride 32): rows forward (task = row and TU column), columns forward,
+// quantised, dequantised and inverted (task = column and TU row), rows
+// inverse with the reconstruction; the work plane between the passes.
+template <int TS>
+__device__ __forceinline__ void w32_tu(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
+                                       int16_t* __restrict__ work, int16_t* __restrict__ lev,
+                                       uint16_t* __restrict__ rec, const QuantParams& q, int rbase, int lane,
+                                       uint32_t& sse, uint32_t& bits) {
+    constexpr int L = TS == 8 ? 3 : 4;
+    constexpr int NTU = 32 / TS;        // TU columns in the region
+    constexpr int R = 16 * NTU / 32;    // row tasks per lane (16 rows x NTU TU columns)
+    constexpr int C = 32 * (16 / TS) / 32;  // column tasks per lane (32 columns x 16/TS TU rows)
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+        const int t = lane + 32 * j;
+        const int o = rbase + (t / NTU) * 32 + (t % NTU) * TS;
+        int x[TS], yv[TS];
+        load_seg<TS, false>(cur + o, x);
+        load_seg<TS, false>(pred + o, yv);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) x[i] -= yv[i];
+        fwd1d<TS>(x, yv);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) yv[i] = rshift_round(yv[i], L + kBitDepth - 9);
+        store_seg<TS>(work + o, yv);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int j = 0; j < C; ++j) {
+        const int o = rbase + j * TS * 32 + lane;
+        int col[TS], cf[TS];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) col[i] = work[o + 32 * i];
+        fwd1d<TS>(col, cf);
+#pragma unroll
+        for (int i = 0; i < TS; ++i)
+            lev[o + 32 * i] = (int16_t)quant_rate_deq(rshift_round(cf[i], L + 6), q, L, bits, col[i]);
+        inv1d<TS>(col, cf);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) work[o + 32 * i] = (int16_t)clip16(rshift_round(cf[i], 7));
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int j = 0; j < R; ++j) {
+        const int t = lane + 32 * j;
+        const int o = rbase + (t / NTU) * 32 + (t % NTU) * TS;
+        int e[TS], r[TS];
+        load_seg<TS, true>(work + o, e);
+        inv1d<TS>(e, r);
+        load_seg<TS, false>(pred + o, e);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) r[i] = clip_pix(e[i] + rshift_round(r[i], 20 - kBitDepth));
+        store_seg<TS>(rec + o, r);
+        load_seg<TS, false>(cur + o, e);
+#pragma unroll
+        for (int i = 0; i < TS; ++i) {
+            const int d = e[i] - r[i];
+            sse += (uint32_t)(d * d);
+        }
+    }
+}
+
+// 64-thread barrier of channel c's two warps (named barriers 1 .. 3).
+__device__ __forceinline__ void w32_pair_sync(int c) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + c) : "memory");
+}
+
+// The 32 x 32 TU of channel c by its two warps, two lanes per row or column
+// (t = 32 h + lane; lane part p = t & 1), as in tu_pass32.
+__device__ __forceinline__ void w32_tu32(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ pred,
+                                         int16_t* __restrict__ work, int16_t* __restrict__ lev,
+                                         uint16_t* __restrict__ rec, const QuantParams& q,
+                                         const int* __restrict__ tab, int c, int t, uint32_t& sse, uint32_t& bits) {
+    constexpr int L = 5;
+    const int p = t & 1, v = t >> 1;
+    const int cb = c * 1024;
+    const unsigned pmask = 3u << ((threadIdx.x & 31) & ~1u);
+    {  // forward row v: lane part p writes y[16p .. 16p + 15]
+        const int base = cb + v * 32;
+        int x[32];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int cv[8], pv[8];
+            load_seg<8, false>(cur + base + 8 * k, cv);
+            load_seg<8, false>(pred + base + 8 * k, pv);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[8 * k + i] = cv[i] - pv[i];
+        }
+        int yh[16];
+        fwd32_half(x, p, tab, yh);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) yh[i] = rshift_round(yh[i], L + kBitDepth - 9);
+        store_seg<16>(work + base + 16 * p, yh);
+    }
+    w32_pair_sync(c);
+    {  // column v: forward, quantise, dequantise (16 coefficients per lane), exchange, inverse
+        const int base = cb + v;
+        int col[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) col[i] = work[base + i * 32];
+        int cf[16];
+        fwd32_half(col, p, tab, cf);
+        int d[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            lev[base + (16 * p + i) * 32] = (int16_t)quant_rate_deq(rshift_round(cf[i], L + 6), q, L, bits, d[i]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int o = __shfl_xor_sync(pmask, d[i], 1);
+            col[i] = p ? o : d[i];
+            col[16 + i] = p ? d[i] : o;
+        }
+        int lo[8], hi[8];
+        inv32_half(col, p, tab, lo, hi);
+        // every lane of the pair has read the whole column before either writes it
+        __syncwarp(pmask);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            work[base + (8 * p + i) * 32] = (int16_t)clip16(rshift_round(lo[i], 7));
+            work[base + (24 - 8 * p + i) * 32] = (int16_t)clip16(rshift_round(hi[i], 7));
+        }
+    }
+    w32_pair_sync(c);
+    {  // inverse row v and reconstruction: lane part p rebuilds x[8p .. 8p + 7] and x[24 - 8p .. 31 - 8p]
+        const int base = cb + v * 32;
+        int e[32];
+        load_seg<32, true>(work + base, e);
+        int lo[8], hi[8];
+        inv32_half(e, p, tab, lo, hi);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int off = hh == 0 ? 8 * p : 24 - 8 * p;
+            int vv[8], pr[8], cu[8];
+            load_seg<8, false>(pred + base + off, pr);
+            load_seg<8, false>(cur + base + off, cu);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                vv[i] = clip_pix(pr[i] + rshift_round(hh == 0 ? lo[i] : hi[i], 20 - kBitDepth));
+                const int dd = cu[i] - vv[i];
+                sse += (uint32_t)(dd * dd);
+            }
+            store_seg<8>(rec + base + off, vv);
+        }
+    }
+}
+
+template <bool kCoherent>
+__device__ uint32_t tqr_cu_w32(const uint16_t* __restrict__ cur, const uint16_t* __restrict__ ref, int64_t plane,
+                               int Hp, int Wp, int x0, int y0, int mvx, int mvy, int qp, unsigned tu_mask,
+                               int64_t lf8, uint16_t* __restrict__ recon, int16_t* __restrict__ levels,
+                               uint8_t* tu_log2, unsigned char* smem) {
+    constexpr int N = 32;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, c = w >> 1, h = w & 1;
+    uint16_t* s_cur = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* s_pred = s_cur + 3 * N * N;
+    int16_t* s_work = reinterpret_cast<int16_t*>(s_pred + 3 * N * N);
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + w32_off_red());
+    int* t32tab = reinterpret_cast<int*>(smem + w32_off_t32());
+    auto lev_of = [&](int b) { return reinterpret_cast<int16_t*>(smem + w32_off_buf(b)); };
+    auto rec_of = [&](int b) { return reinterpret_cast<uint16_t*>(smem + w32_off_buf(b) + w32_plane_bytes()); };
+
+    t32_halves_init(t32tab);  // in flight during the prediction
+    if (tid < 8) red[tid] = 0ull;  // the per-size sums (visible after the next barrier)
+    load_and_predict<N, kW32Threads, kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, s_cur, s_pred,
+                                                reinterpret_cast<int16_t*>(smem + w32_off_buf(0)),
+                                                reinterpret_cast<int16_t*>(smem + w32_off_buf(0) +
+                                                                           tqr_stage_bytes(N)));
+    t32_halves_wait();
+    __syncthreads();
+
+    const int rbase = c * N * N + 16 * h * N;  // the warp's region
+    int64_t bestJ = INT64_MAX;
+    int bestL = 0, best = 0, wb = 0;  // best buffer, buffer being written
+    uint32_t bestBits = 0;
+    // after a size's pass: its totals, and the buffers swapped when it is the best so far
+    auto finish = [&](int L, int slot, uint32_t sse, uint32_t bits) {
+        w32_warp_sums(sse, bits, red, slot);
+        __syncthreads();
+        const uint32_t b = (uint32_t)red[4 + slot] + 3u * (uint32_t)((N >> L) * (N >> L));  // + coded-block flags
+        const int64_t J = (int64_t)(red[slot] << 8) + lf8 * (int64_t)b;
+        if (J <= bestJ) {  // ascending sizes: ties go to the larger
+            bestJ = J;
+            bestL = L;
+            bestBits = b;
+            best = wb;
+            wb ^= 1;
+        }
+    };
+    if (tu_mask & (1u << 2)) {
+        uint32_t sse = 0, bits = 0;
+        const QuantParams q = quant_params(qp, 2);
+        w32_tu4(s_cur, s_pred, lev_of(wb), rec_of(wb), q, rbase, lane, sse, bits);
+        finish(2, 0, sse, bits);
+    }
+    if (tu_mask & (1u << 3)) {
+        uint32_t sse = 0, bits = 0;
+        const QuantParams q = quant_params(qp, 3);
+        w32_tu<8>(s_cur, s_pred, s_work, lev_of(wb), rec_of(wb), q, rbase, lane, sse, bits);
+        finish(3, 1, sse, bits);
+    }
+    if (tu_mask & (1u << 4)) {
+        uint32_t sse = 0, bits = 0;
+        const QuantParams q = quant_params(qp, 4);
+        w32_tu<16>(s_cur, s_pred, s_work, lev_of(wb), rec_of(wb), q, rbase, lane, sse, bits);
+        finish(4, 2, sse, bits);
+    }
+    if (tu_mask & (1u << 5)) {
+        uint32_t sse = 0, bits = 0;
+        const QuantParams q = quant_params(qp, 5);
+        w32_tu32(s_cur, s_pred, s_work, lev_of(wb), rec_of(wb), q, t32tab, c, 32 * h + lane, sse, bits);
+        finish(5, 3, sse, bits);
+    }
+    copy_out<N, kW32Threads>(rec_of(best), lev_of(best), recon, levels, plane, Wp, x0, y0);
+    if (tid == 0 && tu_log2) *tu_log2 = (uint8_t)bestL;
+    const uint32_t mvbits = ref ? (uint32_t)(se_len(mvx) + se_len(mvy)) : 0u;
+    return 2u + mvbits + bestBits;
+}
+
 // Transform/quantise/reconstruct the CU at (x0, y0).  cur/ref/recon/levels:
 // the group's frame [3][Hp][Wp] (ref == nullptr: first frame).  Returns the
 // CU's rate-proxy bits; writes recon (and levels) and *tu_log2.  kPredGiven:
@@ -731,6 +1038,9 @@ __device__ uint32_t tqr_cu(const uint16_t* __restrict__ cur, const uint16_t* __r
     if constexpr (N <= 16) {
         return tqr_cu_conc<N, NT, kCoherent, kPredGiven>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask,
                                                          lf8, recon, levels, tu_log2, smem);
+    } else if constexpr (N == 32 && NT == kW32Threads && !kPredGiven) {
+        return tqr_cu_w32<kCoherent>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask, lf8, recon, levels,
+                                     tu_log2, smem);
     } else {
         return tqr_cu_seq<N, NT, kCoherent, kPredGiven>(cur, ref, plane, Hp, Wp, x0, y0, mvx, mvy, qp, tu_mask, lf8,
                                                         recon, levels, tu_log2, smem);
