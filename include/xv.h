@@ -285,10 +285,16 @@ xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result*
 
 /* xv_encode_batch with the cubes coming from HOST memory: for every job whose
  * host_src[i] is not NULL, that host cube ([bands][T][H][W] of the job's
- * dtype, bands T H W elements, pinned memory makes the copy asynchronous) is
- * first copied into the job's device buffer jobs[i].src on `stream`; then the
- * batch runs exactly as xv_encode_batch (same output, same host results).
- * host_src may be NULL (no copies).  Synchronous. */
+ * dtype, bands T H W elements) is copied into the job's device buffer
+ * jobs[i].src, and the batch computes exactly what xv_encode_batch computes
+ * (same output, same host results).  With pinned host cubes, in the
+ * per-frame mode the copies run on a stream of their own, smallest cube
+ * first, and each job's min/max, quantisation and chain start as soon as its
+ * own cube has arrived, so the uploads overlap the encoding of the jobs
+ * already on the device; with the persistent kernel, or when a cube is in
+ * pageable memory, the copies precede the batch.  The captured graph is
+ * keyed by the host pointers too.  host_src may be NULL (no copies).
+ * Synchronous. */
 xv_status xv_encode_batch_from_host(xv_ctx* ctx, const xv_job* jobs, const void* const* host_src, int njobs,
                                     xv_result* results, void* stream);
 

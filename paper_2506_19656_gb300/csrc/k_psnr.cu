@@ -188,8 +188,20 @@ __global__ void k_psnr_final(const PsnrPart* part, int nblk, PsnrPart* out) {
 
 }  // namespace
 
-int psnr_blocks_per_band(int64_t n) {
+// Blocks per band: one per 2048 samples, at most 256, and together at most
+// one wave of the blocks resident at once (k_psnr<float, 4>, the variant
+// with the most registers), so that no partial second wave runs alone.
+int psnr_blocks_per_band(int64_t n, int bands) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_psnr<float, 4>, kThreads, 0) != cudaSuccess || per < 1) {
+        (void)cudaGetLastError();
+        per = 1;
+    }
     int64_t want = (n + kThreads * 8 - 1) / (kThreads * 8);
+    const int64_t wave = (int64_t)sms * per / (bands > 0 ? bands : 1);
+    if (want > wave) want = wave;
     if (want > 256) want = 256;
     return (int)(want < 1 ? 1 : want);
 }

@@ -69,7 +69,7 @@ extern "C" xv_status xv_psnr_noalloc(const void* src, xv_dtype dt, int bands, in
         set_error("bad cube %dx%dx%d or planes %dx%d", T, H, W, Hp, Wp);
         return XV_EINVAL;
     }
-    const int nblk = psnr_blocks_per_band((int64_t)T * H * W);
+    const int nblk = psnr_blocks_per_band((int64_t)T * H * W, bands);
     if (nblk > kMaxBlocksPerBand) {
         set_error("%d partial sums per band exceed the fixed scratch (%d)", nblk, kMaxBlocksPerBand);
         return XV_EINVAL;

@@ -209,12 +209,20 @@ k_quant_pack(const T* __restrict__ src, int bands, int T_, int H, int W, int Hp,
     }
 }
 
-int grid_for(int64_t items) {
-    int dev = 0, sms = 0;
+// Grid of a grid-stride kernel over `items` threads' work: at most one full
+// wave of the blocks that are resident at once (a second, partial wave would
+// leave most of the GPU idle while it runs).
+template <typename K>
+int grid_for(K kernel, int64_t items) {
+    int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t want = (items + kThreads - 1) / kThreads;
-    int64_t cap = (int64_t)sms * 8;  // 8 resident blocks of 256 per SM
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess || per < 1) {
+        (void)cudaGetLastError();
+        per = 1;
+    }
+    const int64_t want = (items + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sms * per;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
@@ -255,13 +263,12 @@ cudaError_t launch_quantize_pack(const void* src, xv_dtype dt, int bands, int T,
     const int G = (bands + 2) / 3;
     const int64_t items = (int64_t)G * T * 3 * Hp * (Wp / 8);
     if (items == 0) return cudaSuccess;
-    const int grid = grid_for(items);
     if (dt == XV_F32)
-        k_quant_pack<float><<<grid, kThreads, 0, st>>>(static_cast<const float*>(src), bands, T, H, W, Hp, Wp,
-                                                        bq, planes, items);
+        k_quant_pack<float><<<grid_for(k_quant_pack<float>, items), kThreads, 0, st>>>(
+            static_cast<const float*>(src), bands, T, H, W, Hp, Wp, bq, planes, items);
     else
-        k_quant_pack<uint16_t><<<grid, kThreads, 0, st>>>(static_cast<const uint16_t*>(src), bands, T, H, W, Hp,
-                                                           Wp, bq, planes, items);
+        k_quant_pack<uint16_t><<<grid_for(k_quant_pack<uint16_t>, items), kThreads, 0, st>>>(
+            static_cast<const uint16_t*>(src), bands, T, H, W, Hp, Wp, bq, planes, items);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,12 @@ struct xv_ctx {
     cudaStream_t side[16] = {};
     cudaEvent_t side_ev[16] = {};
     cudaEvent_t fork_ev = nullptr;
-    DevBuf b_mv, b_exact;
+    // xv_encode_batch_from_host: the cubes' uploads on their own stream, one
+    // completion event per job
+    cudaStream_t up_st = nullptr;
+    cudaEvent_t up_join = nullptr;
+    std::vector<cudaEvent_t> up_ev;
+    DevBuf b_mv, b_exact, b_mm_enc;
     DevBuf peak_buf;                         // xv_measure_peak's input and sink
     DevBuf dev_err;                          // status word the per-frame search sets on a copy timeout
     long long tma_polls = 1ll << 24;         // bound of the search window copy's wait (test hook)
@@ -249,25 +254,29 @@ xv_status check_launch(cudaError_t e, const char* what) {
 constexpr int kLaunchMinmax = 3, kLaunchBandq = 1, kLaunchQuant = 1, kLaunchMe = 1, kLaunchTqr = 1, kLaunchPsnr = 2,
               kLaunchPersist = 1;
 
-// min/max (unless fixed) and the per-band quantiser constants into `bq`.
+// min/max (unless fixed) and the per-band quantiser constants into `bq`;
+// `scratch` (2 x bands words) is the reduction's, the context's own when
+// null.
 xv_status prepare_bands(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W, double* minmax,
-                        int fixed, BandQ* bq, cudaStream_t st) {
+                        int fixed, BandQ* bq, cudaStream_t st, unsigned* scratch = nullptr) {
     if (fixed) {
         c->launches += kLaunchBandq;
         return check_launch(xvh::launch_bandq(minmax, bands, bq, st), "band constants");
     }
-    xv_status s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * bands);
-    if (s) return s;
+    if (!scratch) {
+        xv_status s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * bands);
+        if (s) return s;
+        scratch = (unsigned*)c->mm_enc.ptr;
+    }
     c->launches += kLaunchMinmax;
-    return check_launch(xvh::launch_minmax(src, dt, bands, (int64_t)T * H * W, (unsigned*)c->mm_enc.ptr, minmax, bq, st),
-                        "min/max");
+    return check_launch(xvh::launch_minmax(src, dt, bands, (int64_t)T * H * W, scratch, minmax, bq, st), "min/max");
 }
 
 // PSNR of one cube into `r` (host), from device band constants `bq`.
 xv_status psnr_into(xv_ctx* c, const void* src, xv_dtype dt, int bands, int T, int H, int W,
                     const uint16_t* planes, const uint16_t* recon, int Hp, int Wp, const BandQ* bq, double* psnr,
                     double* mse, uint64_t* sse10, double* mean, cudaStream_t st) {
-    const int nblk = xvh::psnr_blocks_per_band((int64_t)T * H * W);
+    const int nblk = xvh::psnr_blocks_per_band((int64_t)T * H * W, bands);
     xv_status s = ensure(c, c->psnr_part, sizeof(xvh::PsnrPart) * (size_t)nblk * bands);
     if (s) return s;
     if ((s = ensure(c, c->psnr_out, sizeof(xvh::PsnrPart) * bands))) return s;
@@ -365,7 +374,7 @@ void xv_destroy(xv_ctx* c) {
     cudaDeviceSynchronize();
     DevBuf* bufs[] = {&c->mm_enc, &c->bandq, &c->psnr_part, &c->psnr_out, &c->tmp_mv, &c->tmp_bits, &c->tmp_minmax, &c->tmp_cbf,
                       &c->b_jobs, &c->b_items, &c->b_rowdone, &c->b_depcnt, &c->b_ctl, &c->b_bits, &c->b_bandq,
-                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals, &c->b_mv, &c->b_exact,
+                      &c->b_minmax, &c->b_cls, &c->b_part, &c->b_out, &c->b_totals, &c->b_mv, &c->b_exact, &c->b_mm_enc,
                       &c->met_part, &c->met_out, &c->pca_part, &c->peak_buf, &c->dev_err};
     for (DevBuf* b : bufs) release(c, *b);
     for (cudaGraphExec_t& gx : c->graph)
@@ -376,6 +385,9 @@ void xv_destroy(xv_ctx* c) {
         if (c->side_ev[k]) cudaEventDestroy(c->side_ev[k]);
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->up_st) cudaStreamDestroy(c->up_st);
+    if (c->up_join) cudaEventDestroy(c->up_join);
+    for (cudaEvent_t ev : c->up_ev) cudaEventDestroy(ev);
     if (c->work) cudaStreamDestroy(c->work);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -833,6 +845,18 @@ xv_status ensure_side_streams(xv_ctx* c) {
     return XV_OK;
 }
 
+xv_status ensure_upload_stream(xv_ctx* c, int njobs) {
+    cudaError_t e = cudaSuccess;
+    if (!c->up_st) e = cudaStreamCreateWithFlags(&c->up_st, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->up_join) e = cudaEventCreateWithFlags(&c->up_join, cudaEventDisableTiming);
+    while (e == cudaSuccess && (int)c->up_ev.size() < njobs) {
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) == cudaSuccess) c->up_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "upload stream");
+    return XV_OK;
+}
+
 bool valid_djob(const xv_djob* j) {
     if (!j) { set_error("job is NULL"); return false; }
     if (!valid_params(&j->p) || !valid_frame(j->G, j->Hp, j->Wp, j->p.ctu)) return false;
@@ -855,9 +879,14 @@ bool valid_djob(const xv_djob* j) {
 
 }  // namespace
 
-extern "C" {
-
-xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* results, void* stream) {
+// xv_encode_batch, and with `host_src` (HOST [njobs], entries may be NULL)
+// xv_encode_batch_from_host: job i's cube is first copied from host_src[i]
+// to its src.  In the per-frame mode the copies of pinned cubes run on their
+// own stream, smallest cube first, and each job's setup and chain wait only
+// for its own cube, so the uploads overlap the encoding of the jobs already
+// on the device; otherwise they precede the batch on its stream.
+static xv_status encode_batch_impl(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* results, void* stream,
+                                   const void* const* host_src) {
     if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
     if (njobs < 1 || njobs > 255 || !jobs || !results) { set_error("njobs %d: must be 1..255 with jobs and results", njobs); return XV_EINVAL; }
     for (int i = 0; i < njobs; ++i)
@@ -884,7 +913,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         nbits += (int64_t)G * j.T;
         row_off[i] = nrows;
         nrows += (int64_t)G * j.T * (Hp / j.p.ctu);
-        nblk[i] = xvh::psnr_blocks_per_band((int64_t)j.T * j.H * j.W);
+        nblk[i] = xvh::psnr_blocks_per_band((int64_t)j.T * j.H * j.W, j.bands);
         part_off[i] = nparts;
         nparts += (int64_t)nblk[i] * j.bands;
         mv_off[i] = nmv;
@@ -917,11 +946,41 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     if ((s = ensure(c, c->b_part, sizeof(xvh::PsnrPart) * nparts))) return s;
     if ((s = ensure(c, c->b_out, sizeof(xvh::PsnrPart) * XV_MAX_BANDS * njobs))) return s;
     if ((s = ensure(c, c->b_totals, sizeof(unsigned long long) * njobs))) return s;
-    if ((s = ensure(c, c->mm_enc, sizeof(unsigned) * 2 * XV_MAX_BANDS))) return s;
+    if ((s = ensure(c, c->b_mm_enc, sizeof(unsigned) * 2 * XV_MAX_BANDS * njobs))) return s;
     if ((s = ensure(c, c->b_mv, sizeof(int16_t) * (nmv > 0 ? nmv : 1)))) return s;
     if ((s = ensure(c, c->b_exact, sizeof(unsigned long long)))) return s;
     if ((s = ensure_side_streams(c))) return s;
     if ((s = ensure_err_word(c))) return s;
+    // host uploads: bytes per job, and the order of the overlapped copies
+    std::vector<size_t> up_bytes(njobs, 0);
+    std::vector<int> up_order;
+    if (host_src) {
+        if ((s = ensure_upload_stream(c, njobs))) return s;
+        for (int i = 0; i < njobs; ++i) {
+            if (!host_src[i]) continue;
+            const xv_job& j = jobs[i];
+            up_bytes[i] = (size_t)j.bands * j.T * j.H * j.W * (j.dtype == XV_F32 ? 4 : 2);
+            up_order.push_back(i);
+        }
+        std::stable_sort(up_order.begin(), up_order.end(), [&](int a, int b) { return up_bytes[a] < up_bytes[b]; });
+    }
+    auto upload = [&](int i, cudaStream_t us) -> xv_status {
+        cudaError_t ue = cudaMemcpyAsync(const_cast<void*>(jobs[i].src), host_src[i], up_bytes[i],
+                                         cudaMemcpyHostToDevice, us);
+        return ue == cudaSuccess ? XV_OK : cuda_fail(ue, "host cube upload");
+    };
+    // copies from pageable memory cannot be captured: those batches copy
+    // everything on the batch stream first, outside the graphs
+    std::vector<int> pre_upload;
+    for (int i : up_order) {
+        cudaPointerAttributes pa{};
+        const bool pinned = cudaPointerGetAttributes(&pa, host_src[i]) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+        if (!pinned) {
+            (void)cudaGetLastError();
+            pre_upload.swap(up_order);
+            break;
+        }
+    }
     const size_t stage_bytes = sizeof(xvh::BatchCtl) * 4 + sizeof(unsigned long long) * njobs +
                                (sizeof(xvh::PsnrPart) + sizeof(BandQ)) * XV_MAX_BANDS * njobs + sizeof(unsigned long long);
     if (c->h_stage_bytes < stage_bytes) {
@@ -976,17 +1035,29 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
 
     // ---- the batch as three stream-ordered, capturable parts: setup,
     // persistent kernels, results; the timing events go between them
-    auto part_setup = [&]() -> xv_status {
-        for (int i = 0; i < njobs; ++i) {
-            const xv_job& j = jobs[i];
-            double* mm = j.minmax ? j.minmax : mm_all + 2 * XV_MAX_BANDS * i;
-            BandQ* bq = bq_all + XV_MAX_BANDS * i;
-            xv_status r = prepare_bands(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, mm, j.minmax_fixed, bq, st);
+    // job i's min/max, quantiser constants and planes, on stream ss (its own
+    // min/max scratch, so that jobs can run this concurrently)
+    auto job_setup = [&](int i, cudaStream_t ss) -> xv_status {
+        const xv_job& j = jobs[i];
+        double* mm = j.minmax ? j.minmax : mm_all + 2 * XV_MAX_BANDS * i;
+        BandQ* bq = bq_all + XV_MAX_BANDS * i;
+        xv_status r = prepare_bands(c, j.src, j.dtype, j.bands, j.T, j.H, j.W, mm, j.minmax_fixed, bq, ss,
+                                    (unsigned*)c->b_mm_enc.ptr + 2 * XV_MAX_BANDS * i);
+        if (r) return r;
+        c->launches += kLaunchQuant;
+        return check_launch(xvh::launch_quantize_pack(j.src, j.dtype, j.bands, j.T, j.H, j.W, jd[i].Hp, jd[i].Wp, bq,
+                                                      j.planes, ss),
+                            "quantize_pack");
+    };
+    // with_jobs: the host uploads and every job's setup here, on the batch
+    // stream (else part_frames runs them per job, overlapped)
+    auto part_setup = [&](bool with_jobs) -> xv_status {
+        for (size_t k = 0; with_jobs && k < up_order.size(); ++k) {
+            xv_status r = upload(up_order[k], st);
             if (r) return r;
-            c->launches += kLaunchQuant;
-            r = check_launch(xvh::launch_quantize_pack(j.src, j.dtype, j.bands, j.T, j.H, j.W, jd[i].Hp, jd[i].Wp, bq,
-                                                       j.planes, st),
-                             "quantize_pack");
+        }
+        for (int i = 0; with_jobs && i < njobs; ++i) {
+            xv_status r = job_setup(i, st);
             if (r) return r;
         }
         c->launches += 1;
@@ -1003,12 +1074,18 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
             if (total[k] && nt[k] == kFramesMode) return true;
         return false;
     };
-    auto run_frames = [&]() -> xv_status {
+    auto run_frames = [&](bool overlap_up) -> xv_status {
         cudaError_t err = cudaSuccess;
         unsigned long long* exact = (unsigned long long*)c->b_exact.ptr;
         for (int i = 0; i < njobs; ++i) {
             const xv_job& j = jobs[i];
             cudaStream_t ss = c->side[i % kSideStreams];
+            if (overlap_up) {  // the job's cube, then its setup
+                if (up_bytes[i] && (err = cudaStreamWaitEvent(ss, c->up_ev[i], 0)) != cudaSuccess)
+                    return cuda_fail(err, "upload wait");
+                xv_status r = job_setup(i, ss);
+                if (r) return r;
+            }
             const int G = jd[i].G, T = j.T, Hp = jd[i].Hp, Wp = jd[i].Wp;
             const int64_t npu = (int64_t)jd[i].nx * jd[i].ny, fsz = 3LL * Hp * Wp;
             int16_t* mv = j.mv ? j.mv : (int16_t*)c->b_mv.ptr + mv_off[i];
@@ -1048,15 +1125,30 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     // side streams are joined even when a launch fails, so that no work of
     // the batch is left running after the call returns (and a capture stays
     // well formed).
-    auto part_frames = [&]() -> xv_status {
+    auto part_frames = [&](bool overlap_up) -> xv_status {
         cudaError_t err = cudaMemsetAsync(c->b_exact.ptr, 0, sizeof(unsigned long long), st);
         if (err == cudaSuccess) err = cudaEventRecord(c->fork_ev, st);
         const int nside = njobs < kSideStreams ? njobs : kSideStreams;
         int forked = 0;  // side streams that joined the fork
         for (int k = 0; k < nside && err == cudaSuccess; ++k)
             if ((err = cudaStreamWaitEvent(c->side[k], c->fork_ev, 0)) == cudaSuccess) forked = k + 1;
-        xv_status r = err != cudaSuccess ? cuda_fail(err, "fork") : run_frames();
+        // the host uploads, smallest cube first, each announcing its job's cube
+        bool up_forked = false;
+        xv_status r = XV_OK;
+        if (err == cudaSuccess && overlap_up) {
+            if ((err = cudaStreamWaitEvent(c->up_st, c->fork_ev, 0)) == cudaSuccess) up_forked = true;
+            for (size_t k = 0; err == cudaSuccess && !r && k < up_order.size(); ++k) {
+                if ((r = upload(up_order[k], c->up_st))) break;
+                err = cudaEventRecord(c->up_ev[up_order[k]], c->up_st);
+            }
+        }
+        if (!r) r = err != cudaSuccess ? cuda_fail(err, "fork") : run_frames(overlap_up);
         cudaError_t je = cudaSuccess;
+        if (up_forked) {
+            cudaError_t a = cudaEventRecord(c->up_join, c->up_st);
+            if (a == cudaSuccess) a = cudaStreamWaitEvent(st, c->up_join, 0);
+            je = a;
+        }
         for (int k = 0; k < forked; ++k) {
             cudaError_t a = cudaEventRecord(c->side_ev[k], c->side[k]);
             if (a == cudaSuccess) a = cudaStreamWaitEvent(st, c->side_ev[k], 0);
@@ -1082,8 +1174,10 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         c->batch_cfg[k] = code;
         return XV_OK;
     };
+    // the per-frame mode of a batch with pinned host sources overlaps their uploads
+    auto overlap_up = [&](const int nt[4]) { return !up_order.empty() && frames_mode(nt); };
     auto part_kernels = [&](const int nt[4]) -> xv_status {
-        if (frames_mode(nt)) return part_frames();
+        if (frames_mode(nt)) return part_frames(overlap_up(nt));
         xv_status r = XV_OK;
         for (int k = 0; k < 4; ++k) {
             if (!total[k]) continue;
@@ -1122,7 +1216,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         return XV_OK;
     };
     auto body = [&](const int nt[4]) -> xv_status {
-        xv_status r = part_setup();
+        xv_status r = part_setup(!overlap_up(nt));
         cudaError_t err;
         if (!r && (err = cudaEventRecord(c->ev0, st)) != cudaSuccess) r = cuda_fail(err, "event");
         if (!r) r = part_kernels(nt);
@@ -1134,6 +1228,8 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     // order after the caller's stream
     if ((e = cudaEventRecord(c->ev_in, caller)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c->ev_in, 0)) != cudaSuccess)
         return cuda_fail(e, "stream order");
+    for (int i : pre_upload)
+        if ((s = upload(i, st))) return s;
 
     // ---- configuration per CTU class: forced, cached, or tuned now
     int nt[4] = {256, 256, 256, 256};
@@ -1161,7 +1257,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
         // class's persistent launches are independent of the other classes',
         // so each class keeps its fastest configuration; the per-frame mode
         // wins when it beats the sum of those.
-        if ((s = part_setup())) return s;  // the planes and counters every candidate reads
+        if ((s = part_setup(true))) return s;  // the cubes, planes and counters every candidate reads
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune setup");
         const uint64_t launches_before = c->launches;
         auto time_graph = [&](const std::function<xv_status()>& record, float* med) -> xv_status {
@@ -1216,7 +1312,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
             persist_total += best;
         }
         float frames_ms = 0.f;
-        if ((s = time_graph([&]() { return part_frames(); }, &frames_ms))) return s;
+        if ((s = time_graph([&]() { return part_frames(false); }, &frames_ms))) return s;
         {
             char line[64];
             snprintf(line, sizeof line, "frames %.3f;", frames_ms);
@@ -1254,6 +1350,10 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                  c->b_ctl.ptr, c->b_cls.ptr, c->b_items.ptr, c->b_part.ptr, c->b_out.ptr, c->b_totals.ptr,
                  c->h_stage, c->b_mv.ptr, c->b_exact.ptr, c->wait_budget);
         key += "|" + std::to_string(c->tma_polls) + (c->tma_off ? "n" : "t");
+        for (int i = 0; host_src && i < njobs; ++i) {  // the uploads' sources
+            snprintf(buf, sizeof buf, "h%p;", host_src[i]);
+            key += buf;
+        }
         key += buf;
         if (!c->graph[0] || key != c->graph_key) {
             for (cudaGraphExec_t& gx : c->graph)
@@ -1263,7 +1363,7 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
                 cudaGraph_t graph = nullptr;
                 if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                     return cuda_fail(e, "begin capture");
-                xv_status r = part == 0 ? part_setup() : part == 1 ? part_kernels(nt) : part_results();
+                xv_status r = part == 0 ? part_setup(!overlap_up(nt)) : part == 1 ? part_kernels(nt) : part_results();
                 e = cudaStreamEndCapture(st, &graph);
                 if (r) { if (graph) cudaGraphDestroy(graph); c->launches = launches_before; return r; }
                 if (e != cudaSuccess) { c->launches = launches_before; return cuda_fail(e, "end capture"); }
@@ -1357,23 +1457,15 @@ xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* r
     return XV_OK;
 }
 
+extern "C" {
+
+xv_status xv_encode_batch(xv_ctx* c, const xv_job* jobs, int njobs, xv_result* results, void* stream) {
+    return encode_batch_impl(c, jobs, njobs, results, stream, nullptr);
+}
+
 xv_status xv_encode_batch_from_host(xv_ctx* c, const xv_job* jobs, const void* const* host_src, int njobs,
                                     xv_result* results, void* stream) {
-    if (!c) { set_error("ctx is NULL"); return XV_EINVAL; }
-    if (njobs < 1 || njobs > 255 || !jobs || !results) { set_error("njobs %d: must be 1..255 with jobs and results", njobs); return XV_EINVAL; }
-    if (host_src) {
-        DeviceGuard g(c->device);
-        for (int i = 0; i < njobs; ++i) {
-            if (!host_src[i]) continue;
-            if (!valid_job(&jobs[i])) return XV_EINVAL;
-            const xv_job& j = jobs[i];
-            const size_t bytes = (size_t)j.bands * j.T * j.H * j.W * (j.dtype == XV_F32 ? 4 : 2);
-            cudaError_t e = cudaMemcpyAsync(const_cast<void*>(j.src), host_src[i], bytes, cudaMemcpyHostToDevice,
-                                            (cudaStream_t)stream);
-            if (e != cudaSuccess) return cuda_fail(e, "host cube upload");
-        }
-    }
-    return xv_encode_batch(c, jobs, njobs, results, stream);
+    return encode_batch_impl(c, jobs, njobs, results, stream, host_src);
 }
 
 xv_status xv_measure_peak(xv_ctx* c, int kind, double* rate, double* ms_out) {

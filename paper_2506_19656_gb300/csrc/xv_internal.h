@@ -98,7 +98,7 @@ struct PsnrPart {
     unsigned long long count;
     double pad;
 };
-int psnr_blocks_per_band(int64_t rows_per_band);
+int psnr_blocks_per_band(int64_t samples_per_band, int bands);
 cudaError_t launch_psnr(const void* src, xv_dtype dt, int bands, int T, int H, int W, const uint16_t* planes,
                         const uint16_t* recon, int Hp, int Wp, const BandQ* bq, PsnrPart* part, int nblk,
                         PsnrPart* out, cudaStream_t st);

@@ -71,7 +71,7 @@ size_t request_bytes(const xv_request& q, int* G_, int* Hp_, int* Wp_, int* nblk
     const int ctu = q.p.ctu, G = (q.bands + 2) / 3;
     const int Hp = (q.H + ctu - 1) / ctu * ctu, Wp = (q.W + ctu - 1) / ctu * ctu;
     const int64_t npu = (int64_t)(Hp / ctu) * (Wp / ctu), fr = (int64_t)G * q.T;
-    const int nblk = psnr_blocks_per_band((int64_t)q.T * q.H * q.W);
+    const int nblk = psnr_blocks_per_band((int64_t)q.T * q.H * q.W, q.bands);
     const size_t esz = q.dtype == XV_F32 ? 4 : 2;
     size_t b = 0;
     b += align256(esz * (size_t)q.bands * q.T * q.H * q.W);    // source

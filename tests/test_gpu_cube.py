@@ -253,6 +253,46 @@ def test_batch_graph_capture_and_replay(xv):
         ctx.close()
 
 
+@pytest.mark.parametrize("block_size, pinned", [(1, True), (128, True), (1, False)])
+def test_batch_from_host_uploads_every_cube(xv, block_size, pinned):
+    """xv_encode_batch_from_host: the cubes come from pinned host memory
+    (per-frame mode: on their own stream, smallest first, each job starting
+    when its own cube has arrived; persistent: before the batch) or from
+    pageable memory (copied before the captured graphs).  The device
+    sources hold garbage before every call, one job's cube is already on the
+    device (no host source), and the second call replays the captured graph,
+    which must copy again: every output is the oracle's."""
+    specs = [((4, 5, 40, 56), 8, 6, 0b1100, 30), ((3, 2, 37, 53), 8, 5, 0b1100, 22),
+             ((5, 3, 33, 41), 8, 4, 0b1100, 27)]
+    ctx = xv.Context(0)
+    try:
+        made, hosts, wants = [], [], []
+        for i, (shape, ctu, R, mask, qp) in enumerate(specs):
+            cube, _ = synth.tiny_cube(700 + i, T=shape[1], H=shape[2], W=shape[3], bands=shape[0])
+            wants.append(oracle.encode_cube(cube, ctu, R, mask, qp))
+            made.append(gpu_job(xv, cube, ctu, R, mask, qp))
+            h = torch.from_numpy(cube.copy())
+            hosts.append(None if i == 1 else (h.pin_memory() if pinned else h))
+        jobs = [m[0] for m in made]
+        xv.xv_debug_force_block_size(ctx, block_size)
+        try:
+            for _ in range(2):
+                for (j, b), h in zip(made, hosts):
+                    if h is not None:
+                        b["src"].fill_(float("nan"))
+                    b["recon"].zero_()
+                    b["mv"].zero_()
+                results = xv.xv_encode_batch_from_host(ctx, jobs, hosts)
+                assert xv.xv_last_batch_block_size(ctx) == block_size
+                for (j, b), r, w in zip(made, results, wants):
+                    assert_matches(b, r, w)
+            assert xv.xv_batch_graph_stats(ctx)[0] == 1
+        finally:
+            xv.xv_debug_force_block_size(ctx, 0)
+    finally:
+        ctx.close()
+
+
 def test_full_resolution_dynamicearthnet_and_era5_prefixes(xv, ctx):
     """Full-size frames of the DynamicEarthNet-shaped (1024x1024 uint16, CTU 64,
     R 64, TU 4-32) and ERA5-shaped (721x1440 float32, padded to 736, CTU 32,
