@@ -1139,19 +1139,24 @@ def kernels_alone(ctx, cfg, bufs, flush, stream, reps=3):
                  bits=torch.zeros_like(b["bits"]))
         calls.append((b, o, p, G, T, Hp, Wp, npu))
 
+    def chunks(T):  # frames 1..T-1 as calls of at most 255 "groups" (the entry points' limit)
+        return [(f0, min(255, T - f0)) for f0 in range(1, T, 255)]
+
     def run_me():
         for b, o, p, G, T, Hp, Wp, npu in calls:
             for g in range(G):
-                xv.xv_motion_search(ctx, b["planes"][g, 1], b["recon"][g, 0], T - 1, 3 * Hp * Wp, Hp, Wp, p,
-                                    o["mv"][g, 1], pu_gstride=npu)
+                for f0, n in chunks(T):
+                    xv.xv_motion_search(ctx, b["planes"][g, f0], b["recon"][g, f0 - 1], n, 3 * Hp * Wp, Hp, Wp, p,
+                                        o["mv"][g, f0], pu_gstride=npu)
 
     def run_tqr():
         for b, o, p, G, T, Hp, Wp, npu in calls:
             o["bits"].zero_()  # the transform adds each CU's bits to its frame's total
             for g in range(G):
-                xv.xv_transform_quant_recon(ctx, b["planes"][g, 1], b["recon"][g, 0], b["mv"][g, 1], T - 1,
-                                            3 * Hp * Wp, Hp, Wp, p, npu, o["recon"][g, 1], o["levels"][g, 1],
-                                            o["tu"][g, 1], o["bits"][g, 1], 1)
+                for f0, n in chunks(T):
+                    xv.xv_transform_quant_recon(ctx, b["planes"][g, f0], b["recon"][g, f0 - 1], b["mv"][g, f0], n,
+                                                3 * Hp * Wp, Hp, Wp, p, npu, o["recon"][g, f0], o["levels"][g, f0],
+                                                o["tu"][g, f0], o["bits"][g, f0], 1)
 
     def timed(fn):
         best = None
@@ -1171,7 +1176,7 @@ def kernels_alone(ctx, cfg, bufs, flush, stream, reps=3):
         assert torch.equal(o["mv"][:, 1:], b["mv"][:, 1:]), "motion search alone differs from the encode"
         for k, kb in (("recon", "recon"), ("levels", "levels"), ("tu", "tu_log2"), ("bits", "bits")):
             assert torch.equal(o[k][:, 1:], b[kb][:, 1:]), f"transform alone: {k} differs from the encode"
-    launches = sum(c[3] for c in calls)
+    launches = sum(c[3] * len(chunks(c[4])) for c in calls)
     del calls
     torch.cuda.empty_cache()
     return me_ms, tqr_ms, launches
