@@ -1222,7 +1222,13 @@ def secondary_line(ctx, dev, flush, stream, steps=10):
     search's effective ALU fraction."""
     from paper_2506_19656_gb300 import xv
     import torch
-    cfg, lengths, _, _, jobs, bufs = workload_jobs("deepextremecubes", 0, dev, qps=(22, 27, 32))
+    global CTU
+    saved, CTU = CTU, 0  # the workload's own CTU size (16), not the headline's tuned one
+    try:
+        cfg, lengths, _, _, jobs, bufs = workload_jobs("deepextremecubes", 0, dev, qps=(22, 27, 32))
+    finally:
+        CTU = saved
+    assert cfg.ctu == 16
     for _ in range(3):
         xv.xv_encode_batch(ctx, jobs)
     torch.cuda.synchronize()
@@ -1232,18 +1238,28 @@ def secondary_line(ctx, dev, flush, stream, steps=10):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        xv.xv_encode_batch(ctx, jobs)
+        res = xv.xv_encode_batch(ctx, jobs)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
         kms.append(xv.xv_last_batch_kernel_ms(ctx))
+    block_size = xv.xv_last_batch_block_size(ctx)
+    tune_log = xv.xv_last_tune_log(ctx)
+    # the last step's outputs against the per-cube path's (bit-exact)
+    recon = [b["recon"].clone() for b in bufs]
+    for j, b, r, rec in zip(jobs, bufs, res, recon):
+        want = xv.xv_encode_cube(ctx, j)
+        assert want["total_bits"] == r["total_bits"] and torch.equal(b["recon"], rec), \
+            "the DeepExtremeCubes-shaped batch differs from the per-cube path"
     work_mpx = 3 * sum(cfg.bands * T * cfg.H * cfg.W for T in lengths) / 1e6
     ad = 3 * sum(algorithmic_ad(cfg, T) for T in lengths)
     k = statistics.mean(kms)
     out = {"workload": cfg.name, "qps": [22, 27, 32], "value": work_mpx / (statistics.mean(ms) / 1e3),
            "unit": "Mpx·band/s", "ms_per_step": statistics.mean(ms), "steps": steps,
-           "block_size": xv.xv_last_batch_block_size(ctx), "encode_section_ms": k,
-           "search_effective_gad_s": ad / (k / 1e3) / 1e9}
+           "block_size": block_size, "encode_section_ms": k,
+           "search_effective_gad_s": ad / (k / 1e3) / 1e9,
+           "autotune_ms": parse_tune_log(tune_log) if tune_log else None,
+           "checked": "the last step's reconstruction and rates equal xv_encode_cube's"}
     del jobs, bufs
     torch.cuda.empty_cache()
     return out
