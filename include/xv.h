@@ -289,8 +289,9 @@ xv_status xv_encode_batch(xv_ctx* ctx, const xv_job* jobs, int njobs, xv_result*
  * jobs[i].src, and the batch computes exactly what xv_encode_batch computes
  * (same output, same host results).  With pinned host cubes, in the
  * per-frame mode the copies run on a stream of their own, smallest cube
- * first, and each job's min/max, quantisation and chain start as soon as its
- * own cube has arrived, so the uploads overlap the encoding of the jobs
+ * first, and each job's min/max, quantisation and chain start as soon as the
+ * copies into its source buffer (its own, or another job's into the same
+ * memory) have arrived, so the uploads overlap the encoding of the jobs
  * already on the device; with the persistent kernel, or when a cube is in
  * pageable memory, the copies precede the batch.  The captured graph is
  * keyed by the host pointers too.  host_src may be NULL (no copies).

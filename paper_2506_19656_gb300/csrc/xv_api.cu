@@ -1080,9 +1080,14 @@ static xv_status encode_batch_impl(xv_ctx* c, const xv_job* jobs, int njobs, xv_
         for (int i = 0; i < njobs; ++i) {
             const xv_job& j = jobs[i];
             cudaStream_t ss = c->side[i % kSideStreams];
-            if (overlap_up) {  // the job's cube, then its setup
-                if (up_bytes[i] && (err = cudaStreamWaitEvent(ss, c->up_ev[i], 0)) != cudaSuccess)
-                    return cuda_fail(err, "upload wait");
+            if (overlap_up) {  // every upload into the job's cube (its own, or another job's into the same buffer), then its setup
+                const char* a0 = static_cast<const char*>(j.src);
+                const char* a1 = a0 + (size_t)j.bands * j.T * j.H * j.W * (j.dtype == XV_F32 ? 4 : 2);
+                for (int u : up_order) {
+                    const char* b0 = static_cast<const char*>(jobs[u].src);
+                    if (b0 < a1 && a0 < b0 + up_bytes[u] && (err = cudaStreamWaitEvent(ss, c->up_ev[u], 0)) != cudaSuccess)
+                        return cuda_fail(err, "upload wait");
+                }
                 xv_status r = job_setup(i, ss);
                 if (r) return r;
             }

@@ -260,8 +260,9 @@ def test_batch_from_host_uploads_every_cube(xv, block_size, pinned):
     when its own cube has arrived; persistent: before the batch) or from
     pageable memory (copied before the captured graphs).  The device
     sources hold garbage before every call, one job's cube is already on the
-    device (no host source), and the second call replays the captured graph,
-    which must copy again: every output is the oracle's."""
+    device (no host source), another job shares an uploaded job's device
+    buffer without a host source of its own, and the second call replays the
+    captured graph, which must copy again: every output is the oracle's."""
     specs = [((4, 5, 40, 56), 8, 6, 0b1100, 30), ((3, 2, 37, 53), 8, 5, 0b1100, 22),
              ((5, 3, 33, 41), 8, 4, 0b1100, 27)]
     ctx = xv.Context(0)
@@ -273,6 +274,18 @@ def test_batch_from_host_uploads_every_cube(xv, block_size, pinned):
             made.append(gpu_job(xv, cube, ctu, R, mask, qp))
             h = torch.from_numpy(cube.copy())
             hosts.append(None if i == 1 else (h.pin_memory() if pinned else h))
+        # first in the list: a job at another QP that reads the first cube's
+        # device buffer and has no host source of its own; it must wait for
+        # that cube's upload
+        cube0, _ = synth.tiny_cube(700, T=5, H=40, W=56, bands=4)
+        p0 = xv.xv_params_init(8, 6, 0b1100, 22)
+        b0 = xv.alloc_cube_buffers(4, 5, 40, 56, p0)
+        b0["src"] = made[0][1]["src"]
+        j0 = xv.make_job(b0["src"], p0, b0["planes"], b0["recon"], minmax=b0["minmax"], mv=b0["mv"], cost=b0["cost"],
+                         levels=b0["levels"], tu_log2=b0["tu_log2"], bits=b0["bits"])
+        made.insert(0, (j0, b0))
+        hosts.insert(0, None)
+        wants.insert(0, oracle.encode_cube(cube0, 8, 6, 0b1100, 22))
         jobs = [m[0] for m in made]
         xv.xv_debug_force_block_size(ctx, block_size)
         try:
