@@ -306,6 +306,33 @@ def test_batch_from_host_uploads_every_cube(xv, block_size, pinned):
         ctx.close()
 
 
+def test_batch_from_host_more_jobs_than_side_streams(xv):
+    """Eighteen small cubes from pinned host memory in the per-frame mode:
+    jobs share the sixteen side streams (and their uploads one stream), and
+    every output is still the oracle's."""
+    ctx = xv.Context(0)
+    try:
+        made, hosts, wants = [], [], []
+        for i in range(18):
+            T, H, W = 2 + i % 3, 24 + 8 * (i % 4), 40 - 8 * (i % 3)
+            cube, _ = synth.tiny_cube(900 + i, T=T, H=H, W=W, bands=3 + i % 2)
+            qp = (22, 27, 32)[i % 3]
+            wants.append(oracle.encode_cube(cube, 8, 4, 0b1100, qp))
+            made.append(gpu_job(xv, cube, 8, 4, 0b1100, qp))
+            hosts.append(torch.from_numpy(cube.copy()).pin_memory())
+        for j, b in made:
+            b["src"].fill_(float("nan"))
+        xv.xv_debug_force_block_size(ctx, 1)
+        try:
+            results = xv.xv_encode_batch_from_host(ctx, [m[0] for m in made], hosts)
+        finally:
+            xv.xv_debug_force_block_size(ctx, 0)
+        for (j, b), r, w in zip(made, results, wants):
+            assert_matches(b, r, w)
+    finally:
+        ctx.close()
+
+
 def test_full_resolution_dynamicearthnet_and_era5_prefixes(xv, ctx):
     """Full-size frames of the DynamicEarthNet-shaped (1024x1024 uint16, CTU 64,
     R 64, TU 4-32) and ERA5-shaped (721x1440 float32, padded to 736, CTU 32,

@@ -194,6 +194,40 @@ def test_transform_quant_recon(xv, ctx, ctu, mask, qp, first):
         assert int(to_np(bits)[g]) == w["bits"]
 
 
+@pytest.mark.parametrize("mask", [0b100000, 0b101000, 0b110100, 0b011000, 0b111100])
+@pytest.mark.parametrize("qp,content", [(-12, "extreme"), (0, "smooth"), (22, "extreme"), (45, "smooth")])
+def test_transform_ctu32_size_subsets(xv, ctx, mask, qp, content):
+    """CTU 32's warp-owned transform over subsets of the TU sizes (its
+    best/current buffers swap only on improving sizes) and QPs from -12 to 45,
+    on smooth planes and on extreme ones (full-range noise against an
+    unrelated reference: residuals near +-1023, the largest coefficients and
+    levels): every output equals the oracle's."""
+    ctu, G, Hp, Wp = 32, 2, 64, 96
+    if content == "smooth":
+        cur, ref = me_case(700 + qp, G, Hp, Wp)
+    else:
+        rng = np.random.default_rng(800 + qp)
+        cur = rng.integers(0, 1024, (G, 3, Hp, Wp)).astype(np.uint16)
+        ref = (1023 - cur).astype(np.uint16)
+    npu = (Hp // ctu) * (Wp // ctu)
+    rng = np.random.default_rng(qp + 900)
+    mv = rng.integers(-4 * 9, 4 * 9 + 1, (G, npu, 2)).astype(np.int16)
+    p = xv.xv_params_init(ctu, 8, mask, qp)
+    recon = torch.zeros((G, 3, Hp, Wp), dtype=torch.uint16, device="cuda")
+    levels = torch.zeros((G, 3, Hp, Wp), dtype=torch.int16, device="cuda")
+    tu = torch.zeros((G, npu), dtype=torch.uint8, device="cuda")
+    bits = torch.zeros((G,), dtype=torch.int64, device="cuda")
+    xv.xv_transform_quant_recon(ctx, to_dev(cur), to_dev(ref), to_dev(mv), G, 3 * Hp * Wp, Hp, Wp, p, npu, recon,
+                                levels, tu, bits, 1)
+    torch.cuda.synchronize()
+    for g in range(G):
+        w = oracle.tqr_frame(cur[g], ref[g], mv[g], ctu, mask, qp)
+        assert np.array_equal(to_np(recon)[g], w["recon"])
+        assert np.array_equal(to_np(levels)[g], w["levels"])
+        assert np.array_equal(to_np(tu)[g], w["tu_log2"])
+        assert int(to_np(bits)[g]) == w["bits"]
+
+
 @pytest.mark.parametrize("dtype", ["f32", "u16"])
 def test_psnr(xv, ctx, dtype):
     rng = np.random.default_rng(5)
