@@ -55,9 +55,11 @@ __host__ __device__ constexpr int me_stride(int N, int R) {
 // the rest need the exact SAD and the result is that of the full search.
 // The reference sums come from a table of SB x SB box sums at every window
 // position.  For CTU 16 and 64 it is built and used K row classes at a time
-// (box rows y with y - 4 = m mod K, m = 0..K-1): CTU 64 for the whole table
-// would not fit next to the window, and at CTU 16 the smaller table keeps
-// five blocks per SM resident.
+// (box rows y with y - 4 = m mod K, m = 0..K-1) by default: CTU 64 for the
+// whole table would not fit next to the window, and at CTU 16 the smaller
+// table keeps five blocks per SM resident in the persistent kernel.  The
+// per-frame search at CTU 16 builds the whole table at once where it fits
+// (me_pu's KC): one build and one bound pass instead of four of each.
 __host__ __device__ constexpr int me_sb(int N) { return N <= 16 ? 4 : (N == 32 ? 8 : 16); }
 __host__ __device__ constexpr int me_kcls(int N) { return N == 64 || N == 16 ? 4 : 1; }
 __host__ __device__ constexpr int me_side(int R) { return 2 * R + 1; }
@@ -72,9 +74,7 @@ __host__ __device__ constexpr int me_units(int R) { return me_side(R) * me_ngxa(
 // bank groups) and rows of one class
 __host__ __device__ constexpr int me_tab_stride(int N, int R) { return (8 * me_ngxa(R) + N - me_sb(N) + 7) / 8 * 8; }
 __host__ __device__ constexpr int me_tab_pitch(int N, int R) { return (me_tab_stride(N, R) - 4 + 31) / 32 * 32 + 4; }
-__host__ __device__ constexpr int me_tab_rows(int N, int R) {
-    return (2 * R + N - me_sb(N) + me_kcls(N)) / me_kcls(N);
-}
+__host__ __device__ constexpr int me_tab_rows(int N, int R, int K) { return (2 * R + N - me_sb(N) + K) / K; }
 
 // Byte offsets of the shared-memory regions (every region 16-byte aligned).
 // The scratch region holds the pruning tables during the integer search and
@@ -98,16 +98,18 @@ __host__ __device__ constexpr size_t me_planes_bytes(int N) { return me_align16(
 // pruning view: box table (later the survivor list), sub-block sums of the
 // PU, per-unit bounds
 __host__ __device__ constexpr size_t me_max(size_t a, size_t b) { return a > b ? a : b; }
-__host__ __device__ constexpr size_t me_tab_bytes(int N, int R) {
-    return me_align16(me_max((size_t)me_tab_rows(N, R) * me_tab_pitch(N, R) * 4, (size_t)me_units(R) * 2));
+// (K = the box table's row classes; the two-argument forms take me_kcls(N))
+__host__ __device__ constexpr size_t me_tab_bytes(int N, int R, int K) {
+    return me_align16(me_max((size_t)me_tab_rows(N, R, K) * me_tab_pitch(N, R) * 4, (size_t)me_units(R) * 2));
 }
-__host__ __device__ constexpr size_t me_off_bsub(int N, int R) { return me_off_scr(N, R) + me_tab_bytes(N, R); }
-__host__ __device__ constexpr size_t me_off_ulb(int N, int R) {
-    return me_off_bsub(N, R) + me_align16((size_t)(N / me_sb(N)) * (N / me_sb(N)) * 4);
+__host__ __device__ constexpr size_t me_off_bsub(int N, int R, int K) { return me_off_scr(N, R) + me_tab_bytes(N, R, K); }
+__host__ __device__ constexpr size_t me_off_ulb(int N, int R, int K) {
+    return me_off_bsub(N, R, K) + me_align16((size_t)(N / me_sb(N)) * (N / me_sb(N)) * 4);
 }
-__host__ __device__ constexpr size_t me_smem_bytes(int N, int R) {
-    return me_max(me_off_scr(N, R) + me_planes_bytes(N), me_off_ulb(N, R) + me_align16((size_t)me_units(R) * 4));
+__host__ __device__ constexpr size_t me_smem_bytes(int N, int R, int K) {
+    return me_max(me_off_scr(N, R) + me_planes_bytes(N), me_off_ulb(N, R, K) + me_align16((size_t)me_units(R) * 4));
 }
+__host__ __device__ constexpr size_t me_smem_bytes(int N, int R) { return me_smem_bytes(N, R, me_kcls(N)); }
 
 // Samples in the window and block are stored as the float 2^23 + v (v <= 1023).
 // Its bit pattern is 0x4B000000 | v, so __sad on the raw bits gives |a - b|
@@ -425,12 +427,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 }
 
 // Motion estimation of the PU at (x0, y0).  cur0/ref0: channel-0 planes.
-// Must be called by all NT threads of the block; smem holds me_smem_bytes.
+// Must be called by all NT threads of the block; smem holds
+// me_smem_bytes(N, R, KC) (KC: the box table's row classes, see me_kcls).
 // With `tmap` (a tensor map over the reference planes, see window_tma_issue;
 // tz = the group's coordinate in it) the window comes by TMA where it lies
 // inside the plane; a copy that does not complete within the wait bound sets
 // *err to XV_ETIMEOUT (the result is then not valid).
-template <int N, int NT, bool kCoherent = false>
+template <int N, int NT, bool kCoherent = false, int KC = me_kcls(N)>
 __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __restrict__ ref0,
                           int Hp, int Wp, int x0, int y0, int R, int64_t lmv, unsigned char* smem,
                           const void* tmap = nullptr, int tz = 0, int* err = nullptr,
@@ -521,7 +524,7 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     }
     {  // sub-block sums and the survivor counts start at 0; the three
        // block-minimum slots at ~0
-        int* bs = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
+        int* bs = reinterpret_cast<int*>(smem + me_off_bsub(N, R, KC));
         constexpr int nsb = (N / me_sb(N)) * (N / me_sb(N));
         for (int i = tid; i < nsb + 13; i += NT) {
             if (i < nsb) bs[i] = 0;
@@ -541,15 +544,16 @@ __device__ MeResult me_pu(const uint16_t* __restrict__ cur0, const uint16_t* __r
     // candidate per dy, column group gx = ngx), else it is covered by an
     // 8-wide unit that discards the candidates beyond R.  Unit u = gx * side
     // + dy + R.
-    constexpr int SB = me_sb(N), NS = N / SB, K = me_kcls(N);
+    constexpr int SB = me_sb(N), NS = N / SB, K = KC;
+    static_assert(SB % K == 0, "row classes divide the sub-block side");
     const int side = me_side(R);
     const int ngx = me_ngx(R), ngxa = me_ngxa(R);
     const int units = side * ngxa;
     const int TS = me_tab_stride(N, R), TP = me_tab_pitch(N, R);
     uint32_t* tab = reinterpret_cast<uint32_t*>(smem + me_off_scr(N, R));
     uint16_t* list = reinterpret_cast<uint16_t*>(smem + me_off_scr(N, R));  // after the bounds
-    int* bsub = reinterpret_cast<int*>(smem + me_off_bsub(N, R));
-    uint32_t* ulb = reinterpret_cast<uint32_t*>(smem + me_off_ulb(N, R));
+    int* bsub = reinterpret_cast<int*>(smem + me_off_bsub(N, R, KC));
+    uint32_t* ulb = reinterpret_cast<uint32_t*>(smem + me_off_ulb(N, R, KC));
 
     // sub-block sums of the PU: one task per (sub-block, row), summing SB
     // biased words (the bias cancels modulo 2^32)
