@@ -55,13 +55,14 @@ __host__ __device__ constexpr int me_stride(int N, int R) {
 // the rest need the exact SAD and the result is that of the full search.
 // The reference sums come from a table of SB x SB box sums at every window
 // position.  For CTU 16 and 64 it is built and used K row classes at a time
-// (box rows y with y - 4 = m mod K, m = 0..K-1) by default: CTU 64 for the
-// whole table would not fit next to the window, and at CTU 16 the smaller
-// table keeps five blocks per SM resident in the persistent kernel.  The
-// per-frame search at CTU 16 builds the whole table at once where it fits
-// (me_pu's KC): one build and one bound pass instead of four of each.
+// (box rows y with y - 4 = m mod K, m = 0..K-1) by default: at CTU 64 the
+// whole table would not fit next to the window (two classes do, up to 178 KB
+// at R = 64, and measured 13 % faster than four), and at CTU 16 four classes
+// keep five blocks per SM resident in the persistent kernel.  The per-frame
+// search at CTU 16 builds the whole table at once where it fits (me_pu's KC):
+// one build and one bound pass instead of four of each.
 __host__ __device__ constexpr int me_sb(int N) { return N <= 16 ? 4 : (N == 32 ? 8 : 16); }
-__host__ __device__ constexpr int me_kcls(int N) { return N == 64 || N == 16 ? 4 : 1; }
+__host__ __device__ constexpr int me_kcls(int N) { return N == 64 ? 2 : (N == 16 ? 4 : 1); }
 __host__ __device__ constexpr int me_side(int R) { return 2 * R + 1; }
 __host__ __device__ constexpr bool me_lastcol(int R) { return me_side(R) % 8 == 1; }
 // 8-wide column groups of candidates, plus the single last column when
